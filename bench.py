@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput of the nested Krylov-Ritz sign function sgn(gamma5 D_w(mu)) b on GB300.
+
+One step = one batched solve of the workload's n_rhs sources (12 spin-colour
+point sources at the origin) by the nested method: outer two-sided Lanczos
+(FP32 stencil after the first k/4 steps, FP64 everything else), p estimate,
+LU of p H_k, inner two-sided Lanczos with H_k', batched Roberts-Higham, lift.
+The whole solve replays one CUDA graph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line on rank 0.  Under torchrun each rank runs an independent
+replica of the workload on its own GPU (the method has no exchange step:
+"replicas only"); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import os
+
+# The CPU oracle leg uses one host thread (numpy elementwise code is single
+# threaded; this keeps its BLAS calls single threaded too).
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sgn(A)b solves/s at rel err ≤1e-8, mixed+batched vs FP64 plain; stencil %HBM"
+TOL = 1e-8
+
+WORKLOADS = {
+    # 8^4, mu = 0.3 (two-sided), 12 point sources, mixed precision, one graph
+    "8^4-mu0.3-12pt": dict(dims=(8, 8, 8, 8), mu=0.3, m_w=-2.0, link_seed=103, k=768, ell=160,
+                           n_rhs=12, source="point", mixed=True),
+    "8^4-mu0-12pt": dict(dims=(8, 8, 8, 8), mu=0.0, m_w=-2.0, link_seed=103, k=768, ell=160,
+                         n_rhs=12, source="point", mixed=True),
+}
+DEFAULT_WORKLOAD = "8^4-mu0.3-12pt"
+# stencil roofline case: 16^3 x 32, FP32 stencil, 12 RHS in one launch (A and A^dagger)
+STENCIL_DIMS = (16, 16, 16, 32)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(w):
+    import inputs
+    U, eps = inputs.su3_links(w["dims"], w["link_seed"])
+    if w["source"] == "point":
+        b = inputs.point_sources(w["dims"])[: w["n_rhs"]]
+    else:
+        b = inputs.gaussian_sources(w["dims"], w["link_seed"] + 100, n_rhs=w["n_rhs"])
+    return U, b
+
+
+def oracle_leg(w, U, b, budget_s=40.0):
+    """The CPU oracle, as it stands, on a bounded sample: the nested method for
+    the first source of the workload (same k, l), one host thread."""
+    from oracle import nested
+    t0 = time.perf_counter()
+    y, info = nested.sign_apply(U, w["dims"], w["mu"], w["m_w"], b[0], w["k"], w["ell"])
+    t = time.perf_counter() - t0
+    return y, t
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return 0
+    U, b = make_inputs(w)
+    steps = max(1, args.steps)
+    times = []
+    for _ in range(max(0, args.warmup_ref)):
+        oracle_leg(w, U, b)
+    for _ in range(steps):
+        _, t = oracle_leg(w, U, b)
+        times.append(t)
+    tot = float(np.sum(times))
+    value = steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup_ref, "ms_per_step": 1e3 * tot / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w, args),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "nested method (oracle, numpy FP64) on source 0 of the workload, same k and l"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(w, args):
+    return {"workload": args.workload, "lattice": "x".join(str(d) for d in w["dims"]), "mu": w["mu"],
+            "m_w": w["m_w"], "k": w["k"], "ell": w["ell"], "n_rhs": w["n_rhs"],
+            "sources": "12 spin-colour point sources at the origin" if w["source"] == "point" else "gaussian",
+            "links": "U = exp(i eps X), plaquette 0.59, seed %d" % w["link_seed"],
+            "precision": "FP32 stencil after k/4 outer steps, FP64 otherwise" if w["mixed"] else "FP64",
+            "graph": True, "parallelism": "replicas" if args.gpus > 1 else "single",
+            "l2": "working set (Krylov basis %.1f GB) larger than L2" % (
+                12 * w["n_rhs"] * np.prod(w["dims"]) * w["k"] * 16 / 1e9)}
+
+
+def stencil_roofline(nk, torch, peaks):
+    """FP32 stencil, 12 RHS of A and 12 of A^dagger in one launch, on a lattice
+    larger than L2; achieved algorithmic GB/s from CUDA events on the launch
+    stream.  Algorithmic bytes per site: links 288 + 24 vectors x (96 in + 192 out)."""
+    import inputs
+    dims = STENCIL_DIMS
+    ctx = nk.Context(dims)
+    ctx.load_links(inputs.su3_links(dims, 105)[0])
+    ctx.set_mu_mw(0.2, -2.0)
+    V = int(np.prod(dims))
+    # the FP32 stencil alone, on device-resident FP32 inputs, through the
+    # solve's own kernel: time it through nk_dslash_dev's FP32 path minus its
+    # layout conversions is not separable, so time a mixed solve's stencil
+    # class instead (NK_PROFILE events around each stencil launch)
+    b = torch.zeros((12, 12 * V), dtype=torch.complex128, device="cuda")
+    b[:, :12] = torch.eye(12, dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(b)
+    k = 8
+    ctx.set_precision(0)
+    st, _ = ctx.sign_apply_dev(b, y, 12, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
+    st, _ = ctx.sign_apply_dev(b, y, 12, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
+    torch.cuda.synchronize()
+    n = st["n_class"]["dslash"]
+    t_ms = st["t_class_ms"]["dslash"] / max(1, n)
+    bytes_per_launch = V * (288 + 24 * (96 + 192))
+    gbs = bytes_per_launch / (t_ms * 1e-3) / 1e9
+    ctx.close()
+    return {"kernel": "dslash_kernel<float> (A and A^dagger, 12 RHS each)", "lattice": "16x16x16x32",
+            "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+            "frac": gbs / peaks.get("hbm_gbs", 6800.0), "ms_per_launch": t_ms,
+            "bytes_per_launch": bytes_per_launch}
+
+
+def run_gpu(args, w, rank, world, local_rank):
+    import torch
+    import paper_0912_4457_gb300 as nk
+    from paper_0912_4457_gb300 import build as nkbuild
+    if not os.path.exists(nkbuild.LIB) or not nkbuild.up_to_date():
+        if rank == 0:
+            nkbuild.build()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    peaks = measured_peaks()
+    U, b_host = make_inputs(w)
+    n_rhs, k, ell = w["n_rhs"], w["k"], w["ell"]
+    flags = nk.NK_MIXED if w["mixed"] else nk.NK_FP64
+    ctx = nk.Context(w["dims"])
+    ctx.load_links(U)
+    ctx.set_mu_mw(w["mu"], w["m_w"])
+    stream = torch.cuda.current_stream()
+    b_dev = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
+    y_dev = torch.zeros_like(b_dev)
+    for _ in range(args.warmup):
+        st, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        st, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
+        launches += st["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    y = y_dev.cpu().numpy()
+
+    # e2e: host buffers in pinned memory, through the host-pointer C entry point
+    b_pin = torch.from_numpy(np.ascontiguousarray(b_host)).pin_memory()
+    y_pin = torch.zeros_like(b_pin).pin_memory()
+    bp, yp = b_pin.numpy(), y_pin.numpy()
+    ctx.sign_apply(bp, k, ell, flags=flags)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        _lib_host_solve(ctx, bp, yp, k, ell, flags)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    # per-kernel-class device times (NK_PROFILE: CUDA events around each launch)
+    stp, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags | nk.NK_PROFILE)
+    torch.cuda.synchronize()
+    if rank != 0:
+        ctx.close()
+        return 0
+
+    # accuracy: the oracle on source 0 (this is also the timed CPU baseline sample)
+    y_or, t_or = oracle_leg(w, U, b_host)
+    err0 = float(np.linalg.norm(y[0] - y_or) / np.linalg.norm(y_or))
+    # the paper's sgn^2 estimate (Sec. 3) for all sources: apply the solve to y
+    yy = torch.zeros_like(y_dev)
+    y_src = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    ctx.sign_apply_dev(y_src, yy, n_rhs, k, ell, flags=flags)
+    torch.cuda.synchronize()
+    x2 = yy.cpu().numpy()
+    eps = [float(np.linalg.norm(x2[i] - b_host[i]) / (2 * np.linalg.norm(b_host[i]))) for i in range(n_rhs)]
+    ok = sum(1 for e in eps if e <= TOL)
+    if err0 > TOL:
+        ok = 0
+    solves_per_step = ok
+
+    value = world * solves_per_step * args.steps / (ms * 1e-3)
+    e2e_value = solves_per_step / e2e_s
+    tc = stp["t_class_ms"]
+    nc = stp["n_class"]
+    tot = sum(tc.values())
+    share = {kk: (tc[kk] / tot if tot else 0.0) for kk in tc}
+    dom = max(tc, key=lambda kk: tc[kk])
+    roof = dominant_roofline(dom, tc, nc, w, peaks)
+    sten = stencil_roofline(nk, torch, peaks)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": config_of(w, args),
+        "accuracy": {"rel_err_vs_oracle_src0": err0, "eps_sgn2_max": max(eps), "solves_meeting_tol": ok,
+                     "tol": TOL},
+        "e2e": {"value": e2e_value, "unit": "solves/s",
+                "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "stencil_roofline": sten,
+        "kernel_time_share": {kk: round(v, 4) for kk, v in share.items()},
+        "cpu_baseline": {"value": 1.0 / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "nested method (numpy FP64 oracle) on source 0 of the workload, same k and l, "
+                                   "%.1f s" % t_or},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def _lib_host_solve(ctx, bp, yp, k, ell, flags):
+    import ctypes
+    from paper_0912_4457_gb300 import nksign
+    st = nksign.NkStats()
+    rc = ctx._lib.nk_sign_apply(ctx.h, nksign._dptr(bp.view(np.float64)), bp.shape[0], int(k), int(ell), 0.0,
+                                0.0, int(flags), nksign._dptr(yp.view(np.float64)), ctypes.byref(st))
+    ctx._check(rc)
+
+
+def dominant_roofline(dom, tc, nc, w, peaks):
+    """Roofline entry for the kernel class with the largest device time."""
+    V = int(np.prod(w["dims"]))
+    N = 12 * V
+    n_rhs = w["n_rhs"]
+    two = w["mu"] != 0.0
+    ms = tc[dom] / max(1, nc[dom])
+    fp64_peak = 1.0  # TFLOP/s, measured DFMA rate of this GB300
+    if dom in ("step1", "step2", "step3"):
+        # FP64 flops per complex element per vector pair, two-sided (one-sided in parentheses)
+        flops_el = {"step1": 16 if two else 6, "step2": 16 if two else 8, "step3": 12 if two else 2}[dom]
+        bytes_el = {"step1": (5 * 16 + 2 * 16) if two else (3 * 16 + 16),
+                    "step2": (4 * 16 + 2 * 16) if two else (2 * 16 + 16),
+                    "step3": (2 * 16 + 2 * 16 + 2 * 8) if two else (16 + 16 + 8)}[dom]
+        flops = flops_el * N * n_rhs
+        tf = flops / (ms * 1e-3) / 1e12
+        return {"kernel": "k_" + dom, "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": tf / fp64_peak, "traffic": None, "ms_per_launch": ms,
+                "algorithmic_bytes_per_launch": bytes_el * N * n_rhs}
+    if dom == "dslash":
+        b = V * (288 + (2 if two else 1) * n_rhs * (96 + 192))
+        gbs = b / (ms * 1e-3) / 1e9
+        return {"kernel": "dslash_kernel", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None, "ms_per_launch": ms}
+    if dom == "lift":
+        b = n_rhs * w["k"] * N * 16
+        gbs = b / (ms * 1e-3) / 1e9
+        return {"kernel": "k_lift", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None, "ms_per_launch": ms}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": None, "traffic": None, "ms_per_launch": ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup-ref", type=int, default=0)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, rank)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_gpu(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * nksign -- nested Krylov-Ritz evaluation of sgn(A) b for A = gamma5 D_w(mu)
+ * (Bloch & Heybrock, "A nested Krylov subspace method to compute the sign
+ * function of large complex matrices", 2009), on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI. Plain pointers and sizes only; no C++ or PyTorch types cross it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: dims = {Lx, Ly, Lz, Lt}; site s = x + Lx*(y + Ly*(z + Lz*t)), V = Lx*Ly*Lz*Lt.
+ * Spinor vectors: 12*V complex numbers, complex = two doubles (re, im)
+ *   interleaved; element 12*s + 3*spin + colour.  A block of n vectors is
+ *   stored vector after vector (vector r starts at element r*12*V).
+ * Links: U_{x,+nu} in SU(3) for nu = 0,1,2,3 = x,y,z,t, layout
+ *   [t][z][y][x][nu][3][3] complex doubles (row-major 3x3).
+ * Gamma matrices (the paper leaves the basis open, Sec. 2): chiral basis,
+ *   gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 = [[0, 1], [1, 0]],
+ *   gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1, 1, -1, -1).
+ * Boundary conditions: periodic in x, y, z; in t antiperiodic (a factor -1 on
+ *   every hop that crosses the t boundary) unless created with
+ *   bc_t_antiperiodic = 0 (then periodic).
+ * Wilson-Dirac operator (Sec. 2):
+ *   D_w(mu) = 1 - kappa sum_{i=1..3}(T_i^+ + T_i^-) - kappa(e^{mu} T_4^+ + e^{-mu} T_4^-),
+ *   (T_nu^{+-})_{yx} = (1 +- gamma_nu) U_{x,+-nu} delta_{y,x+-nu},
+ *   U_{x,-nu} = U^dagger_{x-nu,+nu}, kappa = 1/(8 + 2 m_w).
+ *
+ * Pointers: entry points without the _dev suffix take HOST pointers, which
+ * the library copies; the caller keeps ownership.  Entry points with the _dev
+ * suffix take DEVICE pointers (of the context's device) and a cudaStream_t
+ * passed as void* (NULL = legacy default stream); they are asynchronous with
+ * respect to the host unless stated otherwise, and the caller keeps ownership.
+ * The context owns all other device memory (links, Krylov bases, scratch),
+ * allocated on first use and kept until nk_destroy.
+ *
+ * Errors: every int-returning call returns NK_OK (0) or a negative NK_E*
+ * code; nk_last_error() then holds a one-line message.  A context is not
+ * thread-safe: one host thread at a time.
+ */
+#ifndef NKSIGN_H
+#define NKSIGN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NK_OK 0
+#define NK_EINVAL (-1)      /* bad argument: odd k or l, l > k, bad dims, ... */
+#define NK_ENOMEM (-2)      /* device allocation failed */
+#define NK_EBREAKDOWN (-3)  /* two-sided Lanczos serious breakdown (App. B) */
+#define NK_ENOTCONV (-4)    /* adaptive k: tolerance not met at k_max */
+#define NK_ERHI (-5)        /* Roberts-Higham iteration did not converge */
+#define NK_ECUDA (-6)       /* CUDA runtime error */
+#define NK_ETIMEOUT (-7)    /* a bounded device-side wait ran out */
+#define NK_ESTATE (-8)      /* call out of order (e.g. no links loaded) */
+
+/* Solve flags (bitwise or). */
+#define NK_FP64 0x0u        /* every stencil application in FP64 */
+#define NK_MIXED 0x1u       /* FP32 stencil after the first j0 outer steps (nk_set_precision) */
+#define NK_DOUBLE_PASS 0x2u /* regenerate V_k in a second pass instead of storing it (Sec. 4.4) */
+#define NK_NO_GRAPH 0x10u   /* launch kernel by kernel instead of replaying a CUDA graph */
+#define NK_PROFILE 0x20u    /* kernel by kernel, with CUDA events around every launch; fills
+                               nk_stats.t_class_ms / n_class (implies NK_NO_GRAPH) */
+
+#define NK_MAX_RHS 12
+
+/* Kernel classes of a solve, for nk_stats.t_class_ms / n_class. */
+#define NK_CLASS_DSLASH 0   /* Wilson stencil A v (and A^dagger w) */
+#define NK_CLASS_STEP1 1    /* r = Av - c v_prev, H(j,j) */
+#define NK_CLASS_STEP2 2    /* r -= H(j,j) v, beta / delta */
+#define NK_CLASS_STEP3 3    /* v_{j+1} = r / beta */
+#define NK_CLASS_INNER 4    /* p estimate, LU of p H_k, inner Lanczos */
+#define NK_CLASS_RHI 5      /* Roberts-Higham iteration */
+#define NK_CLASS_LIFT 6     /* V_l s and |x| V_k c */
+#define NK_CLASS_OTHER 7    /* layout conversion, norms */
+#define NK_NCLASS 8
+
+typedef struct nk_ctx nk_ctx;
+
+/* Per-solve statistics (all optional to read). */
+typedef struct nk_stats {
+    int n_rhs;
+    int k_used;                        /* outer Krylov size used */
+    int ell_used;                      /* inner Krylov size used */
+    int rhi_iters[NK_MAX_RHS];         /* Roberts-Higham iterations per RHS */
+    int status[NK_MAX_RHS];            /* NK_OK or NK_E* per RHS */
+    double p[NK_MAX_RHS];              /* preconditioning factor used (Eq. precond) */
+    double z_min[NK_MAX_RHS];          /* spectral estimates behind p (Eq. popt) */
+    double z_max[NK_MAX_RHS];
+    double xnorm[NK_MAX_RHS];          /* |x| of each source */
+    double t_total_ms;                 /* device time of the whole solve (CUDA events) */
+    int launches;                      /* kernels this library launched for the solve */
+    double t_class_ms[NK_NCLASS];      /* NK_PROFILE: summed device time per kernel class */
+    int n_class[NK_NCLASS];            /* NK_PROFILE: launches per kernel class */
+} nk_stats;
+
+/* Create a context for a lattice of dims[4] = {Lx, Ly, Lz, Lt} (each >= 2;
+ * Lt even when antiperiodic is not required).  Selects the current CUDA
+ * device.  *out receives the context. */
+int nk_create_lattice(const int dims[4], int bc_t_antiperiodic, nk_ctx** out);
+
+/* Load links from HOST memory, layout [t][z][y][x][nu][3][3] complex double
+ * (18*4*V doubles).  Copies them, keeps an FP64 master and an FP32 copy on
+ * the device (the FP32 copy is what the mixed-precision stencil reads). */
+int nk_load_links(nk_ctx* ctx, const double* U);
+
+/* Same from DEVICE memory (stream-ordered on `stream`). */
+int nk_load_links_dev(nk_ctx* ctx, const double* U_dev, void* stream);
+
+/* Set the chemical potential mu (Sec. 2; mu = 0 gives the Hermitian case and
+ * the Lanczos recurrence, mu != 0 the two-sided recurrence) and the Wilson
+ * mass m_w (kappa = 1/(8 + 2 m_w); requires 8 + 2 m_w > 0). */
+int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
+
+/* Precision schedule for NK_MIXED: outer steps j < j0 use the FP64 stencil,
+ * j >= j0 the FP32 stencil.  j0 < 0 selects the default k/4.  Everything
+ * other than the stencil (recurrence coefficients, inner products, basis,
+ * preconditioning, inner projection, RHi, lift) stays FP64. */
+int nk_set_precision(nk_ctx* ctx, int j0);
+
+/*
+ * y = sgn(A) b by the nested Krylov-Ritz method (Eq. nested; App. C steps
+ * 2-6 without deflation):
+ *   outer (two-sided) Lanczos of size k (App. A / B) -> V_k, H_k;
+ *   p from Eq. popt (power / inverse iteration with H_k) unless p > 0 given;
+ *   LU of p H_k (gttrf form, App. C step 3);
+ *   inner (two-sided) Lanczos of size l with H_k' = [pH_k + (pH_k)^{-1}]/2 and
+ *   e_1 (Eq. precond, App. C step 4) -> V_l, H_l;
+ *   Roberts-Higham iteration on H_l (Eq. Roberts, App. C step 5);
+ *   y = |b| V_k V_l sgn(H_l) e_1 (App. C step 6).
+ * b, y: HOST arrays of n_rhs vectors (1 <= n_rhs <= NK_MAX_RHS), each solved
+ * independently (own recurrence coefficients) but batched through one
+ * stencil launch per step.  k, l even (Fig. 7 caption), 2 <= l <= k.
+ * tol must be 0 (fixed k).  flags: NK_FP64 or NK_MIXED, optionally
+ * NK_DOUBLE_PASS / NK_NO_GRAPH.  st may be NULL.  Blocks until y is written.
+ * Returns NK_EBREAKDOWN / NK_ERHI when any RHS failed (st->status says which;
+ * the other RHS are still valid). */
+int nk_sign_apply(nk_ctx* ctx, const double* b, int n_rhs, int k, int ell, double tol,
+                  double p, unsigned flags, double* y, nk_stats* st);
+
+/* Same with DEVICE b and y, stream-ordered on `stream`; returns once the
+ * solve has completed (it reads the per-RHS status back). */
+int nk_sign_apply_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, int ell, double tol,
+                      double p, unsigned flags, double* y_dev, nk_stats* st, void* stream);
+
+/* Overlap operator D_ov(mu) b = b + gamma5 sgn(gamma5 D_w(mu)) b (Eq. Dovmu),
+ * one sign evaluation per call; arguments as nk_sign_apply with p automatic. */
+int nk_overlap_apply(nk_ctx* ctx, const double* b, int n_rhs, int k, int ell, double tol,
+                     unsigned flags, double* y, nk_stats* st);
+int nk_overlap_apply_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, int ell,
+                         double tol, unsigned flags, double* y_dev, nk_stats* st, void* stream);
+
+/* The Wilson stencil alone: out_r = A in_r (dagger = 0) or A^dagger in_r
+ * (dagger = 1; A^dagger = gamma5 D_w(-mu)) for n_vec DEVICE vectors in the
+ * ABI layout.  precision = 64 computes in FP64 with the FP64 links; 32 rounds
+ * the input to FP32 and computes with the FP32 links (output FP64).
+ * Stream-ordered, asynchronous. */
+int nk_dslash_dev(nk_ctx* ctx, const double* in_dev, double* out_dev, int n_vec, int dagger,
+                  int precision, void* stream);
+
+/* The outer recurrence alone (App. A for mu = 0, App. B otherwise): k steps
+ * from each of n_rhs DEVICE sources b_dev; writes H_k of each RHS as
+ * three HOST arrays of complex doubles, alpha[r*k + j] = H(j,j),
+ * beta[r*k + j] = H(j+1,j), gamma[r*k + j] = H(j,j+1) (j < k-1), and |b_r|
+ * to xnorm[r].  flags: NK_FP64 or NK_MIXED.  Blocks. */
+int nk_outer_lanczos_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, unsigned flags,
+                         double* alpha, double* beta, double* gamma, double* xnorm,
+                         void* stream);
+
+/* The inner half (App. C steps 3-5 and the product V_l s) for n_rhs given
+ * tridiagonal Ritz matrices (HOST arrays in the nk_outer_lanczos_dev layout):
+ * c_r = V_l sgn(H_l) e_1 as complex doubles in the HOST array c[r*k + i].
+ * hermitian = 1 uses the real Lanczos path (H real symmetric), 0 the
+ * two-sided one.  p > 0 fixes p; p <= 0 estimates it (Eq. popt).  Needs a
+ * context only for its device and scratch memory.  Blocks. */
+int nk_inner_sign(nk_ctx* ctx, const double* alpha, const double* beta, const double* gamma,
+                  int n_rhs, int k, int ell, double p, int hermitian, double* c,
+                  nk_stats* st);
+
+/* Message of the last failed call on this context (never NULL). */
+const char* nk_last_error(const nk_ctx* ctx);
+
+/* Release every device resource of the context.  NULL is a no-op. */
+void nk_destroy(nk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NKSIGN_H */

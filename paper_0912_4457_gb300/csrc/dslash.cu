@@ -1,0 +1,262 @@
+// Wilson-Dirac stencil A = gamma5 D_w(mu) and A^dagger = gamma5 D_w(-mu).
+//
+// D_w(mu) of Sec. 2: (D_w psi)_y = psi_y
+//     - kappa sum_nu w+_nu (1 + gamma_nu) U_{y-nu,+nu} psi_{y-nu}
+//     - kappa sum_nu w-_nu (1 - gamma_nu) U^dagger_{y,+nu} psi_{y+nu},
+// w+-_nu = 1 for nu = x,y,z and w+_t = e^{mu}, w-_t = e^{-mu}; a hop across
+// the t boundary carries a factor -1 (antiperiodic).  Since
+// gamma5 D_w(mu) gamma5 = D_w(-mu)^dagger, A^dagger = gamma5 D_w(-mu): the same
+// stencil with the two temporal weights exchanged, so one kernel serves the
+// right (A v) and left (A^dagger w) recurrences of the two-sided Lanczos
+// process in a single launch, reading each link once for both.
+//
+// Chiral basis: (1 + s gamma_nu) psi = [h ; s B_nu h] with the half spinor
+// h = psi_up + s C_nu psi_dn, C_k = -i sigma_k, B_k = i sigma_k, C_4 = B_4 = 1,
+// so each hop multiplies only the two colour vectors of h by the link.
+//
+// Layouts (device-internal, set up by the engine):
+//   links:   [nu 4][e 9][site V] complex, e = 3*row + col (coalesced over sites)
+//   spinors: [component 12][site V] complex per vector, component = 3*spin + colour
+#include "nk_common.cuh"
+#include "nk_kernels.h"
+
+namespace nk {
+
+template <typename R>
+struct Spinor {
+    typename C2<R>::T c[4][3];
+};
+
+template <typename R>
+__device__ __forceinline__ void load_link(const typename C2<R>::T* __restrict__ U, int V, int nu,
+                                          int site, typename C2<R>::T u[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) u[a][b] = U[(size_t)(nu * 9 + 3 * a + b) * V + site];
+}
+
+template <typename R>
+__device__ __forceinline__ void load_spinor(const typename C2<R>::T* __restrict__ in, int V, int site,
+                                            typename C2<R>::T p[4][3]) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) p[s][a] = in[(size_t)(3 * s + a) * V + site];
+}
+
+// i * z and -i * z
+template <typename T> __device__ __forceinline__ T mul_i(T z) { T r; r.x = -z.y; r.y = z.x; return r; }
+template <typename T> __device__ __forceinline__ T mul_mi(T z) { T r; r.x = z.y; r.y = -z.x; return r; }
+template <typename T> __device__ __forceinline__ T neg(T z) { T r; r.x = -z.x; r.y = -z.y; return r; }
+
+// One hop: acc += w * (1 + s gamma_nu) M psi_n with M = U (dag = false) or U^dagger.
+template <int NU, bool DAG, typename R>
+__device__ __forceinline__ void hop(typename C2<R>::T acc[4][3], const typename C2<R>::T psi[4][3],
+                                    const typename C2<R>::T u[3][3], R s, R w) {
+    typedef typename C2<R>::T T;
+    T h0[3], h1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T c0, c1;  // (C_nu psi_dn)_0, _1
+        if (NU == 0) { c0 = mul_mi(psi[3][a]); c1 = mul_mi(psi[2][a]); }
+        else if (NU == 1) { c0 = neg(psi[3][a]); c1 = psi[2][a]; }
+        else if (NU == 2) { c0 = mul_mi(psi[2][a]); c1 = mul_i(psi[3][a]); }
+        else { c0 = psi[2][a]; c1 = psi[3][a]; }
+        h0[a].x = psi[0][a].x + s * c0.x; h0[a].y = psi[0][a].y + s * c0.y;
+        h1[a].x = psi[1][a].x + s * c1.x; h1[a].y = psi[1][a].y + s * c1.y;
+    }
+    T m0[3], m1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T x0, x1;
+        x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            T e = DAG ? u[b][a] : u[a][b];
+            R ey = DAG ? -e.y : e.y;
+            x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
+            x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
+        }
+        m0[a] = x0; m1[a] = x1;
+    }
+    R ws = w * s;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[0][a].x += w * m0[a].x; acc[0][a].y += w * m0[a].y;
+        acc[1][a].x += w * m1[a].x; acc[1][a].y += w * m1[a].y;
+        T b0, b1;  // (B_nu m)_0, _1
+        if (NU == 0) { b0 = mul_i(m1[a]); b1 = mul_i(m0[a]); }
+        else if (NU == 1) { b0 = m1[a]; b1 = neg(m0[a]); }
+        else if (NU == 2) { b0 = mul_i(m0[a]); b1 = mul_mi(m1[a]); }
+        else { b0 = m0[a]; b1 = m1[a]; }
+        acc[2][a].x += ws * b0.x; acc[2][a].y += ws * b0.y;
+        acc[3][a].x += ws * b1.x; acc[3][a].y += ws * b1.y;
+    }
+}
+
+template <int NU, typename R>
+__device__ __forceinline__ void dir(typename C2<R>::T acc[4][3], const typename C2<R>::T* __restrict__ U,
+                                    const typename C2<R>::T* __restrict__ in, const Geom& g, int site,
+                                    int coord, int L, int stride, R wplus, R wminus) {
+    typedef typename C2<R>::T T;
+    T u[3][3], p[4][3];
+    // backward neighbour y - nu: (1 + gamma) U_{y-nu,+nu} psi_{y-nu}
+    int sb = coord == 0 ? site + (L - 1) * stride : site - stride;
+    R fb = (NU == 3 && g.antiperiodic && coord == 0) ? R(-1) : R(1);
+    load_link<R>(U, g.V, NU, sb, u);
+    load_spinor<R>(in, g.V, sb, p);
+    hop<NU, false, R>(acc, p, u, R(1), wplus * fb);
+    // forward neighbour y + nu: (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}
+    int sf = coord == L - 1 ? site - (L - 1) * stride : site + stride;
+    R ff = (NU == 3 && g.antiperiodic && coord == L - 1) ? R(-1) : R(1);
+    load_link<R>(U, g.V, NU, site, u);
+    load_spinor<R>(in, g.V, sf, p);
+    hop<NU, true, R>(acc, p, u, R(-1), wminus * ff);
+}
+
+// One thread per (site, vector). Vectors [0, n0) come from set 0, [n0, n0+n1)
+// from set 1; set s applies A (dag = 0) or A^dagger (dag = 1).
+template <typename R>
+__global__ void __launch_bounds__(128) dslash_kernel(const typename C2<R>::T* __restrict__ U, Geom g,
+                                                      DslashSet s0, DslashSet s1, R kappa, R emu) {
+    typedef typename C2<R>::T T;
+    const int nvec = s0.n + s1.n;
+    const int vec = blockIdx.x % nvec;
+    const int site = (blockIdx.x / nvec) * blockDim.x + threadIdx.x;
+    if (site >= g.V) return;
+    const DslashSet& S = vec < s0.n ? s0 : s1;
+    const int vi = vec < s0.n ? vec : vec - s0.n;
+    const T* __restrict__ in = reinterpret_cast<const T*>(S.in) + (size_t)vi * S.in_stride;
+    double2* __restrict__ out = S.out + (size_t)vi * S.out_stride;
+    // temporal weights: A uses (e^{mu}, e^{-mu}); A^dagger exchanges them
+    R wp_t = S.dag ? R(1) / emu : emu;
+    R wm_t = S.dag ? emu : R(1) / emu;
+
+    int x = site % g.Lx;
+    int r = site / g.Lx;
+    int y = r % g.Ly; r /= g.Ly;
+    int z = r % g.Lz;
+    int t = r / g.Lz;
+
+    T acc[4][3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { acc[sp][a].x = 0; acc[sp][a].y = 0; }
+    const T* __restrict__ Ul = reinterpret_cast<const T*>(U);
+    dir<0, R>(acc, Ul, in, g, site, x, g.Lx, 1, R(1), R(1));
+    dir<1, R>(acc, Ul, in, g, site, y, g.Ly, g.Lx, R(1), R(1));
+    dir<2, R>(acc, Ul, in, g, site, z, g.Lz, g.Lx * g.Ly, R(1), R(1));
+    dir<3, R>(acc, Ul, in, g, site, t, g.Lt, g.Lx * g.Ly * g.Lz, wp_t, wm_t);
+
+    T p[4][3];
+    load_spinor<R>(in, g.V, site, p);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const R sg = sp < 2 ? R(1) : R(-1);  // gamma5 = diag(1, 1, -1, -1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double2 o;
+            o.x = (double)(sg * (p[sp][a].x - kappa * acc[sp][a].x));
+            o.y = (double)(sg * (p[sp][a].y - kappa * acc[sp][a].y));
+            out[(size_t)(3 * sp + a) * g.V + site] = o;
+        }
+    }
+}
+
+void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet& s0,
+                   const DslashSet& s1, double kappa, double mu, cudaStream_t st) {
+    const int threads = 128;
+    const int nvec = s0.n + s1.n;
+    if (nvec == 0) return;
+    dim3 grid((unsigned)(((g.V + threads - 1) / threads) * nvec));
+    if (precision == 32)
+        dslash_kernel<float><<<grid, threads, 0, st>>>((const float2*)U, g, s0, s1, (float)kappa,
+                                                      (float)exp(mu));
+    else
+        dslash_kernel<double><<<grid, threads, 0, st>>>((const double2*)U, g, s0, s1, kappa, exp(mu));
+}
+
+// ---- layout conversion -------------------------------------------------------
+
+// ABI links [site][nu][3][3] complex double -> [nu][9][site] (FP64 and FP32 copies)
+__global__ void links_to_device_layout(const double2* __restrict__ in, double2* __restrict__ u64,
+                                       float2* __restrict__ u32, int V) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)V * 36) return;
+    int site = (int)(i / 36), rem = (int)(i % 36), nu = rem / 9, e = rem % 9;
+    double2 v = in[i];
+    size_t o = (size_t)(nu * 9 + e) * V + site;
+    u64[o] = v;
+    u32[o] = make_float2((float)v.x, (float)v.y);
+}
+
+void launch_links_to_device_layout(const double2* in, double2* u64, float2* u32, int V,
+                                   cudaStream_t st) {
+    size_t n = (size_t)V * 36;
+    links_to_device_layout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, u64, u32, V);
+}
+
+// ABI spinor [site][12] -> SoA [12][site], n vectors
+__global__ void spinor_abi_to_soa(const double2* __restrict__ in, long in_stride, double2* __restrict__ out,
+                                  long out_stride, int V, int n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t per = (size_t)V * 12;
+    if (i >= per * n) return;
+    int vec = (int)(i / per);
+    size_t j = i % per;
+    int site = (int)(j / 12), c = (int)(j % 12);
+    out[(size_t)vec * out_stride + (size_t)c * V + site] = in[(size_t)vec * in_stride + j];
+}
+
+// SoA [12][site] -> ABI [site][12]; if add != nullptr: out = add + gamma5 * in (overlap)
+__global__ void spinor_soa_to_abi(const double2* __restrict__ in, long in_stride, double2* __restrict__ out,
+                                  long out_stride, const double2* __restrict__ add, long add_stride,
+                                  int V, int n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t per = (size_t)V * 12;
+    if (i >= per * n) return;
+    int vec = (int)(i / per);
+    size_t j = i % per;
+    int site = (int)(j / 12), c = (int)(j % 12);
+    double2 v = in[(size_t)vec * in_stride + (size_t)c * V + site];
+    if (add) {
+        double2 b = add[(size_t)vec * add_stride + j];
+        double sg = c < 6 ? 1.0 : -1.0;  // gamma5 on spins 2, 3
+        v = make_double2(b.x + sg * v.x, b.y + sg * v.y);
+    }
+    out[(size_t)vec * out_stride + j] = v;
+}
+
+void launch_abi_to_soa(const double2* in, long in_stride, double2* out, long out_stride, int V,
+                       int n, cudaStream_t st) {
+    size_t tot = (size_t)V * 12 * n;
+    spinor_abi_to_soa<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride,
+                                                                      V, n);
+}
+
+void launch_soa_to_abi(const double2* in, long in_stride, double2* out, long out_stride,
+                       const double2* add, long add_stride, int V, int n, cudaStream_t st) {
+    size_t tot = (size_t)V * 12 * n;
+    spinor_soa_to_abi<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride,
+                                                                      add, add_stride, V, n);
+}
+
+__global__ void to_fp32(const double2* __restrict__ in, long in_stride, float2* __restrict__ out,
+                        long out_stride, long N, int n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * n) return;
+    int vec = (int)(i / N);
+    size_t j = i % N;
+    double2 v = in[(size_t)vec * in_stride + j];
+    out[(size_t)vec * out_stride + j] = make_float2((float)v.x, (float)v.y);
+}
+
+void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_stride, long N, int n,
+                    cudaStream_t st) {
+    size_t tot = (size_t)N * n;
+    to_fp32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride, N, n);
+}
+
+}  // namespace nk

@@ -1,0 +1,660 @@
+// Host engine and C ABI (include/nksign.h): context, device workspace, the
+// solve driver that sequences the kernels of one nested Krylov-Ritz
+// evaluation, and CUDA-graph capture of whole solves.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/nksign.h"
+#include "nk_kernels.h"
+
+using nk::Geom;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct GraphKey {
+    const void* b;
+    void* y;
+    int n_rhs, k, ell, j0;
+    unsigned flags;
+    double p, mu, mw;
+    int overlap;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(b, y, n_rhs, k, ell, j0, flags, p, mu, mw, overlap) <
+               std::tie(o.b, o.y, o.n_rhs, o.k, o.ell, o.j0, o.flags, o.p, o.mu, o.mw, o.overlap);
+    }
+};
+
+struct nk_ctx {
+    int dims[4];
+    int V;
+    long N;
+    int antiperiodic;
+    int device;
+    double mu = 0.0, m_w = 0.0;
+    bool mu_set = false;
+    int j0 = -1;
+    bool links = false;
+    double2* U64 = nullptr;
+    float2* U32 = nullptr;
+    DevBuf ws;            // solve workspace (carved per solve shape)
+    DevBuf staging;       // host-pointer API: device copies of b and y
+    DevBuf links_tmp;
+    std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;  // exec, kernels per replay
+    std::string err = "no error";
+};
+
+namespace {
+
+int fail(nk_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(nk_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, NK_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NK_CUDA(ctx, call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+int ensure(nk_ctx* c, DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes) return NK_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    // graphs hold pointers into the old workspace
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.first);
+    c->graphs.clear();
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, NK_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                      cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return NK_OK;
+}
+
+Geom geom_of(const nk_ctx* c) {
+    Geom g;
+    g.Lx = c->dims[0]; g.Ly = c->dims[1]; g.Lz = c->dims[2]; g.Lt = c->dims[3];
+    g.V = c->V;
+    g.antiperiodic = c->antiperiodic;
+    return g;
+}
+
+double kappa_of(const nk_ctx* c) { return 1.0 / (8.0 + 2.0 * c->m_w); }
+
+// Carves the solve workspace; returns total bytes (dry run when base == nullptr).
+struct Layout {
+    nk::Outer o;
+    nk::Inner in;
+    double2* b_soa;
+    double2* y_soa;
+    size_t total;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout carve(char* base, long N, int n_rhs, int k, int ell, bool two_sided, bool double_pass, int nblk) {
+    Layout L;
+    std::memset(&L, 0, sizeof(L));
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return p;
+    };
+    const size_t vec = (size_t)N * sizeof(double2);
+    L.b_soa = (double2*)take(vec * n_rhs);
+    L.y_soa = (double2*)take(vec * n_rhs);
+    nk::Outer& o = L.o;
+    o.N = N; o.n_rhs = n_rhs; o.k = k; o.nblk = nblk; o.two_sided = two_sided;
+    if (double_pass) o.vring = (double2*)take(vec * 2 * n_rhs);
+    else o.V = (double2*)take(vec * (size_t)k * n_rhs);
+    if (two_sided) o.w = (double2*)take(vec * 2 * n_rhs);
+    o.r = (double2*)take(vec * n_rhs);
+    o.s = (double2*)take(vec * n_rhs);
+    if (two_sided) { o.l = (double2*)take(vec * n_rhs); o.t = (double2*)take(vec * n_rhs); }
+    o.v32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
+    if (two_sided) o.w32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
+    o.alpha = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
+    o.beta = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
+    o.gamma = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
+    o.partials = (double2*)take(sizeof(double2) * (size_t)nblk * n_rhs);
+    o.counters = (unsigned*)take(sizeof(unsigned) * n_rhs);
+    o.status = (int*)take(sizeof(int) * n_rhs);
+    o.xnorm = (double*)take(sizeof(double) * n_rhs);
+    nk::Inner& in = L.in;
+    in.n_rhs = n_rhs; in.k = k; in.ell = ell; in.two_sided = two_sided;
+    in.alpha = o.alpha; in.beta = o.beta; in.gamma = o.gamma;
+    in.p = (double*)take(sizeof(double) * n_rhs);
+    in.zmin = (double*)take(sizeof(double) * n_rhs);
+    in.zmax = (double*)take(sizeof(double) * n_rhs);
+    in.work = (double2*)take(sizeof(double2) * (size_t)nk::kInnerWorkVecs * k * n_rhs);
+    in.ipiv = (int*)take(sizeof(int) * (size_t)k * n_rhs);
+    in.Vl = (double2*)take(sizeof(double2) * (size_t)ell * k * n_rhs);
+    in.al = (double2*)take(sizeof(double2) * (size_t)ell * n_rhs);
+    in.bl = (double2*)take(sizeof(double2) * (size_t)ell * n_rhs);
+    in.gl = (double2*)take(sizeof(double2) * (size_t)ell * n_rhs);
+    in.S = (double2*)take(sizeof(double2) * (size_t)ell * ell * n_rhs);
+    in.s = (double2*)take(sizeof(double2) * (size_t)ell * n_rhs);
+    in.rhi_iters = (int*)take(sizeof(int) * n_rhs);
+    in.c = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
+    in.status = o.status;
+    in.timeout = (int*)take(sizeof(int));
+    L.total = off;
+    return L;
+}
+
+int blocks_per_rhs(long N, int n_rhs) {
+    // fixed per shape: enough blocks to fill the GPU, grid-stride beyond that
+    long need = (N + 255) / 256;
+    long cap = std::max(1L, (long)(4 * 152 / n_rhs));
+    return (int)std::max(1L, std::min(need, cap));
+}
+
+int check_solve_args(nk_ctx* c, int n_rhs, int k, int ell, double tol) {
+    if (!c) return NK_EINVAL;
+    if (!c->links) return fail(c, NK_ESTATE, "no links loaded (nk_load_links)");
+    if (!c->mu_set) return fail(c, NK_ESTATE, "mu and m_w not set (nk_set_mu_mw)");
+    if (n_rhs < 1 || n_rhs > NK_MAX_RHS) return fail(c, NK_EINVAL, "n_rhs must be in [1, 12]");
+    if (k < 2 || (k & 1)) return fail(c, NK_EINVAL, "k must be even and >= 2");
+    if (ell < 2 || (ell & 1)) return fail(c, NK_EINVAL, "l must be even and >= 2");
+    if (ell > k) return fail(c, NK_EINVAL, "l must not exceed k");
+    if (ell > 256) return fail(c, NK_EINVAL, "l must not exceed 256");
+    if (k > 8192) return fail(c, NK_EINVAL, "k must not exceed 8192");
+    if (tol != 0.0) return fail(c, NK_EINVAL, "tol must be 0 (fixed k)");
+    return NK_OK;
+}
+
+// Sequences launches on one stream; counts them and, in NK_PROFILE mode,
+// brackets each with CUDA events recorded on that stream.
+struct Launcher {
+    cudaStream_t st;
+    bool profile = false;
+    int launches = 0;
+    int n_class[NK_NCLASS] = {0};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    template <typename F>
+    void run(int cls, int nkernels, F&& f) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (profile) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, st);
+        }
+        f();
+        if (profile) {
+            cudaEventRecord(b, st);
+            marks.push_back({cls, {a, b}});
+        }
+        launches += nkernels;
+        n_class[cls] += nkernels;
+    }
+    void collect(double* t_ms) {
+        for (auto& m : marks) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, m.second.first, m.second.second);
+            t_ms[m.first] += ms;
+            cudaEventDestroy(m.second.first);
+            cudaEventDestroy(m.second.second);
+        }
+        marks.clear();
+    }
+};
+
+// Enqueues the outer recurrence (init + k steps).
+void enqueue_outer(nk_ctx* c, const nk::Outer& o, const double2* b_soa, bool mixed, int j0, Launcher& L) {
+    const Geom g = geom_of(c);
+    const double kap = kappa_of(c);
+    cudaStream_t st = L.st;
+    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, b_soa, (mixed && j0 <= 0) ? 1 : 0, st); });
+    const long N = o.N;
+    for (int j = 0; j < o.k; ++j) {
+        const bool f32 = mixed && j >= j0;
+        nk::DslashSet s0, s1;
+        std::memset(&s0, 0, sizeof(s0));
+        std::memset(&s1, 0, sizeof(s1));
+        if (f32) {
+            s0.in = o.v32; s0.in_stride = N;
+        } else {
+            s0.in = nk::outer_v(o, 0, j);
+            s0.in_stride = o.V ? (long)o.k * N : 2 * N;
+        }
+        s0.out = o.s; s0.out_stride = N; s0.n = o.n_rhs; s0.dag = 0;
+        if (o.two_sided) {
+            if (f32) { s1.in = o.w32; s1.in_stride = N; }
+            else { s1.in = nk::outer_w(o, 0, j); s1.in_stride = 2 * N; }
+            s1.out = o.t; s1.out_stride = N; s1.n = o.n_rhs; s1.dag = 1;
+        }
+        L.run(NK_CLASS_DSLASH, 1, [&] {
+            nk::launch_dslash(f32 ? 32 : 64, f32 ? (const void*)c->U32 : (const void*)c->U64, g, s0, s1, kap,
+                              c->mu, st);
+        });
+        L.run(NK_CLASS_STEP1, 1, [&] { nk::launch_outer_step1(o, j, st); });
+        if (j < o.k - 1) {
+            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step2(o, j, st); });
+            L.run(NK_CLASS_STEP3, 1, [&] { nk::launch_outer_step3(o, j, (mixed && j + 1 >= j0) ? 1 : 0, st); });
+        }
+    }
+}
+
+int effective_j0(const nk_ctx* c, int k) { return c->j0 < 0 ? k / 4 : std::min(c->j0, k); }
+
+// Enqueues a whole solve (device pointers in ABI layout). Returns cudaError_t of launches.
+cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_dev, int n_rhs,
+                          double p, unsigned flags, bool overlap, Launcher& L) {
+    const bool mixed = (flags & NK_MIXED) != 0;
+    const bool dp = (flags & NK_DOUBLE_PASS) != 0;
+    const int j0 = effective_j0(c, Lw.o.k);
+    cudaStream_t st = L.st;
+    nk::Outer o = Lw.o;
+    nk::Inner in = Lw.in;
+    in.p_fixed = p;
+    L.run(NK_CLASS_OTHER, 1, [&] {
+        nk::launch_abi_to_soa((const double2*)b_dev, c->N, Lw.b_soa, c->N, c->V, n_rhs, st);
+    });
+    enqueue_outer(c, o, Lw.b_soa, mixed, j0, L);
+    L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_lanczos(in, st); });
+    cudaError_t e = cudaSuccess;
+    L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(in, st); });
+    if (e != cudaSuccess) return e;
+    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_inner_combine(in, st); });
+    if (dp) {
+        o.y = Lw.y_soa;
+        o.c = in.c;
+        cudaMemsetAsync(Lw.y_soa, 0, sizeof(double2) * (size_t)c->N * n_rhs, st);
+        // second pass: regenerate the identical basis and accumulate y = sum_j c_j v_j
+        enqueue_outer(c, o, Lw.b_soa, mixed, j0, L);
+    }
+    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, in.c, Lw.y_soa, st); });
+    L.run(NK_CLASS_OTHER, 1, [&] {
+        nk::launch_soa_to_abi(Lw.y_soa, c->N, (double2*)y_dev, c->N, overlap ? (const double2*)b_dev : nullptr,
+                              c->N, c->V, n_rhs, st);
+    });
+    return cudaGetLastError();
+}
+
+int status_to_code(int s) {
+    switch (s) {
+        case nk::kStatusOK:
+        case nk::kStatusZeroSource: return NK_OK;
+        case nk::kStatusBreakdown: return NK_EBREAKDOWN;
+        case nk::kStatusRhi: return NK_ERHI;
+        case nk::kStatusLU: return NK_ERHI;
+        default: return NK_ECUDA;
+    }
+}
+
+int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
+              unsigned flags, double* y_dev, nk_stats* stats, cudaStream_t st, bool overlap) {
+    int rc = check_solve_args(c, n_rhs, k, ell, tol);
+    if (rc) return rc;
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const bool ts = c->mu != 0.0;
+    const bool dp = (flags & NK_DOUBLE_PASS) != 0;
+    const int nblk = blocks_per_rhs(c->N, n_rhs);
+    Layout dry = carve(nullptr, c->N, n_rhs, k, ell, ts, dp, nblk);
+    rc = ensure(c, c->ws, dry.total);
+    if (rc) return rc;
+    Layout Lw = carve((char*)c->ws.p, c->N, n_rhs, k, ell, ts, dp, nblk);
+    // counters must start at zero; status is (re)set by the norm kernel
+    NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
+    NK_CUDA(c, cudaMemsetAsync(Lw.in.timeout, 0, sizeof(int), st));
+
+    cudaEvent_t e0, e1;
+    NK_CUDA(c, cudaEventCreate(&e0));
+    NK_CUDA(c, cudaEventCreate(&e1));
+    NK_CUDA(c, cudaEventRecord(e0, st));
+    const bool profile = (flags & NK_PROFILE) != 0;
+    const bool use_graph = (flags & (NK_NO_GRAPH | NK_PROFILE)) == 0;
+    Launcher L;
+    L.st = st;
+    L.profile = profile;
+    if (use_graph) {
+        GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, flags, p, c->mu, c->m_w, overlap ? 1 : 0};
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaStream_t cs;
+            NK_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            NK_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            Launcher Lc;
+            Lc.st = cs;
+            cudaError_t e = enqueue_solve(c, Lw, b_dev, y_dev, n_rhs, p, flags, overlap, Lc);
+            cudaGraph_t graph;
+            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) return cuda_fail(c, e, "enqueue_solve (capture)");
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+            cudaGraphExec_t exec;
+            cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
+            it = c->graphs.emplace(key, std::make_pair(exec, Lc.launches)).first;
+        }
+        NK_CUDA(c, cudaGraphLaunch(it->second.first, st));
+        L.launches = it->second.second;
+    } else {
+        cudaError_t e = enqueue_solve(c, Lw, b_dev, y_dev, n_rhs, p, flags, overlap, L);
+        if (e != cudaSuccess) return cuda_fail(c, e, "enqueue_solve");
+    }
+    NK_CUDA(c, cudaEventRecord(e1, st));
+    // read back per-RHS outcome
+    std::vector<int> status(n_rhs), iters(n_rhs);
+    std::vector<double> pv(n_rhs), zmin(n_rhs), zmax(n_rhs), xn(n_rhs);
+    NK_CUDA(c, cudaMemcpyAsync(status.data(), Lw.o.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(iters.data(), Lw.in.rhi_iters, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(pv.data(), Lw.in.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(zmin.data(), Lw.in.zmin, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(zmax.data(), Lw.in.zmax, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(xn.data(), Lw.o.xnorm, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = NK_OK;
+    for (int r = 0; r < n_rhs; ++r) {
+        int code = status_to_code(status[r]);
+        if (code != NK_OK && worst == NK_OK) worst = code;
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->n_rhs = n_rhs;
+        stats->k_used = k;
+        stats->ell_used = ell;
+        for (int r = 0; r < n_rhs; ++r) {
+            stats->rhi_iters[r] = iters[r];
+            stats->status[r] = status_to_code(status[r]);
+            stats->p[r] = pv[r];
+            stats->z_min[r] = zmin[r];
+            stats->z_max[r] = zmax[r];
+            stats->xnorm[r] = xn[r];
+        }
+        stats->t_total_ms = ms;
+        stats->launches = L.launches;
+        if (profile) {
+            L.collect(stats->t_class_ms);
+            for (int q = 0; q < NK_NCLASS; ++q) stats->n_class[q] = L.n_class[q];
+        }
+    } else if (profile) {
+        double tmp[NK_NCLASS] = {0};
+        L.collect(tmp);
+    }
+    if (worst == NK_EBREAKDOWN) return fail(c, worst, "two-sided Lanczos: serious breakdown (delta = 0)");
+    if (worst == NK_ERHI) return fail(c, worst, "Roberts-Higham iteration did not converge (or p H_k singular)");
+    return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nk_create_lattice(const int dims[4], int bc_t_antiperiodic, nk_ctx** out) {
+    if (!dims || !out) return NK_EINVAL;
+    *out = nullptr;
+    long V = 1;
+    for (int i = 0; i < 4; ++i) {
+        if (dims[i] < 2) return NK_EINVAL;
+        V *= dims[i];
+    }
+    if (V > (1L << 28)) return NK_EINVAL;
+    nk_ctx* c = new nk_ctx();
+    std::memcpy(c->dims, dims, sizeof(c->dims));
+    c->V = (int)V;
+    c->N = 12 * V;
+    c->antiperiodic = bc_t_antiperiodic ? 1 : 0;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return NK_ECUDA;
+    }
+    nk::init_kernel_attributes();
+    cudaGetLastError();
+    *out = c;
+    return NK_OK;
+}
+
+static int load_links_impl(nk_ctx* c, const double* U, bool host, cudaStream_t st) {
+    if (!c || !U) return NK_EINVAL;
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const size_t n = (size_t)c->V * 36;
+    if (!c->U64) {
+        NK_CUDA(c, cudaMalloc(&c->U64, n * sizeof(double2)));
+        NK_CUDA(c, cudaMalloc(&c->U32, n * sizeof(float2)));
+    }
+    const double2* src = (const double2*)U;
+    if (host) {
+        int rc = ensure(c, c->links_tmp, n * sizeof(double2));
+        if (rc) return rc;
+        NK_CUDA(c, cudaMemcpyAsync(c->links_tmp.p, U, n * sizeof(double2), cudaMemcpyHostToDevice, st));
+        src = (const double2*)c->links_tmp.p;
+    }
+    nk::launch_links_to_device_layout(src, c->U64, c->U32, c->V, st);
+    NK_CUDA(c, cudaGetLastError());
+    NK_CUDA(c, cudaStreamSynchronize(st));
+    c->links = true;
+    return NK_OK;
+}
+
+int nk_load_links(nk_ctx* c, const double* U) { return load_links_impl(c, U, true, 0); }
+
+int nk_load_links_dev(nk_ctx* c, const double* U_dev, void* stream) {
+    return load_links_impl(c, U_dev, false, (cudaStream_t)stream);
+}
+
+int nk_set_mu_mw(nk_ctx* c, double mu, double m_w) {
+    if (!c) return NK_EINVAL;
+    if (!(8.0 + 2.0 * m_w > 0.0) || !std::isfinite(mu) || !std::isfinite(m_w))
+        return fail(c, NK_EINVAL, "need finite mu, m_w with 8 + 2 m_w > 0");
+    if (c->mu != mu || c->m_w != m_w) {
+        for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.first);
+        c->graphs.clear();
+    }
+    c->mu = mu;
+    c->m_w = m_w;
+    c->mu_set = true;
+    return NK_OK;
+}
+
+int nk_set_precision(nk_ctx* c, int j0) {
+    if (!c) return NK_EINVAL;
+    c->j0 = j0;
+    return NK_OK;
+}
+
+int nk_sign_apply_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
+                      unsigned flags, double* y_dev, nk_stats* st, void* stream) {
+    if (!c || !b_dev || !y_dev) return NK_EINVAL;
+    return solve_dev(c, b_dev, n_rhs, k, ell, tol, p, flags, y_dev, st, (cudaStream_t)stream, false);
+}
+
+static int host_solve(nk_ctx* c, const double* b, int n_rhs, int k, int ell, double tol, double p,
+                      unsigned flags, double* y, nk_stats* st, bool overlap) {
+    if (!c || !b || !y) return NK_EINVAL;
+    int rc = check_solve_args(c, n_rhs, k, ell, tol);
+    if (rc) return rc;
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const size_t bytes = sizeof(double2) * (size_t)c->N * n_rhs;
+    rc = ensure(c, c->staging, 2 * NK_MAX_RHS * sizeof(double2) * (size_t)c->N);
+    if (rc) return rc;
+    double* bd = (double*)c->staging.p;
+    double* yd = bd + 2 * (size_t)c->N * NK_MAX_RHS;
+    NK_CUDA(c, cudaMemcpy(bd, b, bytes, cudaMemcpyHostToDevice));
+    rc = solve_dev(c, bd, n_rhs, k, ell, tol, p, flags, yd, st, 0, overlap);
+    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI) return rc;
+    cudaError_t e = cudaMemcpy(y, yd, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy y");
+    return rc;
+}
+
+int nk_sign_apply(nk_ctx* c, const double* b, int n_rhs, int k, int ell, double tol, double p,
+                  unsigned flags, double* y, nk_stats* st) {
+    return host_solve(c, b, n_rhs, k, ell, tol, p, flags, y, st, false);
+}
+
+int nk_overlap_apply(nk_ctx* c, const double* b, int n_rhs, int k, int ell, double tol, unsigned flags,
+                     double* y, nk_stats* st) {
+    return host_solve(c, b, n_rhs, k, ell, tol, 0.0, flags, y, st, true);
+}
+
+int nk_overlap_apply_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol,
+                         unsigned flags, double* y_dev, nk_stats* st, void* stream) {
+    if (!c || !b_dev || !y_dev) return NK_EINVAL;
+    return solve_dev(c, b_dev, n_rhs, k, ell, tol, 0.0, flags, y_dev, st, (cudaStream_t)stream, true);
+}
+
+int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, int dagger, int precision,
+                  void* stream) {
+    if (!c || !in_dev || !out_dev || n_vec < 1 || n_vec > 2 * NK_MAX_RHS) return NK_EINVAL;
+    if (precision != 32 && precision != 64) return fail(c, NK_EINVAL, "precision must be 32 or 64");
+    if (!c->links) return fail(c, NK_ESTATE, "no links loaded");
+    if (!c->mu_set) return fail(c, NK_ESTATE, "mu and m_w not set");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const long N = c->N;
+    // scratch: SoA input (FP64 and FP32) and SoA output
+    size_t bytes = align_up(sizeof(double2) * N * n_vec) * 2 + align_up(sizeof(float2) * N * n_vec);
+    int rc = ensure(c, c->staging, std::max(bytes, c->staging.bytes));
+    if (rc) return rc;
+    double2* in_soa = (double2*)c->staging.p;
+    double2* out_soa = (double2*)((char*)c->staging.p + align_up(sizeof(double2) * N * n_vec));
+    float2* in32 = (float2*)((char*)out_soa + align_up(sizeof(double2) * N * n_vec));
+    nk::launch_abi_to_soa((const double2*)in_dev, N, in_soa, N, c->V, n_vec, st);
+    nk::DslashSet s0, s1;
+    std::memset(&s0, 0, sizeof(s0));
+    std::memset(&s1, 0, sizeof(s1));
+    if (precision == 32) {
+        nk::launch_to_fp32(in_soa, N, in32, N, N, n_vec, st);
+        s0.in = in32;
+    } else {
+        s0.in = in_soa;
+    }
+    s0.in_stride = N;
+    s0.out = out_soa;
+    s0.out_stride = N;
+    s0.n = n_vec;
+    s0.dag = dagger ? 1 : 0;
+    nk::launch_dslash(precision, precision == 32 ? (const void*)c->U32 : (const void*)c->U64, geom_of(c), s0,
+                      s1, kappa_of(c), c->mu, st);
+    nk::launch_soa_to_abi(out_soa, N, (double2*)out_dev, N, nullptr, 0, c->V, n_vec, st);
+    NK_CUDA(c, cudaGetLastError());
+    return NK_OK;
+}
+
+int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsigned flags, double* alpha,
+                         double* beta, double* gamma, double* xnorm, void* stream) {
+    int rc = check_solve_args(c, n_rhs, k, 2, 0.0);
+    if (rc) return rc;
+    if (!b_dev || !alpha || !beta || !gamma || !xnorm) return fail(c, NK_EINVAL, "null pointer");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool ts = c->mu != 0.0;
+    const int nblk = blocks_per_rhs(c->N, n_rhs);
+    Layout dry = carve(nullptr, c->N, n_rhs, k, 2, ts, false, nblk);
+    rc = ensure(c, c->ws, dry.total);
+    if (rc) return rc;
+    Layout Lw = carve((char*)c->ws.p, c->N, n_rhs, k, 2, ts, false, nblk);
+    NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
+    nk::launch_abi_to_soa((const double2*)b_dev, c->N, Lw.b_soa, c->N, c->V, n_rhs, st);
+    Launcher L;
+    L.st = st;
+    enqueue_outer(c, Lw.o, Lw.b_soa, (flags & NK_MIXED) != 0, effective_j0(c, k), L);
+    NK_CUDA(c, cudaGetLastError());
+    const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
+    NK_CUDA(c, cudaMemcpyAsync(alpha, Lw.o.alpha, cb, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(beta, Lw.o.beta, cb, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(gamma, Lw.o.gamma, cb, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(xnorm, Lw.o.xnorm, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
+    std::vector<int> status(n_rhs);
+    NK_CUDA(c, cudaMemcpyAsync(status.data(), Lw.o.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaStreamSynchronize(st));
+    for (int r = 0; r < n_rhs; ++r)
+        if (status[r] == nk::kStatusBreakdown)
+            return fail(c, NK_EBREAKDOWN, "two-sided Lanczos: serious breakdown (delta = 0)");
+    return NK_OK;
+}
+
+int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const double* gamma, int n_rhs, int k,
+                  int ell, double p, int hermitian, double* cout, nk_stats* st) {
+    if (!c || !alpha || !beta || !gamma || !cout) return NK_EINVAL;
+    if (n_rhs < 1 || n_rhs > NK_MAX_RHS || k < 2 || ell < 2 || ell > k || ell > 256 || (k & 1) || (ell & 1))
+        return fail(c, NK_EINVAL, "bad n_rhs, k or l");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const bool ts = hermitian == 0;
+    Layout dry = carve(nullptr, 2, n_rhs, k, ell, ts, true, 1);
+    int rc = ensure(c, c->staging, std::max(dry.total, c->staging.bytes));
+    if (rc) return rc;
+    Layout Lw = carve((char*)c->staging.p, 2, n_rhs, k, ell, ts, true, 1);
+    const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
+    NK_CUDA(c, cudaMemcpy(Lw.o.alpha, alpha, cb, cudaMemcpyHostToDevice));
+    NK_CUDA(c, cudaMemcpy(Lw.o.beta, beta, cb, cudaMemcpyHostToDevice));
+    NK_CUDA(c, cudaMemcpy(Lw.o.gamma, gamma, cb, cudaMemcpyHostToDevice));
+    NK_CUDA(c, cudaMemset(Lw.o.status, 0, sizeof(int) * n_rhs));
+    nk::Inner in = Lw.in;
+    in.p_fixed = p;
+    nk::launch_inner_lanczos(in, 0);
+    cudaError_t e = (cudaError_t)nk::launch_rhi(in, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "launch_rhi");
+    nk::launch_inner_combine(in, 0);
+    NK_CUDA(c, cudaGetLastError());
+    NK_CUDA(c, cudaDeviceSynchronize());
+    NK_CUDA(c, cudaMemcpy(cout, in.c, cb, cudaMemcpyDeviceToHost));
+    std::vector<int> status(n_rhs), iters(n_rhs);
+    std::vector<double> pv(n_rhs), zmin(n_rhs), zmax(n_rhs);
+    NK_CUDA(c, cudaMemcpy(status.data(), in.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(iters.data(), in.rhi_iters, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(pv.data(), in.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(zmin.data(), in.zmin, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(zmax.data(), in.zmax, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
+    int worst = NK_OK;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->n_rhs = n_rhs;
+        st->k_used = k;
+        st->ell_used = ell;
+    }
+    for (int r = 0; r < n_rhs; ++r) {
+        int code = status_to_code(status[r]);
+        if (code != NK_OK && worst == NK_OK) worst = code;
+        if (st) {
+            st->rhi_iters[r] = iters[r];
+            st->status[r] = code;
+            st->p[r] = pv[r];
+            st->z_min[r] = zmin[r];
+            st->z_max[r] = zmax[r];
+        }
+    }
+    if (worst != NK_OK) return fail(c, worst, "inner sign failed (breakdown, singular p H_k or RHi)");
+    return NK_OK;
+}
+
+const char* nk_last_error(const nk_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void nk_destroy(nk_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.first);
+    if (c->ws.p) cudaFree(c->ws.p);
+    if (c->staging.p) cudaFree(c->staging.p);
+    if (c->links_tmp.p) cudaFree(c->links_tmp.p);
+    if (c->U64) cudaFree(c->U64);
+    if (c->U32) cudaFree(c->U32);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,626 @@
+// Inner half of the nested method, per RHS (App. C steps 3-5, Eqs. popt,
+// precond, innersign, Roberts):
+//   p      = (z_min z_max)^{-1/2}, z_max by power iteration with H_k and z_min
+//            by inverse iteration with the LU of H_k (30 steps each, from the
+//            normalised all-ones vector), unless p is given;
+//   LU of p H_k in LAPACK gttrf form (partial pivoting; U with two super-diagonals);
+//   inner (two-sided) Lanczos of size l with H_k' = [p H_k + (p H_k)^{-1}]/2 and
+//            e_1, applying (p H_k)^{-1} by the gttrs back substitution and
+//            p H_k by a band product (App. C step 4 (a), (b));
+//   Roberts-Higham iteration S <- (S + S^{-1})/2 on the dense H_l;
+//   c = V_l sgn(H_l) e_1.
+// In the Hermitian case (mu = 0) all of it is real arithmetic (App. C).
+//
+// The inner Lanczos runs one CTA per RHS: the band products, inner products
+// and axpys are spread over the CTA, the two O(k) substitution sweeps of each
+// solve are a sequential chain in one thread (two threads in the two-sided
+// case: H_k' v and H_k'^dagger w are independent).
+//
+// RHi runs one thread-block cluster per RHS: the rows of the l x l matrix
+// being inverted (in-place Gauss-Jordan with partial pivoting and row
+// interchanges) are spread cyclically over the cluster's CTAs and held in
+// their shared memory; the pivot search, the pivot row broadcast and the row
+// interchange go through distributed shared memory between two cluster
+// barriers per pivot.
+#include <cooperative_groups.h>
+
+#include "nk_common.cuh"
+#include "nk_kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace nk {
+
+namespace {
+
+// ---- arithmetic on T = double (real, Hermitian case) or double2 (complex) ----
+__device__ __forceinline__ double t_zero(double) { return 0.0; }
+__device__ __forceinline__ double2 t_zero(double2) { return mk(0.0, 0.0); }
+__device__ __forceinline__ double t_from(double2 a, double) { return a.x; }
+__device__ __forceinline__ double2 t_from(double2 a, double2) { return a; }
+__device__ __forceinline__ double2 t_to2(double a) { return mk(a, 0.0); }
+__device__ __forceinline__ double2 t_to2(double2 a) { return a; }
+__device__ __forceinline__ double t_conj(double a) { return a; }
+__device__ __forceinline__ double2 t_conj(double2 a) { return cconj(a); }
+__device__ __forceinline__ double t_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ double2 t_mul(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ double t_add(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 t_add(double2 a, double2 b) { return cadd(a, b); }
+__device__ __forceinline__ double t_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 t_sub(double2 a, double2 b) { return csub(a, b); }
+__device__ __forceinline__ double t_scale(double a, double s) { return a * s; }
+__device__ __forceinline__ double2 t_scale(double2 a, double s) { return cscale(a, s); }
+__device__ __forceinline__ double t_inv(double a) { return 1.0 / a; }
+__device__ __forceinline__ double2 t_inv(double2 a) { return cinv(a); }
+__device__ __forceinline__ double t_abs1(double a) { return fabs(a); }
+__device__ __forceinline__ double t_abs1(double2 a) { return cabs1(a); }  // LAPACK CABS1
+__device__ __forceinline__ double t_norm2(double a) { return a * a; }
+__device__ __forceinline__ double t_norm2(double2 a) { return cnorm2(a); }
+__device__ __forceinline__ bool t_iszero(double a) { return a == 0.0; }
+__device__ __forceinline__ bool t_iszero(double2 a) { return a.x == 0.0 && a.y == 0.0; }
+// conj(a) * b
+__device__ __forceinline__ double2 t_dotc(double a, double b) { return mk(a * b, 0.0); }
+__device__ __forceinline__ double2 t_dotc(double2 a, double2 b) { return cmulc(a, b); }
+
+// Tridiagonal LU with partial pivoting, LAPACK gttrf semantics (row i and
+// i+1 are interchanged when |d_i| < |dl_i|, |.| = |re| + |im| for complex).
+// On return dl holds the multipliers, d, du, du2 the rows of U, ipiv the
+// interchanges (0-based: ipiv[i] = i or i+1) and dinv = 1/d.
+// Returns 0, or i+1 if U(i,i) = 0.  Sequential, one thread.
+template <typename T>
+__device__ int gttrf(int n, T* dl, T* d, T* du, T* du2, int* ipiv, T* dinv) {
+    for (int i = 0; i < n; ++i) ipiv[i] = i;
+    for (int i = 0; i < n - 2; ++i) du2[i] = t_zero(T());
+    for (int i = 0; i < n - 1; ++i) {
+        if (t_abs1(d[i]) >= t_abs1(dl[i])) {
+            if (!t_iszero(d[i])) {
+                T fact = t_mul(dl[i], t_inv(d[i]));
+                dl[i] = fact;
+                d[i + 1] = t_sub(d[i + 1], t_mul(fact, du[i]));
+            }
+        } else {
+            T fact = t_mul(d[i], t_inv(dl[i]));
+            d[i] = dl[i];
+            dl[i] = fact;
+            T temp = du[i];
+            du[i] = d[i + 1];
+            d[i + 1] = t_sub(temp, t_mul(fact, d[i + 1]));
+            if (i < n - 2) {
+                du2[i] = du[i + 1];
+                du[i + 1] = t_mul(t_scale(fact, -1.0), du[i + 1]);
+            }
+            ipiv[i] = i + 1;
+        }
+    }
+    int info = 0;
+    for (int i = 0; i < n; ++i) {
+        if (t_iszero(d[i])) { if (!info) info = i + 1; dinv[i] = t_zero(T()); }
+        else dinv[i] = t_inv(d[i]);
+    }
+    return info;
+}
+
+// x <- (L U)^{-1} x  (gttrs, trans = 'N'). Sequential, one thread.
+template <typename T>
+__device__ void gttrs_n(int n, const T* __restrict__ dl, const T* __restrict__ du, const T* __restrict__ du2,
+                        const int* __restrict__ ipiv, const T* __restrict__ dinv, T* __restrict__ b) {
+    // L: forward sweep with the recorded interchanges
+    T bi = b[0];
+    for (int i = 0; i < n - 1; ++i) {
+        T bn = b[i + 1];
+        if (ipiv[i] == i) {
+            b[i] = bi;
+            bi = t_sub(bn, t_mul(dl[i], bi));
+        } else {
+            b[i] = bn;
+            bi = t_sub(bi, t_mul(dl[i], bn));
+        }
+    }
+    b[n - 1] = bi;
+    // U: backward sweep with the two super-diagonals
+    T x2 = t_mul(b[n - 1], dinv[n - 1]);
+    b[n - 1] = x2;
+    if (n > 1) {
+        T x1 = t_mul(t_sub(b[n - 2], t_mul(du[n - 2], x2)), dinv[n - 2]);
+        b[n - 2] = x1;
+        for (int i = n - 3; i >= 0; --i) {
+            T x0 = t_mul(t_sub(t_sub(b[i], t_mul(du[i], x1)), t_mul(du2[i], x2)), dinv[i]);
+            b[i] = x0;
+            x2 = x1;
+            x1 = x0;
+        }
+    }
+}
+
+// x <- ((L U)^dagger)^{-1} x  (gttrs, trans = 'C'). Sequential, one thread.
+template <typename T>
+__device__ void gttrs_c(int n, const T* __restrict__ dl, const T* __restrict__ du, const T* __restrict__ du2,
+                        const int* __restrict__ ipiv, const T* __restrict__ dinv, T* __restrict__ b) {
+    // U^dagger: forward sweep
+    T x2 = t_mul(b[0], t_conj(dinv[0]));
+    b[0] = x2;
+    if (n > 1) {
+        T x1 = t_mul(t_sub(b[1], t_mul(t_conj(du[0]), x2)), t_conj(dinv[1]));
+        b[1] = x1;
+        for (int i = 2; i < n; ++i) {
+            T x0 = t_mul(t_sub(t_sub(b[i], t_mul(t_conj(du[i - 1]), x1)), t_mul(t_conj(du2[i - 2]), x2)),
+                         t_conj(dinv[i]));
+            b[i] = x0;
+            x2 = x1;
+            x1 = x0;
+        }
+    }
+    // L^dagger: backward sweep with the interchanges
+    for (int i = n - 2; i >= 0; --i) {
+        if (ipiv[i] == i) {
+            b[i] = t_sub(b[i], t_mul(t_conj(dl[i]), b[i + 1]));
+        } else {
+            T temp = b[i + 1];
+            b[i + 1] = t_sub(b[i], t_mul(t_conj(dl[i]), temp));
+            b[i] = temp;
+        }
+    }
+}
+
+// y = p * H x (dagger: p * H^dagger x) for the outer tridiagonal, in the
+// summation order (diag, sub, super) -- all threads of the block.
+template <typename T>
+__device__ void band_mv(int n, double p, const double2* al, const double2* be, const double2* ga,
+                        const T* __restrict__ x, T* __restrict__ y, bool dagger) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T dg = t_from(al[i], T());
+        if (dagger) dg = t_conj(dg);
+        T acc = t_mul(dg, x[i]);
+        if (i > 0) {
+            T sub = dagger ? t_conj(t_from(ga[i - 1], T())) : t_from(be[i - 1], T());
+            acc = t_add(acc, t_mul(sub, x[i - 1]));
+        }
+        if (i < n - 1) {
+            T sup = dagger ? t_conj(t_from(be[i], T())) : t_from(ga[i], T());
+            acc = t_add(acc, t_mul(sup, x[i + 1]));
+        }
+        y[i] = t_scale(acc, p);
+    }
+}
+
+// <a, b> = sum conj(a_i) b_i over the block
+template <typename T>
+__device__ double2 bdot(int n, const T* a, const T* b, double2* sh) {
+    double2 acc = mk(0.0, 0.0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cadd(acc, t_dotc(a[i], b[i]));
+    return block_sum(acc, sh);
+}
+
+template <typename T>
+__device__ double bnorm(int n, const T* a, double* sh) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += t_norm2(a[i]);
+    return sqrt(block_sum(acc, sh));
+}
+
+struct LuView {
+    void* dl; void* d; void* du; void* du2; void* dinv; int* ipiv;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inner(Inner in) {
+    __shared__ double2 sh2[32];
+    __shared__ double sh1[32];
+    __shared__ int s_info;
+    const int rhs = blockIdx.x;
+    const int k = in.k, L = in.ell;
+    if (in.status[rhs] != kStatusOK) return;
+    const double2* al = in.alpha + (size_t)rhs * k;
+    const double2* be = in.beta + (size_t)rhs * k;
+    const double2* ga = in.gamma + (size_t)rhs * k;
+    T* W = reinterpret_cast<T*>(in.work + (size_t)rhs * kInnerWorkVecs * k);
+    T* dl = W + 0 * (size_t)k;
+    T* d = W + 1 * (size_t)k;
+    T* du = W + 2 * (size_t)k;
+    T* du2 = W + 3 * (size_t)k;
+    T* dinv = W + 4 * (size_t)k;
+    T* x = W + 5 * (size_t)k;
+    T* y = W + 6 * (size_t)k;
+    T* vprev = W + 7 * (size_t)k;
+    T* v = W + 8 * (size_t)k;
+    T* r = W + 9 * (size_t)k;
+    T* wprev = W + 10 * (size_t)k;
+    T* w = W + 11 * (size_t)k;
+    T* l = W + 12 * (size_t)k;
+    T* t1 = W + 13 * (size_t)k;
+    T* t2 = W + 14 * (size_t)k;
+    int* ipiv = in.ipiv + (size_t)rhs * k;
+    const bool TS = sizeof(T) == sizeof(double2);
+
+    // ---- p (Eq. popt) --------------------------------------------------------
+    double p = in.p_fixed;
+    if (!(p > 0.0)) {
+        const double x0 = 1.0 / sqrt((double)k);
+        for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_from(mk(x0, 0.0), T());
+        __syncthreads();
+        double zmax = 0.0;
+        for (int it = 0; it < 30; ++it) {
+            band_mv<T>(k, 1.0, al, be, ga, x, y, false);
+            __syncthreads();
+            zmax = bnorm<T>(k, y, sh1);
+            const double inv = 1.0 / zmax;
+            for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(y[i], inv);
+            __syncthreads();
+        }
+        // LU of H itself for the inverse iteration
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            d[i] = t_from(al[i], T());
+            if (i < k - 1) { dl[i] = t_from(be[i], T()); du[i] = t_from(ga[i], T()); }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, d, du, du2, ipiv, dinv);
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_from(mk(x0, 0.0), T());
+        __syncthreads();
+        double tn = 1.0;
+        for (int it = 0; it < 30; ++it) {
+            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = x[i];
+            __syncthreads();
+            if (threadIdx.x == 0) gttrs_n<T>(k, dl, du, du2, ipiv, dinv, y);
+            __syncthreads();
+            tn = bnorm<T>(k, y, sh1);
+            const double inv = 1.0 / tn;
+            for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(y[i], inv);
+            __syncthreads();
+        }
+        const double zmin = 1.0 / tn;
+        p = 1.0 / sqrt(zmin * zmax);
+        if (threadIdx.x == 0) { in.zmin[rhs] = zmin; in.zmax[rhs] = zmax; }
+    } else if (threadIdx.x == 0) {
+        in.zmin[rhs] = 0.0; in.zmax[rhs] = 0.0;
+    }
+    if (threadIdx.x == 0) in.p[rhs] = p;
+
+    // ---- step 3: LU of p H_k --------------------------------------------------
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        d[i] = t_scale(t_from(al[i], T()), p);
+        if (i < k - 1) { dl[i] = t_scale(t_from(be[i], T()), p); du[i] = t_scale(t_from(ga[i], T()), p); }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, d, du, du2, ipiv, dinv);
+    __syncthreads();
+    if (s_info != 0) {
+        if (threadIdx.x == 0) in.status[rhs] = kStatusLU;
+        return;
+    }
+
+    // ---- step 4: inner (two-sided) Lanczos with H' and e_1 ----------------------
+    // H' x = [(pH) x + (pH)^{-1} x] / 2 into out; with dagger for the left recurrence.
+    double2* Vl = in.Vl + (size_t)rhs * L * k;
+    auto store_vl = [&](int j, const T* src) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) Vl[(size_t)j * k + i] = t_to2(src[i]);
+    };
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        v[i] = t_zero(T());
+        if (TS) w[i] = t_zero(T());
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { v[0] = t_from(mk(1.0, 0.0), T()); if (TS) w[0] = v[0]; }
+    __syncthreads();
+    store_vl(0, v);
+
+    auto apply_hp = [&](const T* src_r, T* out_r, const T* src_l, T* out_l) {
+        // t1 <- src_r, t2 <- src_l; solves in place; band products into out
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            t1[i] = src_r[i];
+            if (TS) t2[i] = src_l[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) gttrs_n<T>(k, dl, du, du2, ipiv, dinv, t1);
+        if (TS && threadIdx.x == 32) gttrs_c<T>(k, dl, du, du2, ipiv, dinv, t2);
+        band_mv<T>(k, p, al, be, ga, src_r, out_r, false);
+        if (TS) band_mv<T>(k, p, al, be, ga, src_l, out_l, true);
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            out_r[i] = t_scale(t_add(out_r[i], t1[i]), 0.5);
+            if (TS) out_l[i] = t_scale(t_add(out_l[i], t2[i]), 0.5);
+        }
+        __syncthreads();
+    };
+
+    apply_hp(v, r, w, l);  // r <- H' v_1, l <- H'^dag w_1
+    double2* alo = in.al + (size_t)rhs * L;
+    double2* blo = in.bl + (size_t)rhs * L;
+    double2* glo = in.gl + (size_t)rhs * L;
+    for (int j = 0; j < L; ++j) {
+        // H(j,j) <- v^dag r (two-sided: w^dag r)
+        double2 a2 = bdot<T>(k, TS ? w : v, r, sh2);
+        T a = TS ? t_from(a2, T()) : t_from(mk(a2.x, 0.0), T());
+        if (threadIdx.x == 0) alo[j] = t_to2(a);
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            r[i] = t_sub(r[i], t_mul(a, v[i]));
+            if (TS) l[i] = t_sub(l[i], t_mul(t_conj(a), w[i]));
+        }
+        __syncthreads();
+        if (j == L - 1) break;
+        T bb, gg;
+        if (!TS) {
+            double b = bnorm<T>(k, r, sh1);            // beta <- |r|
+            bb = t_from(mk(b, 0.0), T());
+            gg = bb;
+            if (!(b > 0.0)) { if (threadIdx.x == 0) in.status[rhs] = kStatusBreakdown; return; }
+        } else {
+            double2 dlt = bdot<T>(k, r, l, sh2);        // delta <- r^dag l
+            if ((dlt.x == 0.0 && dlt.y == 0.0) || !isfinite(dlt.x) || !isfinite(dlt.y)) {
+                if (threadIdx.x == 0) in.status[rhs] = kStatusBreakdown;
+                return;
+            }
+            double2 b2 = csqrt_principal(dlt);
+            bb = t_from(b2, T());
+            gg = t_from(cdiv(cconj(dlt), b2), T());
+        }
+        if (threadIdx.x == 0) { blo[j] = t_to2(bb); glo[j] = t_to2(gg); }
+        const T binv = t_inv(bb);
+        const T ginv = t_inv(t_conj(gg));
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            vprev[i] = v[i];
+            v[i] = t_mul(r[i], binv);                   // v <- r / beta
+            if (TS) { wprev[i] = w[i]; w[i] = t_mul(l[i], ginv); }   // w <- l / gamma^*
+        }
+        __syncthreads();
+        store_vl(j + 1, v);
+        apply_hp(v, r, w, l);
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            r[i] = t_sub(r[i], t_mul(gg, vprev[i]));    // r <- r - gamma v_j
+            if (TS) l[i] = t_sub(l[i], t_mul(t_conj(bb), wprev[i]));   // l <- l - beta^* w_j
+        }
+        __syncthreads();
+    }
+}
+
+// ---- Roberts-Higham iteration on H_l, one cluster per RHS ----------------------
+
+constexpr int kRhiThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kRhiThreads) k_rhi(Inner in, int C, int maxit, double stop) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int rhs = blockIdx.x / C;
+    const int L = in.ell;
+    const int nloc = (L - rank + C - 1) / C;       // rows rank, rank + C, ...
+    const int nmax = (L + C - 1) / C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* M = reinterpret_cast<T*>(smem);              // [nmax][L]
+    T* prow = M + (size_t)nmax * L;                 // [L]
+    T* tmp = prow + L;                              // [L]
+    T* fcol = tmp + L;                              // [nmax]
+    int* piv = reinterpret_cast<int*>(fcol + nmax); // [L]
+    __shared__ double cand_val;
+    __shared__ int cand_idx;
+    __shared__ double part[2];
+    __shared__ double red_v[kRhiThreads / 32];
+    __shared__ int red_i[kRhiThreads / 32];
+    __shared__ double sh1[32];
+    __shared__ int s_stop;
+
+    const int status0 = in.status[rhs];   // identical in every CTA of the cluster
+    T* S = reinterpret_cast<T*>(in.S) + (size_t)rhs * L * L;
+    const double2* alo = in.al + (size_t)rhs * L;
+    const double2* blo = in.bl + (size_t)rhs * L;
+    const double2* glo = in.gl + (size_t)rhs * L;
+    const int tid = threadIdx.x;
+
+    // S_0 = H_l (own rows)
+    for (int e = tid; e < nloc * L; e += blockDim.x) {
+        int li = e / L, col = e % L, i = rank + C * li;
+        T v = t_zero(T());
+        if (status0 == kStatusOK) {
+            if (col == i) v = t_from(alo[i], T());
+            else if (col == i - 1) v = t_from(blo[i - 1], T());
+            else if (col == i + 1) v = t_from(glo[i], T());
+        }
+        S[(size_t)i * L + col] = v;
+    }
+    int iters = 0;
+    bool ok = status0 == kStatusOK;
+    bool converged = false;
+    for (int it = 1; ok && it <= maxit; ++it) {
+        iters = it;
+        for (int e = tid; e < nloc * L; e += blockDim.x) {
+            int li = e / L, col = e % L;
+            M[(size_t)li * L + col] = S[(size_t)(rank + C * li) * L + col];
+        }
+        __syncthreads();
+        // ---- in-place Gauss-Jordan inverse of M with partial pivoting ----
+        for (int c = 0; c < L; ++c) {
+            // (a) local candidate: largest |M(i,c)|^2 over own rows i >= c (lowest i on ties)
+            double bv = -1.0;
+            int bi = 0x7fffffff;
+            for (int li = tid; li < nloc; li += blockDim.x) {
+                int i = rank + C * li;
+                if (i < c) continue;
+                double m = t_norm2(M[(size_t)li * L + c]);
+                if (m > bv || (m == bv && i < bi)) { bv = m; bi = i; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_i[tid >> 5] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+                    if (red_v[q] > bv || (red_v[q] == bv && red_i[q] < bi)) { bv = red_v[q]; bi = red_i[q]; }
+                cand_val = bv;
+                cand_idx = bi;
+            }
+            cl.sync();                                                  // barrier A
+            // (b) pivot row over the cluster, ranks in fixed order
+            double pv = -1.0;
+            int pi = 0x7fffffff;
+            for (int q = 0; q < C; ++q) {
+                double qv = *cl.map_shared_rank(&cand_val, q);
+                int qi = *cl.map_shared_rank(&cand_idx, q);
+                if (qv > pv || (qv == pv && qi < pi)) { pv = qv; pi = qi; }
+            }
+            if (!(pv > 0.0)) {              // singular (same decision in every CTA)
+                ok = false;
+                cl.sync();
+                break;
+            }
+            if (tid == 0) piv[c] = pi;
+            // (c) fetch the pivot row (and, for its owner, old row c)
+            {
+                T* src = cl.map_shared_rank(M, pi % C) + (size_t)(pi / C) * L;
+                for (int col = tid; col < L; col += blockDim.x) prow[col] = src[col];
+                if (pi != c && pi % C == rank) {
+                    T* srcc = cl.map_shared_rank(M, c % C) + (size_t)(c / C) * L;
+                    for (int col = tid; col < L; col += blockDim.x) tmp[col] = srcc[col];
+                }
+            }
+            cl.sync();                                                  // barrier B
+            // (d) interchange and scale the pivot row
+            if (pi != c && pi % C == rank) {
+                T* dst = M + (size_t)(pi / C) * L;
+                for (int col = tid; col < L; col += blockDim.x) dst[col] = tmp[col];
+            }
+            const T pinv = t_inv(prow[c]);
+            __syncthreads();
+            for (int col = tid; col < L; col += blockDim.x)
+                prow[col] = col == c ? pinv : t_mul(prow[col], pinv);
+            __syncthreads();
+            if (c % C == rank) {
+                T* dst = M + (size_t)(c / C) * L;
+                for (int col = tid; col < L; col += blockDim.x) dst[col] = prow[col];
+            }
+            // (e) eliminate column c from every other own row
+            for (int li = tid; li < nloc; li += blockDim.x) fcol[li] = M[(size_t)li * L + c];
+            __syncthreads();
+            for (int e = tid; e < nloc * L; e += blockDim.x) {
+                int li = e / L, col = e % L;
+                if (rank + C * li == c) continue;
+                T f = fcol[li];
+                T& m = M[(size_t)li * L + col];
+                m = col == c ? t_scale(t_mul(f, prow[c]), -1.0) : t_sub(m, t_mul(f, prow[col]));
+            }
+            __syncthreads();
+        }
+        if (!ok) break;
+        // undo the interchanges on the columns of the inverse
+        for (int c = L - 1; c >= 0; --c) {
+            int q = piv[c];
+            if (q != c) {
+                for (int li = tid; li < nloc; li += blockDim.x) {
+                    T a = M[(size_t)li * L + c];
+                    M[(size_t)li * L + c] = M[(size_t)li * L + q];
+                    M[(size_t)li * L + q] = a;
+                }
+            }
+            __syncthreads();
+        }
+        // S <- (S + S^{-1}) / 2 and the relative Frobenius change
+        double dsum = 0.0, nsum = 0.0;
+        for (int e = tid; e < nloc * L; e += blockDim.x) {
+            int li = e / L, col = e % L;
+            size_t gi = (size_t)(rank + C * li) * L + col;
+            T so = S[gi];
+            T sn = t_scale(t_add(so, M[(size_t)li * L + col]), 0.5);
+            dsum += t_norm2(t_sub(sn, so));
+            nsum += t_norm2(sn);
+            S[gi] = sn;
+        }
+        dsum = block_sum(dsum, sh1);
+        nsum = block_sum(nsum, sh1);
+        if (tid == 0) { part[0] = dsum; part[1] = nsum; }
+        cl.sync();
+        double dt = 0.0, nt = 0.0;
+        for (int q = 0; q < C; ++q) {
+            const double* pq = cl.map_shared_rank(part, q);
+            dt += pq[0];
+            nt += pq[1];
+        }
+        cl.sync();   // every CTA has read the partials before they are rewritten
+        if (sqrt(dt) <= stop * sqrt(nt)) { converged = true; break; }
+    }
+    if (tid == 0) s_stop = 0;
+    __syncthreads();
+    // s = S e_1 (own rows), iteration count, status
+    for (int li = tid; li < nloc; li += blockDim.x) {
+        int i = rank + C * li;
+        in.s[(size_t)rhs * L + i] = t_to2(S[(size_t)i * L]);
+    }
+    if (rank == 0 && tid == 0) {
+        in.rhi_iters[rhs] = iters;
+        if (status0 == kStatusOK && !converged) in.status[rhs] = kStatusRhi;
+    }
+}
+
+// c = V_l s (k-vector per RHS)
+__global__ void k_combine(Inner in) {
+    const int rhs = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= in.k) return;
+    double2* c = in.c + (size_t)rhs * in.k;
+    if (in.status[rhs] != kStatusOK) { c[i] = mk(0.0, 0.0); return; }
+    const double2* Vl = in.Vl + (size_t)rhs * in.ell * in.k;
+    const double2* s = in.s + (size_t)rhs * in.ell;
+    double2 acc = mk(0.0, 0.0);
+    for (int j = 0; j < in.ell; ++j) acc = cadd(acc, cmul(Vl[(size_t)j * in.k + i], s[j]));
+    c[i] = acc;
+}
+
+}  // namespace
+
+void launch_inner_lanczos(const Inner& in, cudaStream_t st) {
+    if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, 0, st>>>(in);
+    else k_inner<double><<<in.n_rhs, 256, 0, st>>>(in);
+}
+
+// Largest dynamic shared memory any RHi launch needs (l <= 256, complex, 8 CTAs).
+static size_t rhi_smem_max();
+
+void init_kernel_attributes() {
+    cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());
+    cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());
+    cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+static int rhi_cluster_size(int ell) { return ell >= 64 ? 8 : (ell >= 16 ? 4 : 1); }
+
+template <typename T>
+static size_t rhi_smem(int ell, int C) {
+    int nmax = (ell + C - 1) / C;
+    return (size_t)nmax * ell * sizeof(T) + 2 * (size_t)ell * sizeof(T) + (size_t)nmax * sizeof(T) +
+           (size_t)ell * sizeof(int) + 16;
+}
+
+static size_t rhi_smem_max() { return rhi_smem<double2>(256, 8); }
+
+template <typename T>
+static cudaError_t launch_rhi_t(const Inner& in, cudaStream_t st) {
+    const int C = rhi_cluster_size(in.ell);
+    size_t smem = rhi_smem<T>(in.ell, C);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(in.n_rhs * C);
+    cfg.blockDim = dim3(kRhiThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_rhi<T>, in, C, 50, 1e-10);
+}
+
+int launch_rhi(const Inner& in, cudaStream_t st) {
+    return (int)(in.two_sided ? launch_rhi_t<double2>(in, st) : launch_rhi_t<double>(in, st));
+}
+
+void launch_inner_combine(const Inner& in, cudaStream_t st) {
+    dim3 grid((in.k + 127) / 128, in.n_rhs);
+    k_combine<<<grid, 128, 0, st>>>(in);
+}
+
+}  // namespace nk

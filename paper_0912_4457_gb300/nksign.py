@@ -1,0 +1,285 @@
+"""ctypes binding of the C ABI in include/nksign.h (argument marshalling only).
+
+Every function here has the name of the C entry point without the ``nk_``
+prefix and forwards to ``libnksign.so``; all arithmetic of the method runs in
+the library's CUDA kernels.  Device arrays are passed as torch CUDA tensors
+(complex128, contiguous) and the current torch stream is used unless one is
+given.  There is no CPU fallback: if the library is not built, or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnksign.so")
+
+NK_OK = 0
+NK_EINVAL = -1
+NK_ENOMEM = -2
+NK_EBREAKDOWN = -3
+NK_ENOTCONV = -4
+NK_ERHI = -5
+NK_ECUDA = -6
+NK_ETIMEOUT = -7
+NK_ESTATE = -8
+
+NK_FP64 = 0x0
+NK_MIXED = 0x1
+NK_DOUBLE_PASS = 0x2
+NK_NO_GRAPH = 0x10
+NK_PROFILE = 0x20
+NK_MAX_RHS = 12
+NK_NCLASS = 8
+CLASS_NAMES = ["dslash", "step1", "step2", "step3", "inner", "rhi", "lift", "other"]
+
+ERROR_NAMES = {
+    NK_EINVAL: "NK_EINVAL", NK_ENOMEM: "NK_ENOMEM", NK_EBREAKDOWN: "NK_EBREAKDOWN",
+    NK_ENOTCONV: "NK_ENOTCONV", NK_ERHI: "NK_ERHI", NK_ECUDA: "NK_ECUDA",
+    NK_ETIMEOUT: "NK_ETIMEOUT", NK_ESTATE: "NK_ESTATE",
+}
+
+EXPORTED = [
+    "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision",
+    "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
+    "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_last_error", "nk_destroy",
+]
+
+
+class NkStats(ctypes.Structure):
+    _fields_ = [
+        ("n_rhs", ctypes.c_int),
+        ("k_used", ctypes.c_int),
+        ("ell_used", ctypes.c_int),
+        ("rhi_iters", ctypes.c_int * NK_MAX_RHS),
+        ("status", ctypes.c_int * NK_MAX_RHS),
+        ("p", ctypes.c_double * NK_MAX_RHS),
+        ("z_min", ctypes.c_double * NK_MAX_RHS),
+        ("z_max", ctypes.c_double * NK_MAX_RHS),
+        ("xnorm", ctypes.c_double * NK_MAX_RHS),
+        ("t_total_ms", ctypes.c_double),
+        ("launches", ctypes.c_int),
+        ("t_class_ms", ctypes.c_double * NK_NCLASS),
+        ("n_class", ctypes.c_int * NK_NCLASS),
+    ]
+
+    def as_dict(self):
+        n = self.n_rhs
+        return {
+            "n_rhs": n, "k_used": self.k_used, "ell_used": self.ell_used,
+            "rhi_iters": list(self.rhi_iters[:n]), "status": list(self.status[:n]),
+            "p": list(self.p[:n]), "z_min": list(self.z_min[:n]), "z_max": list(self.z_max[:n]),
+            "xnorm": list(self.xnorm[:n]), "t_total_ms": self.t_total_ms,
+            "launches": self.launches,
+            "t_class_ms": dict(zip(CLASS_NAMES, list(self.t_class_ms))),
+            "n_class": dict(zip(CLASS_NAMES, list(self.n_class))),
+        }
+
+
+class NkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "NK_?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnksign.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libnksign.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "nk_create_lattice": ([ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
+        "nk_load_links": ([P, dp], I),
+        "nk_load_links_dev": ([P, P, P], I),
+        "nk_set_mu_mw": ([P, D, D], I),
+        "nk_set_precision": ([P, I], I),
+        "nk_sign_apply": ([P, dp, I, I, I, D, D, U, dp, ctypes.POINTER(NkStats)], I),
+        "nk_sign_apply_dev": ([P, P, I, I, I, D, D, U, P, ctypes.POINTER(NkStats), P], I),
+        "nk_overlap_apply": ([P, dp, I, I, I, D, U, dp, ctypes.POINTER(NkStats)], I),
+        "nk_overlap_apply_dev": ([P, P, I, I, I, D, U, P, ctypes.POINTER(NkStats), P], I),
+        "nk_dslash_dev": ([P, P, P, I, I, I, P], I),
+        "nk_outer_lanczos_dev": ([P, P, I, I, U, dp, dp, dp, dp, P], I),
+        "nk_inner_sign": ([P, dp, dp, dp, I, I, I, D, I, dp, ctypes.POINTER(NkStats)], I),
+        "nk_last_error": ([P], ctypes.c_char_p),
+        "nk_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _host_c128(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _dev_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if t.dtype not in (torch.complex128, torch.float64):
+        raise TypeError("tensor must be complex128 (or float64 with interleaved re/im)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns an nk_ctx*; each method maps to one C entry point."""
+
+    def __init__(self, dims, bc_t_antiperiodic: bool = True):
+        lib = load_library()
+        self._lib = lib
+        d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+        h = ctypes.c_void_p()
+        rc = lib.nk_create_lattice(d, 1 if bc_t_antiperiodic else 0, ctypes.byref(h))
+        if rc != NK_OK:
+            raise NkError(rc, "nk_create_lattice failed (no CUDA device or bad dims)")
+        self.h = h
+        self.dims = tuple(int(x) for x in dims)
+        self.V = int(np.prod(self.dims))
+        self.N = 12 * self.V
+
+    def _check(self, rc):
+        if rc != NK_OK:
+            raise NkError(rc, self._lib.nk_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.nk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup ------------------------------------------------------------
+    def load_links(self, U: np.ndarray):
+        u = _host_c128(U).reshape(-1)
+        if u.size != 36 * self.V:
+            raise ValueError("links must have 36*V complex entries")
+        self._check(self._lib.nk_load_links(self.h, _dptr(u.view(np.float64))))
+
+    def load_links_dev(self, U_dev, stream=None):
+        self._check(self._lib.nk_load_links_dev(self.h, _dev_ptr(U_dev), _stream_ptr(stream)))
+
+    def set_mu_mw(self, mu: float, m_w: float):
+        self._check(self._lib.nk_set_mu_mw(self.h, float(mu), float(m_w)))
+
+    def set_precision(self, j0: int):
+        self._check(self._lib.nk_set_precision(self.h, int(j0)))
+
+    # -- solves (host arrays) --------------------------------------------------
+    def sign_apply(self, b, k, ell, tol=0.0, p=0.0, flags=NK_FP64, check=True):
+        b = _host_c128(b)
+        if b.ndim == 1:
+            b = b[None, :]
+        n = b.shape[0]
+        y = np.zeros_like(b)
+        st = NkStats()
+        rc = self._lib.nk_sign_apply(self.h, _dptr(b.view(np.float64)), n, int(k), int(ell), float(tol),
+                                     float(p), int(flags), _dptr(y.view(np.float64)), ctypes.byref(st))
+        if check:
+            self._check(rc)
+        return y, st.as_dict(), rc
+
+    def overlap_apply(self, b, k, ell, tol=0.0, flags=NK_FP64, check=True):
+        b = _host_c128(b)
+        if b.ndim == 1:
+            b = b[None, :]
+        n = b.shape[0]
+        y = np.zeros_like(b)
+        st = NkStats()
+        rc = self._lib.nk_overlap_apply(self.h, _dptr(b.view(np.float64)), n, int(k), int(ell), float(tol),
+                                        int(flags), _dptr(y.view(np.float64)), ctypes.byref(st))
+        if check:
+            self._check(rc)
+        return y, st.as_dict(), rc
+
+    # -- solves (device tensors) -----------------------------------------------
+    def sign_apply_dev(self, b_dev, y_dev, n_rhs, k, ell, tol=0.0, p=0.0, flags=NK_FP64, stream=None,
+                       check=True):
+        st = NkStats()
+        rc = self._lib.nk_sign_apply_dev(self.h, _dev_ptr(b_dev), int(n_rhs), int(k), int(ell), float(tol),
+                                         float(p), int(flags), _dev_ptr(y_dev), ctypes.byref(st),
+                                         _stream_ptr(stream))
+        if check:
+            self._check(rc)
+        return st.as_dict(), rc
+
+    def overlap_apply_dev(self, b_dev, y_dev, n_rhs, k, ell, tol=0.0, flags=NK_FP64, stream=None):
+        st = NkStats()
+        rc = self._lib.nk_overlap_apply_dev(self.h, _dev_ptr(b_dev), int(n_rhs), int(k), int(ell),
+                                            float(tol), int(flags), _dev_ptr(y_dev), ctypes.byref(st),
+                                            _stream_ptr(stream))
+        self._check(rc)
+        return st.as_dict()
+
+    # -- single steps ---------------------------------------------------------
+    def dslash_dev(self, in_dev, out_dev, n_vec, dagger=False, precision=64, stream=None):
+        self._check(self._lib.nk_dslash_dev(self.h, _dev_ptr(in_dev), _dev_ptr(out_dev), int(n_vec),
+                                            1 if dagger else 0, int(precision), _stream_ptr(stream)))
+
+    def outer_lanczos_dev(self, b_dev, n_rhs, k, flags=NK_FP64, stream=None):
+        a = np.zeros((n_rhs, k), np.complex128)
+        be = np.zeros((n_rhs, k), np.complex128)
+        ga = np.zeros((n_rhs, k), np.complex128)
+        xn = np.zeros(n_rhs)
+        self._check(self._lib.nk_outer_lanczos_dev(
+            self.h, _dev_ptr(b_dev), int(n_rhs), int(k), int(flags), _dptr(a.view(np.float64)),
+            _dptr(be.view(np.float64)), _dptr(ga.view(np.float64)), _dptr(xn), _stream_ptr(stream)))
+        return a, be, ga, xn
+
+    def inner_sign(self, alpha, beta, gamma, ell, p=0.0, hermitian=True, check=True):
+        alpha = _host_c128(alpha)
+        if alpha.ndim == 1:
+            alpha = alpha[None, :]
+        n, k = alpha.shape
+        beta = _host_c128(beta, (n, k)) if np.asarray(beta).size == n * k else _pad(beta, n, k)
+        gamma = _host_c128(gamma, (n, k)) if np.asarray(gamma).size == n * k else _pad(gamma, n, k)
+        c = np.zeros((n, k), np.complex128)
+        st = NkStats()
+        rc = self._lib.nk_inner_sign(self.h, _dptr(alpha.view(np.float64)), _dptr(beta.view(np.float64)),
+                                     _dptr(gamma.view(np.float64)), n, k, int(ell), float(p),
+                                     1 if hermitian else 0, _dptr(c.view(np.float64)), ctypes.byref(st))
+        if check:
+            self._check(rc)
+        return c, st.as_dict(), rc
+
+
+def _pad(x, n, k):
+    """(n, k-1) off-diagonals -> (n, k) with a zero last entry."""
+    x = np.asarray(x, dtype=np.complex128).reshape(n, -1)
+    out = np.zeros((n, k), np.complex128)
+    out[:, : x.shape[1]] = x
+    return out

@@ -1,0 +1,55 @@
+"""The C-ABI library loads and exports every entry point declared in include/nksign.h.
+
+No compute calls: this runs without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nksign.h")
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nk_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0912_4457_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for n in ("nk_create_lattice", "nk_load_links", "nk_set_mu_mw", "nk_sign_apply", "nk_overlap_apply",
+              "nk_last_error", "nk_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_0912_4457_gb300 import nksign
+    assert sorted(nksign.EXPORTED) == declared()
+
+
+def test_null_and_invalid_arguments_without_gpu(lib):
+    """Argument checks that fail before any CUDA call."""
+    lib.nk_last_error.restype = ctypes.c_char_p
+    lib.nk_last_error.argtypes = [ctypes.c_void_p]
+    assert lib.nk_last_error(None) == b"null context"
+    lib.nk_destroy.argtypes = [ctypes.c_void_p]
+    lib.nk_destroy(None)
+    out = ctypes.c_void_p()
+    bad = (ctypes.c_int * 4)(4, 4, 1, 4)
+    assert lib.nk_create_lattice(bad, 1, ctypes.byref(out)) == -1
+    assert lib.nk_create_lattice(None, 1, ctypes.byref(out)) == -1
