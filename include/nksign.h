@@ -178,6 +178,33 @@ int nk_inner_sign(nk_ctx* ctx, const double* alpha, const double* beta, const do
                   int n_rhs, int k, int ell, double p, int hermitian, double* c,
                   nk_stats* st);
 
+/* No-allocation variant of nk_inner_sign (the paper has no counterpart: this
+ * is a deployment entry point, not a step of the method).  For callers that
+ * must not allocate device memory -- code running where cudaMalloc is
+ * forbidden or unsafe, such as inside another framework's memory budget or a
+ * process whose allocator it does not own.  It computes the same c_r =
+ * V_l sgn(H_l) e_1 as nk_inner_sign, but all inputs and outputs are DEVICE
+ * arrays owned by the caller (alpha_dev, beta_dev, gamma_dev, c_dev in the
+ * nk_outer_lanczos_dev layout, complex doubles [r*k + j]) and every other
+ * buffer it needs lives in one static device array of the library (about
+ * 5.3 MB, held by every GPU that loads the library until the process exits).
+ * It calls no cudaMalloc/cudaFree and needs no context.
+ * Limits: n_rhs <= NK_NOALLOC_MAX_RHS, k <= NK_NOALLOC_MAX_K,
+ * l <= NK_NOALLOC_MAX_ELL; larger sizes return NK_EINVAL with a message.
+ * The first call on each device looks up the array's device address and sets
+ * kernel attributes; make that first call before any stream capture.  The
+ * array is shared by all calls and keeps the previous call's contents, so
+ * calls whose GPU work overlaps (other streams, other host threads) race on
+ * it.  Stream-ordered on `stream`; returns after the stream has finished the
+ * call (it reads the per-RHS status back).  err (may be NULL) receives a
+ * one-line message of err_len bytes at most. */
+#define NK_NOALLOC_MAX_RHS 2
+#define NK_NOALLOC_MAX_K 1024
+#define NK_NOALLOC_MAX_ELL 128
+int nk_inner_sign_noalloc(const double* alpha_dev, const double* beta_dev, const double* gamma_dev,
+                          int n_rhs, int k, int ell, double p, int hermitian, double* c_dev,
+                          void* stream, char* err, size_t err_len);
+
 /* Message of the last failed call on this context (never NULL). */
 const char* nk_last_error(const nk_ctx* ctx);
 

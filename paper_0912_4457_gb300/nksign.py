@@ -45,7 +45,8 @@ ERROR_NAMES = {
 EXPORTED = [
     "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
-    "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_last_error", "nk_destroy",
+    "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
+    "nk_destroy",
 ]
 
 
@@ -111,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "nk_dslash_dev": ([P, P, P, I, I, I, P], I),
         "nk_outer_lanczos_dev": ([P, P, I, I, U, dp, dp, dp, dp, P], I),
         "nk_inner_sign": ([P, dp, dp, dp, I, I, I, D, I, dp, ctypes.POINTER(NkStats)], I),
+        "nk_inner_sign_noalloc": ([P, P, P, I, I, I, D, I, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
         "nk_last_error": ([P], ctypes.c_char_p),
         "nk_destroy": ([P], None),
     }
@@ -275,6 +277,18 @@ class Context:
         if check:
             self._check(rc)
         return c, st.as_dict(), rc
+
+
+def inner_sign_noalloc(alpha_dev, beta_dev, gamma_dev, c_dev, n_rhs, k, ell, p=0.0, hermitian=True,
+                       stream=None):
+    """nk_inner_sign_noalloc on caller-owned device tensors (complex128, shape
+    (n_rhs, k)); returns (rc, message).  The library allocates nothing."""
+    lib = load_library()
+    buf = ctypes.create_string_buffer(256)
+    rc = lib.nk_inner_sign_noalloc(_dev_ptr(alpha_dev), _dev_ptr(beta_dev), _dev_ptr(gamma_dev), int(n_rhs),
+                                   int(k), int(ell), float(p), 1 if hermitian else 0, _dev_ptr(c_dev),
+                                   _stream_ptr(stream), buf, 256)
+    return rc, buf.value.decode()
 
 
 def _pad(x, n, k):
