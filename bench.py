@@ -169,36 +169,45 @@ def config_of(w, args):
 
 
 def stencil_roofline(nk, torch, peaks):
-    """FP32 stencil, 12 RHS of A and 12 of A^dagger in one launch, on a lattice
-    larger than L2; achieved algorithmic GB/s from CUDA events on the launch
-    stream.  Algorithmic bytes per site: links 288 + 24 vectors x (96 in + 192 out)."""
+    """The solver's stencil kernel (FP32 Wilson stencil for 12 RHS of A and 12
+    of A^dagger in one launch, fused with the first half of the Lanczos step)
+    on 16^3 x 32, a lattice whose vectors are larger than L2.  Achieved
+    algorithmic GB/s from CUDA events around each launch on the launch stream
+    (NK_PROFILE), over a 16-step mixed solve with every stencil in FP32.
+
+    Algorithmic bytes of launch j (each array moved once): FP32 links 288 B/site;
+    per right vector FP32 input 96, FP64 q_{j-1} 192 (j > 0), FP64 dot vector
+    p_j 192, FP64 output r 192 (j < k-1); per left vector (j < k-1) FP32 input
+    96, FP64 p_{j-1} 192 (j > 0), FP64 output 192."""
     import inputs
     dims = STENCIL_DIMS
     ctx = nk.Context(dims)
     ctx.load_links(inputs.su3_links(dims, 105)[0])
     ctx.set_mu_mw(0.2, -2.0)
     V = int(np.prod(dims))
-    # the FP32 stencil alone, on device-resident FP32 inputs, through the
-    # solve's own kernel: time it through nk_dslash_dev's FP32 path minus its
-    # layout conversions is not separable, so time a mixed solve's stencil
-    # class instead (NK_PROFILE events around each stencil launch)
-    b = torch.zeros((12, 12 * V), dtype=torch.complex128, device="cuda")
+    n = 12
+    b = torch.zeros((n, 12 * V), dtype=torch.complex128, device="cuda")
     b[:, :12] = torch.eye(12, dtype=torch.complex128, device="cuda")
     y = torch.zeros_like(b)
-    k = 8
+    k = 16
     ctx.set_precision(0)
-    st, _ = ctx.sign_apply_dev(b, y, 12, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
-    st, _ = ctx.sign_apply_dev(b, y, 12, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
+    ctx.sign_apply_dev(b, y, n, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
+    st, _ = ctx.sign_apply_dev(b, y, n, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
     torch.cuda.synchronize()
-    n = st["n_class"]["dslash"]
-    t_ms = st["t_class_ms"]["dslash"] / max(1, n)
-    bytes_per_launch = V * (288 + 24 * (96 + 192))
-    gbs = bytes_per_launch / (t_ms * 1e-3) / 1e9
+    t_ms = st["t_class_ms"]["dslash"]
+    launches = st["n_class"]["dslash"]
+    total = 0
+    for j in range(k):
+        bj = 288 + n * (96 + (192 if j > 0 else 0) + 192 + (192 if j < k - 1 else 0))
+        if j < k - 1:
+            bj += n * (96 + (192 if j > 0 else 0) + 192)
+        total += V * bj
+    gbs = total / (t_ms * 1e-3) / 1e9
     ctx.close()
-    return {"kernel": "dslash_kernel<float> (A and A^dagger, 12 RHS each)", "lattice": "16x16x16x32",
-            "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-            "frac": gbs / peaks.get("hbm_gbs", 6800.0), "ms_per_launch": t_ms,
-            "bytes_per_launch": bytes_per_launch}
+    return {"kernel": "k_dslash_step1<float, two-sided> (12 RHS A + 12 RHS A^dagger per launch)",
+            "lattice": "16x16x16x32", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
+            "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "ms_per_launch": t_ms / launches,
+            "bytes_per_launch": total / launches, "launches": launches}
 
 
 def run_gpu(args, w, rank, world, local_rank):
@@ -328,29 +337,34 @@ def _lib_host_solve(ctx, bp, yp, k, ell, flags):
 
 
 def dominant_roofline(dom, tc, nc, w, peaks):
-    """Roofline entry for the kernel class with the largest device time."""
+    """Roofline entry for the kernel class with the largest device time.
+
+    Algorithmic bytes and FP64 flops per complex vector element (each moved or
+    computed once), for n_rhs sources, two-sided (Hermitian in parentheses):
+      step2: reads q_{j+1}, q_j, p_{j+1}, p_j; writes q_{j+1}, p_{j+1} and their
+             FP32 copies: 112 B (56 B); 24 FP64 flops (8) -- bound by FP64;
+      dslash (fused with step 1): per site links 288 B (FP32) + per vector
+             FP32 input 96 B, FP64 q_{j-1} and dot vector 2x192 B, FP64 output 192 B.
+    """
     V = int(np.prod(w["dims"]))
     N = 12 * V
     n_rhs = w["n_rhs"]
     two = w["mu"] != 0.0
     ms = tc[dom] / max(1, nc[dom])
     fp64_peak = 1.0  # TFLOP/s, measured DFMA rate of this GB300 (see DESIGN.md)
-    if dom in ("step1", "step2", "step3"):
-        # FP64 flops per complex element per vector pair, two-sided (one-sided in parentheses)
-        flops_el = {"step1": 16 if two else 6, "step2": 16 if two else 8, "step3": 12 if two else 2}[dom]
-        bytes_el = {"step1": (5 * 16 + 2 * 16) if two else (3 * 16 + 16),
-                    "step2": (4 * 16 + 2 * 16) if two else (2 * 16 + 16),
-                    "step3": (2 * 16 + 2 * 16 + 2 * 8) if two else (16 + 16 + 8)}[dom]
-        flops = flops_el * N * n_rhs
+    if dom == "step2":
+        flops = (24 if two else 8) * N * n_rhs
         tf = flops / (ms * 1e-3) / 1e12
-        return {"kernel": "k_" + dom, "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+        return {"kernel": "k_step2", "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": tf / fp64_peak, "traffic": None, "ms_per_launch": ms,
-                "algorithmic_bytes_per_launch": bytes_el * N * n_rhs}
+                "algorithmic_bytes_per_launch": (112 if two else 56) * N * n_rhs}
     if dom == "dslash":
-        b = V * (288 + (2 if two else 1) * n_rhs * (96 + 192))
+        nv = (2 if two else 1) * n_rhs
+        b = V * (288 + nv * (96 + 192)) + V * n_rhs * 2 * 192
         gbs = b / (ms * 1e-3) / 1e9
-        return {"kernel": "dslash_kernel", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None, "ms_per_launch": ms}
+        return {"kernel": "k_dslash_step1", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None, "ms_per_launch": ms,
+                "note": "average over FP64- and FP32-stencil launches"}
     if dom == "lift":
         b = n_rhs * w["k"] * N * 16
         gbs = b / (ms * 1e-3) / 1e9

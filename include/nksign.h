@@ -66,10 +66,11 @@ extern "C" {
 #define NK_MAX_RHS 12
 
 /* Kernel classes of a solve, for nk_stats.t_class_ms / n_class. */
-#define NK_CLASS_DSLASH 0   /* Wilson stencil A v (and A^dagger w) */
-#define NK_CLASS_STEP1 1    /* r = Av - c v_prev, H(j,j) */
-#define NK_CLASS_STEP2 2    /* r -= H(j,j) v, beta / delta */
-#define NK_CLASS_STEP3 3    /* v_{j+1} = r / beta */
+#define NK_CLASS_DSLASH 0   /* Wilson stencil A v (and A^dagger w) fused with
+                               r = Av - c v_prev and the H(j,j) reduction */
+#define NK_CLASS_STEP1 1    /* (unused: fused into NK_CLASS_DSLASH) */
+#define NK_CLASS_STEP2 2    /* r -= H(j,j) v, beta / delta, FP32 copies */
+#define NK_CLASS_STEP3 3    /* (unused: the basis is kept unnormalised) */
 #define NK_CLASS_INNER 4    /* p estimate, LU of p H_k, inner Lanczos */
 #define NK_CLASS_RHI 5      /* Roberts-Higham iteration */
 #define NK_CLASS_LIFT 6     /* V_l s and |x| V_k c */
@@ -131,7 +132,7 @@ int nk_set_precision(nk_ctx* ctx, int j0);
  *   y = |b| V_k V_l sgn(H_l) e_1 (App. C step 6).
  * b, y: HOST arrays of n_rhs vectors (1 <= n_rhs <= NK_MAX_RHS), each solved
  * independently (own recurrence coefficients) but batched through one
- * stencil launch per step.  k, l even (Fig. 7 caption), 2 <= l <= k.
+ * stencil launch per step.  k, l even (Fig. 7 caption), 2 <= l <= k, k <= 1536, l <= 256.
  * tol must be 0 (fixed k).  flags: NK_FP64 or NK_MIXED, optionally
  * NK_DOUBLE_PASS / NK_NO_GRAPH.  st may be NULL.  Blocks until y is written.
  * Returns NK_EBREAKDOWN / NK_ERHI when any RHS failed (st->status says which;

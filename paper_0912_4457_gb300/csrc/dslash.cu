@@ -115,11 +115,72 @@ __device__ __forceinline__ void dir(typename C2<R>::T acc[4][3], const typename 
     hop<NU, true, R>(acc, p, u, R(-1), wminus * ff);
 }
 
+// precision-generic conversions (float via the integer pipe, see nk_common.cuh)
+__device__ __forceinline__ double to_double(float a) { return f2d_int(a); }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(df a) { return df_to_double(a); }
+template <typename R> __device__ __forceinline__ R from_double(double d);
+template <> __device__ __forceinline__ float from_double<float>(double d) { return d2f_int(d); }
+template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
+template <> __device__ __forceinline__ df from_double<df>(double d) { return df_from_double(d); }
+// a two-float kernel argument from a host double
+static df df_host(double d) {
+    df r;
+    r.hi = (float)d;
+    r.lo = (float)(d - (double)r.hi);
+    return r;
+}
+// s - c p and s + c p with explicit FMA (4 FP64 instructions each)
+__device__ __forceinline__ double2 caxpy_neg(double2 s, double2 c, double2 p) {
+    return make_double2(fma(-c.x, p.x, fma(c.y, p.y, s.x)), fma(-c.x, p.y, fma(-c.y, p.x, s.y)));
+}
+__device__ __forceinline__ double2 caxpy_pos(double2 s, double2 c, double2 p) {
+    return make_double2(fma(c.x, p.x, fma(-c.y, p.y, s.x)), fma(c.x, p.y, fma(c.y, p.x, s.y)));
+}
+
+// out = gamma5 (psi - kappa * hops)(site) for one vector: A psi (dag = 0) or
+// A^dagger psi = gamma5 D_w(-mu) psi (dag = 1), in precision R.
+template <typename R>
+__device__ __forceinline__ void stencil_site(const typename C2<R>::T* __restrict__ U,
+                                             const typename C2<R>::T* __restrict__ in, const Geom& g,
+                                             int site, int dag, R kappa, R emu, R emu_inv,
+                                             typename C2<R>::T out[4][3]) {
+    typedef typename C2<R>::T T;
+    // temporal weights: A uses (e^{mu}, e^{-mu}); A^dagger exchanges them
+    const R wp_t = dag ? emu_inv : emu;
+    const R wm_t = dag ? emu : emu_inv;
+    int x = site % g.Lx;
+    int r = site / g.Lx;
+    int y = r % g.Ly; r /= g.Ly;
+    int z = r % g.Lz;
+    int t = r / g.Lz;
+    T acc[4][3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { acc[sp][a].x = 0; acc[sp][a].y = 0; }
+    dir<0, R>(acc, U, in, g, site, x, g.Lx, 1, R(1), R(1));
+    dir<1, R>(acc, U, in, g, site, y, g.Ly, g.Lx, R(1), R(1));
+    dir<2, R>(acc, U, in, g, site, z, g.Lz, g.Lx * g.Ly, R(1), R(1));
+    dir<3, R>(acc, U, in, g, site, t, g.Lt, g.Lx * g.Ly * g.Lz, wp_t, wm_t);
+    T p[4][3];
+    load_spinor<R>(in, g.V, site, p);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const R sg = sp < 2 ? R(1) : R(-1);  // gamma5 = diag(1, 1, -1, -1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            out[sp][a].x = sg * (p[sp][a].x - kappa * acc[sp][a].x);
+            out[sp][a].y = sg * (p[sp][a].y - kappa * acc[sp][a].y);
+        }
+    }
+}
+
 // One thread per (site, vector). Vectors [0, n0) come from set 0, [n0, n0+n1)
 // from set 1; set s applies A (dag = 0) or A^dagger (dag = 1).
 template <typename R>
 __global__ void __launch_bounds__(128) dslash_kernel(const typename C2<R>::T* __restrict__ U, Geom g,
-                                                      DslashSet s0, DslashSet s1, R kappa, R emu) {
+                                                      DslashSet s0, DslashSet s1, R kappa, R emu, R emu_inv) {
     typedef typename C2<R>::T T;
     const int nvec = s0.n + s1.n;
     const int vec = blockIdx.x % nvec;
@@ -129,40 +190,13 @@ __global__ void __launch_bounds__(128) dslash_kernel(const typename C2<R>::T* __
     const int vi = vec < s0.n ? vec : vec - s0.n;
     const T* __restrict__ in = reinterpret_cast<const T*>(S.in) + (size_t)vi * S.in_stride;
     double2* __restrict__ out = S.out + (size_t)vi * S.out_stride;
-    // temporal weights: A uses (e^{mu}, e^{-mu}); A^dagger exchanges them
-    R wp_t = S.dag ? R(1) / emu : emu;
-    R wm_t = S.dag ? emu : R(1) / emu;
-
-    int x = site % g.Lx;
-    int r = site / g.Lx;
-    int y = r % g.Ly; r /= g.Ly;
-    int z = r % g.Lz;
-    int t = r / g.Lz;
-
-    T acc[4][3];
+    T o[4][3];
+    stencil_site<R>(U, in, g, site, S.dag, kappa, emu, emu_inv, o);
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) { acc[sp][a].x = 0; acc[sp][a].y = 0; }
-    const T* __restrict__ Ul = reinterpret_cast<const T*>(U);
-    dir<0, R>(acc, Ul, in, g, site, x, g.Lx, 1, R(1), R(1));
-    dir<1, R>(acc, Ul, in, g, site, y, g.Ly, g.Lx, R(1), R(1));
-    dir<2, R>(acc, Ul, in, g, site, z, g.Lz, g.Lx * g.Ly, R(1), R(1));
-    dir<3, R>(acc, Ul, in, g, site, t, g.Lt, g.Lx * g.Ly * g.Lz, wp_t, wm_t);
-
-    T p[4][3];
-    load_spinor<R>(in, g.V, site, p);
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp) {
-        const R sg = sp < 2 ? R(1) : R(-1);  // gamma5 = diag(1, 1, -1, -1)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double2 o;
-            o.x = (double)(sg * (p[sp][a].x - kappa * acc[sp][a].x));
-            o.y = (double)(sg * (p[sp][a].y - kappa * acc[sp][a].y));
-            out[(size_t)(3 * sp + a) * g.V + site] = o;
-        }
-    }
+        for (int a = 0; a < 3; ++a)
+            out[(size_t)(3 * sp + a) * g.V + site] = make_double2(to_double(o[sp][a].x), to_double(o[sp][a].y));
 }
 
 void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet& s0,
@@ -173,16 +207,148 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
     dim3 grid((unsigned)(((g.V + threads - 1) / threads) * nvec));
     if (precision == 32)
         dslash_kernel<float><<<grid, threads, 0, st>>>((const float2*)U, g, s0, s1, (float)kappa,
-                                                      (float)exp(mu));
+                                                      (float)exp(mu), (float)exp(-mu));
+    else if (precision == 48)
+        dslash_kernel<df><<<grid, threads, 0, st>>>((const dfc*)U, g, s0, s1, df_host(kappa), df_host(exp(mu)),
+                                                   df_host(exp(-mu)));
     else
-        dslash_kernel<double><<<grid, threads, 0, st>>>((const double2*)U, g, s0, s1, kappa, exp(mu));
+        dslash_kernel<double><<<grid, threads, 0, st>>>((const double2*)U, g, s0, s1, kappa, exp(mu), exp(-mu));
+}
+
+// ---- fused stencil + first half of an outer Lanczos step ------------------------
+//
+// For outer step j (see lanczos.cu for the unnormalised basis q_j, p_j):
+//   right vectors (side 0, one per RHS):
+//     s = A q_j / n_j;  r = s - (c_{j-1}/n_{j-1}) q_{j-1}  (c = beta, two-sided gamma)
+//     r -> q_{j+1};  partial of H(j,j) = v_j^dag r  (two-sided w_j^dag r)
+//   left vectors (side 1, two-sided only):
+//     t = A^dag p_j / m_j;  l = t - (beta^*_{j-1}/m_{j-1}) p_{j-1};  l -> p_{j+1}
+// The stencil runs in precision R (FP32 reads the FP32 copies of q_j, p_j and
+// the FP32 links; the scale 1/n_j is applied in R too); from the stencil
+// output on, everything is FP64.  The blocks of side 0 reduce H(j,j) with the
+// deterministic two-stage scheme.  In double-pass mode side 0 also
+// accumulates y += c'_j q_j at its own site.
+constexpr int kStencilThreads = 128;
+
+template <typename R, bool TS>
+__global__ void __launch_bounds__(kStencilThreads) k_dslash_step1(
+    const typename C2<R>::T* __restrict__ U, Geom g, Outer o, int j, R kappa, R emu, R emu_inv,
+    const typename C2<R>::T* __restrict__ qin, long qin_stride, const typename C2<R>::T* __restrict__ pin,
+    long pin_stride) {
+    typedef typename C2<R>::T T;
+    __shared__ double2 sh[32];
+    __shared__ double2 coef[3];
+    const int nvec = TS ? 2 * o.n_rhs : o.n_rhs;
+    const int vec = blockIdx.x % nvec;
+    const int sb = blockIdx.x / nvec;
+    const int nsb = gridDim.x / nvec;
+    const int side = vec / o.n_rhs;      // 0: A q_j, 1: A^dagger p_j
+    const int rhs = vec % o.n_rhs;
+    if (o.status[rhs] != kStatusOK) return;
+    if (side == 1 && j == o.k - 1) return;   // the last step needs no left vector
+    const size_t hb = (size_t)rhs * o.k;
+    if (threadIdx.x == 0) {
+        const double2 zero = make_double2(0.0, 0.0);
+        if (side == 0) {
+            coef[0] = cinv(scale_n(o, rhs, j));
+            coef[1] = j > 0 ? cdiv(TS ? o.gamma[hb + j - 1] : o.beta[hb + j - 1], scale_n(o, rhs, j - 1)) : zero;
+            coef[2] = TS ? cinv(cconj(scale_m(o, rhs, j))) : cinv(scale_n(o, rhs, j));
+        } else {
+            coef[0] = cinv(scale_m(o, rhs, j));
+            coef[1] = j > 0 ? cdiv(cconj(o.beta[hb + j - 1]), scale_m(o, rhs, j - 1)) : zero;
+            coef[2] = zero;
+        }
+    }
+    __syncthreads();
+    const int site = sb * blockDim.x + threadIdx.x;
+    double2 acc = make_double2(0.0, 0.0);
+    if (site < g.V) {
+        const T* __restrict__ in = side == 0 ? qin + (size_t)rhs * qin_stride : pin + (size_t)rhs * pin_stride;
+        T out[4][3];
+        stencil_site<R>(U, in, g, site, side, kappa, emu, emu_inv, out);
+        const double2 c1 = coef[1];
+        // the scale 1/n_j (1/m_j) in the stencil's precision
+        T scr;
+        scr.x = from_double<R>(coef[0].x);
+        scr.y = from_double<R>(coef[0].y);
+        double2* __restrict__ nxt = side == 0 ? (j < o.k - 1 ? outer_q(o, rhs, j + 1) : nullptr)
+                                              : outer_p(o, rhs, j + 1);
+        const double2* __restrict__ prv = j > 0 ? (side == 0 ? outer_q(o, rhs, j - 1) : outer_p(o, rhs, j - 1))
+                                                : nullptr;
+        const double2* __restrict__ dotv = side == 0 ? (TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j)) : nullptr;
+        double2* __restrict__ yacc = (side == 0 && o.y) ? o.y + (size_t)rhs * o.N : nullptr;
+        const double2 cpj = yacc ? o.cp[hb + j] : make_double2(0.0, 0.0);
+        const double2* __restrict__ qj = yacc ? outer_q(o, rhs, j) : nullptr;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const size_t idx = (size_t)(3 * sp + a) * g.V + site;
+                const T v = out[sp][a];
+                double2 rr;
+                if (TS) rr = make_double2(to_double(v.x * scr.x - v.y * scr.y), to_double(v.x * scr.y + v.y * scr.x));
+                else rr = make_double2(to_double(v.x * scr.x), to_double(v.y * scr.x));
+                if (prv) {
+                    const double2 pv = prv[idx];
+                    if (TS) rr = caxpy_neg(rr, c1, pv);                     // r - c1 pv
+                    else rr = make_double2(fma(-c1.x, pv.x, rr.x), fma(-c1.x, pv.y, rr.y));
+                }
+                if (nxt) nxt[idx] = rr;
+                if (dotv) {
+                    const double2 d = dotv[idx];
+                    acc.x = fma(d.x, rr.x, fma(d.y, rr.y, acc.x));          // conj(d) r
+                    if (TS) acc.y = fma(d.x, rr.y, fma(-d.y, rr.x, acc.y));
+                }
+                if (yacc) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
+            }
+        }
+    }
+    if (side == 0) {
+        double2 part = block_sum(acc, sh);
+        if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, sb, nsb)) {
+            double2 tot = sum_partials(o.partials + (size_t)rhs * o.npart, nsb, sh);
+            if (threadIdx.x == 0) {
+                // Hermitian: H(j,j) = Re(q_j^dag r) / n_j, real (App. C); two-sided: (p_j^dag r) / m_j^*
+                o.alpha[hb + j] = TS ? cmul(coef[2], tot) : make_double2(tot.x * coef[2].x, 0.0);
+                o.counters[rhs] = 0u;
+            }
+        }
+    }
+}
+
+int dslash_step1_blocks(const Geom& g) { return (g.V + kStencilThreads - 1) / kStencilThreads; }
+
+template <typename R, typename T>
+static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R kappa, R emu, R emu_inv, const T* qin,
+                           long qs, const T* pin, long ps, cudaStream_t st) {
+    const int nvec = o.two_sided ? 2 * o.n_rhs : o.n_rhs;
+    dim3 grid((unsigned)(dslash_step1_blocks(g) * nvec));
+    if (o.two_sided)
+        k_dslash_step1<R, true><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+    else
+        k_dslash_step1<R, false><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+}
+
+void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
+                         double mu, cudaStream_t st) {
+    if (precision == 32) {
+        launch_step1_t<float, float2>((const float2*)U, g, o, j, (float)kappa, (float)exp(mu), (float)exp(-mu), o.q32,
+                                      o.N, o.p32, o.N, st);
+    } else if (precision == 48) {
+        launch_step1_t<df, dfc>((const dfc*)U, g, o, j, df_host(kappa), df_host(exp(mu)), df_host(exp(-mu)), o.qdf,
+                                o.N, o.pdf, o.N, st);
+    } else {
+        const long qs = o.q_ring ? 3 * o.N : (long)o.k * o.N;
+        launch_step1_t<double, double2>((const double2*)U, g, o, j, kappa, exp(mu), exp(-mu), outer_q(o, 0, j), qs,
+                                        o.two_sided ? outer_p(o, 0, j) : nullptr, 3 * o.N, st);
+    }
 }
 
 // ---- layout conversion -------------------------------------------------------
 
-// ABI links [site][nu][3][3] complex double -> [nu][9][site] (FP64 and FP32 copies)
+// ABI links [site][nu][3][3] complex double -> [nu][9][site] (FP64, FP32 and two-float copies)
 __global__ void links_to_device_layout(const double2* __restrict__ in, double2* __restrict__ u64,
-                                       float2* __restrict__ u32, int V) {
+                                       float2* __restrict__ u32, dfc* __restrict__ udf, int V) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)V * 36) return;
     int site = (int)(i / 36), rem = (int)(i % 36), nu = rem / 9, e = rem % 9;
@@ -190,12 +356,16 @@ __global__ void links_to_device_layout(const double2* __restrict__ in, double2* 
     size_t o = (size_t)(nu * 9 + e) * V + site;
     u64[o] = v;
     u32[o] = make_float2((float)v.x, (float)v.y);
+    dfc w;
+    w.x = df_from_double(v.x);
+    w.y = df_from_double(v.y);
+    udf[o] = w;
 }
 
-void launch_links_to_device_layout(const double2* in, double2* u64, float2* u32, int V,
+void launch_links_to_device_layout(const double2* in, double2* u64, float2* u32, dfc* udf, int V,
                                    cudaStream_t st) {
     size_t n = (size_t)V * 36;
-    links_to_device_layout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, u64, u32, V);
+    links_to_device_layout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, u64, u32, udf, V);
 }
 
 // ABI spinor [site][12] -> SoA [12][site], n vectors
@@ -251,6 +421,24 @@ __global__ void to_fp32(const double2* __restrict__ in, long in_stride, float2* 
     size_t j = i % N;
     double2 v = in[(size_t)vec * in_stride + j];
     out[(size_t)vec * out_stride + j] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void to_df(const double2* __restrict__ in, long in_stride, dfc* __restrict__ out, long out_stride,
+                      long N, int n) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * n) return;
+    int vec = (int)(i / N);
+    size_t j = i % N;
+    double2 v = in[(size_t)vec * in_stride + j];
+    dfc w;
+    w.x = df_from_double(v.x);
+    w.y = df_from_double(v.y);
+    out[(size_t)vec * out_stride + j] = w;
+}
+
+void launch_to_df(const double2* in, long in_stride, dfc* out, long out_stride, long N, int n, cudaStream_t st) {
+    size_t tot = (size_t)N * n;
+    to_df<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride, N, n);
 }
 
 void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_stride, long N, int n,

@@ -46,6 +46,7 @@ struct nk_ctx {
     bool links = false;
     double2* U64 = nullptr;
     float2* U32 = nullptr;
+    nk::dfc* Udf = nullptr;   // two-float links for the early stencil steps of NK_MIXED
     DevBuf ws;            // solve workspace (carved per solve shape)
     DevBuf staging;       // host-pointer API: device copies of b and y
     DevBuf links_tmp;
@@ -102,14 +103,14 @@ double kappa_of(const nk_ctx* c) { return 1.0 / (8.0 + 2.0 * c->m_w); }
 struct Layout {
     nk::Outer o;
     nk::Inner in;
-    double2* b_soa;
     double2* y_soa;
+    double2* cp;      // lift coefficients c'_j, [rhs][k]
     size_t total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout carve(char* base, long N, int n_rhs, int k, int ell, bool two_sided, bool double_pass, int nblk) {
+Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_sided, bool double_pass, int nblk) {
     Layout L;
     std::memset(&L, 0, sizeof(L));
     size_t off = 0;
@@ -118,26 +119,27 @@ Layout carve(char* base, long N, int n_rhs, int k, int ell, bool two_sided, bool
         off += align_up(bytes);
         return p;
     };
+    const long N = 12L * g.V;
     const size_t vec = (size_t)N * sizeof(double2);
-    L.b_soa = (double2*)take(vec * n_rhs);
     L.y_soa = (double2*)take(vec * n_rhs);
     nk::Outer& o = L.o;
     o.N = N; o.n_rhs = n_rhs; o.k = k; o.nblk = nblk; o.two_sided = two_sided;
-    if (double_pass) o.vring = (double2*)take(vec * 2 * n_rhs);
-    else o.V = (double2*)take(vec * (size_t)k * n_rhs);
-    if (two_sided) o.w = (double2*)take(vec * 2 * n_rhs);
-    o.r = (double2*)take(vec * n_rhs);
-    o.s = (double2*)take(vec * n_rhs);
-    if (two_sided) { o.l = (double2*)take(vec * n_rhs); o.t = (double2*)take(vec * n_rhs); }
-    o.v32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
-    if (two_sided) o.w32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
+    o.npart = std::max(nblk, nk::dslash_step1_blocks(g));
+    o.q_ring = double_pass ? 1 : 0;
+    o.Q = (double2*)take(vec * (double_pass ? 3 : (size_t)k) * n_rhs);
+    if (two_sided) o.P = (double2*)take(vec * 3 * n_rhs);
+    o.q32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
+    if (two_sided) o.p32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
+    o.qdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
+    if (two_sided) o.pdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     o.alpha = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     o.beta = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     o.gamma = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
-    o.partials = (double2*)take(sizeof(double2) * (size_t)nblk * n_rhs);
+    o.partials = (double2*)take(sizeof(double2) * (size_t)o.npart * n_rhs);
     o.counters = (unsigned*)take(sizeof(unsigned) * n_rhs);
     o.status = (int*)take(sizeof(int) * n_rhs);
     o.xnorm = (double*)take(sizeof(double) * n_rhs);
+    L.cp = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     nk::Inner& in = L.in;
     in.n_rhs = n_rhs; in.k = k; in.ell = ell; in.two_sided = two_sided;
     in.alpha = o.alpha; in.beta = o.beta; in.gamma = o.gamma;
@@ -176,7 +178,7 @@ int check_solve_args(nk_ctx* c, int n_rhs, int k, int ell, double tol) {
     if (ell < 2 || (ell & 1)) return fail(c, NK_EINVAL, "l must be even and >= 2");
     if (ell > k) return fail(c, NK_EINVAL, "l must not exceed k");
     if (ell > 256) return fail(c, NK_EINVAL, "l must not exceed 256");
-    if (k > 8192) return fail(c, NK_EINVAL, "k must not exceed 8192");
+    if (k > nk::kMaxInnerK) return fail(c, NK_EINVAL, "k must not exceed 1536");
     if (tol != 0.0) return fail(c, NK_EINVAL, "tol must be 0 (fixed k)");
     return NK_OK;
 }
@@ -217,40 +219,33 @@ struct Launcher {
     }
 };
 
-// Enqueues the outer recurrence (init + k steps).
-void enqueue_outer(nk_ctx* c, const nk::Outer& o, const double2* b_soa, bool mixed, int j0, Launcher& L) {
+// Enqueues the outer recurrence: norm/init, then per step the fused stencil
+// kernel and step 2 (the FP32 stencil from step j0 on in mixed mode).
+void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& L) {
     const Geom g = geom_of(c);
     const double kap = kappa_of(c);
     cudaStream_t st = L.st;
-    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, b_soa, (mixed && j0 <= 0) ? 1 : 0, st); });
-    const long N = o.N;
+    // the input copy the stencil of step j reads: two-float before j0, FP32 after
+    auto copy_for = [&](int j) { return !mixed ? nk::kCopyNone : (j < j0 ? nk::kCopyDF : nk::kCopy32); };
+    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_for(0), st); });
     for (int j = 0; j < o.k; ++j) {
-        const bool f32 = mixed && j >= j0;
-        nk::DslashSet s0, s1;
-        std::memset(&s0, 0, sizeof(s0));
-        std::memset(&s1, 0, sizeof(s1));
-        if (f32) {
-            s0.in = o.v32; s0.in_stride = N;
-        } else {
-            s0.in = nk::outer_v(o, 0, j);
-            s0.in_stride = o.V ? (long)o.k * N : 2 * N;
-        }
-        s0.out = o.s; s0.out_stride = N; s0.n = o.n_rhs; s0.dag = 0;
-        if (o.two_sided) {
-            if (f32) { s1.in = o.w32; s1.in_stride = N; }
-            else { s1.in = nk::outer_w(o, 0, j); s1.in_stride = 2 * N; }
-            s1.out = o.t; s1.out_stride = N; s1.n = o.n_rhs; s1.dag = 1;
-        }
+        const int prec = !mixed ? 64 : (j < j0 ? 48 : 32);
+        const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
         L.run(NK_CLASS_DSLASH, 1, [&] {
-            nk::launch_dslash(f32 ? 32 : 64, f32 ? (const void*)c->U32 : (const void*)c->U64, g, s0, s1, kap,
-                              c->mu, st);
+            nk::launch_dslash_step1(prec, U, g, o, j, kap,
+                                    c->mu, st);
         });
-        L.run(NK_CLASS_STEP1, 1, [&] { nk::launch_outer_step1(o, j, st); });
-        if (j < o.k - 1) {
-            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step2(o, j, st); });
-            L.run(NK_CLASS_STEP3, 1, [&] { nk::launch_outer_step3(o, j, (mixed && j + 1 >= j0) ? 1 : 0, st); });
-        }
+        if (j < o.k - 1)
+            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step2(o, j, copy_for(j + 1), st); });
     }
+}
+
+// b (ABI layout, device) -> q_0 of every RHS
+void enqueue_load_sources(nk_ctx* c, const nk::Outer& o, const double* b_dev, int n_rhs, Launcher& L) {
+    const long qs = o.q_ring ? 3 * c->N : (long)o.k * c->N;
+    L.run(NK_CLASS_OTHER, 1, [&] {
+        nk::launch_abi_to_soa((const double2*)b_dev, c->N, nk::outer_q(o, 0, 0), qs, c->V, n_rhs, L.st);
+    });
 }
 
 int effective_j0(const nk_ctx* c, int k) { return c->j0 < 0 ? k / 4 : std::min(c->j0, k); }
@@ -265,23 +260,25 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     nk::Outer o = Lw.o;
     nk::Inner in = Lw.in;
     in.p_fixed = p;
-    L.run(NK_CLASS_OTHER, 1, [&] {
-        nk::launch_abi_to_soa((const double2*)b_dev, c->N, Lw.b_soa, c->N, c->V, n_rhs, st);
-    });
-    enqueue_outer(c, o, Lw.b_soa, mixed, j0, L);
+    enqueue_load_sources(c, o, b_dev, n_rhs, L);
+    enqueue_outer(c, o, mixed, j0, L);
     L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_lanczos(in, st); });
     cudaError_t e = cudaSuccess;
     L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(in, st); });
     if (e != cudaSuccess) return e;
-    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_inner_combine(in, st); });
+    L.run(NK_CLASS_LIFT, 2, [&] {
+        nk::launch_inner_combine(in, st);
+        nk::launch_lift_coef(o, in.c, Lw.cp, st);
+    });
     if (dp) {
+        // second pass: regenerate the identical basis and accumulate y = sum_j c'_j q_j
         o.y = Lw.y_soa;
-        o.c = in.c;
+        o.cp = Lw.cp;
         cudaMemsetAsync(Lw.y_soa, 0, sizeof(double2) * (size_t)c->N * n_rhs, st);
-        // second pass: regenerate the identical basis and accumulate y = sum_j c_j v_j
-        enqueue_outer(c, o, Lw.b_soa, mixed, j0, L);
+        enqueue_load_sources(c, o, b_dev, n_rhs, L);
+        enqueue_outer(c, o, mixed, j0, L);
     }
-    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, in.c, Lw.y_soa, st); });
+    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, Lw.cp, Lw.y_soa, st); });
     L.run(NK_CLASS_OTHER, 1, [&] {
         nk::launch_soa_to_abi(Lw.y_soa, c->N, (double2*)y_dev, c->N, overlap ? (const double2*)b_dev : nullptr,
                               c->N, c->V, n_rhs, st);
@@ -308,10 +305,10 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     const bool ts = c->mu != 0.0;
     const bool dp = (flags & NK_DOUBLE_PASS) != 0;
     const int nblk = blocks_per_rhs(c->N, n_rhs);
-    Layout dry = carve(nullptr, c->N, n_rhs, k, ell, ts, dp, nblk);
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, nblk);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, c->N, n_rhs, k, ell, ts, dp, nblk);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, nblk);
     // counters must start at zero; status is (re)set by the norm kernel
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
     NK_CUDA(c, cudaMemsetAsync(Lw.in.timeout, 0, sizeof(int), st));
@@ -436,6 +433,7 @@ static int load_links_impl(nk_ctx* c, const double* U, bool host, cudaStream_t s
     if (!c->U64) {
         NK_CUDA(c, cudaMalloc(&c->U64, n * sizeof(double2)));
         NK_CUDA(c, cudaMalloc(&c->U32, n * sizeof(float2)));
+        NK_CUDA(c, cudaMalloc(&c->Udf, n * 16));
     }
     const double2* src = (const double2*)U;
     if (host) {
@@ -444,7 +442,7 @@ static int load_links_impl(nk_ctx* c, const double* U, bool host, cudaStream_t s
         NK_CUDA(c, cudaMemcpyAsync(c->links_tmp.p, U, n * sizeof(double2), cudaMemcpyHostToDevice, st));
         src = (const double2*)c->links_tmp.p;
     }
-    nk::launch_links_to_device_layout(src, c->U64, c->U32, c->V, st);
+    nk::launch_links_to_device_layout(src, c->U64, c->U32, c->Udf, c->V, st);
     NK_CUDA(c, cudaGetLastError());
     NK_CUDA(c, cudaStreamSynchronize(st));
     c->links = true;
@@ -521,14 +519,15 @@ int nk_overlap_apply_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int e
 int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, int dagger, int precision,
                   void* stream) {
     if (!c || !in_dev || !out_dev || n_vec < 1 || n_vec > 2 * NK_MAX_RHS) return NK_EINVAL;
-    if (precision != 32 && precision != 64) return fail(c, NK_EINVAL, "precision must be 32 or 64");
+    if (precision != 32 && precision != 48 && precision != 64)
+        return fail(c, NK_EINVAL, "precision must be 32, 48 or 64");
     if (!c->links) return fail(c, NK_ESTATE, "no links loaded");
     if (!c->mu_set) return fail(c, NK_ESTATE, "mu and m_w not set");
     NK_CUDA(c, cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
     const long N = c->N;
     // scratch: SoA input (FP64 and FP32) and SoA output
-    size_t bytes = align_up(sizeof(double2) * N * n_vec) * 2 + align_up(sizeof(float2) * N * n_vec);
+    size_t bytes = align_up(sizeof(double2) * N * n_vec) * 3;
     int rc = ensure(c, c->staging, std::max(bytes, c->staging.bytes));
     if (rc) return rc;
     double2* in_soa = (double2*)c->staging.p;
@@ -541,6 +540,9 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
     if (precision == 32) {
         nk::launch_to_fp32(in_soa, N, in32, N, N, n_vec, st);
         s0.in = in32;
+    } else if (precision == 48) {
+        nk::launch_to_df(in_soa, N, (nk::dfc*)in32, N, N, n_vec, st);
+        s0.in = in32;
     } else {
         s0.in = in_soa;
     }
@@ -549,7 +551,9 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
     s0.out_stride = N;
     s0.n = n_vec;
     s0.dag = dagger ? 1 : 0;
-    nk::launch_dslash(precision, precision == 32 ? (const void*)c->U32 : (const void*)c->U64, geom_of(c), s0,
+    nk::launch_dslash(precision,
+                      precision == 32 ? (const void*)c->U32 : (precision == 48 ? (const void*)c->Udf : (const void*)c->U64),
+                      geom_of(c), s0,
                       s1, kappa_of(c), c->mu, st);
     nk::launch_soa_to_abi(out_soa, N, (double2*)out_dev, N, nullptr, 0, c->V, n_vec, st);
     NK_CUDA(c, cudaGetLastError());
@@ -565,15 +569,15 @@ int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsig
     cudaStream_t st = (cudaStream_t)stream;
     const bool ts = c->mu != 0.0;
     const int nblk = blocks_per_rhs(c->N, n_rhs);
-    Layout dry = carve(nullptr, c->N, n_rhs, k, 2, ts, false, nblk);
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, nblk);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, c->N, n_rhs, k, 2, ts, false, nblk);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, nblk);
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
-    nk::launch_abi_to_soa((const double2*)b_dev, c->N, Lw.b_soa, c->N, c->V, n_rhs, st);
     Launcher L;
     L.st = st;
-    enqueue_outer(c, Lw.o, Lw.b_soa, (flags & NK_MIXED) != 0, effective_j0(c, k), L);
+    enqueue_load_sources(c, Lw.o, b_dev, n_rhs, L);
+    enqueue_outer(c, Lw.o, (flags & NK_MIXED) != 0, effective_j0(c, k), L);
     NK_CUDA(c, cudaGetLastError());
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpyAsync(alpha, Lw.o.alpha, cb, cudaMemcpyDeviceToHost, st));
@@ -592,14 +596,19 @@ int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsig
 int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const double* gamma, int n_rhs, int k,
                   int ell, double p, int hermitian, double* cout, nk_stats* st) {
     if (!c || !alpha || !beta || !gamma || !cout) return NK_EINVAL;
-    if (n_rhs < 1 || n_rhs > NK_MAX_RHS || k < 2 || ell < 2 || ell > k || ell > 256 || (k & 1) || (ell & 1))
+    if (n_rhs < 1 || n_rhs > NK_MAX_RHS || k < 2 || ell < 2 || ell > k || ell > 256 || (k & 1) || (ell & 1) ||
+        k > nk::kMaxInnerK)
         return fail(c, NK_EINVAL, "bad n_rhs, k or l");
     NK_CUDA(c, cudaSetDevice(c->device));
     const bool ts = hermitian == 0;
-    Layout dry = carve(nullptr, 2, n_rhs, k, ell, ts, true, 1);
+    Geom tiny;
+    tiny.Lx = tiny.Ly = tiny.Lz = tiny.Lt = 1;
+    tiny.V = 1;
+    tiny.antiperiodic = 0;
+    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, 1);
     int rc = ensure(c, c->staging, std::max(dry.total, c->staging.bytes));
     if (rc) return rc;
-    Layout Lw = carve((char*)c->staging.p, 2, n_rhs, k, ell, ts, true, 1);
+    Layout Lw = carve((char*)c->staging.p, tiny, n_rhs, k, ell, ts, true, 1);
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpy(Lw.o.alpha, alpha, cb, cudaMemcpyHostToDevice));
     NK_CUDA(c, cudaMemcpy(Lw.o.beta, beta, cb, cudaMemcpyHostToDevice));
@@ -654,6 +663,7 @@ void nk_destroy(nk_ctx* c) {
     if (c->links_tmp.p) cudaFree(c->links_tmp.p);
     if (c->U64) cudaFree(c->U64);
     if (c->U32) cudaFree(c->U32);
+    if (c->Udf) cudaFree(c->Udf);
     delete c;
 }
 

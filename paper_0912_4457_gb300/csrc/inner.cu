@@ -100,68 +100,6 @@ __device__ int gttrf(int n, T* dl, T* d, T* du, T* du2, int* ipiv, T* dinv) {
     return info;
 }
 
-// x <- (L U)^{-1} x  (gttrs, trans = 'N'). Sequential, one thread.
-template <typename T>
-__device__ void gttrs_n(int n, const T* __restrict__ dl, const T* __restrict__ du, const T* __restrict__ du2,
-                        const int* __restrict__ ipiv, const T* __restrict__ dinv, T* __restrict__ b) {
-    // L: forward sweep with the recorded interchanges
-    T bi = b[0];
-    for (int i = 0; i < n - 1; ++i) {
-        T bn = b[i + 1];
-        if (ipiv[i] == i) {
-            b[i] = bi;
-            bi = t_sub(bn, t_mul(dl[i], bi));
-        } else {
-            b[i] = bn;
-            bi = t_sub(bi, t_mul(dl[i], bn));
-        }
-    }
-    b[n - 1] = bi;
-    // U: backward sweep with the two super-diagonals
-    T x2 = t_mul(b[n - 1], dinv[n - 1]);
-    b[n - 1] = x2;
-    if (n > 1) {
-        T x1 = t_mul(t_sub(b[n - 2], t_mul(du[n - 2], x2)), dinv[n - 2]);
-        b[n - 2] = x1;
-        for (int i = n - 3; i >= 0; --i) {
-            T x0 = t_mul(t_sub(t_sub(b[i], t_mul(du[i], x1)), t_mul(du2[i], x2)), dinv[i]);
-            b[i] = x0;
-            x2 = x1;
-            x1 = x0;
-        }
-    }
-}
-
-// x <- ((L U)^dagger)^{-1} x  (gttrs, trans = 'C'). Sequential, one thread.
-template <typename T>
-__device__ void gttrs_c(int n, const T* __restrict__ dl, const T* __restrict__ du, const T* __restrict__ du2,
-                        const int* __restrict__ ipiv, const T* __restrict__ dinv, T* __restrict__ b) {
-    // U^dagger: forward sweep
-    T x2 = t_mul(b[0], t_conj(dinv[0]));
-    b[0] = x2;
-    if (n > 1) {
-        T x1 = t_mul(t_sub(b[1], t_mul(t_conj(du[0]), x2)), t_conj(dinv[1]));
-        b[1] = x1;
-        for (int i = 2; i < n; ++i) {
-            T x0 = t_mul(t_sub(t_sub(b[i], t_mul(t_conj(du[i - 1]), x1)), t_mul(t_conj(du2[i - 2]), x2)),
-                         t_conj(dinv[i]));
-            b[i] = x0;
-            x2 = x1;
-            x1 = x0;
-        }
-    }
-    // L^dagger: backward sweep with the interchanges
-    for (int i = n - 2; i >= 0; --i) {
-        if (ipiv[i] == i) {
-            b[i] = t_sub(b[i], t_mul(t_conj(dl[i]), b[i + 1]));
-        } else {
-            T temp = b[i + 1];
-            b[i + 1] = t_sub(b[i], t_mul(t_conj(dl[i]), temp));
-            b[i] = temp;
-        }
-    }
-}
-
 // y = p * H x (dagger: p * H^dagger x) for the outer tridiagonal, in the
 // summation order (diag, sub, super) -- all threads of the block.
 template <typename T>
@@ -191,6 +129,21 @@ __device__ double2 bdot(int n, const T* a, const T* b, double2* sh) {
     return block_sum(acc, sh);
 }
 
+// a <- a - (u^dag a) u, u of unit norm (all threads of the block)
+template <typename T>
+__device__ void project_out(int n, const T* u, T* a, double2* sh) {
+    double2 d = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d = cadd(d, t_dotc(u[i], a[i]));
+    d = block_sum(d, sh);
+    const T dc = t_from(d, T());
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = t_sub(a[i], t_mul(dc, u[i]));
+    __syncthreads();
+}
+
+// a Ritz pair counts as converged when its residual is at most this
+// fraction of the Ritz value (p estimate)
+constexpr double kPResidTol = 0.1;
+
 template <typename T>
 __device__ double bnorm(int n, const T* a, double* sh) {
     double acc = 0.0;
@@ -198,9 +151,212 @@ __device__ double bnorm(int n, const T* a, double* sh) {
     return sqrt(block_sum(acc, sh));
 }
 
-struct LuView {
-    void* dl; void* d; void* du; void* du2; void* dinv; int* ipiv;
-};
+// ---- tridiagonal solves as warp-level scans of affine maps ---------------------
+//
+// The substitution sweeps of gttrs are linear recurrences.  A sequential chain
+// leaves GB300's FP64 pipe 31/32 idle (a warp instruction with one active lane
+// costs the pipe as much as a full one) and is latency bound, so each sweep
+// runs on one warp as a parallel prefix over affine maps:
+//   first order  (L sweep with interchanges):  s <- a s + c
+//   second order (U sweep, two super-diagonals): X <- M X + v, X = (x_i, x_{i+1})
+// Each lane composes the maps of its contiguous chunk, an exclusive shuffle
+// scan composes the chunks before it, and the lane then walks its chunk from
+// the state that scan gives.  The result is the LAPACK gttrs solution up to
+// rounding order.  The U coefficients are precomputed once per LU:
+//   x_i = e_i x_{i+1} + f_i x_{i+2} + y_i / d_i,   e_i = -du_i/d_i, f_i = -du2_i/d_i,
+// and for the conjugate-transpose solve
+//   x_i = eh_i x_{i-1} + fh_i x_{i-2} + b_i / d_i^*, eh_i = -(du_{i-1}/d_i)^*, fh_i = -(du2_{i-2}/d_i)^*.
+
+constexpr unsigned kFull = 0xffffffffu;
+__device__ __forceinline__ double shup(double v, int o) { return __shfl_up_sync(kFull, v, o); }
+__device__ __forceinline__ double2 shup(double2 v, int o) {
+    return mk(__shfl_up_sync(kFull, v.x, o), __shfl_up_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ double shdn(double v, int o) { return __shfl_down_sync(kFull, v, o); }
+__device__ __forceinline__ double2 shdn(double2 v, int o) {
+    return mk(__shfl_down_sync(kFull, v.x, o), __shfl_down_sync(kFull, v.y, o));
+}
+__device__ __forceinline__ double t_one(double) { return 1.0; }
+__device__ __forceinline__ double2 t_one(double2) { return mk(1.0, 0.0); }
+// a * b + c
+__device__ __forceinline__ double t_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double2 t_fma(double2 a, double2 b, double2 c) {
+    return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+template <typename T> struct Aff1 { T a, c; };                  // s -> a s + c
+template <typename T> struct Aff2 { T m00, m01, m10, m11, v0, v1; };  // X -> M X + v
+
+template <typename T> __device__ __forceinline__ Aff1<T> id1() { return {t_one(T()), t_zero(T())}; }
+template <typename T> __device__ __forceinline__ Aff2<T> id2() {
+    return {t_one(T()), t_zero(T()), t_zero(T()), t_one(T()), t_zero(T()), t_zero(T())};
+}
+// g o f (f applied first)
+template <typename T> __device__ __forceinline__ Aff1<T> comp(const Aff1<T>& g, const Aff1<T>& f) {
+    return {t_mul(g.a, f.a), t_fma(g.a, f.c, g.c)};
+}
+template <typename T> __device__ __forceinline__ Aff2<T> comp(const Aff2<T>& g, const Aff2<T>& f) {
+    Aff2<T> r;
+    r.m00 = t_fma(g.m00, f.m00, t_mul(g.m01, f.m10));
+    r.m01 = t_fma(g.m00, f.m01, t_mul(g.m01, f.m11));
+    r.m10 = t_fma(g.m10, f.m00, t_mul(g.m11, f.m10));
+    r.m11 = t_fma(g.m10, f.m01, t_mul(g.m11, f.m11));
+    r.v0 = t_fma(g.m00, f.v0, t_fma(g.m01, f.v1, g.v0));
+    r.v1 = t_fma(g.m10, f.v0, t_fma(g.m11, f.v1, g.v1));
+    return r;
+}
+template <typename T> __device__ __forceinline__ Aff1<T> shup(const Aff1<T>& f, int o) { return {shup(f.a, o), shup(f.c, o)}; }
+template <typename T> __device__ __forceinline__ Aff1<T> shdn(const Aff1<T>& f, int o) { return {shdn(f.a, o), shdn(f.c, o)}; }
+template <typename T> __device__ __forceinline__ Aff2<T> shup(const Aff2<T>& f, int o) {
+    return {shup(f.m00, o), shup(f.m01, o), shup(f.m10, o), shup(f.m11, o), shup(f.v0, o), shup(f.v1, o)};
+}
+template <typename T> __device__ __forceinline__ Aff2<T> shdn(const Aff2<T>& f, int o) {
+    return {shdn(f.m00, o), shdn(f.m01, o), shdn(f.m10, o), shdn(f.m11, o), shdn(f.v0, o), shdn(f.v1, o)};
+}
+
+// Exclusive scan over lanes: ascending (lower lanes' maps applied first) or
+// descending (higher lanes' maps applied first).  Lane 0 (31) gets identity.
+template <typename M> __device__ __forceinline__ M warp_exscan_up(M f, M ident) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        M p = shup(f, o);
+        if (lane >= o) f = comp(f, p);
+    }
+    M ex = shup(f, 1);
+    return lane == 0 ? ident : ex;
+}
+template <typename M> __device__ __forceinline__ M warp_exscan_down(M f, M ident) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        M p = shdn(f, o);
+        if (lane + o < 32) f = comp(f, p);
+    }
+    M ex = shdn(f, 1);
+    return lane == 31 ? ident : ex;
+}
+
+// Output of a sweep: plain store, or out = (out + x)/2 (the H' combination).
+template <typename T> __device__ __forceinline__ void put(T* out, int i, T x, bool half_add) {
+    out[i] = half_add ? t_scale(t_add(out[i], x), 0.5) : x;
+}
+
+// L sweep of (LU)^{-1}: y <- L^{-1} P b (forward, with the recorded interchanges).  in != out.
+template <typename T>
+__device__ void warp_L_fwd(int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
+                           const T* __restrict__ in, T* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int C = (n + 31) / 32;
+    const int lo = min(lane * C, n), hi = min(lo + C, n);
+    const int shi = min(hi, n - 1);   // steps i in [lo, shi)
+    Aff1<T> F = id1<T>();
+    for (int i = lo; i < shi; ++i) {
+        const T bn = in[i + 1];
+        Aff1<T> f = ipiv[i] == i ? Aff1<T>{t_scale(dl[i], -1.0), bn} : Aff1<T>{t_one(T()), t_scale(t_mul(dl[i], bn), -1.0)};
+        F = comp(f, F);
+    }
+    const Aff1<T> G = warp_exscan_up(F, id1<T>());
+    T st = t_fma(G.a, in[0], G.c);
+    for (int i = lo; i < shi; ++i) {
+        const T bn = in[i + 1];
+        if (ipiv[i] == i) {
+            out[i] = st;
+            st = t_fma(t_scale(dl[i], -1.0), st, bn);
+        } else {
+            out[i] = bn;
+            st = t_sub(st, t_mul(dl[i], bn));
+        }
+    }
+    if (lo < hi && hi == n) out[n - 1] = st;
+}
+
+// U sweep: x_i = e_i x_{i+1} + f_i x_{i+2} + y_i dinv_i (descending).
+template <typename T>
+__device__ void warp_U_bwd(int n, const T* __restrict__ e, const T* __restrict__ f, const T* __restrict__ dinv,
+                           const T* __restrict__ y, T* __restrict__ out, bool half_add) {
+    const int lane = threadIdx.x & 31;
+    const int C = (n + 31) / 32;
+    const int lo = min(lane * C, n), hi = min(lo + C, n);
+    Aff2<T> F = id2<T>();
+    for (int i = hi - 1; i >= lo; --i) {
+        Aff2<T> m = {e[i], f[i], t_one(T()), t_zero(T()), t_mul(y[i], dinv[i]), t_zero(T())};
+        F = comp(m, F);
+    }
+    const Aff2<T> G = warp_exscan_down(F, id2<T>());
+    T x1 = G.v0, x2 = G.v1;   // (x_{hi}, x_{hi+1})
+    for (int i = hi - 1; i >= lo; --i) {
+        const T x0 = t_fma(e[i], x1, t_fma(f[i], x2, t_mul(y[i], dinv[i])));
+        put(out, i, x0, half_add);
+        x2 = x1;
+        x1 = x0;
+    }
+}
+
+// U^dagger sweep: x_i = eh_i x_{i-1} + fh_i x_{i-2} + b_i conj(dinv_i) (ascending).  in != out.
+template <typename T>
+__device__ void warp_UH_fwd(int n, const T* __restrict__ eh, const T* __restrict__ fh, const T* __restrict__ dinv,
+                            const T* __restrict__ in, T* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int C = (n + 31) / 32;
+    const int lo = min(lane * C, n), hi = min(lo + C, n);
+    Aff2<T> F = id2<T>();
+    for (int i = lo; i < hi; ++i) {
+        Aff2<T> m = {eh[i], fh[i], t_one(T()), t_zero(T()), t_mul(in[i], t_conj(dinv[i])), t_zero(T())};
+        F = comp(m, F);
+    }
+    const Aff2<T> G = warp_exscan_up(F, id2<T>());
+    T x1 = G.v0, x2 = G.v1;   // (x_{lo-1}, x_{lo-2})
+    for (int i = lo; i < hi; ++i) {
+        const T x0 = t_fma(eh[i], x1, t_fma(fh[i], x2, t_mul(in[i], t_conj(dinv[i]))));
+        out[i] = x0;
+        x2 = x1;
+        x1 = x0;
+    }
+}
+
+// L^dagger sweep of ((LU)^dagger)^{-1} (descending, interchanges undone).  in != out.
+template <typename T>
+__device__ void warp_LH_bwd(int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
+                            const T* __restrict__ in, T* __restrict__ out, bool half_add) {
+    const int lane = threadIdx.x & 31;
+    const int C = (n + 31) / 32;
+    const int lo = min(lane * C, n), hi = min(lo + C, n);
+    const int shi = min(hi, n - 1);   // steps i in [lo, shi), walked downwards
+    Aff1<T> F = id1<T>();
+    for (int i = shi - 1; i >= lo; --i) {
+        Aff1<T> f = ipiv[i] == i ? Aff1<T>{t_scale(t_conj(dl[i]), -1.0), in[i]} : Aff1<T>{t_one(T()), t_zero(T())};
+        F = comp(f, F);
+    }
+    const Aff1<T> G = warp_exscan_down(F, id1<T>());
+    T st = t_fma(G.a, in[n - 1], G.c);   // s_{shi}: the value at position shi entering step shi - 1
+    for (int i = shi - 1; i >= lo; --i) {
+        const T cdl = t_conj(dl[i]);
+        if (ipiv[i] == i) {
+            put(out, i + 1, st, half_add);
+            st = t_sub(in[i], t_mul(cdl, st));
+        } else {
+            put(out, i + 1, t_sub(in[i], t_mul(cdl, st)), half_add);
+        }
+    }
+    if (lo == 0 && lo < hi) put(out, 0, st, half_add);
+}
+
+// After gttrf (which left du in e and du2 in f): the U coefficients of both
+// solves.  All threads of the block.
+template <typename T>
+__device__ void lu_coefficients(int n, T* e, T* f, T* eh, T* fh, const T* dinv) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        eh[i] = i >= 1 ? t_scale(t_conj(t_mul(e[i - 1], dinv[i])), -1.0) : t_zero(T());
+        fh[i] = i >= 2 ? t_scale(t_conj(t_mul(f[i - 2], dinv[i])), -1.0) : t_zero(T());
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        e[i] = i < n - 1 ? t_scale(t_mul(e[i], dinv[i]), -1.0) : t_zero(T());
+        f[i] = i < n - 2 ? t_scale(t_mul(f[i], dinv[i]), -1.0) : t_zero(T());
+    }
+    __syncthreads();
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_inner(Inner in) {
@@ -213,12 +369,19 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     const double2* al = in.alpha + (size_t)rhs * k;
     const double2* be = in.beta + (size_t)rhs * k;
     const double2* ga = in.gamma + (size_t)rhs * k;
+    // LU factors (in solve-ready form) and the two solve vectors in shared
+    // memory.  While gttrf runs, d lives in t1, du in e and du2 in f.
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* dl = reinterpret_cast<T*>(smem);
+    T* dinv = dl + k;
+    T* e = dinv + k;
+    T* f = e + k;
+    T* eh = f + k;
+    T* fh = eh + k;
+    T* t1 = fh + k;
+    T* t2 = t1 + k;
+    int* ipiv = reinterpret_cast<int*>(t2 + k);
     T* W = reinterpret_cast<T*>(in.work + (size_t)rhs * kInnerWorkVecs * k);
-    T* dl = W + 0 * (size_t)k;
-    T* d = W + 1 * (size_t)k;
-    T* du = W + 2 * (size_t)k;
-    T* du2 = W + 3 * (size_t)k;
-    T* dinv = W + 4 * (size_t)k;
     T* x = W + 5 * (size_t)k;
     T* y = W + 6 * (size_t)k;
     T* vprev = W + 7 * (size_t)k;
@@ -227,10 +390,20 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     T* wprev = W + 10 * (size_t)k;
     T* w = W + 11 * (size_t)k;
     T* l = W + 12 * (size_t)k;
-    T* t1 = W + 13 * (size_t)k;
-    T* t2 = W + 14 * (size_t)k;
-    int* ipiv = in.ipiv + (size_t)rhs * k;
     const bool TS = sizeof(T) == sizeof(double2);
+    const int warp = threadIdx.x >> 5;
+
+    // LU of s * H in gttrf form, then the solve coefficients
+    auto factor = [&](double sc) {
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            t1[i] = t_scale(t_from(al[i], T()), sc);
+            if (i < k - 1) { dl[i] = t_scale(t_from(be[i], T()), sc); e[i] = t_scale(t_from(ga[i], T()), sc); }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, t1, e, f, ipiv, dinv);
+        __syncthreads();
+        lu_coefficients<T>(k, e, f, eh, fh, dinv);
+    };
 
     // ---- p (Eq. popt) --------------------------------------------------------
     double p = in.p_fixed;
@@ -247,28 +420,53 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
             for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(y[i], inv);
             __syncthreads();
         }
-        // LU of H itself for the inverse iteration
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            d[i] = t_from(al[i], T());
-            if (i < k - 1) { dl[i] = t_from(be[i], T()); du[i] = t_from(ga[i], T()); }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, d, du, du2, ipiv, dinv);
-        __syncthreads();
+        // inverse iteration with the LU of H itself
+        factor(1.0);
         for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_from(mk(x0, 0.0), T());
         __syncthreads();
         double tn = 1.0;
         for (int it = 0; it < 30; ++it) {
-            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = x[i];
-            __syncthreads();
-            if (threadIdx.x == 0) gttrs_n<T>(k, dl, du, du2, ipiv, dinv, y);
+            if (warp == 0) {
+                warp_L_fwd<T>(k, dl, ipiv, x, t1);
+                __syncwarp();
+                warp_U_bwd<T>(k, e, f, dinv, t1, y, false);
+            }
             __syncthreads();
             tn = bnorm<T>(k, y, sh1);
             const double inv = 1.0 / tn;
             for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(y[i], inv);
             __syncthreads();
         }
-        const double zmin = 1.0 / tn;
+        double zmin = 1.0 / tn;
+        // Accept the smallest Ritz value only if its Ritz pair has converged
+        // (residual |H(k-1,k-2)| |x_{k-1}| <= 0.1 z); otherwise it is a spurious
+        // value in the spectral gap: iterate again with that direction projected out.
+        const double resid = k >= 2 ? sqrt(cnorm2(be[k - 2])) * sqrt(t_norm2(x[k - 1])) : 0.0;
+        if (resid > kPResidTol * zmin) {
+            T* x1 = vprev;
+            for (int i = threadIdx.x; i < k; i += blockDim.x) x1[i] = x[i];
+            __syncthreads();
+            for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_from(mk(x0, 0.0), T());
+            __syncthreads();
+            project_out<T>(k, x1, x, sh2);
+            const double xn = bnorm<T>(k, x, sh1);
+            for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(x[i], 1.0 / xn);
+            __syncthreads();
+            for (int it = 0; it < 30; ++it) {
+                if (warp == 0) {
+                    warp_L_fwd<T>(k, dl, ipiv, x, t1);
+                    __syncwarp();
+                    warp_U_bwd<T>(k, e, f, dinv, t1, y, false);
+                }
+                __syncthreads();
+                project_out<T>(k, x1, y, sh2);
+                tn = bnorm<T>(k, y, sh1);
+                const double inv = 1.0 / tn;
+                for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(y[i], inv);
+                __syncthreads();
+            }
+            zmin = 1.0 / tn;
+        }
         p = 1.0 / sqrt(zmin * zmax);
         if (threadIdx.x == 0) { in.zmin[rhs] = zmin; in.zmax[rhs] = zmax; }
     } else if (threadIdx.x == 0) {
@@ -277,13 +475,7 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     if (threadIdx.x == 0) in.p[rhs] = p;
 
     // ---- step 3: LU of p H_k --------------------------------------------------
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        d[i] = t_scale(t_from(al[i], T()), p);
-        if (i < k - 1) { dl[i] = t_scale(t_from(be[i], T()), p); du[i] = t_scale(t_from(ga[i], T()), p); }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, d, du, du2, ipiv, dinv);
-    __syncthreads();
+    factor(p);
     if (s_info != 0) {
         if (threadIdx.x == 0) in.status[rhs] = kStatusLU;
         return;
@@ -304,21 +496,21 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     __syncthreads();
     store_vl(0, v);
 
+    // out_r = H' src_r = [(pH) src_r + (pH)^{-1} src_r]/2 and, two-sided,
+    // out_l = H'^dagger src_l: band products by the whole block, then the
+    // (pH)^{-1} solve on warp 0 and the ((pH)^dagger)^{-1} solve on warp 1.
     auto apply_hp = [&](const T* src_r, T* out_r, const T* src_l, T* out_l) {
-        // t1 <- src_r, t2 <- src_l; solves in place; band products into out
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            t1[i] = src_r[i];
-            if (TS) t2[i] = src_l[i];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) gttrs_n<T>(k, dl, du, du2, ipiv, dinv, t1);
-        if (TS && threadIdx.x == 32) gttrs_c<T>(k, dl, du, du2, ipiv, dinv, t2);
         band_mv<T>(k, p, al, be, ga, src_r, out_r, false);
         if (TS) band_mv<T>(k, p, al, be, ga, src_l, out_l, true);
         __syncthreads();
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {
-            out_r[i] = t_scale(t_add(out_r[i], t1[i]), 0.5);
-            if (TS) out_l[i] = t_scale(t_add(out_l[i], t2[i]), 0.5);
+        if (warp == 0) {
+            warp_L_fwd<T>(k, dl, ipiv, src_r, t1);
+            __syncwarp();
+            warp_U_bwd<T>(k, e, f, dinv, t1, out_r, true);
+        } else if (TS && warp == 1) {
+            warp_UH_fwd<T>(k, eh, fh, dinv, src_l, t2);
+            __syncwarp();
+            warp_LH_bwd<T>(k, dl, ipiv, t2, out_l, true);
         }
         __syncthreads();
     };
@@ -569,15 +761,25 @@ __global__ void k_combine(Inner in) {
 
 }  // namespace
 
+size_t inner_smem_bytes(int k, bool two_sided) {
+    return (size_t)k * (8 * (two_sided ? sizeof(double2) : sizeof(double)) + sizeof(int));
+}
+
 void launch_inner_lanczos(const Inner& in, cudaStream_t st) {
-    if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, 0, st>>>(in);
-    else k_inner<double><<<in.n_rhs, 256, 0, st>>>(in);
+    size_t smem = inner_smem_bytes(in.k, in.two_sided);
+    if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, smem, st>>>(in);
+    else k_inner<double><<<in.n_rhs, 256, smem, st>>>(in);
 }
 
 // Largest dynamic shared memory any RHi launch needs (l <= 256, complex, 8 CTAs).
 static size_t rhi_smem_max();
+size_t inner_smem_bytes(int k, bool two_sided);
 
 void init_kernel_attributes() {
+    cudaFuncSetAttribute(k_inner<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)inner_smem_bytes(kMaxInnerK, false));
+    cudaFuncSetAttribute(k_inner<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)inner_smem_bytes(kMaxInnerK, true));
     cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());
     cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());
     cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

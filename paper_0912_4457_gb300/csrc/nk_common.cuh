@@ -97,6 +97,133 @@ __device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
     return t;
 }
 
+// Two-stage deterministic reduction, stage 1: thread 0 of each block writes
+// its block's partial; the block that arrives last (integer ticket, no
+// floating-point atomics) returns true and finishes the sum in fixed order.
+__device__ __forceinline__ bool finish_partial(double2 part, double2* partials, unsigned* counter,
+                                               int slot, int nslots) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[slot] = part;
+        __threadfence();
+        unsigned ticket = atomicAdd(counter, 1u);
+        last = (ticket == (unsigned)nslots - 1u);
+    }
+    __syncthreads();
+    return last;
+}
+
+// Stage 2: fixed-order sum of the nslots partials (all threads of the last block).
+__device__ __forceinline__ double2 sum_partials(const double2* partials, int nslots, double2* sh) {
+    __threadfence();
+    double2 a = mk(0.0, 0.0);
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        double2 v = __ldcg(partials + i);
+        a.x += v.x; a.y += v.y;
+    }
+    return block_sum(a, sh);
+}
+
+// ---- float <-> double on the integer pipe ---------------------------------------
+// On GB300 the FP64 pipe is 1/64 of the FP32 rate and cvt.f64.f32 /
+// cvt.f32.f64 issue on it too, so the hot kernels move between the formats
+// with integer bit operations instead (IEEE 754 binary32 <-> binary64 field
+// layout).  Zero is handled exactly; subnormal, infinite or NaN inputs, or
+// results outside the normal float range, fall back to the conversion
+// instruction (never taken for the vectors of this method).
+
+// float -> double, exact
+__device__ __forceinline__ double f2d_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned a = u & 0x7fffffffu;
+    if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (a < 0x00800000u || a >= 0x7f800000u) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((a >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(a << 29));
+}
+
+// double -> float, rounded to nearest (ties away from zero in magnitude; ties
+// occur with probability 2^-29 and differ from round-to-even by one ulp)
+__device__ __forceinline__ float d2f_int(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned long long a = u & 0x7fffffffffffffffULL;
+    const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
+    if (a == 0ULL) return __uint_as_float(s);
+    // normal float results need 897 <= biased exponent <= 1150
+    if (a < (897ULL << 52) || a >= (1151ULL << 52)) return __double2float_rn(d);
+    unsigned long long t = (a >> 29) + ((a >> 28) & 1ULL);
+    t -= 896ULL << 23;
+    if (t >= (255ULL << 23)) return __double2float_rn(d);
+    return __uint_as_float(s | (unsigned)t);
+}
+
+// double -> (hi, lo) floats with hi + lo == d to about 2^-48 relative: hi is d
+// truncated to 24 significant bits (exact in float), lo the remaining 29
+// bits rounded to a float.
+__device__ __forceinline__ float2 d2ff_int(double d) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned long long a = u & 0x7fffffffffffffffULL;
+    const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
+    if (a == 0ULL) return make_float2(__uint_as_float(s), 0.0f);
+    if (a < (897ULL << 52) || a >= (1151ULL << 52)) {
+        float hi = __double2float_rz(d);
+        return make_float2(hi, __double2float_rn(d - (double)hi));
+    }
+    const unsigned e = (unsigned)(a >> 52);
+    const float hi = __uint_as_float(s | (unsigned)((a >> 29) - (896ULL << 23)));
+    const unsigned mlo = (unsigned)(a & 0x1fffffffULL);   // d - hi = mlo * 2^(e - 1075)
+    float lo = 0.0f;
+    if (mlo != 0u && e > 948u) {                          // 2^(e-1075) a normal float
+        lo = __uint2float_rn(mlo) * __uint_as_float((e - 1075u + 127u) << 23);
+        lo = __uint_as_float(__float_as_uint(lo) | s);
+    }
+    return make_float2(hi, lo);
+}
+
+// ---- two-float ("df") arithmetic ---------------------------------------------------
+// A value is hi + lo with |lo| <= ulp(hi); about 48 significant bits, computed
+// on the FP32 pipe with the error-free transformations TwoSum (Knuth) and
+// TwoProd via FMA (the double-float arithmetic of Dekker and of Hida, Li and
+// Bailey's double-double library).  The _rn intrinsics keep the compiler from
+// contracting or reassociating the steps.
+struct df {
+    float hi, lo;
+    __host__ __device__ __forceinline__ df() {}
+    __host__ __device__ __forceinline__ df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ __forceinline__ df(int v) : hi((float)v), lo(0.0f) {}
+};
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df& operator+=(df& a, df b) { a = a + b; return a; }
+__device__ __forceinline__ df df_from_double(double d) {
+    const float2 p = d2ff_int(d);
+    return df(p.x, p.y);
+}
+__device__ __forceinline__ double df_to_double(df a) { return f2d_int(a.hi) + f2d_int(a.lo); }
+
+struct __align__(16) dfc {
+    df x, y;
+};
+template <> struct C2<df> { typedef dfc T; };
+
 // Upper bound on spin iterations of any device-side wait (each iteration
 // sleeps ~100 ns), about one second; a wait that runs out sets an error flag.
 constexpr long long kSpinLimit = 10000000LL;

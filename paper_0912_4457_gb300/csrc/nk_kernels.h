@@ -7,6 +7,8 @@
 
 namespace nk {
 
+struct dfc;   // two-float complex (nk_common.cuh)
+
 struct Geom {
     int Lx, Ly, Lz, Lt, V;
     int antiperiodic;
@@ -25,8 +27,9 @@ struct DslashSet {
 
 void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet& s0,
                    const DslashSet& s1, double kappa, double mu, cudaStream_t st);
-void launch_links_to_device_layout(const double2* in, double2* u64, float2* u32, int V,
+void launch_links_to_device_layout(const double2* in, double2* u64, float2* u32, dfc* udf, int V,
                                    cudaStream_t st);
+void launch_to_df(const double2* in, long in_stride, dfc* out, long out_stride, long N, int n, cudaStream_t st);
 void launch_abi_to_soa(const double2* in, long in_stride, double2* out, long out_stride, int V,
                        int n, cudaStream_t st);
 void launch_soa_to_abi(const double2* in, long in_stride, double2* out, long out_stride,
@@ -36,51 +39,65 @@ void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_str
 
 // ---- outer (two-sided) Lanczos recurrence -------------------------------------
 
-// Device buffers of one batched outer recurrence; all per-RHS arrays are
-// indexed [rhs][...].
+// Device buffers of one batched outer recurrence; per-RHS arrays are indexed
+// [rhs][...].  Basis vectors are stored unnormalised (see lanczos.cu):
+// q_j = n_j v_j and p_j = m_j w_j.
 struct Outer {
     long N;          // vector length (12 V complex)
-    int n_rhs, k, nblk;
+    int n_rhs, k, nblk, npart;
     int two_sided;
-    double2* V;      // basis, [rhs][k][N] (single pass) -- or nullptr
-    double2* vring;  // [rhs][2][N] ring of v_{j-1}, v_j when V == nullptr (double pass)
-    double2* w;      // [rhs][2][N] ring of w_{j-1}, w_j (two-sided)
-    double2* r;      // [rhs][N]
-    double2* l;      // [rhs][N]
-    double2* s;      // stencil output A v_j, [rhs][N]
-    double2* t;      // stencil output A^dagger w_j, [rhs][N]
-    float2* v32;     // FP32 copy of v_j, [rhs][N]
-    float2* w32;     // FP32 copy of w_j, [rhs][N]
+    int q_ring;      // 0: Q holds all k vectors [rhs][k][N]; 1: ring [rhs][3][N] (double pass)
+    double2* Q;      // right basis q_j
+    double2* P;      // left vectors p_j, ring [rhs][3][N] (two-sided)
+    float2* q32;     // FP32 copy of the newest q, [rhs][N]
+    float2* p32;     // FP32 copy of the newest p, [rhs][N]
+    dfc* qdf;        // two-float copy of the newest q, [rhs][N]
+    dfc* pdf;        // two-float copy of the newest p, [rhs][N]
     double2* alpha;  // H(j,j), [rhs][k]
     double2* beta;   // H(j+1,j), [rhs][k]
     double2* gamma;  // H(j,j+1), [rhs][k]
-    double2* partials;  // [rhs][nblk]
+    double2* partials;  // [rhs][npart]
     unsigned* counters; // [rhs]
     int* status;        // [rhs]
     double* xnorm;      // [rhs]
-    double2* y;         // double-pass accumulation y = sum_j c_j v_j, [rhs][N]
-    const double2* c;   // double-pass coefficients, [rhs][k]
+    double2* y;         // double pass: accumulation y = sum_j c'_j q_j, [rhs][N]
+    const double2* cp;  // double pass: lift coefficients c'_j, [rhs][k]
 };
 
-__host__ __device__ inline double2* outer_v(const Outer& o, int rhs, int j) {
-    return o.V ? o.V + ((size_t)rhs * o.k + j) * o.N : o.vring + ((size_t)rhs * 2 + (j & 1)) * o.N;
+__host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {
+    return o.Q + (o.q_ring ? ((size_t)rhs * 3 + j % 3) : ((size_t)rhs * o.k + j)) * o.N;
 }
-__host__ __device__ inline double2* outer_w(const Outer& o, int rhs, int j) {
-    return o.w + ((size_t)rhs * 2 + (j & 1)) * o.N;
+__host__ __device__ inline double2* outer_p(const Outer& o, int rhs, int j) {
+    return o.P + ((size_t)rhs * 3 + j % 3) * o.N;
+}
+// n_j (q_j = n_j v_j) and m_j (p_j = m_j w_j)
+__device__ inline double2 scale_n(const Outer& o, int rhs, int j) {
+    return j == 0 ? make_double2(o.xnorm[rhs], 0.0) : o.beta[(size_t)rhs * o.k + j - 1];
+}
+__device__ inline double2 scale_m(const Outer& o, int rhs, int j) {
+    if (j == 0) return make_double2(o.xnorm[rhs], 0.0);
+    double2 g = o.gamma[(size_t)rhs * o.k + j - 1];
+    return make_double2(g.x, -g.y);
 }
 
 // status codes kept on the device (0 = fine)
 constexpr int kStatusOK = 0;
 constexpr int kStatusZeroSource = 1;  // |b| = 0: result is 0
-constexpr int kStatusBreakdown = 2;   // two-sided serious breakdown
+constexpr int kStatusBreakdown = 2;   // serious breakdown (or a zero beta)
 constexpr int kStatusRhi = 3;         // RHi did not converge / singular pivot
 constexpr int kStatusLU = 4;          // singular p H_k
 
-void launch_outer_init(const Outer& o, const double2* b_soa, int write32, cudaStream_t st);
-void launch_outer_step1(const Outer& o, int j, cudaStream_t st);
-void launch_outer_step2(const Outer& o, int j, cudaStream_t st);
-void launch_outer_step3(const Outer& o, int j, int write32, cudaStream_t st);
-void launch_lift(const Outer& o, const double2* c, double2* y, cudaStream_t st);
+// Copy modes for the next stencil's input: none, FP32, two-float.
+constexpr int kCopyNone = 0, kCopy32 = 1, kCopyDF = 2;
+void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st);
+// Fused stencil + first half of step j (dslash.cu); precision 32 (FP32),
+// 48 (two-float) or 64 (FP64).
+void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
+                         double kappa, double mu, cudaStream_t st);
+int dslash_step1_blocks(const Geom& g);
+void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st);
+void launch_lift_coef(const Outer& o, const double2* c, double2* cp, cudaStream_t st);
+void launch_lift(const Outer& o, const double2* cp, double2* y, cudaStream_t st);
 
 // ---- inner part: p estimate, LU of p H_k, inner Lanczos, RHi, c = V_l s -------
 
@@ -108,6 +125,9 @@ struct Inner {
     int* timeout;          // device flag: a bounded wait ran out
 };
 constexpr int kInnerWorkVecs = 16;
+// Largest outer size k the inner kernel supports (its LU factors and solve
+// vectors, 8 complex vectors of length k plus the pivots, fill shared memory).
+constexpr int kMaxInnerK = 1536;
 
 void launch_inner_lanczos(const Inner& in, cudaStream_t st);
 int launch_rhi(const Inner& in, cudaStream_t st);  // returns cudaError_t

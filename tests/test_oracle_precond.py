@@ -134,6 +134,29 @@ def test_lu_partial_pivoting_reconstructs():
     assert any(ipiv[i] - 1 != i for i in range(k - 1))
 
 
+def test_p_estimate_skips_spurious_gap_ritz_value():
+    """Spectrum symmetric about 0 with a gap (-0.5, 0.5): a Ritz matrix of odd
+    size has a spurious Ritz value near zero (Fig. 7 caption); it has not
+    converged, so z_min must come from the converged edge of the gap instead.
+    With even size there is no such value and z_min is the smallest |Ritz value|."""
+    from oracle import krylov
+    rng = np.random.default_rng(9)
+    pos = np.sort(rng.uniform(0.5, 3.0, 200))
+    w = np.concatenate([pos, -pos])
+    x = rng.standard_normal(w.size)
+    for k in (41, 40):
+        res = krylov.lanczos(lambda v: w * v, x, k)
+        ritz = np.sort(np.abs(np.linalg.eigvalsh(res.H())))
+        p, zmin, zmax = nested.estimate_p(res.alpha, res.beta, res.gamma, iters=60)
+        if k % 2:
+            assert ritz[0] < 0.3                  # the spurious value exists
+            assert zmin > 0.45                    # and is skipped
+        else:
+            assert ritz[0] > 0.45
+            assert zmin == pytest.approx(ritz[0], rel=2e-2)
+        assert zmax == pytest.approx(ritz[-1], rel=1e-2)
+
+
 def test_spectral_estimates_hermitian():
     """Power / inverse iteration converge to max|z| and min|z| of H."""
     rng = np.random.default_rng(6)
@@ -141,7 +164,8 @@ def test_spectral_estimates_hermitian():
     a, b, g = _rand_tridiag(k, rng, False)
     z = np.sort(np.abs(np.linalg.eigvalsh(_dense(a, b, g))))
     assert z[-2] / z[-1] < 0.95 and z[0] / z[1] < 0.95      # gaps for fast convergence
-    p, zmin, zmax = nested.estimate_p(a, b, g, iters=400)
+    # a random tridiagonal is not a Lanczos matrix: no residual screening here
+    p, zmin, zmax = nested.estimate_p(a, b, g, iters=400, resid_tol=np.inf)
     assert zmax == pytest.approx(z[-1], rel=1e-10)
     assert zmin == pytest.approx(z[0], rel=1e-10)
     assert p == pytest.approx(precond.p_opt(z[0], z[-1]), rel=1e-10)
