@@ -230,13 +230,13 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
 // accumulates y += c'_j q_j at its own site.
 constexpr int kStencilThreads = 128;
 
-template <typename R, bool TS>
+template <typename R, bool TS, bool PASS2>
 __global__ void __launch_bounds__(kStencilThreads) k_dslash_step1(
     const typename C2<R>::T* __restrict__ U, Geom g, Outer o, int j, R kappa, R emu, R emu_inv,
     const typename C2<R>::T* __restrict__ qin, long qin_stride, const typename C2<R>::T* __restrict__ pin,
     long pin_stride) {
     typedef typename C2<R>::T T;
-    __shared__ double2 sh[32];
+    __shared__ double2 sh[33];
     __shared__ double2 coef[3];
     const int nvec = TS ? 2 * o.n_rhs : o.n_rhs;
     const int vec = blockIdx.x % nvec;
@@ -266,40 +266,53 @@ __global__ void __launch_bounds__(kStencilThreads) k_dslash_step1(
         const T* __restrict__ in = side == 0 ? qin + (size_t)rhs * qin_stride : pin + (size_t)rhs * pin_stride;
         T out[4][3];
         stencil_site<R>(U, in, g, site, side, kappa, emu, emu_inv, out);
-        const double2 c1 = coef[1];
+        const double2 c1 = coef[1];   // zero at j = 0 (the previous vector is then any valid one)
         // the scale 1/n_j (1/m_j) in the stencil's precision
         T scr;
         scr.x = from_double<R>(coef[0].x);
         scr.y = from_double<R>(coef[0].y);
-        double2* __restrict__ nxt = side == 0 ? (j < o.k - 1 ? outer_q(o, rhs, j + 1) : nullptr)
-                                              : outer_p(o, rhs, j + 1);
-        const double2* __restrict__ prv = j > 0 ? (side == 0 ? outer_q(o, rhs, j - 1) : outer_p(o, rhs, j - 1))
-                                                : nullptr;
-        const double2* __restrict__ dotv = side == 0 ? (TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j)) : nullptr;
-        double2* __restrict__ yacc = (side == 0 && o.y) ? o.y + (size_t)rhs * o.N : nullptr;
-        const double2 cpj = yacc ? o.cp[hb + j] : make_double2(0.0, 0.0);
-        const double2* __restrict__ qj = yacc ? outer_q(o, rhs, j) : nullptr;
+        const int jp = j > 0 ? j - 1 : j;
+        if (side == 0) {
+            const double2* __restrict__ prv = outer_q(o, rhs, jp);
+            double2* __restrict__ nxt = outer_q(o, rhs, j + 1);   // at j = k-1 a scratch column
+            const double2* __restrict__ dotv = TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j);
+            double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
+            const double2 cpj = PASS2 ? o.cp[hb + j] : make_double2(0.0, 0.0);
+            const double2* __restrict__ qj = outer_q(o, rhs, j);
 #pragma unroll
-        for (int sp = 0; sp < 4; ++sp) {
+            for (int sp = 0; sp < 4; ++sp) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const size_t idx = (size_t)(3 * sp + a) * g.V + site;
-                const T v = out[sp][a];
-                double2 rr;
-                if (TS) rr = make_double2(to_double(v.x * scr.x - v.y * scr.y), to_double(v.x * scr.y + v.y * scr.x));
-                else rr = make_double2(to_double(v.x * scr.x), to_double(v.y * scr.x));
-                if (prv) {
-                    const double2 pv = prv[idx];
-                    if (TS) rr = caxpy_neg(rr, c1, pv);                     // r - c1 pv
-                    else rr = make_double2(fma(-c1.x, pv.x, rr.x), fma(-c1.x, pv.y, rr.y));
-                }
-                if (nxt) nxt[idx] = rr;
-                if (dotv) {
+                for (int a = 0; a < 3; ++a) {
+                    const size_t idx = (size_t)(3 * sp + a) * g.V + site;
+                    const T v = out[sp][a];
+                    double2 rr;
+                    if (TS) {
+                        rr = make_double2(to_double(v.x * scr.x - v.y * scr.y), to_double(v.x * scr.y + v.y * scr.x));
+                        rr = caxpy_neg(rr, c1, prv[idx]);               // r - c1 q_{j-1}
+                    } else {
+                        rr = make_double2(to_double(v.x * scr.x), to_double(v.y * scr.x));
+                        const double2 pv = prv[idx];
+                        rr = make_double2(fma(-c1.x, pv.x, rr.x), fma(-c1.x, pv.y, rr.y));
+                    }
+                    nxt[idx] = rr;
                     const double2 d = dotv[idx];
                     acc.x = fma(d.x, rr.x, fma(d.y, rr.y, acc.x));          // conj(d) r
                     if (TS) acc.y = fma(d.x, rr.y, fma(-d.y, rr.x, acc.y));
+                    if (PASS2) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
                 }
-                if (yacc) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
+            }
+        } else {
+            const double2* __restrict__ prv = outer_p(o, rhs, jp);
+            double2* __restrict__ nxt = outer_p(o, rhs, j + 1);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const size_t idx = (size_t)(3 * sp + a) * g.V + site;
+                    const T v = out[sp][a];
+                    double2 ll = make_double2(to_double(v.x * scr.x - v.y * scr.y), to_double(v.x * scr.y + v.y * scr.x));
+                    nxt[idx] = caxpy_neg(ll, c1, prv[idx]);             // l - c1 p_{j-1}
+                }
             }
         }
     }
@@ -323,10 +336,18 @@ static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R k
                            long qs, const T* pin, long ps, cudaStream_t st) {
     const int nvec = o.two_sided ? 2 * o.n_rhs : o.n_rhs;
     dim3 grid((unsigned)(dslash_step1_blocks(g) * nvec));
-    if (o.two_sided)
-        k_dslash_step1<R, true><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
-    else
-        k_dslash_step1<R, false><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+    const bool pass2 = o.y != nullptr;
+    if (o.two_sided) {
+        if (pass2)
+            k_dslash_step1<R, true, true><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+        else
+            k_dslash_step1<R, true, false><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+    } else {
+        if (pass2)
+            k_dslash_step1<R, false, true><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+        else
+            k_dslash_step1<R, false, false><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+    }
 }
 
 void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
@@ -338,7 +359,7 @@ void launch_dslash_step1(int precision, const void* U, const Geom& g, const Oute
         launch_step1_t<df, dfc>((const dfc*)U, g, o, j, df_host(kappa), df_host(exp(mu)), df_host(exp(-mu)), o.qdf,
                                 o.N, o.pdf, o.N, st);
     } else {
-        const long qs = o.q_ring ? 3 * o.N : (long)o.k * o.N;
+        const long qs = (long)o.qcols * o.N;
         launch_step1_t<double, double2>((const double2*)U, g, o, j, kappa, exp(mu), exp(-mu), outer_q(o, 0, j), qs,
                                         o.two_sided ? outer_p(o, 0, j) : nullptr, 3 * o.N, st);
     }

@@ -126,7 +126,8 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.N = N; o.n_rhs = n_rhs; o.k = k; o.nblk = nblk; o.two_sided = two_sided;
     o.npart = std::max(nblk, nk::dslash_step1_blocks(g));
     o.q_ring = double_pass ? 1 : 0;
-    o.Q = (double2*)take(vec * (double_pass ? 3 : (size_t)k) * n_rhs);
+    o.qcols = double_pass ? 3 : k + 1;   // single pass: k basis vectors + one scratch column
+    o.Q = (double2*)take(vec * (size_t)o.qcols * n_rhs);
     if (two_sided) o.P = (double2*)take(vec * 3 * n_rhs);
     o.q32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
     if (two_sided) o.p32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
@@ -163,8 +164,10 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
 }
 
 int blocks_per_rhs(long N, int n_rhs) {
-    // fixed per shape: enough blocks to fill the GPU, grid-stride beyond that
-    long need = (N + 255) / 256;
+    // fixed per shape (deterministic reductions): about 8 elements per thread
+    // so the per-thread share of the FP64 reduction stays small, at most
+    // 4 x 152 blocks over all RHS, grid-stride beyond that
+    long need = (N + 2047) / 2048;
     long cap = std::max(1L, (long)(4 * 152 / n_rhs));
     return (int)std::max(1L, std::min(need, cap));
 }
@@ -242,7 +245,7 @@ void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& 
 
 // b (ABI layout, device) -> q_0 of every RHS
 void enqueue_load_sources(nk_ctx* c, const nk::Outer& o, const double* b_dev, int n_rhs, Launcher& L) {
-    const long qs = o.q_ring ? 3 * c->N : (long)o.k * c->N;
+    const long qs = (long)o.qcols * c->N;
     L.run(NK_CLASS_OTHER, 1, [&] {
         nk::launch_abi_to_soa((const double2*)b_dev, c->N, nk::outer_q(o, 0, 0), qs, c->V, n_rhs, L.st);
     });

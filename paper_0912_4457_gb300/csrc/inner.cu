@@ -50,6 +50,8 @@ __device__ __forceinline__ double t_sub(double a, double b) { return a - b; }
 __device__ __forceinline__ double2 t_sub(double2 a, double2 b) { return csub(a, b); }
 __device__ __forceinline__ double t_scale(double a, double s) { return a * s; }
 __device__ __forceinline__ double2 t_scale(double2 a, double s) { return cscale(a, s); }
+__device__ __forceinline__ double t_neg(double a) { return -a; }
+__device__ __forceinline__ double2 t_neg(double2 a) { return mk(-a.x, -a.y); }
 __device__ __forceinline__ double t_inv(double a) { return 1.0 / a; }
 __device__ __forceinline__ double2 t_inv(double2 a) { return cinv(a); }
 __device__ __forceinline__ double t_abs1(double a) { return fabs(a); }
@@ -360,7 +362,7 @@ __device__ void lu_coefficients(int n, T* e, T* f, T* eh, T* fh, const T* dinv) 
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_inner(Inner in) {
-    __shared__ double2 sh2[32];
+    __shared__ double2 sh2[33];
     __shared__ double sh1[32];
     __shared__ int s_info;
     const int rhs = blockIdx.x;
@@ -677,22 +679,26 @@ __global__ void __launch_bounds__(kRhiThreads) k_rhi(Inner in, int C, int maxit,
             const T pinv = t_inv(prow[c]);
             __syncthreads();
             for (int col = tid; col < L; col += blockDim.x)
-                prow[col] = col == c ? pinv : t_mul(prow[col], pinv);
+                if (col != c) prow[col] = t_mul(prow[col], pinv);
+            __syncthreads();
+            if (tid == 0) prow[c] = pinv;
             __syncthreads();
             if (c % C == rank) {
                 T* dst = M + (size_t)(c / C) * L;
                 for (int col = tid; col < L; col += blockDim.x) dst[col] = prow[col];
             }
-            // (e) eliminate column c from every other own row
+            // (e) eliminate column c from every other own row: M(i,:) -= M(i,c) prow,
+            // then M(i,c) = -M(i,c) pinv (the multipliers, read first)
             for (int li = tid; li < nloc; li += blockDim.x) fcol[li] = M[(size_t)li * L + c];
             __syncthreads();
             for (int e = tid; e < nloc * L; e += blockDim.x) {
-                int li = e / L, col = e % L;
-                if (rank + C * li == c) continue;
-                T f = fcol[li];
+                const int li = e / L, col = e % L;
+                if (rank + C * li == c || col == c) continue;
                 T& m = M[(size_t)li * L + col];
-                m = col == c ? t_scale(t_mul(f, prow[c]), -1.0) : t_sub(m, t_mul(f, prow[col]));
+                m = t_fma(t_neg(fcol[li]), prow[col], m);
             }
+            for (int li = tid; li < nloc; li += blockDim.x)
+                if (rank + C * li != c) M[(size_t)li * L + c] = t_mul(t_neg(fcol[li]), pinv);
             __syncthreads();
         }
         if (!ok) break;

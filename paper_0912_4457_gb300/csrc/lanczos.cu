@@ -34,7 +34,7 @@ namespace {
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads) k_norm(Outer o) {
-    __shared__ double2 sh[32];
+    __shared__ double2 sh[33];
     const int rhs = blockIdx.y;
     const double2* x = outer_q(o, rhs, 0);
     double acc = 0.0;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Outer o, int copy_mode) {
 
 template <bool TS>
 __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mode) {
-    __shared__ double2 sh[32];
+    __shared__ double2 sh[33];
     __shared__ double2 coef[2];
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) k_lift(Outer o, const double2* __res
     double2* yo = y + (size_t)rhs * o.N;
     if (o.status[rhs] != kStatusOK) { yo[i] = mk(0.0, 0.0); return; }
     const double2* cr = cp + (size_t)rhs * o.k;
-    const double2* Qr = o.Q + (size_t)rhs * o.k * o.N;
+    const double2* Qr = o.Q + (size_t)rhs * o.qcols * o.N;
     double2 acc = mk(0.0, 0.0);
     for (int j = 0; j < o.k; ++j) {
         double2 cj = __ldg(cr + j);

@@ -76,15 +76,27 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Block sum of a double2 (blockDim.x a multiple of 32, <= 1024). Every thread
 // of the block receives the same value; the summation order is fixed.
-__device__ __forceinline__ double2 block_sum(double2 v, double2* sh /* >= 32 */) {
+// Only warp 0 does the second level (FP64 adds are scarce on GB300); the
+// result is broadcast through shared memory.
+__device__ __forceinline__ double2 block_sum(double2 v, double2* sh /* >= 33 */) {
     v = warp_sum(v);
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) sh[w] = v;
     __syncthreads();
-    double2 t = lane < nw ? sh[lane] : mk(0.0, 0.0);
-    t = warp_sum(t);
-    return t;
+    if (w == 0) {
+        double2 t = lane < nw ? sh[lane] : mk(0.0, 0.0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (o < nw) {   // nw is a power of two: only the levels that combine real partials
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+            }
+        }
+        if (lane == 0) sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
 }
 __device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
     v = warp_sum(v);
@@ -127,19 +139,23 @@ __device__ __forceinline__ double2 sum_partials(const double2* partials, int nsl
 // ---- float <-> double on the integer pipe ---------------------------------------
 // On GB300 the FP64 pipe is 1/64 of the FP32 rate and cvt.f64.f32 /
 // cvt.f32.f64 issue on it too, so the hot kernels move between the formats
-// with integer bit operations instead (IEEE 754 binary32 <-> binary64 field
-// layout).  Zero is handled exactly; subnormal, infinite or NaN inputs, or
-// results outside the normal float range, fall back to the conversion
-// instruction (never taken for the vectors of this method).
+// with integer bit operations only (IEEE 754 binary32 <-> binary64 field
+// layout), with no conversion instruction even on a predicated-off path.
+// Normal numbers and zero convert exactly / round to nearest; the edge cases
+// the vectors of this method never reach are mapped without a conversion
+// instruction: float subnormals and double results below the normal float
+// range become signed zero, overflow becomes infinity, NaN stays NaN.
 
-// float -> double, exact
+// float -> double, exact for normal floats and zero
 __device__ __forceinline__ double f2d_int(float f) {
     const unsigned u = __float_as_uint(f);
+    const unsigned s = u & 0x80000000u;
     const unsigned a = u & 0x7fffffffu;
-    if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-    if (a < 0x00800000u || a >= 0x7f800000u) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | ((a >> 3) + (896u << 20));
-    return __hiloint2double((int)hi, (int)(a << 29));
+    unsigned hi = s | ((a >> 3) + (896u << 20));
+    unsigned lo = a << 29;
+    if (a < 0x00800000u) { hi = s; lo = 0u; }                        // zero, subnormal -> 0
+    if (a >= 0x7f800000u) { hi = s | 0x7ff00000u | ((a >> 3) & 0x000fffffu); }   // inf / NaN
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // double -> float, rounded to nearest (ties away from zero in magnitude; ties
@@ -148,35 +164,30 @@ __device__ __forceinline__ float d2f_int(double d) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(d);
     const unsigned long long a = u & 0x7fffffffffffffffULL;
     const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
-    if (a == 0ULL) return __uint_as_float(s);
-    // normal float results need 897 <= biased exponent <= 1150
-    if (a < (897ULL << 52) || a >= (1151ULL << 52)) return __double2float_rn(d);
-    unsigned long long t = (a >> 29) + ((a >> 28) & 1ULL);
-    t -= 896ULL << 23;
-    if (t >= (255ULL << 23)) return __double2float_rn(d);
-    return __uint_as_float(s | (unsigned)t);
+    // (t wraps around below the normal float range; the underflow rule is applied last)
+    unsigned long long t = (a >> 29) + ((a >> 28) & 1ULL) - (896ULL << 23);
+    unsigned r = (unsigned)t;
+    if (a >= (1151ULL << 52) || t >= (255ULL << 23)) r = 0x7f800000u;  // overflow -> inf
+    if (a < (897ULL << 52)) r = 0u;                                    // below normal floats -> 0
+    if (a > 0x7ff0000000000000ULL) r = 0x7fc00000u;                     // NaN
+    return __uint_as_float(s | r);
 }
 
 // double -> (hi, lo) floats with hi + lo == d to about 2^-48 relative: hi is d
-// truncated to 24 significant bits (exact in float), lo the remaining 29
-// bits rounded to a float.
+// truncated to 24 significant bits (exact in float), lo the remaining 29 bits
+// rounded to a float.  Outside the normal float range: (d2f_int(d), 0).
 __device__ __forceinline__ float2 d2ff_int(double d) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(d);
     const unsigned long long a = u & 0x7fffffffffffffffULL;
     const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
-    if (a == 0ULL) return make_float2(__uint_as_float(s), 0.0f);
-    if (a < (897ULL << 52) || a >= (1151ULL << 52)) {
-        float hi = __double2float_rz(d);
-        return make_float2(hi, __double2float_rn(d - (double)hi));
-    }
     const unsigned e = (unsigned)(a >> 52);
-    const float hi = __uint_as_float(s | (unsigned)((a >> 29) - (896ULL << 23)));
-    const unsigned mlo = (unsigned)(a & 0x1fffffffULL);   // d - hi = mlo * 2^(e - 1075)
-    float lo = 0.0f;
-    if (mlo != 0u && e > 948u) {                          // 2^(e-1075) a normal float
-        lo = __uint2float_rn(mlo) * __uint_as_float((e - 1075u + 127u) << 23);
-        lo = __uint_as_float(__float_as_uint(lo) | s);
-    }
+    const bool normal = a >= (897ULL << 52) && a < (1151ULL << 52);
+    float hi = __uint_as_float(s | (unsigned)((a >> 29) - (896ULL << 23)));
+    const unsigned mlo = (unsigned)(a & 0x1fffffffULL);               // d - hi = mlo * 2^(e - 1075)
+    float lo = __uint2float_rn(mlo) * __uint_as_float(((e > 948u ? e : 949u) - 948u) << 23);
+    lo = __uint_as_float(__float_as_uint(lo) | s);
+    if (e <= 948u) lo = 0.0f;
+    if (!normal) { hi = d2f_int(d); lo = 0.0f; }
     return make_float2(hi, lo);
 }
 

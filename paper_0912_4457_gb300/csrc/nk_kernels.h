@@ -46,7 +46,8 @@ struct Outer {
     long N;          // vector length (12 V complex)
     int n_rhs, k, nblk, npart;
     int two_sided;
-    int q_ring;      // 0: Q holds all k vectors [rhs][k][N]; 1: ring [rhs][3][N] (double pass)
+    int q_ring;      // 0: Q holds all k vectors (+1 scratch) [rhs][k+1][N]; 1: ring [rhs][3][N] (double pass)
+    int qcols;       // vectors per RHS in Q: k + 1 or 3
     double2* Q;      // right basis q_j
     double2* P;      // left vectors p_j, ring [rhs][3][N] (two-sided)
     float2* q32;     // FP32 copy of the newest q, [rhs][N]
@@ -65,7 +66,7 @@ struct Outer {
 };
 
 __host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {
-    return o.Q + (o.q_ring ? ((size_t)rhs * 3 + j % 3) : ((size_t)rhs * o.k + j)) * o.N;
+    return o.Q + ((size_t)rhs * o.qcols + (o.q_ring ? j % 3 : j)) * o.N;
 }
 __host__ __device__ inline double2* outer_p(const Outer& o, int rhs, int j) {
     return o.P + ((size_t)rhs * 3 + j % 3) * o.N;

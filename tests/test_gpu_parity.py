@@ -83,6 +83,28 @@ def test_dslash_fp64_fp32(dims, mu, dagger):
     ctx.close()
 
 
+def test_dslash_zeros_and_tiny_values():
+    """Exact zeros and values far below the float range (flushed to zero by
+    the FP32 / two-float input conversion) must not produce inf or NaN."""
+    dims = (4, 4, 4, 4)
+    ctx = make_ctx(dims, 11, 0.3)
+    U = links(dims, 11)
+    x = inputs.gaussian_sources(dims, 15, n_rhs=2)
+    x[0, ::3] = 0.0
+    x[1, ::5] *= 1e-200
+    x[1, 1::7] = 0.0
+    xd = to_dev(x)
+    for prec, tol in ((64, 1e-13), (48, 2e-13), (32, 2e-6)):
+        out = torch.zeros_like(xd)
+        ctx.dslash_dev(xd, out, 2, precision=prec)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        for i in range(2):
+            assert rel(got[i], dirac.apply_A(x[i], U, dims, 0.3, M_W)) < tol, (prec, i)
+    ctx.close()
+
+
 def test_dslash_periodic_t_and_many_vectors():
     dims = (4, 2, 2, 6)
     ctx = make_ctx(dims, 13, 0.5, antiperiodic=False)
