@@ -354,6 +354,27 @@ def run_gpu(args, w, rank, world, local_rank):
     return 0
 
 
+def run_ncu(args, w):
+    """--warmup kernel-by-kernel solves, then one more: the launches an ncu
+    launch list or capture selects from (skip the warm-up ones with -s)."""
+    import torch
+    import paper_0912_4457_gb300 as nk
+    U, b_host = make_inputs(w)
+    ctx = nk.Context(w["dims"])
+    ctx.load_links(U)
+    ctx.set_mu_mw(w["mu"], w["m_w"])
+    ctx.set_precision(w.get("j0", -1))
+    flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_NO_GRAPH
+    b_dev = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
+    y_dev = torch.zeros_like(b_dev)
+    for _ in range(args.warmup + 1):
+        st, _ = ctx.sign_apply_dev(b_dev, y_dev, w["n_rhs"], w["k"], w["ell"], flags=flags)
+    torch.cuda.synchronize()
+    print("launches per solve %d, device ms %.3f" % (st["launches"], st["t_total_ms"]), file=sys.stderr)
+    ctx.close()
+    return 0
+
+
 def _lib_host_solve(ctx, bp, yp, k, ell, flags):
     import ctypes
     from paper_0912_4457_gb300 import nksign
@@ -408,6 +429,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--warmup-ref", type=int, default=0)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--mode", choices=["bench", "ncu"], default="bench",
+                    help="ncu: run --warmup solves and then one solve kernel by kernel (no graph, no oracle, "
+                         "no output line), for launch lists and captures under ncu")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -416,6 +440,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w, rank)
+    if args.mode == "ncu":
+        return run_ncu(args, w)
     if world > 1:
         import torch
         import torch.distributed as dist
