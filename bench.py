@@ -406,7 +406,7 @@ def dominant_roofline(dom, tc, nc, w, peaks):
         return {"kernel": "k_step2", "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": tf / fp64_peak, "traffic": None, "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": (112 if two else 56) * N * n_rhs}
-    if dom == "dslash":
+    if dom in ("dslash", "dslash_df", "dslash64"):
         nv = (2 if two else 1) * n_rhs
         b = V * (288 + nv * (96 + 192)) + V * n_rhs * 2 * 192
         gbs = b / (ms * 1e-3) / 1e9

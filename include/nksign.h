@@ -66,11 +66,11 @@ extern "C" {
 #define NK_MAX_RHS 12
 
 /* Kernel classes of a solve, for nk_stats.t_class_ms / n_class. */
-#define NK_CLASS_DSLASH 0   /* Wilson stencil A v (and A^dagger w) fused with
-                               r = Av - c v_prev and the H(j,j) reduction */
-#define NK_CLASS_STEP1 1    /* (unused: fused into NK_CLASS_DSLASH) */
-#define NK_CLASS_STEP2 2    /* r -= H(j,j) v, beta / delta, FP32 copies */
-#define NK_CLASS_STEP3 3    /* (unused: the basis is kept unnormalised) */
+#define NK_CLASS_DSLASH 0     /* FP32 Wilson stencil A v (and A^dagger w) fused with
+                                 r = Av - c v_prev and the H(j,j) reduction */
+#define NK_CLASS_DSLASH_DF 1  /* the same with the two-float (about 48-bit) stencil */
+#define NK_CLASS_STEP2 2      /* r -= H(j,j) v, beta / delta, stencil input copies */
+#define NK_CLASS_DSLASH64 3   /* the same with the FP64 stencil */
 #define NK_CLASS_INNER 4    /* p estimate, LU of p H_k, inner Lanczos */
 #define NK_CLASS_RHI 5      /* Roberts-Higham iteration */
 #define NK_CLASS_LIFT 6     /* V_l s and |x| V_k c */
@@ -82,7 +82,9 @@ typedef struct nk_ctx nk_ctx;
 /* Per-solve statistics (all optional to read). */
 typedef struct nk_stats {
     int n_rhs;
-    int k_used;                        /* outer Krylov size used */
+    int k_used;                        /* outer Krylov size used (largest over the RHS) */
+    int k_rhs[NK_MAX_RHS];             /* outer Krylov size used per RHS (adaptive k) */
+    int checks;                        /* adaptive k: convergence checks made */
     int ell_used;                      /* inner Krylov size used */
     int rhi_iters[NK_MAX_RHS];         /* Roberts-Higham iterations per RHS */
     int status[NK_MAX_RHS];            /* NK_OK or NK_E* per RHS */
@@ -120,6 +122,11 @@ int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
  * preconditioning, inner projection, RHi, lift) stays FP64. */
 int nk_set_precision(nk_ctx* ctx, int j0);
 
+/* Adaptive k: the outer size at the first convergence check (even; 0 selects
+ * NK_ADAPT_FIRST(l)).  A predicted k (nk_mlp_predict) goes here, so that a
+ * good prediction costs a single check. */
+int nk_set_adapt_start(nk_ctx* ctx, int k_first);
+
 /*
  * y = sgn(A) b by the nested Krylov-Ritz method (Eq. nested; App. C steps
  * 2-6 without deflation):
@@ -133,10 +140,20 @@ int nk_set_precision(nk_ctx* ctx, int j0);
  * b, y: HOST arrays of n_rhs vectors (1 <= n_rhs <= NK_MAX_RHS), each solved
  * independently (own recurrence coefficients) but batched through one
  * stencil launch per step.  k, l even (Fig. 7 caption), 2 <= l <= k, k <= 1536, l <= 256.
- * tol must be 0 (fixed k).  flags: NK_FP64 or NK_MIXED, optionally
- * NK_DOUBLE_PASS / NK_NO_GRAPH.  st may be NULL.  Blocks until y is written.
- * Returns NK_EBREAKDOWN / NK_ERHI when any RHS failed (st->status says which;
- * the other RHS are still valid). */
+ * tol = 0: fixed k.  tol > 0: adaptive k (the paper fixes k; this stopping
+ * rule is the library's): k is the maximum, the outer recurrence is
+ * checked every NK_ADAPT_STEP steps from NK_ADAPT_FIRST(l) on (or from
+ * nk_set_adapt_start), each check computes c = V_l sgn(H_l) e_1 from the
+ * current H_k, and a RHS stops growing k once |c - c_prev| <= tol |c| at two
+ * consecutive checks (its result is taken at that k); a RHS that never
+ * meets it uses k_max and gets status NK_ENOTCONV (its result is still
+ * written).  Adaptive solves are launched kernel by kernel.  flags: NK_FP64
+ * or NK_MIXED, optionally NK_DOUBLE_PASS (fixed k only) / NK_NO_GRAPH.  st
+ * may be NULL.  Blocks until y is written.  Returns NK_EBREAKDOWN / NK_ERHI /
+ * NK_ENOTCONV when any RHS failed (st->status says which; the other RHS are
+ * still valid). */
+#define NK_ADAPT_STEP 64
+#define NK_ADAPT_FIRST(l) ((((l) + 63) / 64) * 64)
 int nk_sign_apply(nk_ctx* ctx, const double* b, int n_rhs, int k, int ell, double tol,
                   double p, unsigned flags, double* y, nk_stats* st);
 

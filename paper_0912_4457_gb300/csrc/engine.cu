@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <string>
@@ -43,6 +44,7 @@ struct nk_ctx {
     double mu = 0.0, m_w = 0.0;
     bool mu_set = false;
     int j0 = -1;
+    int adapt_start = 0;   // adaptive k: first check (0: NK_ADAPT_FIRST(l))
     bool links = false;
     double2* U64 = nullptr;
     float2* U32 = nullptr;
@@ -105,6 +107,9 @@ struct Layout {
     nk::Inner in;
     double2* y_soa;
     double2* cp;      // lift coefficients c'_j, [rhs][k]
+    double2* c_prev;  // adaptive k: c of the previous check (finally the accepted c), [rhs][k]
+    double2* dn;      // adaptive k: (|c - c_prev|, |c|) per RHS
+    int* kused;       // basis vectors that enter the lift, per RHS
     size_t total;
 };
 
@@ -157,6 +162,9 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     in.s = (double2*)take(sizeof(double2) * (size_t)ell * n_rhs);
     in.rhi_iters = (int*)take(sizeof(int) * n_rhs);
     in.c = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
+    L.c_prev = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
+    L.dn = (double2*)take(sizeof(double2) * n_rhs);
+    L.kused = (int*)take(sizeof(int) * n_rhs);
     in.status = o.status;
     in.timeout = (int*)take(sizeof(int));
     L.total = off;
@@ -182,7 +190,7 @@ int check_solve_args(nk_ctx* c, int n_rhs, int k, int ell, double tol) {
     if (ell > k) return fail(c, NK_EINVAL, "l must not exceed k");
     if (ell > 256) return fail(c, NK_EINVAL, "l must not exceed 256");
     if (k > nk::kMaxInnerK) return fail(c, NK_EINVAL, "k must not exceed 1536");
-    if (tol != 0.0) return fail(c, NK_EINVAL, "tol must be 0 (fixed k)");
+    if (!(tol >= 0.0) || !(tol < 1.0)) return fail(c, NK_EINVAL, "tol must be in [0, 1)");
     return NK_OK;
 }
 
@@ -222,25 +230,36 @@ struct Launcher {
     }
 };
 
-// Enqueues the outer recurrence: norm/init, then per step the fused stencil
-// kernel and step 2 (the FP32 stencil from step j0 on in mixed mode).
-void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& L) {
+// The outer recurrence: norm/init, then per step the fused stencil kernel and
+// step 2 (mixed mode: the two-float stencil before step j0, FP32 from j0 on).
+int copy_mode_for(bool mixed, int j0, int j) {
+    return !mixed ? nk::kCopyNone : (j < j0 ? nk::kCopyDF : nk::kCopy32);
+}
+
+void enqueue_outer_init(const nk::Outer& o, bool mixed, int j0, Launcher& L) {
+    cudaStream_t st = L.st;
+    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_mode_for(mixed, j0, 0), st); });
+}
+
+// steps j in [j_begin, j_end); step 2 runs for every step but the last of the
+// whole recurrence (j = o.k - 1)
+void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int j_begin, int j_end, Launcher& L) {
     const Geom g = geom_of(c);
     const double kap = kappa_of(c);
     cudaStream_t st = L.st;
-    // the input copy the stencil of step j reads: two-float before j0, FP32 after
-    auto copy_for = [&](int j) { return !mixed ? nk::kCopyNone : (j < j0 ? nk::kCopyDF : nk::kCopy32); };
-    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_for(0), st); });
-    for (int j = 0; j < o.k; ++j) {
+    for (int j = j_begin; j < j_end; ++j) {
         const int prec = !mixed ? 64 : (j < j0 ? 48 : 32);
         const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
-        L.run(NK_CLASS_DSLASH, 1, [&] {
-            nk::launch_dslash_step1(prec, U, g, o, j, kap,
-                                    c->mu, st);
-        });
+        const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
+        L.run(cls, 1, [&] { nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
         if (j < o.k - 1)
-            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step2(o, j, copy_for(j + 1), st); });
+            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), st); });
     }
+}
+
+void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& L, int steps = -1) {
+    enqueue_outer_init(o, mixed, j0, L);
+    enqueue_outer_steps(c, o, mixed, j0, 0, steps < 0 ? o.k : steps, L);
 }
 
 // b (ABI layout, device) -> q_0 of every RHS
@@ -264,6 +283,7 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     nk::Inner in = Lw.in;
     in.p_fixed = p;
     enqueue_load_sources(c, o, b_dev, n_rhs, L);
+    L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_fill_int(Lw.kused, n_rhs, o.k, st); });
     enqueue_outer(c, o, mixed, j0, L);
     L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_lanczos(in, st); });
     cudaError_t e = cudaSuccess;
@@ -271,7 +291,7 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     if (e != cudaSuccess) return e;
     L.run(NK_CLASS_LIFT, 2, [&] {
         nk::launch_inner_combine(in, st);
-        nk::launch_lift_coef(o, in.c, Lw.cp, st);
+        nk::launch_lift_coef(o, in.c, Lw.kused, Lw.cp, st);
     });
     if (dp) {
         // second pass: regenerate the identical basis and accumulate y = sum_j c'_j q_j
@@ -281,7 +301,96 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
         enqueue_load_sources(c, o, b_dev, n_rhs, L);
         enqueue_outer(c, o, mixed, j0, L);
     }
-    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, Lw.cp, Lw.y_soa, st); });
+    L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, Lw.cp, Lw.kused, Lw.y_soa, st); });
+    L.run(NK_CLASS_OTHER, 1, [&] {
+        nk::launch_soa_to_abi(Lw.y_soa, c->N, (double2*)y_dev, c->N, overlap ? (const double2*)b_dev : nullptr,
+                              c->N, c->V, n_rhs, st);
+    });
+    return cudaGetLastError();
+}
+
+// Adaptive k (tol > 0): the outer recurrence runs in chunks; at each check the
+// inner part gives c = V_l sgn(H_l) e_1 from the current H_k (the leading k x k
+// block), and a RHS is frozen at that k once |c - c_prev| <= tol |c| at two
+// consecutive checks.  Launched kernel by kernel (host decisions between chunks).
+cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_dev, int n_rhs, int kmax, int ell,
+                           double tol, double p, unsigned flags, bool overlap, Launcher& L,
+                           std::vector<int>& kused_h, std::vector<int>& notconv, int& checks) {
+    cudaStream_t st = L.st;
+    const bool mixed = (flags & NK_MIXED) != 0;
+    const int j0 = effective_j0(c, kmax);
+    nk::Outer o = Lw.o;
+    nk::Inner in = Lw.in;
+    in.p_fixed = p;
+    in.kstride = kmax;
+    enqueue_load_sources(c, o, b_dev, n_rhs, L);
+    enqueue_outer_init(o, mixed, j0, L);
+    cudaMemsetAsync(Lw.c_prev, 0, sizeof(double2) * (size_t)kmax * n_rhs, st);
+    int first = c->adapt_start > 0 ? c->adapt_start : NK_ADAPT_FIRST(ell);
+    first = std::max(2, std::min(kmax, first + (first & 1)));
+    std::vector<int> hits(n_rhs, 0), frozen(n_rhs, 0), status(n_rhs, 0);
+    std::vector<double2> dn(n_rhs);
+    kused_h.assign(n_rhs, kmax);
+    notconv.assign(n_rhs, 1);
+    checks = 0;
+    int j = 0, kc = first;
+    while (true) {
+        enqueue_outer_steps(c, o, mixed, j0, j, kc, L);
+        nk::Inner ic = in;
+        ic.k = kc;
+        ic.ell = std::min(ell, kc);
+        L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_lanczos(ic, st); });
+        cudaError_t e = cudaSuccess;
+        L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(ic, st); });
+        if (e != cudaSuccess) return e;
+        L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_inner_combine(ic, st); });
+        L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_adapt_delta(o, in.c, Lw.c_prev, kc, Lw.dn, st); });
+        e = cudaMemcpyAsync(dn.data(), Lw.dn, sizeof(double2) * n_rhs, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), o.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        ++checks;
+        bool all = true, changed = false;
+        for (int r = 0; r < n_rhs; ++r) {
+            if (frozen[r]) continue;
+            if (status[r] != nk::kStatusOK) {   // zero source or failure: nothing more to do
+                frozen[r] = 1;
+                kused_h[r] = kc;
+                notconv[r] = 0;
+                continue;
+            }
+            const double rel = dn[r].y > 0.0 ? dn[r].x / dn[r].y : 0.0;
+            hits[r] = rel <= tol ? hits[r] + 1 : 0;
+            if (hits[r] >= 2) {
+                frozen[r] = 1;
+                kused_h[r] = kc;
+                notconv[r] = 0;
+                status[r] = nk::kStatusConverged;
+                changed = true;
+            } else {
+                all = false;
+            }
+        }
+        if (all || kc >= kmax) break;
+        if (changed) {
+            e = cudaMemcpyAsync(o.status, status.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+        }
+        j = kc;
+        kc = std::min(kmax, kc + NK_ADAPT_STEP);
+    }
+    // frozen RHS rejoin the lift; the accepted c of every RHS is in c_prev
+    for (int r = 0; r < n_rhs; ++r)
+        if (status[r] == nk::kStatusConverged) status[r] = nk::kStatusOK;
+    cudaError_t e = cudaMemcpyAsync(o.status, status.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Lw.kused, kused_h.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    L.run(NK_CLASS_LIFT, 2, [&] {
+        nk::launch_lift_coef(o, Lw.c_prev, Lw.kused, Lw.cp, st);
+        nk::launch_lift(o, Lw.cp, Lw.kused, Lw.y_soa, st);
+    });
     L.run(NK_CLASS_OTHER, 1, [&] {
         nk::launch_soa_to_abi(Lw.y_soa, c->N, (double2*)y_dev, c->N, overlap ? (const double2*)b_dev : nullptr,
                               c->N, c->V, n_rhs, st);
@@ -321,11 +430,19 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     NK_CUDA(c, cudaEventCreate(&e1));
     NK_CUDA(c, cudaEventRecord(e0, st));
     const bool profile = (flags & NK_PROFILE) != 0;
-    const bool use_graph = (flags & (NK_NO_GRAPH | NK_PROFILE)) == 0;
+    const bool adaptive = tol > 0.0;
+    if (adaptive && dp) return fail(c, NK_EINVAL, "adaptive k (tol > 0) needs single-pass storage");
+    const bool use_graph = !adaptive && (flags & (NK_NO_GRAPH | NK_PROFILE)) == 0;
     Launcher L;
     L.st = st;
     L.profile = profile;
-    if (use_graph) {
+    std::vector<int> kused_h(n_rhs, k), notconv(n_rhs, 0);
+    int checks = 0;
+    if (adaptive) {
+        cudaError_t e = solve_adaptive(c, Lw, b_dev, y_dev, n_rhs, k, ell, tol, p, flags, overlap, L, kused_h,
+                                       notconv, checks);
+        if (e != cudaSuccess) return cuda_fail(c, e, "adaptive solve");
+    } else if (use_graph) {
         GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, flags, p, c->mu, c->m_w, overlap ? 1 : 0};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
@@ -368,18 +485,22 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int worst = NK_OK;
+    std::vector<int> codes(n_rhs);
     for (int r = 0; r < n_rhs; ++r) {
-        int code = status_to_code(status[r]);
-        if (code != NK_OK && worst == NK_OK) worst = code;
+        codes[r] = status_to_code(status[r]);
+        if (codes[r] == NK_OK && notconv[r]) codes[r] = NK_ENOTCONV;
+        if (codes[r] != NK_OK && worst == NK_OK) worst = codes[r];
     }
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->n_rhs = n_rhs;
-        stats->k_used = k;
+        stats->k_used = *std::max_element(kused_h.begin(), kused_h.end());
         stats->ell_used = ell;
+        stats->checks = checks;
         for (int r = 0; r < n_rhs; ++r) {
+            stats->k_rhs[r] = kused_h[r];
             stats->rhi_iters[r] = iters[r];
-            stats->status[r] = status_to_code(status[r]);
+            stats->status[r] = codes[r];
             stats->p[r] = pv[r];
             stats->z_min[r] = zmin[r];
             stats->z_max[r] = zmax[r];
@@ -397,6 +518,7 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     }
     if (worst == NK_EBREAKDOWN) return fail(c, worst, "two-sided Lanczos: serious breakdown (delta = 0)");
     if (worst == NK_ERHI) return fail(c, worst, "Roberts-Higham iteration did not converge (or p H_k singular)");
+    if (worst == NK_ENOTCONV) return fail(c, worst, "adaptive k: tolerance not met at k_max for some RHS");
     return worst;
 }
 
@@ -478,6 +600,12 @@ int nk_set_precision(nk_ctx* c, int j0) {
     return NK_OK;
 }
 
+int nk_set_adapt_start(nk_ctx* c, int k_first) {
+    if (!c || k_first < 0) return NK_EINVAL;
+    c->adapt_start = k_first;
+    return NK_OK;
+}
+
 int nk_sign_apply_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
                       unsigned flags, double* y_dev, nk_stats* st, void* stream) {
     if (!c || !b_dev || !y_dev) return NK_EINVAL;
@@ -497,7 +625,7 @@ static int host_solve(nk_ctx* c, const double* b, int n_rhs, int k, int ell, dou
     double* yd = bd + 2 * (size_t)c->N * NK_MAX_RHS;
     NK_CUDA(c, cudaMemcpy(bd, b, bytes, cudaMemcpyHostToDevice));
     rc = solve_dev(c, bd, n_rhs, k, ell, tol, p, flags, yd, st, 0, overlap);
-    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI) return rc;
+    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI && rc != NK_ENOTCONV) return rc;
     cudaError_t e = cudaMemcpy(y, yd, bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy y");
     return rc;

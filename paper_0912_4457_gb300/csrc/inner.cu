@@ -368,9 +368,10 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     const int rhs = blockIdx.x;
     const int k = in.k, L = in.ell;
     if (in.status[rhs] != kStatusOK) return;
-    const double2* al = in.alpha + (size_t)rhs * k;
-    const double2* be = in.beta + (size_t)rhs * k;
-    const double2* ga = in.gamma + (size_t)rhs * k;
+    const int ks = in.kstride > 0 ? in.kstride : k;   // row stride of the outer H_k arrays and of c
+    const double2* al = in.alpha + (size_t)rhs * ks;
+    const double2* be = in.beta + (size_t)rhs * ks;
+    const double2* ga = in.gamma + (size_t)rhs * ks;
     // LU factors (in solve-ready form) and the two solve vectors in shared
     // memory.  While gttrf runs, d lives in t1, du in e and du2 in f.
     extern __shared__ __align__(16) unsigned char smem[];
@@ -756,7 +757,7 @@ __global__ void k_combine(Inner in) {
     const int rhs = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= in.k) return;
-    double2* c = in.c + (size_t)rhs * in.k;
+    double2* c = in.c + (size_t)rhs * (in.kstride > 0 ? in.kstride : in.k);
     if (in.status[rhs] != kStatusOK) { c[i] = mk(0.0, 0.0); return; }
     const double2* Vl = in.Vl + (size_t)rhs * in.ell * in.k;
     const double2* s = in.s + (size_t)rhs * in.ell;

@@ -147,18 +147,40 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
     }
 }
 
-// c'_j = |x| c_j / n_j: the lift coefficients on the unnormalised basis.
-__global__ void k_lift_coef(Outer o, const double2* __restrict__ c, double2* __restrict__ cp) {
+// c'_j = |x| c_j / n_j: the lift coefficients on the unnormalised basis
+// (zero from kused on, where the basis and its scales were never computed).
+__global__ void k_lift_coef(Outer o, const double2* __restrict__ c, const int* __restrict__ kused,
+                            double2* __restrict__ cp) {
     const int rhs = blockIdx.y;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= o.k) return;
     double2* out = cp + (size_t)rhs * o.k;
-    if (o.status[rhs] != kStatusOK) { out[j] = mk(0.0, 0.0); return; }
+    if (o.status[rhs] != kStatusOK || j >= kused[rhs]) { out[j] = mk(0.0, 0.0); return; }
     out[j] = cscale(cdiv(c[(size_t)rhs * o.k + j], scale_n(o, rhs, j)), o.xnorm[rhs]);
 }
 
+// per RHS: dn = (|c - c_prev|, |c|) over the first k entries; then c_prev <- c
+__global__ void k_adapt_delta(Outer o, const double2* __restrict__ c, double2* __restrict__ cprev, int k,
+                              double2* __restrict__ dn) {
+    __shared__ double2 sh[33];
+    const int rhs = blockIdx.x;
+    if (o.status[rhs] != kStatusOK) return;   // frozen or failed: keep its accepted c
+    const double2* cr = c + (size_t)rhs * o.k;
+    double2* pr = cprev + (size_t)rhs * o.k;
+    double d = 0.0, n = 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double2 a = cr[j], b = pr[j];
+        d += cnorm2(csub(a, b));
+        n += cnorm2(a);
+    }
+    double2 t = block_sum(mk(d, n), sh);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) pr[j] = cr[j];
+    if (threadIdx.x == 0) dn[rhs] = mk(sqrt(t.x), sqrt(t.y));
+}
+
 // y_r = sum_j c'_r[j] q_j  (reads every basis vector once)
-__global__ void __launch_bounds__(kThreads) k_lift(Outer o, const double2* __restrict__ cp, double2* __restrict__ y) {
+__global__ void __launch_bounds__(kThreads) k_lift(Outer o, const double2* __restrict__ cp,
+                                                    const int* __restrict__ kused, double2* __restrict__ y) {
     const int rhs = blockIdx.y;
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= o.N) return;
@@ -166,8 +188,9 @@ __global__ void __launch_bounds__(kThreads) k_lift(Outer o, const double2* __res
     if (o.status[rhs] != kStatusOK) { yo[i] = mk(0.0, 0.0); return; }
     const double2* cr = cp + (size_t)rhs * o.k;
     const double2* Qr = o.Q + (size_t)rhs * o.qcols * o.N;
+    const int ku = kused[rhs];
     double2 acc = mk(0.0, 0.0);
-    for (int j = 0; j < o.k; ++j) {
+    for (int j = 0; j < ku; ++j) {
         double2 cj = __ldg(cr + j);
         double2 v = Qr[(size_t)j * o.N + i];
         acc.x += cj.x * v.x - cj.y * v.y;
@@ -198,15 +221,28 @@ void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st) {
     else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
 }
 
-void launch_lift_coef(const Outer& o, const double2* c, double2* cp, cudaStream_t st) {
+void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st) {
     dim3 grid((o.k + 127) / 128, o.n_rhs);
-    k_lift_coef<<<grid, 128, 0, st>>>(o, c, cp);
+    k_lift_coef<<<grid, 128, 0, st>>>(o, c, kused, cp);
 }
 
-void launch_lift(const Outer& o, const double2* cp, double2* y, cudaStream_t st) {
+void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y, cudaStream_t st) {
     dim3 grid((unsigned)((o.N + kThreads - 1) / kThreads), o.n_rhs);
     if (o.q_ring) k_zero_bad<<<grid, kThreads, 0, st>>>(o, y);
-    else k_lift<<<grid, kThreads, 0, st>>>(o, cp, y);
+    else k_lift<<<grid, kThreads, 0, st>>>(o, cp, kused, y);
+}
+
+__global__ void k_fill_int(int* p, int n, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+void launch_fill_int(int* p, int n, int value, cudaStream_t st) {
+    k_fill_int<<<(n + 127) / 128, 128, 0, st>>>(p, n, value);
+}
+
+void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st) {
+    k_adapt_delta<<<o.n_rhs, 256, 0, st>>>(o, c, c_prev, k, dn);
 }
 
 }  // namespace nk

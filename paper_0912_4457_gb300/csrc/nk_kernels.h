@@ -87,6 +87,7 @@ constexpr int kStatusZeroSource = 1;  // |b| = 0: result is 0
 constexpr int kStatusBreakdown = 2;   // serious breakdown (or a zero beta)
 constexpr int kStatusRhi = 3;         // RHi did not converge / singular pivot
 constexpr int kStatusLU = 4;          // singular p H_k
+constexpr int kStatusConverged = 5;   // adaptive k: frozen at its converged size (skipped by the kernels)
 
 // Copy modes for the next stencil's input: none, FP32, two-float.
 constexpr int kCopyNone = 0, kCopy32 = 1, kCopyDF = 2;
@@ -97,13 +98,20 @@ void launch_dslash_step1(int precision, const void* U, const Geom& g, const Oute
                          double kappa, double mu, cudaStream_t st);
 int dslash_step1_blocks(const Geom& g);
 void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st);
-void launch_lift_coef(const Outer& o, const double2* c, double2* cp, cudaStream_t st);
-void launch_lift(const Outer& o, const double2* cp, double2* y, cudaStream_t st);
+// kused[rhs]: outer steps whose basis vectors enter the lift of that RHS (k or,
+// adaptive, the converged size); coefficients beyond it are zero.
+void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st);
+void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y, cudaStream_t st);
+void launch_fill_int(int* p, int n, int value, cudaStream_t st);
+// Adaptive k: per RHS (|c - c_prev|, |c|) over the first k entries, then c_prev <- c.
+void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st);
 
 // ---- inner part: p estimate, LU of p H_k, inner Lanczos, RHi, c = V_l s -------
 
 struct Inner {
     int n_rhs, k, ell;
+    int kstride;           // row stride of alpha/beta/gamma and c (0: k); the adaptive
+                           // mode runs the inner part on the leading k x k block of H
     int two_sided;
     const double2* alpha;  // outer H_k, [rhs][k]
     const double2* beta;

@@ -34,7 +34,7 @@ NK_NO_GRAPH = 0x10
 NK_PROFILE = 0x20
 NK_MAX_RHS = 12
 NK_NCLASS = 8
-CLASS_NAMES = ["dslash", "step1", "step2", "step3", "inner", "rhi", "lift", "other"]
+CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other"]
 
 ERROR_NAMES = {
     NK_EINVAL: "NK_EINVAL", NK_ENOMEM: "NK_ENOMEM", NK_EBREAKDOWN: "NK_EBREAKDOWN",
@@ -44,6 +44,7 @@ ERROR_NAMES = {
 
 EXPORTED = [
     "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision",
+    "nk_set_adapt_start",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
     "nk_destroy",
@@ -54,6 +55,8 @@ class NkStats(ctypes.Structure):
     _fields_ = [
         ("n_rhs", ctypes.c_int),
         ("k_used", ctypes.c_int),
+        ("k_rhs", ctypes.c_int * NK_MAX_RHS),
+        ("checks", ctypes.c_int),
         ("ell_used", ctypes.c_int),
         ("rhi_iters", ctypes.c_int * NK_MAX_RHS),
         ("status", ctypes.c_int * NK_MAX_RHS),
@@ -70,7 +73,8 @@ class NkStats(ctypes.Structure):
     def as_dict(self):
         n = self.n_rhs
         return {
-            "n_rhs": n, "k_used": self.k_used, "ell_used": self.ell_used,
+            "n_rhs": n, "k_used": self.k_used, "k_rhs": list(self.k_rhs[:n]), "checks": self.checks,
+            "ell_used": self.ell_used,
             "rhi_iters": list(self.rhi_iters[:n]), "status": list(self.status[:n]),
             "p": list(self.p[:n]), "z_min": list(self.z_min[:n]), "z_max": list(self.z_max[:n]),
             "xnorm": list(self.xnorm[:n]), "t_total_ms": self.t_total_ms,
@@ -105,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "nk_load_links_dev": ([P, P, P], I),
         "nk_set_mu_mw": ([P, D, D], I),
         "nk_set_precision": ([P, I], I),
+        "nk_set_adapt_start": ([P, I], I),
         "nk_sign_apply": ([P, dp, I, I, I, D, D, U, dp, ctypes.POINTER(NkStats)], I),
         "nk_sign_apply_dev": ([P, P, I, I, I, D, D, U, P, ctypes.POINTER(NkStats), P], I),
         "nk_overlap_apply": ([P, dp, I, I, I, D, U, dp, ctypes.POINTER(NkStats)], I),
@@ -200,6 +205,9 @@ class Context:
 
     def set_precision(self, j0: int):
         self._check(self._lib.nk_set_precision(self.h, int(j0)))
+
+    def set_adapt_start(self, k_first: int):
+        self._check(self._lib.nk_set_adapt_start(self.h, int(k_first)))
 
     # -- solves (host arrays) --------------------------------------------------
     def sign_apply(self, b, k, ell, tol=0.0, p=0.0, flags=NK_FP64, check=True):

@@ -345,6 +345,37 @@ def test_double_pass_graph_and_determinism(c1):
     ctx.close()
 
 
+@pytest.mark.parametrize("mu,kmax,ell,flags", [(0.0, 512, 64, NK_FP64), (0.3, 640, 96, NK_MIXED)])
+def test_adaptive_k_stops_and_matches_fixed_k(c1, mu, kmax, ell, flags):
+    """tol > 0: each RHS stops at its own k; the result equals the fixed-k
+    solve at that k bit for bit, and is within a few tol of the dense truth."""
+    dims, U, b, truth = c1
+    ctx = make_ctx(dims, 101, mu)
+    ctx.set_precision(160)   # the default switch k/4 would differ between k_max and k_used
+    b2 = np.stack([b[0], inputs.gaussian_sources(dims, 777)[0]])
+    y, st, rc = ctx.sign_apply(b2, kmax, ell, tol=1e-8, flags=flags)
+    assert rc == 0
+    ku = st["k_rhs"]
+    assert all(64 <= kk < kmax for kk in ku) and st["checks"] >= 2
+    assert rel(y[0], truth[mu]) < 2e-8
+    for r in range(2):
+        yf, _, _ = ctx.sign_apply(b2[r:r + 1], ku[r], ell, flags=flags)
+        assert np.array_equal(y[r], yf[0])
+    ctx.close()
+
+
+def test_adaptive_k_not_converged():
+    dims = (4, 4, 4, 4)
+    ctx = make_ctx(dims, 101, 0.3)
+    b = inputs.gaussian_sources(dims, 201)
+    y, st, rc = ctx.sign_apply(b, 192, 64, tol=1e-13, check=False)
+    assert rc == nksign.NK_ENOTCONV and st["status"][0] == nksign.NK_ENOTCONV
+    assert st["k_rhs"][0] == 192
+    yf, _, _ = ctx.sign_apply(b, 192, 64)
+    assert np.array_equal(y, yf)
+    ctx.close()
+
+
 def test_device_api_and_zero_source():
     dims = (4, 4, 4, 4)
     ctx = make_ctx(dims, 101, 0.0)
