@@ -123,7 +123,7 @@ int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
 int nk_set_precision(nk_ctx* ctx, int j0);
 
 /* Adaptive k: the outer size at the first convergence check (even; 0 selects
- * NK_ADAPT_FIRST(l)).  A predicted k (nk_mlp_predict) goes here, so that a
+ * NK_ADAPT_FIRST(l)).  A predicted k (nk_predict_sizes) goes here, so that a
  * good prediction costs a single check. */
 int nk_set_adapt_start(nk_ctx* ctx, int k_first);
 
@@ -195,6 +195,54 @@ int nk_outer_lanczos_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, uns
 int nk_inner_sign(nk_ctx* ctx, const double* alpha, const double* beta, const double* gamma,
                   int n_rhs, int k, int ell, double p, int hermitian, double* c,
                   nk_stats* st);
+
+/*
+ * Learned subspace sizes.  The paper chooses k and l by hand (Sec. 4.2-4.3);
+ * this predictor is the library's: a 16 -> 64 -> 64 -> 2 perceptron (tanh,
+ * tanh, linear; FP32) from NK_MLP_IN features of the operator and source to
+ * (log2 k, log2 l) reaching a tolerance, trained on runs of the method
+ * itself.  Forward pass, backward pass (mean squared error of the
+ * standardised outputs) and Adam updates are CUDA kernels.  Host arrays;
+ * the calls block.  Parameter layout: W1[64][16], b1[64], W2[64][64], b2[64],
+ * W3[2][64], b3[2] (row = output unit).
+ */
+#define NK_MLP_IN 16
+#define NK_MLP_HIDDEN 64
+#define NK_MLP_OUT 2
+#define NK_MLP_PARAMS (64 * 16 + 64 + 64 * 64 + 64 + 2 * 64 + 2)
+typedef struct nk_mlp nk_mlp;
+/* Glorot-uniform weights from `seed` (splitmix64), zero biases, identity
+ * standardisation.  Uses the current CUDA device. */
+int nk_mlp_create(unsigned long long seed, nk_mlp** out);
+/* Standardisation: inputs x -> (x - xmu)/xsd, targets y -> (y - ymu)/ysd. */
+int nk_mlp_set_norm(nk_mlp* m, const float* xmu, const float* xsd, const float* ymu, const float* ysd);
+int nk_mlp_get_params(nk_mlp* m, float* params);          /* NK_MLP_PARAMS floats */
+int nk_mlp_set_params(nk_mlp* m, const float* params);    /* also resets the Adam state */
+/* Loss and gradient (w.r.t. the parameters) for n <= 256 samples X[n][16], Y[n][2]. */
+int nk_mlp_loss_grad(nk_mlp* m, const float* X, const float* Y, int n, float* loss, float* grad);
+/* `epochs` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) on n <= 256
+ * samples; loss_hist (nullable) receives the loss before each step. */
+int nk_mlp_train(nk_mlp* m, const float* X, const float* Y, int n, int epochs, float lr, float* loss_hist);
+/* Predictions Y[n][2] (de-standardised) for X[n][16]. */
+int nk_mlp_forward(nk_mlp* m, const float* X, int n, float* Y);
+const char* nk_mlp_last_error(const nk_mlp* m);
+void nk_mlp_destroy(nk_mlp* m);
+
+/* The NK_MLP_IN predictor features of one DEVICE source b_dev (ABI layout):
+ *  0 mu, 1 m_w, 2 log10 V, 3 mean plaquette (1/3) Re tr U_mu(x)^+ U_nu(x+mu)^+
+ *  U_mu(x+nu) U_nu(x) (gauge invariant in the hop convention of Sec. 2),
+ *  then from 32 steps of the outer recurrence (App. A / B, FP64 stencil) and
+ *  the inner part on H_32 (l = 32):
+ *  4 log10 z_min, 5 log10 z_max, 6 log10(z_max / z_min), 7 log10 p (Eq. popt),
+ *  8 mean Re H(j,j), 9 std Re H(j,j), 10 max |Im H(j,j)|, 11 mean |H(j+1,j)|,
+ *  12 std |H(j+1,j)|, 13 least-squares slope of log|H(j+1,j)| over j,
+ *  14 log10(|c_24..31| / |c|) of c = V_l sgn(H_l) e_1, 15 RHi iterations.
+ * Blocks. */
+int nk_features(nk_ctx* ctx, const double* b_dev, float* features, void* stream);
+
+/* Predicted sizes for one DEVICE source: features -> predictor -> k (even,
+ * clamped to [64, k_max]) and l (even, clamped to [16, min(k, 256)]). */
+int nk_predict_sizes(nk_ctx* ctx, nk_mlp* m, const double* b_dev, int k_max, int* k, int* ell, void* stream);
 
 /* No-allocation variant of nk_inner_sign (the paper has no counterpart: this
  * is a deployment entry point, not a step of the method).  For callers that

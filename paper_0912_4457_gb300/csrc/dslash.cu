@@ -469,3 +469,69 @@ void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_str
 }
 
 }  // namespace nk
+
+namespace nk {
+
+// ---- mean plaquette (predictor feature) ----------------------------------------
+// (1/3) Re tr U_mu(x)^+ U_nu(x+mu)^+ U_mu(x+nu) U_nu(x), summed over the six
+// planes mu < nu of each site; one partial sum per block.  In the hop
+// convention of Sec. 2 the link U_{x,+nu} transforms as W(x+nu) U W(x)^+, so
+// this is the gauge-invariant closed loop.
+// c = op(a) op(b), op = identity or conjugate transpose
+__device__ __forceinline__ void su3_mul(const double2 a[3][3], bool adag, const double2 b[3][3], bool bdag,
+                                        double2 c[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const double2 x = adag ? make_double2(a[l][i].x, -a[l][i].y) : a[i][l];
+                const double2 y = bdag ? make_double2(b[j][l].x, -b[j][l].y) : b[l][j];
+                s.x += x.x * y.x - x.y * y.y;
+                s.y += x.x * y.y + x.y * y.x;
+            }
+            c[i][j] = s;
+        }
+}
+
+__global__ void k_plaquette(const double2* __restrict__ U, Geom g, double* __restrict__ partial) {
+    __shared__ double sh[33];
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (site < g.V) {
+        const int L[4] = {g.Lx, g.Ly, g.Lz, g.Lt};
+        const int stride[4] = {1, g.Lx, g.Lx * g.Ly, g.Lx * g.Ly * g.Lz};
+        int c[4];
+        int r = site;
+        for (int d = 0; d < 4; ++d) { c[d] = r % L[d]; r /= L[d]; }
+        for (int mu = 0; mu < 4; ++mu) {
+            const int xmu = c[mu] == L[mu] - 1 ? site - (L[mu] - 1) * stride[mu] : site + stride[mu];
+            for (int nu = mu + 1; nu < 4; ++nu) {
+                const int xnu = c[nu] == L[nu] - 1 ? site - (L[nu] - 1) * stride[nu] : site + stride[nu];
+                double2 A[3][3], B[3][3], C[3][3], D[3][3], T1[3][3], T2[3][3];
+                for (int e = 0; e < 9; ++e) {
+                    A[e / 3][e % 3] = U[(size_t)(mu * 9 + e) * g.V + site];
+                    B[e / 3][e % 3] = U[(size_t)(nu * 9 + e) * g.V + xmu];
+                    C[e / 3][e % 3] = U[(size_t)(mu * 9 + e) * g.V + xnu];
+                    D[e / 3][e % 3] = U[(size_t)(nu * 9 + e) * g.V + site];
+                }
+                su3_mul(A, true, B, true, T1);
+                su3_mul(T1, false, C, false, T2);
+                su3_mul(T2, false, D, false, T1);
+                acc += (T1[0][0].x + T1[1][1].x + T1[2][2].x) / 3.0;
+            }
+        }
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+int plaquette_blocks(const Geom& g) { return (g.V + 127) / 128; }
+
+void launch_plaquette(const double2* U, const Geom& g, double* partial, cudaStream_t st) {
+    k_plaquette<<<plaquette_blocks(g), 128, 0, st>>>(U, g, partial);
+}
+
+}  // namespace nk

@@ -783,6 +783,102 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     return NK_OK;
 }
 
+int nk_features(nk_ctx* c, const double* b_dev, float* features, void* stream) {
+    if (!c || !b_dev || !features) return c ? fail(c, NK_EINVAL, "null pointer") : NK_EINVAL;
+    if (!c->links || !c->mu_set) return fail(c, NK_ESTATE, "links or (mu, m_w) not set");
+    const int k = 32, ell = 32;
+    std::vector<double> al(2 * k), be(2 * k), ga(2 * k), cf(2 * k);
+    double xn = 0.0;
+    int rc = nk_outer_lanczos_dev(c, b_dev, 1, k, NK_FP64, al.data(), be.data(), ga.data(), &xn, stream);
+    if (rc) return rc;
+    if (!(xn > 0.0)) return fail(c, NK_EINVAL, "zero source");
+    nk_stats ist;
+    rc = nk_inner_sign(c, al.data(), be.data(), ga.data(), 1, k, ell, 0.0, c->mu == 0.0 ? 1 : 0, cf.data(), &ist);
+    if (rc) return rc;
+
+    // mean plaquette: per-block partial sums, summed here in a fixed order
+    const Geom g = geom_of(c);
+    const int nb = nk::plaquette_blocks(g);
+    rc = ensure(c, c->staging, std::max(c->staging.bytes, sizeof(double) * (size_t)nb));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    nk::launch_plaquette(c->U64, g, (double*)c->staging.p, st);
+    NK_CUDA(c, cudaGetLastError());
+    std::vector<double> part(nb);
+    NK_CUDA(c, cudaMemcpyAsync(part.data(), c->staging.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaStreamSynchronize(st));
+    double plaq = 0.0;
+    for (int i = 0; i < nb; ++i) plaq += part[i];
+    plaq /= 6.0 * c->V;
+
+    double f[NK_MLP_IN];
+    f[0] = c->mu;
+    f[1] = c->m_w;
+    f[2] = std::log10((double)c->V);
+    f[3] = plaq;
+    f[4] = std::log10(ist.z_min[0]);
+    f[5] = std::log10(ist.z_max[0]);
+    f[6] = f[5] - f[4];
+    f[7] = std::log10(ist.p[0]);
+    double m = 0, s2 = 0, im = 0;
+    for (int j = 0; j < k; ++j) {
+        m += al[2 * j];
+        im = std::max(im, std::fabs(al[2 * j + 1]));
+    }
+    m /= k;
+    for (int j = 0; j < k; ++j) s2 += (al[2 * j] - m) * (al[2 * j] - m);
+    f[8] = m;
+    f[9] = std::sqrt(s2 / k);
+    f[10] = im;
+    const int nsub = k - 1;
+    double bm = 0, bs = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int j = 0; j < nsub; ++j) {
+        const double a = std::hypot(be[2 * j], be[2 * j + 1]);
+        const double ly = std::log(std::max(a, 1e-300));
+        bm += a;
+        sx += j; sy += ly; sxx += (double)j * j; sxy += j * ly;
+    }
+    bm /= nsub;
+    for (int j = 0; j < nsub; ++j) {
+        const double a = std::hypot(be[2 * j], be[2 * j + 1]);
+        bs += (a - bm) * (a - bm);
+    }
+    f[11] = bm;
+    f[12] = std::sqrt(bs / nsub);
+    f[13] = (nsub * sxy - sx * sy) / (nsub * sxx - sx * sx);
+    double ct = 0, ca = 0;
+    for (int j = 0; j < k; ++j) {
+        const double a2 = cf[2 * j] * cf[2 * j] + cf[2 * j + 1] * cf[2 * j + 1];
+        ca += a2;
+        if (j >= 24) ct += a2;
+    }
+    f[14] = 0.5 * std::log10(std::max(ct, 1e-300) / ca);
+    f[15] = ist.rhi_iters[0];
+    for (int i = 0; i < NK_MLP_IN; ++i) {
+        if (!std::isfinite(f[i])) return fail(c, NK_EINVAL, "non-finite predictor feature");
+        features[i] = (float)f[i];
+    }
+    return NK_OK;
+}
+
+int nk_predict_sizes(nk_ctx* c, nk_mlp* m, const double* b_dev, int k_max, int* k, int* ell, void* stream) {
+    if (!c || !m || !b_dev || !k || !ell) return c ? fail(c, NK_EINVAL, "null pointer") : NK_EINVAL;
+    if (k_max < 64 || k_max > nk::kMaxInnerK || (k_max & 1)) return fail(c, NK_EINVAL, "bad k_max");
+    float f[NK_MLP_IN], y[NK_MLP_OUT];
+    int rc = nk_features(c, b_dev, f, stream);
+    if (rc) return rc;
+    rc = nk_mlp_forward(m, f, 1, y);
+    if (rc) return fail(c, rc, std::string("predictor: ") + nk_mlp_last_error(m));
+    auto even = [](double v) { return 2 * (int)std::lround(0.5 * v); };
+    const double kp = std::exp2(std::min(std::max((double)y[0], 0.0), 12.0));
+    const double lp = std::exp2(std::min(std::max((double)y[1], 0.0), 12.0));
+    int kk = std::min(std::max(even(kp), 64), k_max);
+    int ll = std::min(std::max(even(lp), 16), std::min(kk, 256));
+    *k = kk;
+    *ell = ll;
+    return NK_OK;
+}
+
 const char* nk_last_error(const nk_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void nk_destroy(nk_ctx* c) {

@@ -29,6 +29,8 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
                    const DslashSet& s1, double kappa, double mu, cudaStream_t st);
 void launch_links_to_device_layout(const double2* in, double2* u64, float2* u32, dfc* udf, int V,
                                    cudaStream_t st);
+int plaquette_blocks(const Geom& g);
+void launch_plaquette(const double2* U, const Geom& g, double* partial, cudaStream_t st);
 void launch_to_df(const double2* in, long in_stride, dfc* out, long out_stride, long N, int n, cudaStream_t st);
 void launch_abi_to_soa(const double2* in, long in_stride, double2* out, long out_stride, int V,
                        int n, cudaStream_t st);

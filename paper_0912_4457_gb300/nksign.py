@@ -48,7 +48,15 @@ EXPORTED = [
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
     "nk_destroy",
+    "nk_mlp_create", "nk_mlp_set_norm", "nk_mlp_get_params", "nk_mlp_set_params", "nk_mlp_loss_grad",
+    "nk_mlp_train", "nk_mlp_forward", "nk_mlp_last_error", "nk_mlp_destroy", "nk_features",
+    "nk_predict_sizes",
 ]
+
+NK_MLP_IN = 16
+NK_MLP_HIDDEN = 64
+NK_MLP_OUT = 2
+NK_MLP_PARAMS = 64 * 16 + 64 + 64 * 64 + 64 + 2 * 64 + 2
 
 
 class NkStats(ctypes.Structure):
@@ -103,6 +111,7 @@ def load_library(path: str = LIB_PATH):
     lib = ctypes.CDLL(path)
     P, I, D, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
     dp = ctypes.POINTER(ctypes.c_double)
+    fp = ctypes.POINTER(ctypes.c_float)
     sig = {
         "nk_create_lattice": ([ctypes.POINTER(ctypes.c_int), I, ctypes.POINTER(P)], I),
         "nk_load_links": ([P, dp], I),
@@ -120,6 +129,17 @@ def load_library(path: str = LIB_PATH):
         "nk_inner_sign_noalloc": ([P, P, P, I, I, I, D, I, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
         "nk_last_error": ([P], ctypes.c_char_p),
         "nk_destroy": ([P], None),
+        "nk_mlp_create": ([ctypes.c_ulonglong, ctypes.POINTER(P)], I),
+        "nk_mlp_set_norm": ([P, fp, fp, fp, fp], I),
+        "nk_mlp_get_params": ([P, fp], I),
+        "nk_mlp_set_params": ([P, fp], I),
+        "nk_mlp_loss_grad": ([P, fp, fp, I, fp, fp], I),
+        "nk_mlp_train": ([P, fp, fp, I, I, ctypes.c_float, fp], I),
+        "nk_mlp_forward": ([P, fp, I, fp], I),
+        "nk_mlp_last_error": ([P], ctypes.c_char_p),
+        "nk_mlp_destroy": ([P], None),
+        "nk_features": ([P, P, fp, P], I),
+        "nk_predict_sizes": ([P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -285,6 +305,94 @@ class Context:
         if check:
             self._check(rc)
         return c, st.as_dict(), rc
+
+    # -- learned subspace sizes ---------------------------------------------
+    def features(self, b_dev, stream=None):
+        """nk_features: the NK_MLP_IN predictor features of one device source."""
+        f = np.zeros(NK_MLP_IN, np.float32)
+        self._check(self._lib.nk_features(self.h, _dev_ptr(b_dev), _fptr(f), _stream_ptr(stream)))
+        return f
+
+    def predict_sizes(self, mlp, b_dev, k_max, stream=None):
+        """nk_predict_sizes: (k, l) for one device source from a trained Mlp."""
+        k = ctypes.c_int()
+        ell = ctypes.c_int()
+        self._check(self._lib.nk_predict_sizes(self.h, mlp.h, _dev_ptr(b_dev), int(k_max), ctypes.byref(k),
+                                               ctypes.byref(ell), _stream_ptr(stream)))
+        return k.value, ell.value
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f32(a, cols):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a.reshape(-1, cols)
+
+
+class Mlp:
+    """Owns an nk_mlp* (the 16 -> 64 -> 64 -> 2 size predictor)."""
+
+    def __init__(self, seed: int = 0):
+        lib = load_library()
+        self._lib = lib
+        h = ctypes.c_void_p()
+        rc = lib.nk_mlp_create(ctypes.c_ulonglong(int(seed)), ctypes.byref(h))
+        if rc != NK_OK:
+            raise NkError(rc, "nk_mlp_create failed")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != NK_OK:
+            raise NkError(rc, self._lib.nk_mlp_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.nk_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_norm(self, xmu, xsd, ymu, ysd):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (xmu, xsd, ymu, ysd)]
+        self._check(self._lib.nk_mlp_set_norm(self.h, *[_fptr(a) for a in arrs]))
+
+    def get_params(self):
+        w = np.zeros(NK_MLP_PARAMS, np.float32)
+        self._check(self._lib.nk_mlp_get_params(self.h, _fptr(w)))
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.size != NK_MLP_PARAMS:
+            raise ValueError("expected %d parameters" % NK_MLP_PARAMS)
+        self._check(self._lib.nk_mlp_set_params(self.h, _fptr(w)))
+
+    def loss_grad(self, X, Y):
+        X, Y = _f32(X, NK_MLP_IN), _f32(Y, NK_MLP_OUT)
+        loss = np.zeros(1, np.float32)
+        g = np.zeros(NK_MLP_PARAMS, np.float32)
+        self._check(self._lib.nk_mlp_loss_grad(self.h, _fptr(X), _fptr(Y), X.shape[0], _fptr(loss), _fptr(g)))
+        return float(loss[0]), g
+
+    def train(self, X, Y, epochs, lr=1e-3):
+        X, Y = _f32(X, NK_MLP_IN), _f32(Y, NK_MLP_OUT)
+        hist = np.zeros(int(epochs), np.float32)
+        self._check(self._lib.nk_mlp_train(self.h, _fptr(X), _fptr(Y), X.shape[0], int(epochs), float(lr),
+                                           _fptr(hist)))
+        return hist
+
+    def forward(self, X):
+        X = _f32(X, NK_MLP_IN)
+        Y = np.zeros((X.shape[0], NK_MLP_OUT), np.float32)
+        self._check(self._lib.nk_mlp_forward(self.h, _fptr(X), X.shape[0], _fptr(Y)))
+        return Y
 
 
 def inner_sign_noalloc(alpha_dev, beta_dev, gamma_dev, c_dev, n_rhs, k, ell, p=0.0, hermitian=True,
