@@ -123,9 +123,44 @@ int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
 int nk_set_precision(nk_ctx* ctx, int j0);
 
 /* Adaptive k: the outer size at the first convergence check (even; 0 selects
- * NK_ADAPT_FIRST(l)).  A predicted k (nk_predict_sizes) goes here, so that a
- * good prediction costs a single check. */
+ * NK_ADAPT_FIRST(l)).  A predicted k (nk_predict_sizes) minus two check
+ * intervals goes here, so that a good prediction costs three checks. */
 int nk_set_adapt_start(nk_ctx* ctx, int k_first);
+
+/*
+ * Launch shape of the outer recurrence (batching of the RHS and the
+ * autotuner; a property of the implementation, not of the method).
+ *  stencil_threads  lattice sites per CTA of the fused stencil kernel, one
+ *                   thread per site and vector: 64, 128 or 256;
+ *  stencil_order    0: consecutive CTAs take all vectors (RHS and, for mu != 0,
+ *                   both sides) of one block of sites, so the links of those
+ *                   sites are read from HBM once and then from L2;
+ *                   1: consecutive CTAs take the site blocks of one vector;
+ *  step2_blocks     CTAs per RHS of the step-2 and norm kernels (grid-stride),
+ *                   1..4096; also the number of partial sums of their
+ *                   deterministic reductions.
+ * A shape belongs to (n_rhs, sidedness of the current mu (mu != 0), the
+ * NK_MIXED bit of flags).  Different shapes sum in different orders, so
+ * results differ at rounding level; one shape is bitwise reproducible.
+ * Unset shapes use 128 / 0 / min(ceil(12 V / 2048), 608 / n_rhs).
+ */
+typedef struct nk_launch {
+    int stencil_threads;
+    int stencil_order;
+    int step2_blocks;
+} nk_launch;
+int nk_set_launch(nk_ctx* ctx, int n_rhs, unsigned flags, const nk_launch* shape);
+int nk_get_launch(nk_ctx* ctx, int n_rhs, unsigned flags, nk_launch* shape);
+/* Times 16 outer steps of every stencil shape (3 x 2), then of step2_blocks
+ * in {b/2, b, 2b, 4b} (b the default) with the fastest stencil shape, on a
+ * synthetic constant source, and keeps the fastest (written to *best and
+ * its time per outer step to *ms_per_step; both nullable).  cache_path
+ * (nullable): a text file of lines
+ *   nk_launch Lx Ly Lz Lt n_rhs two_sided mixed threads order blocks ms_per_step
+ * read first (a matching line is used without timing) and appended to after
+ * timing.  Blocks. */
+int nk_autotune(nk_ctx* ctx, int n_rhs, unsigned flags, const char* cache_path, nk_launch* best,
+                double* ms_per_step);
 
 /*
  * y = sgn(A) b by the nested Krylov-Ritz method (Eq. nested; App. C steps
@@ -220,6 +255,9 @@ int nk_mlp_get_params(nk_mlp* m, float* params);          /* NK_MLP_PARAMS float
 int nk_mlp_set_params(nk_mlp* m, const float* params);    /* also resets the Adam state */
 /* Loss and gradient (w.r.t. the parameters) for n <= 256 samples X[n][16], Y[n][2]. */
 int nk_mlp_loss_grad(nk_mlp* m, const float* X, const float* Y, int n, float* loss, float* grad);
+/* Decoupled weight decay of the Adam steps (w -= lr wd w per step), in [0, 1);
+ * 0 (the default) is plain Adam. */
+int nk_mlp_set_weight_decay(nk_mlp* m, float wd);
 /* `epochs` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) on n <= 256
  * samples; loss_hist (nullable) receives the loss before each step. */
 int nk_mlp_train(nk_mlp* m, const float* X, const float* Y, int n, int epochs, float lr, float* loss_hist);
@@ -253,7 +291,7 @@ int nk_predict_sizes(nk_ctx* ctx, nk_mlp* m, const double* b_dev, int k_max, int
  * arrays owned by the caller (alpha_dev, beta_dev, gamma_dev, c_dev in the
  * nk_outer_lanczos_dev layout, complex doubles [r*k + j]) and every other
  * buffer it needs lives in one static device array of the library (about
- * 5.3 MB, held by every GPU that loads the library until the process exits).
+ * 5.4 MB, held by every GPU that loads the library until the process exits).
  * It calls no cudaMalloc/cudaFree and needs no context.
  * Limits: n_rhs <= NK_NOALLOC_MAX_RHS, k <= NK_NOALLOC_MAX_K,
  * l <= NK_NOALLOC_MAX_ELL; larger sizes return NK_EINVAL with a message.

@@ -8,6 +8,7 @@ so this module follows the textbook definitions:
 
 * forward: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), z = W3 h2 + b3;
 * loss over n samples with targets t: L = (1/n) sum_s |z_s - t_s|^2 / 2;
+* Adam with bias correction and optional decoupled weight decay;
 * inputs and targets are standardised first: x -> (x - xmu)/xsd,
   y -> (y - ymu)/ysd, and predictions are de-standardised;
 * parameters flattened as W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64],
@@ -76,20 +77,21 @@ def loss_grad(w, X, T):
     return L, pack({"W1": dW1, "b1": db1, "W2": dW2, "b2": db2, "W3": dW3, "b3": db3})
 
 
-def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update at step t (1-based): returns (w, m, v)."""
+def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+    """One Adam update at step t (1-based) with decoupled weight decay wd
+    (Loshchilov & Hutter): returns (w, m, v)."""
     m = beta1 * m + (1.0 - beta1) * g
     v = beta2 * v + (1.0 - beta2) * g * g
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
-    return w - lr * mh / (np.sqrt(vh) + eps), m, v
+    return w - lr * (mh / (np.sqrt(vh) + eps) + wd * w), m, v
 
 
 def standardise(X, mu, sd):
     return (np.asarray(X, dtype=np.float64) - mu) / sd
 
 
-def train(w, X, T, epochs, lr):
+def train(w, X, T, epochs, lr, wd=0.0):
     """Full-batch Adam from zero moments; returns (w, loss before each step)."""
     m = np.zeros_like(w)
     v = np.zeros_like(w)
@@ -97,5 +99,5 @@ def train(w, X, T, epochs, lr):
     for t in range(1, epochs + 1):
         L, g = loss_grad(w, X, T)
         hist.append(L)
-        w, m, v = adam_step(w, g, m, v, t, lr)
+        w, m, v = adam_step(w, g, m, v, t, lr, wd=wd)
     return w, np.array(hist)

@@ -228,10 +228,8 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
 // output on, everything is FP64.  The blocks of side 0 reduce H(j,j) with the
 // deterministic two-stage scheme.  In double-pass mode side 0 also
 // accumulates y += c'_j q_j at its own site.
-constexpr int kStencilThreads = 128;
-
 template <typename R, bool TS, bool PASS2>
-__global__ void __launch_bounds__(kStencilThreads) k_dslash_step1(
+__global__ void __launch_bounds__(kStencilMaxThreads) k_dslash_step1(
     const typename C2<R>::T* __restrict__ U, Geom g, Outer o, int j, R kappa, R emu, R emu_inv,
     const typename C2<R>::T* __restrict__ qin, long qin_stride, const typename C2<R>::T* __restrict__ pin,
     long pin_stride) {
@@ -239,9 +237,9 @@ __global__ void __launch_bounds__(kStencilThreads) k_dslash_step1(
     __shared__ double2 sh[33];
     __shared__ double2 coef[3];
     const int nvec = TS ? 2 * o.n_rhs : o.n_rhs;
-    const int vec = blockIdx.x % nvec;
-    const int sb = blockIdx.x / nvec;
     const int nsb = gridDim.x / nvec;
+    const int vec = o.st_order == 0 ? blockIdx.x % nvec : blockIdx.x / nsb;
+    const int sb = o.st_order == 0 ? blockIdx.x / nvec : blockIdx.x % nsb;
     const int side = vec / o.n_rhs;      // 0: A q_j, 1: A^dagger p_j
     const int rhs = vec % o.n_rhs;
     if (o.status[rhs] != kStatusOK) return;
@@ -329,24 +327,25 @@ __global__ void __launch_bounds__(kStencilThreads) k_dslash_step1(
     }
 }
 
-int dslash_step1_blocks(const Geom& g) { return (g.V + kStencilThreads - 1) / kStencilThreads; }
+int dslash_step1_blocks(const Geom& g, int threads) { return (g.V + threads - 1) / threads; }
 
 template <typename R, typename T>
 static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R kappa, R emu, R emu_inv, const T* qin,
                            long qs, const T* pin, long ps, cudaStream_t st) {
     const int nvec = o.two_sided ? 2 * o.n_rhs : o.n_rhs;
-    dim3 grid((unsigned)(dslash_step1_blocks(g) * nvec));
+    dim3 grid((unsigned)(dslash_step1_blocks(g, o.st_threads) * nvec));
+    const int threads = o.st_threads;
     const bool pass2 = o.y != nullptr;
     if (o.two_sided) {
         if (pass2)
-            k_dslash_step1<R, true, true><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, true, true><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
         else
-            k_dslash_step1<R, true, false><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, true, false><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
     } else {
         if (pass2)
-            k_dslash_step1<R, false, true><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, false, true><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
         else
-            k_dslash_step1<R, false, false><<<grid, kStencilThreads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, false, false><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
     }
 }
 

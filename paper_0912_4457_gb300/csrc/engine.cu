@@ -53,6 +53,7 @@ struct nk_ctx {
     DevBuf staging;       // host-pointer API: device copies of b and y
     DevBuf links_tmp;
     std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;  // exec, kernels per replay
+    std::map<std::tuple<int, int, int>, nk_launch> tune;  // (n_rhs, two_sided, mixed) -> launch shape
     std::string err = "no error";
 };
 
@@ -115,7 +116,9 @@ struct Layout {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_sided, bool double_pass, int nblk) {
+Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_sided, bool double_pass,
+             const nk_launch& lc) {
+    const int nblk = lc.step2_blocks;
     Layout L;
     std::memset(&L, 0, sizeof(L));
     size_t off = 0;
@@ -129,7 +132,9 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     L.y_soa = (double2*)take(vec * n_rhs);
     nk::Outer& o = L.o;
     o.N = N; o.n_rhs = n_rhs; o.k = k; o.nblk = nblk; o.two_sided = two_sided;
-    o.npart = std::max(nblk, nk::dslash_step1_blocks(g));
+    o.st_threads = lc.stencil_threads;
+    o.st_order = lc.stencil_order;
+    o.npart = std::max(nblk, nk::dslash_step1_blocks(g, lc.stencil_threads));
     o.q_ring = double_pass ? 1 : 0;
     o.qcols = double_pass ? 3 : k + 1;   // single pass: k basis vectors + one scratch column
     o.Q = (double2*)take(vec * (size_t)o.qcols * n_rhs);
@@ -152,7 +157,7 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     in.p = (double*)take(sizeof(double) * n_rhs);
     in.zmin = (double*)take(sizeof(double) * n_rhs);
     in.zmax = (double*)take(sizeof(double) * n_rhs);
-    in.work = (double2*)take(sizeof(double2) * (size_t)nk::kInnerWorkVecs * k * n_rhs);
+    in.work = (double2*)take(sizeof(double2) * nk::inner_work_elems(k) * n_rhs);
     in.ipiv = (int*)take(sizeof(int) * (size_t)k * n_rhs);
     in.Vl = (double2*)take(sizeof(double2) * (size_t)ell * k * n_rhs);
     in.al = (double2*)take(sizeof(double2) * (size_t)ell * n_rhs);
@@ -178,6 +183,23 @@ int blocks_per_rhs(long N, int n_rhs) {
     long need = (N + 2047) / 2048;
     long cap = std::max(1L, (long)(4 * 152 / n_rhs));
     return (int)std::max(1L, std::min(need, cap));
+}
+
+// The launch shape of a solve: the tuned one for (n_rhs, two-sided, mixed),
+// else the default (128 sites per CTA, vector-fastest grid, blocks_per_rhs).
+nk_launch launch_cfg(const nk_ctx* c, int n_rhs, bool ts, bool mixed) {
+    auto it = c->tune.find(std::make_tuple(n_rhs, ts ? 1 : 0, mixed ? 1 : 0));
+    if (it != c->tune.end()) return it->second;
+    nk_launch d;
+    d.stencil_threads = 128;
+    d.stencil_order = 0;
+    d.step2_blocks = blocks_per_rhs(c->N, n_rhs);
+    return d;
+}
+
+bool valid_launch(const nk_launch& l) {
+    return (l.stencil_threads == 64 || l.stencil_threads == 128 || l.stencil_threads == 256) &&
+           (l.stencil_order == 0 || l.stencil_order == 1) && l.step2_blocks >= 1 && l.step2_blocks <= 4096;
 }
 
 int check_solve_args(nk_ctx* c, int n_rhs, int k, int ell, double tol) {
@@ -353,6 +375,17 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
         bool all = true, changed = false;
         for (int r = 0; r < n_rhs; ++r) {
             if (frozen[r]) continue;
+            const bool inner_failed = status[r] == nk::kStatusRhi || status[r] == nk::kStatusLU ||
+                                      status[r] == nk::kStatusInnerBreakdown;
+            if (inner_failed && kc < kmax) {
+                // the inner part failed on this H_k (e.g. a Ritz value near the
+                // imaginary axis): a failed check; the outer recurrence goes on
+                status[r] = nk::kStatusOK;
+                hits[r] = 0;
+                changed = true;
+                all = false;
+                continue;
+            }
             if (status[r] != nk::kStatusOK) {   // zero source or failure: nothing more to do
                 frozen[r] = 1;
                 kused_h[r] = kc;
@@ -402,7 +435,8 @@ int status_to_code(int s) {
     switch (s) {
         case nk::kStatusOK:
         case nk::kStatusZeroSource: return NK_OK;
-        case nk::kStatusBreakdown: return NK_EBREAKDOWN;
+        case nk::kStatusBreakdown:
+        case nk::kStatusInnerBreakdown: return NK_EBREAKDOWN;
         case nk::kStatusRhi: return NK_ERHI;
         case nk::kStatusLU: return NK_ERHI;
         default: return NK_ECUDA;
@@ -416,11 +450,11 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     NK_CUDA(c, cudaSetDevice(c->device));
     const bool ts = c->mu != 0.0;
     const bool dp = (flags & NK_DOUBLE_PASS) != 0;
-    const int nblk = blocks_per_rhs(c->N, n_rhs);
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, nblk);
+    const nk_launch lc = launch_cfg(c, n_rhs, ts, (flags & NK_MIXED) != 0);
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, lc);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, nblk);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, lc);
     // counters must start at zero; status is (re)set by the norm kernel
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
     NK_CUDA(c, cudaMemsetAsync(Lw.in.timeout, 0, sizeof(int), st));
@@ -606,6 +640,156 @@ int nk_set_adapt_start(nk_ctx* c, int k_first) {
     return NK_OK;
 }
 
+static void clear_graphs(nk_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.first);
+    c->graphs.clear();
+}
+
+static int shape_args(nk_ctx* c, int n_rhs) {
+    if (!c) return NK_EINVAL;
+    if (n_rhs < 1 || n_rhs > NK_MAX_RHS) return fail(c, NK_EINVAL, "bad n_rhs");
+    if (!c->mu_set) return fail(c, NK_ESTATE, "(mu, m_w) not set: the launch shape depends on mu != 0");
+    return NK_OK;
+}
+
+int nk_set_launch(nk_ctx* c, int n_rhs, unsigned flags, const nk_launch* l) {
+    int rc = shape_args(c, n_rhs);
+    if (rc) return rc;
+    if (!l || !valid_launch(*l)) return fail(c, NK_EINVAL, "bad launch shape");
+    c->tune[std::make_tuple(n_rhs, c->mu != 0.0 ? 1 : 0, (flags & NK_MIXED) ? 1 : 0)] = *l;
+    clear_graphs(c);
+    return NK_OK;
+}
+
+int nk_get_launch(nk_ctx* c, int n_rhs, unsigned flags, nk_launch* l) {
+    int rc = shape_args(c, n_rhs);
+    if (rc) return rc;
+    if (!l) return fail(c, NK_EINVAL, "null pointer");
+    *l = launch_cfg(c, n_rhs, c->mu != 0.0, (flags & NK_MIXED) != 0);
+    return NK_OK;
+}
+
+// Time of `steps` outer steps (init included) of n_rhs copies of the source
+// in `src` with launch shape lc: the minimum over three runs after a warm-up.
+static int time_shape(nk_ctx* c, const double* src, int n_rhs, bool mixed, const nk_launch& lc, int steps,
+                      cudaStream_t st, float* best) {
+    const bool ts = c->mu != 0.0;
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, steps, 2, ts, false, lc);
+    int rc = ensure(c, c->ws, dry.total);
+    if (rc) return rc;
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, steps, 2, ts, false, lc);
+    cudaEvent_t e0, e1;
+    NK_CUDA(c, cudaEventCreate(&e0));
+    NK_CUDA(c, cudaEventCreate(&e1));
+    *best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
+        Launcher L;
+        L.st = st;
+        enqueue_load_sources(c, Lw.o, src, n_rhs, L);
+        NK_CUDA(c, cudaEventRecord(e0, st));
+        enqueue_outer(c, Lw.o, mixed, 0, L);   // mixed: the FP32 stencil throughout
+        NK_CUDA(c, cudaEventRecord(e1, st));
+        NK_CUDA(c, cudaGetLastError());
+        NK_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NK_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) *best = std::min(*best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return NK_OK;
+}
+
+int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk_launch* out, double* ms_per_step) {
+    int rc = shape_args(c, n_rhs);
+    if (rc) return rc;
+    if (!c->links) return fail(c, NK_ESTATE, "links not loaded");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const int ts = c->mu != 0.0 ? 1 : 0;
+    const int mixed = (flags & NK_MIXED) ? 1 : 0;
+    const int steps = 16;
+    if (cache_path) {
+        if (FILE* f = std::fopen(cache_path, "r")) {
+            char tag[32];
+            int d[4], nr, t2, mx, th, od, bl;
+            double ms;
+            bool found = false;
+            nk_launch hit;
+            while (std::fscanf(f, "%31s %d %d %d %d %d %d %d %d %d %d %lf", tag, &d[0], &d[1], &d[2], &d[3], &nr,
+                               &t2, &mx, &th, &od, &bl, &ms) == 12) {
+                if (std::strcmp(tag, "nk_launch") != 0) break;
+                if (d[0] == c->dims[0] && d[1] == c->dims[1] && d[2] == c->dims[2] && d[3] == c->dims[3] &&
+                    nr == n_rhs && t2 == ts && mx == mixed) {
+                    hit.stencil_threads = th;
+                    hit.stencil_order = od;
+                    hit.step2_blocks = bl;
+                    if (valid_launch(hit)) {
+                        found = true;
+                        if (ms_per_step) *ms_per_step = ms;
+                    }
+                }
+            }
+            std::fclose(f);
+            if (found) {
+                c->tune[std::make_tuple(n_rhs, ts, mixed)] = hit;
+                clear_graphs(c);
+                if (out) *out = hit;
+                return NK_OK;
+            }
+        }
+    }
+    // synthetic source: every component 0x3F3F3F3F3F3F3F3F (about 4.8e-4)
+    const size_t sb = sizeof(double2) * (size_t)c->N * n_rhs;
+    rc = ensure(c, c->staging, std::max(sb, c->staging.bytes));
+    if (rc) return rc;
+    cudaStream_t st;
+    NK_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    NK_CUDA(c, cudaMemsetAsync(c->staging.p, 0x3F, sb, st));
+    const double* src = (const double*)c->staging.p;
+    nk_launch best = launch_cfg(c, n_rhs, ts != 0, mixed != 0);
+    best.stencil_threads = 128;
+    best.stencil_order = 0;
+    const int b0 = blocks_per_rhs(c->N, n_rhs);
+    best.step2_blocks = b0;
+    float t_best = 1e30f;
+    for (int th : {64, 128, 256})
+        for (int od : {0, 1}) {
+            nk_launch l = best;
+            l.stencil_threads = th;
+            l.stencil_order = od;
+            float t;
+            rc = time_shape(c, src, n_rhs, mixed != 0, l, steps, st, &t);
+            if (rc) { cudaStreamDestroy(st); return rc; }
+            if (t < t_best) { t_best = t; best = l; }
+        }
+    for (int bl : {std::max(1, b0 / 2), 2 * b0, 4 * b0}) {
+        nk_launch l = best;
+        l.step2_blocks = std::min(bl, 4096);
+        float t;
+        rc = time_shape(c, src, n_rhs, mixed != 0, l, steps, st, &t);
+        if (rc) { cudaStreamDestroy(st); return rc; }
+        if (t < t_best) { t_best = t; best = l; }
+    }
+    cudaStreamDestroy(st);
+    c->tune[std::make_tuple(n_rhs, ts, mixed)] = best;
+    clear_graphs(c);
+    const double per_step = t_best / steps;
+    if (out) *out = best;
+    if (ms_per_step) *ms_per_step = per_step;
+    if (cache_path) {
+        if (FILE* f = std::fopen(cache_path, "a")) {
+            std::fprintf(f, "nk_launch %d %d %d %d %d %d %d %d %d %d %.6g\n", c->dims[0], c->dims[1], c->dims[2],
+                         c->dims[3], n_rhs, ts, mixed, best.stencil_threads, best.stencil_order, best.step2_blocks,
+                         per_step);
+            std::fclose(f);
+        } else {
+            return fail(c, NK_EINVAL, "cannot append to the tuning cache file");
+        }
+    }
+    return NK_OK;
+}
+
 int nk_sign_apply_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
                       unsigned flags, double* y_dev, nk_stats* st, void* stream) {
     if (!c || !b_dev || !y_dev) return NK_EINVAL;
@@ -699,11 +883,11 @@ int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsig
     NK_CUDA(c, cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
     const bool ts = c->mu != 0.0;
-    const int nblk = blocks_per_rhs(c->N, n_rhs);
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, nblk);
+    const nk_launch lc = launch_cfg(c, n_rhs, ts, (flags & NK_MIXED) != 0);
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, lc);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, nblk);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, lc);
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
     Launcher L;
     L.st = st;
@@ -736,10 +920,14 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     tiny.Lx = tiny.Ly = tiny.Lz = tiny.Lt = 1;
     tiny.V = 1;
     tiny.antiperiodic = 0;
-    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, 1);
+    nk_launch one;
+    one.stencil_threads = 64;
+    one.stencil_order = 0;
+    one.step2_blocks = 1;
+    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one);
     int rc = ensure(c, c->staging, std::max(dry.total, c->staging.bytes));
     if (rc) return rc;
-    Layout Lw = carve((char*)c->staging.p, tiny, n_rhs, k, ell, ts, true, 1);
+    Layout Lw = carve((char*)c->staging.p, tiny, n_rhs, k, ell, ts, true, one);
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpy(Lw.o.alpha, alpha, cb, cudaMemcpyHostToDevice));
     NK_CUDA(c, cudaMemcpy(Lw.o.beta, beta, cb, cudaMemcpyHostToDevice));

@@ -12,9 +12,10 @@
 // In the Hermitian case (mu = 0) all of it is real arithmetic (App. C).
 //
 // The inner Lanczos runs one CTA per RHS: the band products, inner products
-// and axpys are spread over the CTA, the two O(k) substitution sweeps of each
-// solve are a sequential chain in one thread (two threads in the two-sided
-// case: H_k' v and H_k'^dagger w are independent).
+// and axpys are spread over the CTA; the two O(k) substitution sweeps of each
+// solve are parallel prefix scans on one warp (two warps in the two-sided
+// case: H_k' v and H_k'^dagger w are independent), with the parts of the
+// scans that depend on the LU factors alone tabulated once per LU.
 //
 // RHi runs one thread-block cluster per RHS: the rows of the l x l matrix
 // being inverted (in-place Gauss-Jordan with partial pivoting and row
@@ -186,57 +187,127 @@ __device__ __forceinline__ double2 t_fma(double2 a, double2 b, double2 c) {
     return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
-template <typename T> struct Aff1 { T a, c; };                  // s -> a s + c
-template <typename T> struct Aff2 { T m00, m01, m10, m11, v0, v1; };  // X -> M X + v
+// The maps of a sweep split into a part that depends on the LU factors only
+// (a of s <- a s + c; M of X <- M X + v) and a part that depends on the
+// right-hand side (c; v).  The factor parts of the lane chunks and of every
+// level of the lane scan are composed once per LU (sweep_tables) and kept in
+// a per-RHS table; a solve then composes only the right-hand-side parts:
+// first order 1 complex product per element, second order 3 (the companion
+// matrix [[e, f], [1, 0]] is sparse), and the lane scan 1 (4) products per
+// level.  Composition rules (g after f):
+//   first order   (a, c): a = a_g a_f,  c = a_g c_f + c_g;
+//   second order  (M, v): M = M_g M_f,  v = M_g v_f + v_g.
+// Table rows (row-major [row][lane]): L 0-5, L^dagger 6-11 (a before each of
+// the 5 scan levels, then the exclusive prefix a), U 12-31, U^dagger 32-51
+// (the 4 entries of M before each scan level).
+constexpr int kTabL = 0, kTabLH = 6, kTabU = 12, kTabUH = 32;
 
-template <typename T> __device__ __forceinline__ Aff1<T> id1() { return {t_one(T()), t_zero(T())}; }
-template <typename T> __device__ __forceinline__ Aff2<T> id2() {
-    return {t_one(T()), t_zero(T()), t_zero(T()), t_one(T()), t_zero(T()), t_zero(T())};
+template <typename T> struct Mat2 { T m00, m01, m10, m11; };
+template <typename T> __device__ __forceinline__ Mat2<T> mat_mul(const Mat2<T>& g, const Mat2<T>& f) {
+    return {t_fma(g.m00, f.m00, t_mul(g.m01, f.m10)), t_fma(g.m00, f.m01, t_mul(g.m01, f.m11)),
+            t_fma(g.m10, f.m00, t_mul(g.m11, f.m10)), t_fma(g.m10, f.m01, t_mul(g.m11, f.m11))};
 }
-// g o f (f applied first)
-template <typename T> __device__ __forceinline__ Aff1<T> comp(const Aff1<T>& g, const Aff1<T>& f) {
-    return {t_mul(g.a, f.a), t_fma(g.a, f.c, g.c)};
+template <typename T> __device__ __forceinline__ Mat2<T> shfl_mat(const Mat2<T>& a, int o, bool up) {
+    return up ? Mat2<T>{shup(a.m00, o), shup(a.m01, o), shup(a.m10, o), shup(a.m11, o)}
+              : Mat2<T>{shdn(a.m00, o), shdn(a.m01, o), shdn(a.m10, o), shdn(a.m11, o)};
 }
-template <typename T> __device__ __forceinline__ Aff2<T> comp(const Aff2<T>& g, const Aff2<T>& f) {
-    Aff2<T> r;
-    r.m00 = t_fma(g.m00, f.m00, t_mul(g.m01, f.m10));
-    r.m01 = t_fma(g.m00, f.m01, t_mul(g.m01, f.m11));
-    r.m10 = t_fma(g.m10, f.m00, t_mul(g.m11, f.m10));
-    r.m11 = t_fma(g.m10, f.m01, t_mul(g.m11, f.m11));
-    r.v0 = t_fma(g.m00, f.v0, t_fma(g.m01, f.v1, g.v0));
-    r.v1 = t_fma(g.m10, f.v0, t_fma(g.m11, f.v1, g.v1));
-    return r;
-}
-template <typename T> __device__ __forceinline__ Aff1<T> shup(const Aff1<T>& f, int o) { return {shup(f.a, o), shup(f.c, o)}; }
-template <typename T> __device__ __forceinline__ Aff1<T> shdn(const Aff1<T>& f, int o) { return {shdn(f.a, o), shdn(f.c, o)}; }
-template <typename T> __device__ __forceinline__ Aff2<T> shup(const Aff2<T>& f, int o) {
-    return {shup(f.m00, o), shup(f.m01, o), shup(f.m10, o), shup(f.m11, o), shup(f.v0, o), shup(f.v1, o)};
-}
-template <typename T> __device__ __forceinline__ Aff2<T> shdn(const Aff2<T>& f, int o) {
-    return {shdn(f.m00, o), shdn(f.m01, o), shdn(f.m10, o), shdn(f.m11, o), shdn(f.v0, o), shdn(f.v1, o)};
+// lane chunk [lo, hi) of n elements
+__device__ __forceinline__ void lane_chunk(int n, int& lo, int& hi) {
+    const int lane = threadIdx.x & 31;
+    const int C = (n + 31) / 32;
+    lo = min(lane * C, n);
+    hi = min(lo + C, n);
 }
 
-// Exclusive scan over lanes: ascending (lower lanes' maps applied first) or
-// descending (higher lanes' maps applied first).  Lane 0 (31) gets identity.
-template <typename M> __device__ __forceinline__ M warp_exscan_up(M f, M ident) {
+// first-order factor table: a_i over the chunk steps, then the scan levels
+// (ascending: lower lanes first; descending: higher lanes first)
+template <typename T>
+__device__ void table_first_order(int n, const T* __restrict__ dl, const int* __restrict__ ipiv, bool dagger,
+                                  T* __restrict__ tab) {
+    const int lane = threadIdx.x & 31;
+    int lo, hi;
+    lane_chunk(n, lo, hi);
+    const int shi = min(hi, n - 1);
+    T A = t_one(T());
+    for (int i = lo; i < shi; ++i)
+        if (ipiv[i] == i) A = t_mul(t_scale(dagger ? t_conj(dl[i]) : dl[i], -1.0), A);
+    for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
+        tab[lv * 32 + lane] = A;
+        const T pa = dagger ? shdn(A, o) : shup(A, o);
+        if (dagger ? lane + o < 32 : lane >= o) A = t_mul(A, pa);
+    }
+    const T ex = dagger ? shdn(A, 1) : shup(A, 1);
+    tab[5 * 32 + lane] = (dagger ? lane == 31 : lane == 0) ? t_one(T()) : ex;
+}
+
+// second-order factor table: M_i = [[e_i, f_i], [1, 0]] over the chunk
+// (descending for U, ascending for U^dagger), then the scan levels
+template <typename T>
+__device__ void table_second_order(int n, const T* __restrict__ e, const T* __restrict__ f, bool ascending,
+                                   T* __restrict__ tab) {
+    const int lane = threadIdx.x & 31;
+    int lo, hi;
+    lane_chunk(n, lo, hi);
+    Mat2<T> F = {t_one(T()), t_zero(T()), t_zero(T()), t_one(T())};
+    auto step = [&](int i) {
+        F = {t_fma(e[i], F.m00, t_mul(f[i], F.m10)), t_fma(e[i], F.m01, t_mul(f[i], F.m11)), F.m00, F.m01};
+    };
+    if (ascending) for (int i = lo; i < hi; ++i) step(i);
+    else for (int i = hi - 1; i >= lo; --i) step(i);
+    for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
+        tab[(4 * lv + 0) * 32 + lane] = F.m00;
+        tab[(4 * lv + 1) * 32 + lane] = F.m01;
+        tab[(4 * lv + 2) * 32 + lane] = F.m10;
+        tab[(4 * lv + 3) * 32 + lane] = F.m11;
+        const Mat2<T> P = shfl_mat(F, o, ascending);
+        if (ascending ? lane >= o : lane + o < 32) F = mat_mul(F, P);
+    }
+}
+
+// The four tables of one LU: warps 0-1 (L, U), and 2-3 (the dagger sweeps)
+// when two-sided.  Caller synchronises the block afterwards.
+template <typename T>
+__device__ void sweep_tables(int n, const T* dl, const int* ipiv, const T* e, const T* f, const T* eh,
+                             const T* fh, bool two_sided, T* tab) {
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) table_first_order<T>(n, dl, ipiv, false, tab + kTabL * 32);
+    else if (warp == 1) table_second_order<T>(n, e, f, false, tab + kTabU * 32);
+    else if (two_sided && warp == 2) table_first_order<T>(n, dl, ipiv, true, tab + kTabLH * 32);
+    else if (two_sided && warp == 3) table_second_order<T>(n, eh, fh, true, tab + kTabUH * 32);
+}
+
+// exclusive lane scan of right-hand-side parts with tabulated factor parts
+template <typename T>
+__device__ __forceinline__ T scan_first_order(T c, const T* __restrict__ tab, bool descending) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        M p = shup(f, o);
-        if (lane >= o) f = comp(f, p);
+    for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
+        const T pc = descending ? shdn(c, o) : shup(c, o);
+        if (descending ? lane + o < 32 : lane >= o) c = t_fma(tab[lv * 32 + lane], pc, c);
     }
-    M ex = shup(f, 1);
-    return lane == 0 ? ident : ex;
+    const T ex = descending ? shdn(c, 1) : shup(c, 1);
+    return (descending ? lane == 31 : lane == 0) ? t_zero(T()) : ex;
 }
-template <typename M> __device__ __forceinline__ M warp_exscan_down(M f, M ident) {
+template <typename T>
+__device__ __forceinline__ void scan_second_order(T& v0, T& v1, const T* __restrict__ tab, bool ascending) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        M p = shdn(f, o);
-        if (lane + o < 32) f = comp(f, p);
+    for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
+        const T p0 = ascending ? shup(v0, o) : shdn(v0, o);
+        const T p1 = ascending ? shup(v1, o) : shdn(v1, o);
+        if (ascending ? lane >= o : lane + o < 32) {
+            const T m00 = tab[(4 * lv + 0) * 32 + lane], m01 = tab[(4 * lv + 1) * 32 + lane];
+            const T m10 = tab[(4 * lv + 2) * 32 + lane], m11 = tab[(4 * lv + 3) * 32 + lane];
+            const T n0 = t_fma(m00, p0, t_fma(m01, p1, v0));
+            v1 = t_fma(m10, p0, t_fma(m11, p1, v1));
+            v0 = n0;
+        }
     }
-    M ex = shdn(f, 1);
-    return lane == 31 ? ident : ex;
+    const T e0 = ascending ? shup(v0, 1) : shdn(v0, 1);
+    const T e1 = ascending ? shup(v1, 1) : shdn(v1, 1);
+    const bool first = ascending ? lane == 0 : lane == 31;
+    v0 = first ? t_zero(T()) : e0;
+    v1 = first ? t_zero(T()) : e1;
 }
 
 // Output of a sweep: plain store, or out = (out + x)/2 (the H' combination).
@@ -247,19 +318,17 @@ template <typename T> __device__ __forceinline__ void put(T* out, int i, T x, bo
 // L sweep of (LU)^{-1}: y <- L^{-1} P b (forward, with the recorded interchanges).  in != out.
 template <typename T>
 __device__ void warp_L_fwd(int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                           const T* __restrict__ in, T* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int C = (n + 31) / 32;
-    const int lo = min(lane * C, n), hi = min(lo + C, n);
+                           const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tab) {
+    int lo, hi;
+    lane_chunk(n, lo, hi);
     const int shi = min(hi, n - 1);   // steps i in [lo, shi)
-    Aff1<T> F = id1<T>();
+    T c = t_zero(T());
     for (int i = lo; i < shi; ++i) {
         const T bn = in[i + 1];
-        Aff1<T> f = ipiv[i] == i ? Aff1<T>{t_scale(dl[i], -1.0), bn} : Aff1<T>{t_one(T()), t_scale(t_mul(dl[i], bn), -1.0)};
-        F = comp(f, F);
+        c = ipiv[i] == i ? t_fma(t_scale(dl[i], -1.0), c, bn) : t_fma(t_scale(dl[i], -1.0), bn, c);
     }
-    const Aff1<T> G = warp_exscan_up(F, id1<T>());
-    T st = t_fma(G.a, in[0], G.c);
+    c = scan_first_order(c, tab + kTabL * 32, false);
+    T st = t_fma(tab[(kTabL + 5) * 32 + (threadIdx.x & 31)], in[0], c);
     for (int i = lo; i < shi; ++i) {
         const T bn = in[i + 1];
         if (ipiv[i] == i) {
@@ -276,17 +345,17 @@ __device__ void warp_L_fwd(int n, const T* __restrict__ dl, const int* __restric
 // U sweep: x_i = e_i x_{i+1} + f_i x_{i+2} + y_i dinv_i (descending).
 template <typename T>
 __device__ void warp_U_bwd(int n, const T* __restrict__ e, const T* __restrict__ f, const T* __restrict__ dinv,
-                           const T* __restrict__ y, T* __restrict__ out, bool half_add) {
-    const int lane = threadIdx.x & 31;
-    const int C = (n + 31) / 32;
-    const int lo = min(lane * C, n), hi = min(lo + C, n);
-    Aff2<T> F = id2<T>();
+                           const T* __restrict__ y, T* __restrict__ out, bool half_add, const T* __restrict__ tab) {
+    int lo, hi;
+    lane_chunk(n, lo, hi);
+    T v0 = t_zero(T()), v1 = t_zero(T());
     for (int i = hi - 1; i >= lo; --i) {
-        Aff2<T> m = {e[i], f[i], t_one(T()), t_zero(T()), t_mul(y[i], dinv[i]), t_zero(T())};
-        F = comp(m, F);
+        const T n0 = t_fma(e[i], v0, t_fma(f[i], v1, t_mul(y[i], dinv[i])));
+        v1 = v0;
+        v0 = n0;
     }
-    const Aff2<T> G = warp_exscan_down(F, id2<T>());
-    T x1 = G.v0, x2 = G.v1;   // (x_{hi}, x_{hi+1})
+    scan_second_order(v0, v1, tab + kTabU * 32, false);
+    T x1 = v0, x2 = v1;   // (x_{hi}, x_{hi+1})
     for (int i = hi - 1; i >= lo; --i) {
         const T x0 = t_fma(e[i], x1, t_fma(f[i], x2, t_mul(y[i], dinv[i])));
         put(out, i, x0, half_add);
@@ -298,17 +367,17 @@ __device__ void warp_U_bwd(int n, const T* __restrict__ e, const T* __restrict__
 // U^dagger sweep: x_i = eh_i x_{i-1} + fh_i x_{i-2} + b_i conj(dinv_i) (ascending).  in != out.
 template <typename T>
 __device__ void warp_UH_fwd(int n, const T* __restrict__ eh, const T* __restrict__ fh, const T* __restrict__ dinv,
-                            const T* __restrict__ in, T* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    const int C = (n + 31) / 32;
-    const int lo = min(lane * C, n), hi = min(lo + C, n);
-    Aff2<T> F = id2<T>();
+                            const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tab) {
+    int lo, hi;
+    lane_chunk(n, lo, hi);
+    T v0 = t_zero(T()), v1 = t_zero(T());
     for (int i = lo; i < hi; ++i) {
-        Aff2<T> m = {eh[i], fh[i], t_one(T()), t_zero(T()), t_mul(in[i], t_conj(dinv[i])), t_zero(T())};
-        F = comp(m, F);
+        const T n0 = t_fma(eh[i], v0, t_fma(fh[i], v1, t_mul(in[i], t_conj(dinv[i]))));
+        v1 = v0;
+        v0 = n0;
     }
-    const Aff2<T> G = warp_exscan_up(F, id2<T>());
-    T x1 = G.v0, x2 = G.v1;   // (x_{lo-1}, x_{lo-2})
+    scan_second_order(v0, v1, tab + kTabUH * 32, true);
+    T x1 = v0, x2 = v1;   // (x_{lo-1}, x_{lo-2})
     for (int i = lo; i < hi; ++i) {
         const T x0 = t_fma(eh[i], x1, t_fma(fh[i], x2, t_mul(in[i], t_conj(dinv[i]))));
         out[i] = x0;
@@ -320,18 +389,15 @@ __device__ void warp_UH_fwd(int n, const T* __restrict__ eh, const T* __restrict
 // L^dagger sweep of ((LU)^dagger)^{-1} (descending, interchanges undone).  in != out.
 template <typename T>
 __device__ void warp_LH_bwd(int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                            const T* __restrict__ in, T* __restrict__ out, bool half_add) {
-    const int lane = threadIdx.x & 31;
-    const int C = (n + 31) / 32;
-    const int lo = min(lane * C, n), hi = min(lo + C, n);
+                            const T* __restrict__ in, T* __restrict__ out, bool half_add, const T* __restrict__ tab) {
+    int lo, hi;
+    lane_chunk(n, lo, hi);
     const int shi = min(hi, n - 1);   // steps i in [lo, shi), walked downwards
-    Aff1<T> F = id1<T>();
-    for (int i = shi - 1; i >= lo; --i) {
-        Aff1<T> f = ipiv[i] == i ? Aff1<T>{t_scale(t_conj(dl[i]), -1.0), in[i]} : Aff1<T>{t_one(T()), t_zero(T())};
-        F = comp(f, F);
-    }
-    const Aff1<T> G = warp_exscan_down(F, id1<T>());
-    T st = t_fma(G.a, in[n - 1], G.c);   // s_{shi}: the value at position shi entering step shi - 1
+    T c = t_zero(T());
+    for (int i = shi - 1; i >= lo; --i)
+        if (ipiv[i] == i) c = t_fma(t_scale(t_conj(dl[i]), -1.0), c, in[i]);
+    c = scan_first_order(c, tab + kTabLH * 32, true);
+    T st = t_fma(tab[(kTabLH + 5) * 32 + (threadIdx.x & 31)], in[n - 1], c);   // s_{shi}
     for (int i = shi - 1; i >= lo; --i) {
         const T cdl = t_conj(dl[i]);
         if (ipiv[i] == i) {
@@ -384,7 +450,8 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     T* t1 = fh + k;
     T* t2 = t1 + k;
     int* ipiv = reinterpret_cast<int*>(t2 + k);
-    T* W = reinterpret_cast<T*>(in.work + (size_t)rhs * kInnerWorkVecs * k);
+    T* W = reinterpret_cast<T*>(in.work + (size_t)rhs * inner_work_elems(k));
+    T* tab = W + (size_t)kInnerWorkVecs * k;   // sweep tables of the current LU
     T* x = W + 5 * (size_t)k;
     T* y = W + 6 * (size_t)k;
     T* vprev = W + 7 * (size_t)k;
@@ -406,6 +473,8 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, t1, e, f, ipiv, dinv);
         __syncthreads();
         lu_coefficients<T>(k, e, f, eh, fh, dinv);
+        sweep_tables<T>(k, dl, ipiv, e, f, eh, fh, TS, tab);
+        __syncthreads();
     };
 
     // ---- p (Eq. popt) --------------------------------------------------------
@@ -430,9 +499,9 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         double tn = 1.0;
         for (int it = 0; it < 30; ++it) {
             if (warp == 0) {
-                warp_L_fwd<T>(k, dl, ipiv, x, t1);
+                warp_L_fwd<T>(k, dl, ipiv, x, t1, tab);
                 __syncwarp();
-                warp_U_bwd<T>(k, e, f, dinv, t1, y, false);
+                warp_U_bwd<T>(k, e, f, dinv, t1, y, false, tab);
             }
             __syncthreads();
             tn = bnorm<T>(k, y, sh1);
@@ -457,9 +526,9 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
             __syncthreads();
             for (int it = 0; it < 30; ++it) {
                 if (warp == 0) {
-                    warp_L_fwd<T>(k, dl, ipiv, x, t1);
+                    warp_L_fwd<T>(k, dl, ipiv, x, t1, tab);
                     __syncwarp();
-                    warp_U_bwd<T>(k, e, f, dinv, t1, y, false);
+                    warp_U_bwd<T>(k, e, f, dinv, t1, y, false, tab);
                 }
                 __syncthreads();
                 project_out<T>(k, x1, y, sh2);
@@ -507,13 +576,13 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         if (TS) band_mv<T>(k, p, al, be, ga, src_l, out_l, true);
         __syncthreads();
         if (warp == 0) {
-            warp_L_fwd<T>(k, dl, ipiv, src_r, t1);
+            warp_L_fwd<T>(k, dl, ipiv, src_r, t1, tab);
             __syncwarp();
-            warp_U_bwd<T>(k, e, f, dinv, t1, out_r, true);
+            warp_U_bwd<T>(k, e, f, dinv, t1, out_r, true, tab);
         } else if (TS && warp == 1) {
-            warp_UH_fwd<T>(k, eh, fh, dinv, src_l, t2);
+            warp_UH_fwd<T>(k, eh, fh, dinv, src_l, t2, tab);
             __syncwarp();
-            warp_LH_bwd<T>(k, dl, ipiv, t2, out_l, true);
+            warp_LH_bwd<T>(k, dl, ipiv, t2, out_l, true, tab);
         }
         __syncthreads();
     };
@@ -538,11 +607,11 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
             double b = bnorm<T>(k, r, sh1);            // beta <- |r|
             bb = t_from(mk(b, 0.0), T());
             gg = bb;
-            if (!(b > 0.0)) { if (threadIdx.x == 0) in.status[rhs] = kStatusBreakdown; return; }
+            if (!(b > 0.0)) { if (threadIdx.x == 0) in.status[rhs] = kStatusInnerBreakdown; return; }
         } else {
             double2 dlt = bdot<T>(k, r, l, sh2);        // delta <- r^dag l
             if ((dlt.x == 0.0 && dlt.y == 0.0) || !isfinite(dlt.x) || !isfinite(dlt.y)) {
-                if (threadIdx.x == 0) in.status[rhs] = kStatusBreakdown;
+                if (threadIdx.x == 0) in.status[rhs] = kStatusInnerBreakdown;
                 return;
             }
             double2 b2 = csqrt_principal(dlt);

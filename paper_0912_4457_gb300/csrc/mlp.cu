@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(kMlpMaxBatch) k_mlp_fwd_bwd(MlpDev d, int n, i
     }
 }
 
-// Adam (Kingma & Ba) with bias correction, step number t (1-based)
-__global__ void k_adam(MlpDev d, float lr, float b1, float b2, float eps, int t) {
+// Adam (Kingma & Ba) with bias correction, step number t (1-based), and
+// decoupled weight decay wd (Loshchilov & Hutter: w -= lr wd w; 0 = plain Adam)
+__global__ void k_adam(MlpDev d, float lr, float b1, float b2, float eps, float wd, int t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kParams) return;
     const float g = d.g[i];
@@ -143,7 +144,7 @@ __global__ void k_adam(MlpDev d, float lr, float b1, float b2, float eps, int t)
     d.v[i] = v;
     const float mh = m / (1.0f - powf(b1, (float)t));
     const float vh = v / (1.0f - powf(b2, (float)t));
-    d.w[i] -= lr * mh / (sqrtf(vh) + eps);
+    d.w[i] -= lr * (mh / (sqrtf(vh) + eps) + wd * d.w[i]);
 }
 
 }  // namespace
@@ -152,6 +153,7 @@ struct nk_mlp {
     MlpDev d;
     float xmu[kIn], xsd[kIn], ymu[kOut], ysd[kOut];
     int step = 0;
+    float wd = 0.0f;
     std::string err = "no error";
 };
 
@@ -245,6 +247,13 @@ int nk_mlp_set_norm(nk_mlp* m, const float* xmu, const float* xsd, const float* 
     return NK_OK;
 }
 
+int nk_mlp_set_weight_decay(nk_mlp* m, float wd) {
+    if (!m) return NK_EINVAL;
+    if (!(wd >= 0.0f) || !(wd < 1.0f)) return mlp_fail(m, NK_EINVAL, "weight decay must be in [0, 1)");
+    m->wd = wd;
+    return NK_OK;
+}
+
 int nk_mlp_get_params(nk_mlp* m, float* params) {
     if (!m || !params) return NK_EINVAL;
     MLP_CUDA(m, cudaMemcpy(params, m->d.w, sizeof(float) * kParams, cudaMemcpyDeviceToHost));
@@ -279,7 +288,7 @@ int nk_mlp_train(nk_mlp* m, const float* X, const float* Y, int n, int epochs, f
     for (int e = 0; e < epochs; ++e) {
         k_mlp_fwd_bwd<<<1, kMlpMaxBatch>>>(m->d, n, 1);
         ++m->step;
-        k_adam<<<(kParams + 255) / 256, 256>>>(m->d, lr, 0.9f, 0.999f, 1e-8f, m->step);
+        k_adam<<<(kParams + 255) / 256, 256>>>(m->d, lr, 0.9f, 0.999f, 1e-8f, m->wd, m->step);
         if (loss_hist) MLP_CUDA(m, cudaMemcpyAsync(loss_hist + e, m->d.loss, sizeof(float), cudaMemcpyDeviceToHost, 0));
     }
     MLP_CUDA(m, cudaGetLastError());

@@ -47,6 +47,8 @@ void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_str
 struct Outer {
     long N;          // vector length (12 V complex)
     int n_rhs, k, nblk, npart;
+    int st_threads;  // fused stencil: sites (threads) per CTA, 64 / 128 / 256
+    int st_order;    // fused stencil grid: 0 vector-fastest (link reuse in L2), 1 site-block-fastest
     int two_sided;
     int q_ring;      // 0: Q holds all k vectors (+1 scratch) [rhs][k+1][N]; 1: ring [rhs][3][N] (double pass)
     int qcols;       // vectors per RHS in Q: k + 1 or 3
@@ -90,6 +92,7 @@ constexpr int kStatusBreakdown = 2;   // serious breakdown (or a zero beta)
 constexpr int kStatusRhi = 3;         // RHi did not converge / singular pivot
 constexpr int kStatusLU = 4;          // singular p H_k
 constexpr int kStatusConverged = 5;   // adaptive k: frozen at its converged size (skipped by the kernels)
+constexpr int kStatusInnerBreakdown = 6;  // inner (two-sided) Lanczos on H_k': zero beta or delta
 
 // Copy modes for the next stencil's input: none, FP32, two-float.
 constexpr int kCopyNone = 0, kCopy32 = 1, kCopyDF = 2;
@@ -98,7 +101,8 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st);
 // 48 (two-float) or 64 (FP64).
 void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
                          double kappa, double mu, cudaStream_t st);
-int dslash_step1_blocks(const Geom& g);
+int dslash_step1_blocks(const Geom& g, int threads);
+constexpr int kStencilMaxThreads = 256;
 void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st);
 // kused[rhs]: outer steps whose basis vectors enter the lift of that RHS (k or,
 // adaptive, the converged size); coefficients beyond it are zero.
@@ -122,7 +126,7 @@ struct Inner {
     double* p;             // [rhs] out
     double* zmin;          // [rhs] out
     double* zmax;          // [rhs] out
-    double2* work;         // [rhs][kInnerWorkVecs][k] scratch
+    double2* work;         // [rhs][inner_work_elems(k)] scratch
     int* ipiv;             // [rhs][k]
     double2* Vl;           // inner basis [rhs][ell][k]
     double2* al;           // inner H_l, [rhs][ell]
@@ -136,6 +140,9 @@ struct Inner {
     int* timeout;          // device flag: a bounded wait ran out
 };
 constexpr int kInnerWorkVecs = 16;
+// per RHS: kInnerWorkVecs vectors of length k, then the sweep tables of the LU
+constexpr int kSweepTableElems = 64 * 32;
+__host__ __device__ constexpr size_t inner_work_elems(int k) { return (size_t)kInnerWorkVecs * k + kSweepTableElems; }
 // Largest outer size k the inner kernel supports (its LU factors and solve
 // vectors, 8 complex vectors of length k plus the pivots, fill shared memory).
 constexpr int kMaxInnerK = 1536;

@@ -29,7 +29,7 @@ constexpr int kMaxEll = NK_NOALLOC_MAX_ELL;
 constexpr size_t kAlign = 16;  // 16 double2 = 256 bytes
 constexpr size_t up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kOffWork = 0;
-constexpr size_t kOffVl = kOffWork + up((size_t)kMaxRhs * nk::kInnerWorkVecs * kMaxK);
+constexpr size_t kOffVl = kOffWork + up((size_t)kMaxRhs * nk::inner_work_elems(kMaxK));
 constexpr size_t kOffS = kOffVl + up((size_t)kMaxRhs * kMaxEll * kMaxK);
 constexpr size_t kOffAl = kOffS + up((size_t)kMaxRhs * kMaxEll * kMaxEll);
 constexpr size_t kOffBl = kOffAl + up((size_t)kMaxRhs * kMaxEll);
@@ -128,7 +128,7 @@ extern "C" int nk_inner_sign_noalloc(const double* alpha_dev, const double* beta
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_err(err, err_len, NK_ECUDA, cudaGetErrorString(e));
     for (int r = 0; r < n_rhs; ++r) {
-        if (status[r] == nk::kStatusBreakdown)
+        if (status[r] == nk::kStatusBreakdown || status[r] == nk::kStatusInnerBreakdown)
             return set_err(err, err_len, NK_EBREAKDOWN, "inner two-sided Lanczos: serious breakdown");
         if (status[r] == nk::kStatusRhi || status[r] == nk::kStatusLU)
             return set_err(err, err_len, NK_ERHI, "Roberts-Higham did not converge or p H_k is singular");

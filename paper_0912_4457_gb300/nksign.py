@@ -48,9 +48,9 @@ EXPORTED = [
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
     "nk_destroy",
-    "nk_mlp_create", "nk_mlp_set_norm", "nk_mlp_get_params", "nk_mlp_set_params", "nk_mlp_loss_grad",
+    "nk_mlp_create", "nk_mlp_set_norm", "nk_mlp_set_weight_decay", "nk_mlp_get_params", "nk_mlp_set_params", "nk_mlp_loss_grad",
     "nk_mlp_train", "nk_mlp_forward", "nk_mlp_last_error", "nk_mlp_destroy", "nk_features",
-    "nk_predict_sizes",
+    "nk_predict_sizes", "nk_set_launch", "nk_get_launch", "nk_autotune",
 ]
 
 NK_MLP_IN = 16
@@ -92,6 +92,13 @@ class NkStats(ctypes.Structure):
         }
 
 
+class NkLaunch(ctypes.Structure):
+    _fields_ = [("stencil_threads", ctypes.c_int), ("stencil_order", ctypes.c_int), ("step2_blocks", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.stencil_threads, self.stencil_order, self.step2_blocks)
+
+
 class NkError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "NK_?"), code, msg))
@@ -131,6 +138,7 @@ def load_library(path: str = LIB_PATH):
         "nk_destroy": ([P], None),
         "nk_mlp_create": ([ctypes.c_ulonglong, ctypes.POINTER(P)], I),
         "nk_mlp_set_norm": ([P, fp, fp, fp, fp], I),
+        "nk_mlp_set_weight_decay": ([P, ctypes.c_float], I),
         "nk_mlp_get_params": ([P, fp], I),
         "nk_mlp_set_params": ([P, fp], I),
         "nk_mlp_loss_grad": ([P, fp, fp, I, fp, fp], I),
@@ -140,6 +148,9 @@ def load_library(path: str = LIB_PATH):
         "nk_mlp_destroy": ([P], None),
         "nk_features": ([P, P, fp, P], I),
         "nk_predict_sizes": ([P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
+        "nk_set_launch": ([P, I, U, ctypes.POINTER(NkLaunch)], I),
+        "nk_get_launch": ([P, I, U, ctypes.POINTER(NkLaunch)], I),
+        "nk_autotune": ([P, I, U, ctypes.c_char_p, ctypes.POINTER(NkLaunch), dp], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -306,6 +317,24 @@ class Context:
             self._check(rc)
         return c, st.as_dict(), rc
 
+    # -- launch shape / autotuner -------------------------------------------
+    def set_launch(self, n_rhs, flags, stencil_threads, stencil_order, step2_blocks):
+        lc = NkLaunch(int(stencil_threads), int(stencil_order), int(step2_blocks))
+        self._check(self._lib.nk_set_launch(self.h, int(n_rhs), int(flags), ctypes.byref(lc)))
+
+    def get_launch(self, n_rhs, flags=NK_FP64):
+        lc = NkLaunch()
+        self._check(self._lib.nk_get_launch(self.h, int(n_rhs), int(flags), ctypes.byref(lc)))
+        return lc.as_tuple()
+
+    def autotune(self, n_rhs, flags=NK_FP64, cache_path=None):
+        """nk_autotune: returns ((stencil_threads, stencil_order, step2_blocks), ms per outer step)."""
+        lc = NkLaunch()
+        ms = ctypes.c_double()
+        path = cache_path.encode() if cache_path else None
+        self._check(self._lib.nk_autotune(self.h, int(n_rhs), int(flags), path, ctypes.byref(lc), ctypes.byref(ms)))
+        return lc.as_tuple(), ms.value
+
     # -- learned subspace sizes ---------------------------------------------
     def features(self, b_dev, stream=None):
         """nk_features: the NK_MLP_IN predictor features of one device source."""
@@ -362,6 +391,9 @@ class Mlp:
     def set_norm(self, xmu, xsd, ymu, ysd):
         arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (xmu, xsd, ymu, ysd)]
         self._check(self._lib.nk_mlp_set_norm(self.h, *[_fptr(a) for a in arrs]))
+
+    def set_weight_decay(self, wd):
+        self._check(self._lib.nk_mlp_set_weight_decay(self.h, float(wd)))
 
     def get_params(self):
         w = np.zeros(NK_MLP_PARAMS, np.float32)

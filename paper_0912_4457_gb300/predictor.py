@@ -121,17 +121,44 @@ def build_dataset(n: int, tol: float = 1e-8, first_seed: int = 0, log=print):
     return np.array(X, np.float32), np.array(Y, np.float32), recs
 
 
-def fit(X, Y, epochs: int = 3000, lr: float = 3e-3, seed: int = 0):
-    """(trained nksign.Mlp, loss history, standardisation (xmu, xsd, ymu, ysd))."""
-    m = nksign.Mlp(seed)
-    xsd = X.std(axis=0)
+def fit(X, Y, epochs: int = 2000, lr: float = 1e-3, seed: int = 0, val_frac: float = 0.25, chunk: int = 10,
+        weight_decays=(0.0, 1e-2, 1e-1)):
+    """(trained nksign.Mlp, validation-loss history, standardisation (xmu, xsd, ymu, ysd)).
+
+    A 16 -> 64 -> 64 -> 2 network has far more parameters than there are
+    labelled instances, so training is regularised and stops early: a seeded
+    fraction val_frac of the samples is held out, Adam (with each decoupled
+    weight decay of weight_decays) runs in chunks of `chunk` epochs on the
+    rest, and the parameters with the lowest held-out loss are kept."""
+    n = len(X)
+    order = np.random.default_rng([7, seed]).permutation(n)
+    n_val = int(round(val_frac * n)) if n >= 8 else 0
+    val, fit_idx = order[:n_val], order[n_val:]
+    Xf, Yf = X[fit_idx], Y[fit_idx]
+    xsd = Xf.std(axis=0)
     xsd = np.where(xsd > 1e-6, xsd, 1.0)
-    ysd = Y.std(axis=0)
+    ysd = Yf.std(axis=0)
     ysd = np.where(ysd > 1e-6, ysd, 1.0)
-    norm = (X.mean(axis=0), xsd, Y.mean(axis=0), ysd)
+    norm = (Xf.mean(axis=0), xsd, Yf.mean(axis=0), ysd)
+    m = nksign.Mlp(seed)
     m.set_norm(*norm)
-    hist = m.train(X, Y, epochs, lr)
-    return m, hist, norm
+    if n_val == 0:
+        return m, m.train(Xf, Yf, epochs, lr), norm
+    w_init = m.get_params()
+    best, w_best, hist_best = np.inf, w_init, None
+    for wd in weight_decays:
+        m.set_params(w_init)
+        m.set_weight_decay(wd)
+        hist = []
+        for _ in range(max(1, epochs // chunk)):
+            m.train(Xf, Yf, chunk, lr)
+            L, _ = m.loss_grad(X[val], Y[val])
+            hist.append(L)
+            if L < best:
+                best, w_best, hist_best = L, m.get_params(), hist
+    m.set_params(w_best)
+    m.set_weight_decay(0.0)
+    return m, np.array(hist_best), norm
 
 
 def save_model(path, params, xmu, xsd, ymu, ysd, meta):
@@ -151,45 +178,78 @@ def solve_predicted(ctx, m, b_dev, y_dev, tol: float, k_max: int = K_MAX, flags=
     """Adaptive-k solve of one source with predicted sizes: l = l_pred and the
     checks start at k_pred - 2 * NK_ADAPT_STEP, so that an exact prediction is
     accepted at k_pred after three checks (the first only fills the previous
-    coefficients).  Returns (stats, rc, (k_pred, l_pred))."""
+    coefficients); l is the predicted l times 1.5.  An under-predicted k costs further checks only; if the
+    tolerance is still not met at k_max (l too small for it), the solve is
+    repeated once with l = 256 from the default start.  Returns
+    (stats, rc, (k_pred, l_pred)); stats["fallback"] says whether the
+    repeat ran."""
     k_pred, l_pred = ctx.predict_sizes(m, b_dev, k_max)
+    # l too small never passes the test, so it gets a margin of 1.5x (the
+    # inner part costs O(k l), little against a repeated solve)
+    l_use = min(L_LABEL, k_pred, 2 * int(np.ceil(0.75 * l_pred)))
     ctx.set_adapt_start(max(64, k_pred - 128))
     try:
-        st, rc = ctx.sign_apply_dev(b_dev, y_dev, 1, k_max, l_pred, tol=tol, flags=flags, check=False)
+        st, rc = ctx.sign_apply_dev(b_dev, y_dev, 1, k_max, l_use, tol=tol, flags=flags, check=False)
     finally:
         ctx.set_adapt_start(0)
+    st["fallback"] = False
+    if rc == nksign.NK_ENOTCONV and l_use < L_LABEL:
+        ms = st["t_total_ms"]
+        st, rc = ctx.sign_apply_dev(b_dev, y_dev, 1, k_max, L_LABEL, tol=tol, flags=flags, check=False)
+        st["t_total_ms"] += ms
+        st["fallback"] = True
     return st, rc, (k_pred, l_pred)
 
 
-def evaluate(m, seeds, tol: float = 1e-8, l_default: int = 160, log=print):
-    """Held-out comparison: predicted sizes against adaptive k from its default
-    start with l = l_default.  Accuracy of both is measured against a fixed-k
-    solve at k_used + 256 (l = 256)."""
+def evaluate(m, seeds, tol: float = 1e-8, l_default: int = 160, mean_sizes=None, log=print):
+    """Held-out comparison of three ways to run adaptive k on each instance:
+      default    checks from NK_ADAPT_FIRST(l_default) on, l = l_default;
+      mean       the training set's geometric-mean (k, l) used like a prediction
+                 (checks from k - 128, l x 1.5);
+      predicted  the predictor's (k, l) (solve_predicted).
+    Accuracy is measured against a fixed-k solve 256 steps past the largest
+    accepted k (l = 256).  Times are CUDA-event times of warm repeats."""
     import torch
     rows = []
     for s in seeds:
         inst = sample_instance(s)
         ctx = _context(inst)
         b = torch.from_numpy(inst["b"]).cuda()
-        y0 = torch.empty_like(b)
-        y1 = torch.empty_like(b)
-        st0, rc0 = ctx.sign_apply_dev(b, y0, 1, K_MAX, l_default, tol=tol, check=False)
-        st1, rc1, (kp, lp) = solve_predicted(ctx, m, b, y1, tol)
-        if rc0 != nksign.NK_OK or rc1 != nksign.NK_OK:
-            rows.append({"seed": s, "rc": [rc0, rc1]})
+        ys = {name: torch.empty_like(b) for name in ("default", "mean", "predicted")}
+
+        def run(name):
+            if name == "default":
+                st, rc = ctx.sign_apply_dev(b, ys[name], 1, K_MAX, l_default, tol=tol, check=False)
+                return st, rc
+            if name == "mean":
+                km, lm = mean_sizes
+                l_use = min(L_LABEL, km, 2 * int(np.ceil(0.75 * lm)))
+                ctx.set_adapt_start(max(64, km - 128))
+                try:
+                    st, rc = ctx.sign_apply_dev(b, ys[name], 1, K_MAX, l_use, tol=tol, check=False)
+                finally:
+                    ctx.set_adapt_start(0)
+                return st, rc
+            st, rc, _ = solve_predicted(ctx, m, b, ys[name], tol)
+            return st, rc
+
+        names = ["default", "predicted"] + (["mean"] if mean_sizes else [])
+        out = {name: run(name) for name in names}
+        if any(rc != nksign.NK_OK for _, rc in out.values()):
+            rows.append({"seed": s, "rc": {name: rc for name, (_, rc) in out.items()}})
             ctx.close()
             continue
-        kref = min(K_MAX, max(st0["k_used"], st1["k_used"]) + 256)
+        kref = min(K_MAX, max(st["k_used"] for st, _ in out.values()) + 256)
         ref = torch.empty_like(b)
         ctx.sign_apply_dev(b, ref, 1, kref, min(kref, L_LABEL))
-        # warm timings: repeat each once more and keep the second
-        st0, _ = ctx.sign_apply_dev(b, y0, 1, K_MAX, l_default, tol=tol, check=False)
-        st1, _, _ = solve_predicted(ctx, m, b, y1, tol)
-        row = {"seed": s, "dims": inst["dims"], "mu": round(inst["mu"], 3), "k_pred": kp, "l_pred": lp,
-               "default": {"k": st0["k_used"], "checks": st0["checks"], "ms": round(st0["t_total_ms"], 2),
-                           "err": _rel(y0, ref)},
-               "predicted": {"k": st1["k_used"], "checks": st1["checks"], "ms": round(st1["t_total_ms"], 2),
-                             "err": _rel(y1, ref)}}
+        kp, lp = ctx.predict_sizes(m, b, K_MAX)
+        row = {"seed": s, "dims": inst["dims"], "mu": round(inst["mu"], 3), "k_pred": kp, "l_pred": lp}
+        for name in names:
+            st, _ = run(name)          # warm repeat for the time
+            row[name] = {"k": st["k_used"], "checks": st["checks"], "ms": round(st["t_total_ms"], 2),
+                         "err": _rel(ys[name], ref)}
+            if name == "predicted":
+                row[name]["fallback"] = st["fallback"]
         rows.append(row)
         log(json.dumps(row))
         ctx.close()
@@ -198,42 +258,53 @@ def evaluate(m, seeds, tol: float = 1e-8, l_default: int = 160, log=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--n", type=int, default=64, help="instances (the last quarter is held out)")
+    ap.add_argument("--n", type=int, default=192, help="instances (the last quarter is held out)")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--epochs", type=int, default=2000)
     ap.add_argument("--out", default=WEIGHTS_PATH)
+    ap.add_argument("--dataset", default=None,
+                    help="npz of features and labels: read if it exists, else written after labelling")
     ap.add_argument("--report", default=None, help="JSON summary path")
     a = ap.parse_args(argv)
     n_test = a.n // 4
-    train_seeds = list(range(0, a.n - n_test))
     test_seeds = list(range(a.n - n_test, a.n))
     t0 = time.time()
-    X, Y, recs = build_dataset(len(train_seeds), a.tol, 0)
+    if a.dataset and os.path.exists(a.dataset):
+        z = np.load(a.dataset, allow_pickle=False)
+        X, Y, Xt, Yt = z["X"], z["Y"], z["Xt"], z["Yt"]
+        recs, recs_t = json.loads(str(z["recs"])), json.loads(str(z["recs_t"]))
+    else:
+        X, Y, recs = build_dataset(a.n - n_test, a.tol, 0)
+        Xt, Yt, recs_t = build_dataset(n_test, a.tol, a.n - n_test)
+        if a.dataset:
+            np.savez(a.dataset, X=X, Y=Y, Xt=Xt, Yt=Yt, recs=json.dumps(recs), recs_t=json.dumps(recs_t))
     t_data = time.time() - t0
     m, hist, norm = fit(X, Y, a.epochs)
-    pred = m.forward(X)
-    train_rmse = np.sqrt(np.mean((pred - Y) ** 2, axis=0)).tolist()
-    Xt, Yt, recs_t = build_dataset(n_test, a.tol, a.n - n_test)
+    train_rmse = np.sqrt(np.mean((m.forward(X) - Y) ** 2, axis=0)).tolist()
     test_rmse = np.sqrt(np.mean((m.forward(Xt) - Yt) ** 2, axis=0)).tolist() if len(Xt) else None
-    rows = evaluate(m, test_seeds, a.tol)
+    mean_rmse = np.sqrt(np.mean((Y.mean(axis=0) - Yt) ** 2, axis=0)).tolist() if len(Xt) else None
+    km = 2 * int(round(0.5 * 2 ** Y[:, 0].mean()))
+    lm = 2 * int(round(0.5 * 2 ** Y[:, 1].mean()))
+    rows = evaluate(m, test_seeds, a.tol, mean_sizes=(km, lm))
     ok = [r for r in rows if "default" in r]
+    tot = lambda name, key: float(np.sum([r[name][key] for r in ok]))
     summ = {
-        "n_train": int(len(X)), "n_test": int(len(Xt)), "tol": a.tol, "data_sec": round(t_data, 1),
-        "loss_first_last": [float(hist[0]), float(hist[-1])],
-        "rmse_log2_train": train_rmse, "rmse_log2_test": test_rmse,
-        "default_ms": float(np.sum([r["default"]["ms"] for r in ok])),
-        "predicted_ms": float(np.sum([r["predicted"]["ms"] for r in ok])),
-        "default_checks": int(np.sum([r["default"]["checks"] for r in ok])),
-        "predicted_checks": int(np.sum([r["predicted"]["checks"] for r in ok])),
-        "max_err_default": float(max([r["default"]["err"] for r in ok], default=0.0)),
-        "max_err_predicted": float(max([r["predicted"]["err"] for r in ok], default=0.0)),
+        "n_train": int(len(X)), "n_test": int(len(Xt)), "n_evaluated": len(ok), "tol": a.tol,
+        "data_sec": round(t_data, 1), "val_loss_first_best": [float(hist[0]), float(np.min(hist))],
+        "rmse_log2_train": train_rmse, "rmse_log2_test": test_rmse, "rmse_log2_test_of_mean": mean_rmse,
+        "mean_sizes": [km, lm],
+        "ms": {name: tot(name, "ms") for name in ("default", "mean", "predicted")},
+        "checks": {name: int(tot(name, "checks")) for name in ("default", "mean", "predicted")},
+        "max_err": {name: float(max([r[name]["err"] for r in ok], default=0.0))
+                    for name in ("default", "mean", "predicted")},
+        "fallbacks": int(sum(1 for r in ok if r["predicted"].get("fallback"))),
         "labels_train": [[r["seed"], r["k"], r["l"]] for r in recs],
         "labels_test": [[r["seed"], r["k"], r["l"]] for r in recs_t],
         "rows": rows,
     }
     save_model(a.out, m.get_params(), *norm,
                {k: summ[k] for k in ("n_train", "n_test", "tol", "rmse_log2_train", "rmse_log2_test")})
-    print(json.dumps({k: v for k, v in summ.items() if k != "rows"}))
+    print(json.dumps({k: v for k, v in summ.items() if k not in ("rows", "labels_train", "labels_test")}))
     if a.report:
         with open(a.report, "w") as fh:
             json.dump(summ, fh, indent=1)

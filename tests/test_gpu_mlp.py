@@ -74,6 +74,21 @@ def test_set_params_round_trip_and_training_matches_oracle():
     assert hist[-1] < 0.7 * hist[0]
 
 
+def test_weight_decay_matches_oracle():
+    m = Mlp(seed=11)
+    w0 = m.get_params()
+    m.set_weight_decay(0.05)
+    X, T = _batch(12, 32)
+    hist = m.train(X, T, epochs=20, lr=3e-3)
+    w_or, hist_or = omlp.train(w0.astype(np.float64), X.astype(np.float64), T.astype(np.float64), 20, 3e-3,
+                               wd=0.05)
+    np.testing.assert_allclose(hist, hist_or, rtol=1e-3)
+    w = m.get_params().astype(np.float64)
+    assert np.linalg.norm(w - w_or) <= 1e-2 * np.linalg.norm(w_or - w0)
+    with pytest.raises(NkError):
+        m.set_weight_decay(-1.0)
+
+
 def test_training_is_deterministic():
     X, T = _batch(8, 64)
     out = []

@@ -87,6 +87,15 @@ def test_first_adam_step_is_a_signed_learning_rate_step():
     np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-12)
 
 
+def test_weight_decay_alone_shrinks_the_weights():
+    """With zero gradient the moments stay zero and a step is w -> (1 - lr wd) w."""
+    w = _params(10)
+    z = np.zeros_like(w)
+    w1, m, v = mlp.adam_step(w, z, z, z, 1, 1e-2, wd=0.1)
+    np.testing.assert_allclose(w1, (1.0 - 1e-3) * w, rtol=1e-15)
+    assert not m.any() and not v.any()
+
+
 def test_training_fits_a_small_target():
     """Adam on a smooth target from 48 samples lowers the loss by a large factor."""
     rng = np.random.default_rng(8)
