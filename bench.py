@@ -347,7 +347,7 @@ def run_gpu(args, w, rank, world, local_rank):
     tot = sum(tc.values())
     share = {kk: (tc[kk] / tot if tot else 0.0) for kk in tc}
     dom = max(tc, key=lambda kk: tc[kk])
-    roof = dominant_roofline(dom, tc, nc, w, peaks)
+    roof = dominant_roofline(dom, tc, nc, w, peaks, clocks.get("sm_mhz"))
     sten = stencil_roofline(nk, torch, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -363,7 +363,10 @@ def run_gpu(args, w, rank, world, local_rank):
         "speedup_vs_fp64_plain": (value / world) / (1.0 / (fp64_ms * 1e-3)),
         "gpu_launches": launches,
         "launch_shape": {"stencil_threads": shape[0], "stencil_order": shape[1], "step2_blocks": shape[2],
+                         "early_threads": shape[3], "early_order": shape[4],
                          "autotune_ms_per_outer_step": tune_ms},
+        "rhi_iters": stp["rhi_iters"],
+        "kernel_class_ms": {kk: round(v, 3) for kk, v in tc.items()},
         "roofline": roof,
         "stencil_roofline": sten,
         "kernel_time_share": {kk: round(v, 4) for kk, v in share.items()},
@@ -379,9 +382,14 @@ def run_gpu(args, w, rank, world, local_rank):
 
 def run_ncu(args, w):
     """--warmup kernel-by-kernel solves, then one more: the launches an ncu
-    launch list or capture selects from (skip the warm-up ones with -s)."""
+    launch list or capture selects from (skip the warm-up ones with -s).
+    --ncu-k K shortens the outer recurrence to K steps (the per-launch work of
+    every kernel but the lift is unchanged; the basis then takes K/k of the
+    memory), for captures that must stay small."""
     import torch
     import paper_0912_4457_gb300 as nk
+    if args.ncu_k:   # half of the shortened recurrence in each stencil precision
+        w = dict(w, k=args.ncu_k, ell=min(w["ell"], args.ncu_k), j0=min(w["j0"], args.ncu_k // 2))
     U, b_host = make_inputs(w)
     ctx = nk.Context(w["dims"])
     ctx.load_links(U)
@@ -409,40 +417,57 @@ def _lib_host_solve(ctx, bp, yp, k, ell, flags):
     ctx._check(rc)
 
 
-def dominant_roofline(dom, tc, nc, w, peaks):
+def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
     """Roofline entry for the kernel class with the largest device time.
 
-    Algorithmic bytes and FP64 flops per complex vector element (each moved or
-    computed once), for n_rhs sources, two-sided (Hermitian in parentheses):
-      step2: reads q_{j+1}, q_j, p_{j+1}, p_j; writes q_{j+1}, p_{j+1} and their
-             FP32 copies: 112 B (56 B); 24 FP64 flops (8) -- bound by FP64;
-      dslash (fused with step 1): per site links 288 B (FP32) + per vector
-             FP32 input 96 B, FP64 q_{j-1} and dot vector 2x192 B, FP64 output 192 B.
+    Algorithmic work per launch, n_rhs sources, two-sided (Hermitian in
+    parentheses); each array moved once, each flop of the method counted once:
+      dslash_df: the two-float stencil, 1320 flops per site and vector
+             (2 n_rhs (n_rhs) vectors).  Two-float arithmetic costs 11 FP32
+             instructions per add and 7 per multiply (TwoSum / FMA-TwoProd
+             with renormalisation), 9 on average for the stencil's equal mix, so
+             its ALU peak is the FP32 issue rate / 9:
+             152 SMs x 128 lanes x f_SM / 9 (f_SM the median SM clock sampled
+             during the timed region);
+      dslash (FP32 stencil fused with step 1): per site links 288 B + per
+             vector FP32 input 96 B, FP64 q_{j-1} and dot vector 2 x 192 B,
+             FP64 output 192 B -- HBM;
+      step2: 24 (8) FP64 flops per element -- FP64 ALU, 1.0 TFLOP/s measured
+             DFMA rate;
+      lift: reads V_k once, 16 B x k per element -- HBM.
     """
     V = int(np.prod(w["dims"]))
     N = 12 * V
     n_rhs = w["n_rhs"]
     two = w["mu"] != 0.0
+    nv = (2 if two else 1) * n_rhs
     ms = tc[dom] / max(1, nc[dom])
-    fp64_peak = 1.0  # TFLOP/s, measured DFMA rate of this GB300 (see DESIGN.md)
+    fp64_peak = 1.0  # TFLOP/s, measured DFMA rate of this GB300
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if dom == "dslash_df":
+        flops = 1320.0 * V * nv
+        tf = flops / (ms * 1e-3) / 1e12
+        peak = 152 * 128 * (sm_mhz or 2070.0) * 1e6 / 9.0 / 1e12
+        return {"kernel": "k_dslash_step1<df> (two-float stencil fused with step 1)", "bound": "alu",
+                "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "traffic": None,
+                "ms_per_launch": ms, "flops_per_launch": flops,
+                "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
     if dom == "step2":
         flops = (24 if two else 8) * N * n_rhs
         tf = flops / (ms * 1e-3) / 1e12
         return {"kernel": "k_step2", "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": tf / fp64_peak, "traffic": None, "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": (112 if two else 56) * N * n_rhs}
-    if dom in ("dslash", "dslash_df", "dslash64"):
-        nv = (2 if two else 1) * n_rhs
+    if dom in ("dslash", "dslash64"):
         b = V * (288 + nv * (96 + 192)) + V * n_rhs * 2 * 192
         gbs = b / (ms * 1e-3) / 1e9
         return {"kernel": "k_dslash_step1", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None, "ms_per_launch": ms,
-                "note": "average over FP64- and FP32-stencil launches"}
+                "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "ms_per_launch": ms}
     if dom == "lift":
         b = n_rhs * w["k"] * N * 16
         gbs = b / (ms * 1e-3) / 1e9
         return {"kernel": "k_lift", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "traffic": None, "ms_per_launch": ms}
+                "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "ms_per_launch": ms}
     return {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": None, "traffic": None, "ms_per_launch": ms}
 
@@ -457,6 +482,7 @@ def main():
                     help="ncu: run --warmup solves and then one solve kernel by kernel (no graph, no oracle, "
                          "no output line), for launch lists and captures under ncu")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
     ap.add_argument("--tune-cache", default=None,
                     help="launch-shape cache file (read if it has the workload's shape, else written)")
     args = ap.parse_args()

@@ -138,25 +138,32 @@ int nk_set_adapt_start(nk_ctx* ctx, int k_first);
  *                   1: consecutive CTAs take the site blocks of one vector;
  *  step2_blocks     CTAs per RHS of the step-2 and norm kernels (grid-stride),
  *                   1..4096; also the number of partial sums of their
- *                   deterministic reductions.
+ *                   deterministic reductions;
+ *  early_threads, early_order
+ *                   the stencil shape of the two-float steps before j0 in
+ *                   NK_MIXED mode (unused in NK_FP64 mode).
  * A shape belongs to (n_rhs, sidedness of the current mu (mu != 0), the
  * NK_MIXED bit of flags).  Different shapes sum in different orders, so
  * results differ at rounding level; one shape is bitwise reproducible.
- * Unset shapes use 128 / 0 / min(ceil(12 V / 2048), 608 / n_rhs).
+ * Unset shapes use 128 / 0 / min(ceil(12 V / 2048), 608 / n_rhs) / 128 / 0.
  */
 typedef struct nk_launch {
     int stencil_threads;
     int stencil_order;
     int step2_blocks;
+    int early_threads;
+    int early_order;
 } nk_launch;
 int nk_set_launch(nk_ctx* ctx, int n_rhs, unsigned flags, const nk_launch* shape);
 int nk_get_launch(nk_ctx* ctx, int n_rhs, unsigned flags, nk_launch* shape);
-/* Times 16 outer steps of every stencil shape (3 x 2), then of step2_blocks
- * in {b/2, b, 2b, 4b} (b the default) with the fastest stencil shape, on a
- * synthetic constant source, and keeps the fastest (written to *best and
- * its time per outer step to *ms_per_step; both nullable).  cache_path
- * (nullable): a text file of lines
- *   nk_launch Lx Ly Lz Lt n_rhs two_sided mixed threads order blocks ms_per_step
+/* Times 16 outer steps of every stencil shape (3 x 2) with the FP32 stencil
+ * (NK_MIXED) or the FP64 one, in NK_MIXED mode also every early shape with
+ * the two-float stencil, then step2_blocks in {b/2, b, 2b, 4b} (b the
+ * default) with the fastest stencil shape, on a synthetic constant source,
+ * and keeps the fastest (written to *best and its time per outer step to
+ * *ms_per_step; both nullable).  cache_path (nullable): a text file of lines
+ *   nk_launch Lx Ly Lz Lt n_rhs two_sided mixed threads order blocks
+ *             early_threads early_order ms_per_step
  * read first (a matching line is used without timing) and appended to after
  * timing.  Blocks. */
 int nk_autotune(nk_ctx* ctx, int n_rhs, unsigned flags, const char* cache_path, nk_launch* best,

@@ -17,6 +17,8 @@
 // Layouts (device-internal, set up by the engine):
 //   links:   [nu 4][e 9][site V] complex, e = 3*row + col (coalesced over sites)
 //   spinors: [component 12][site V] complex per vector, component = 3*spin + colour
+#include <type_traits>
+
 #include "nk_common.cuh"
 #include "nk_kernels.h"
 
@@ -26,15 +28,6 @@ template <typename R>
 struct Spinor {
     typename C2<R>::T c[4][3];
 };
-
-template <typename R>
-__device__ __forceinline__ void load_link(const typename C2<R>::T* __restrict__ U, int V, int nu,
-                                          int site, typename C2<R>::T u[3][3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) u[a][b] = U[(size_t)(nu * 9 + 3 * a + b) * V + site];
-}
 
 template <typename R>
 __device__ __forceinline__ void load_spinor(const typename C2<R>::T* __restrict__ in, int V, int site,
@@ -50,46 +43,48 @@ template <typename T> __device__ __forceinline__ T mul_i(T z) { T r; r.x = -z.y;
 template <typename T> __device__ __forceinline__ T mul_mi(T z) { T r; r.x = z.y; r.y = -z.x; return r; }
 template <typename T> __device__ __forceinline__ T neg(T z) { T r; r.x = -z.x; r.y = -z.y; return r; }
 
-// One hop: acc += w * (1 + s gamma_nu) M psi_n with M = U (dag = false) or U^dagger.
+// One hop: acc += w * (1 + s gamma_nu) M psi_n with M = U (dag = false) or
+// U^dagger, U the link of direction NU at site ls and psi the input at site
+// sn.  The spin projection is applied as the components arrive and each row
+// of M psi is accumulated as soon as it is formed, so that neither the whole
+// neighbour spinor nor the whole link is held in registers (this matters
+// most for the two-float instantiation).
 template <int NU, bool DAG, typename R>
-__device__ __forceinline__ void hop(typename C2<R>::T acc[4][3], const typename C2<R>::T psi[4][3],
-                                    const typename C2<R>::T u[3][3], R s, R w) {
+__device__ __forceinline__ void hop(typename C2<R>::T acc[4][3], const typename C2<R>::T* __restrict__ in, int V,
+                                    int sn, const typename C2<R>::T* __restrict__ U, int ls, R s, R w) {
     typedef typename C2<R>::T T;
     T h0[3], h1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        const T p0 = in[(size_t)a * V + sn], p1 = in[(size_t)(3 + a) * V + sn];
+        const T p2 = in[(size_t)(6 + a) * V + sn], p3 = in[(size_t)(9 + a) * V + sn];
         T c0, c1;  // (C_nu psi_dn)_0, _1
-        if (NU == 0) { c0 = mul_mi(psi[3][a]); c1 = mul_mi(psi[2][a]); }
-        else if (NU == 1) { c0 = neg(psi[3][a]); c1 = psi[2][a]; }
-        else if (NU == 2) { c0 = mul_mi(psi[2][a]); c1 = mul_i(psi[3][a]); }
-        else { c0 = psi[2][a]; c1 = psi[3][a]; }
-        h0[a].x = psi[0][a].x + s * c0.x; h0[a].y = psi[0][a].y + s * c0.y;
-        h1[a].x = psi[1][a].x + s * c1.x; h1[a].y = psi[1][a].y + s * c1.y;
+        if (NU == 0) { c0 = mul_mi(p3); c1 = mul_mi(p2); }
+        else if (NU == 1) { c0 = neg(p3); c1 = p2; }
+        else if (NU == 2) { c0 = mul_mi(p2); c1 = mul_i(p3); }
+        else { c0 = p2; c1 = p3; }
+        h0[a].x = p0.x + s * c0.x; h0[a].y = p0.y + s * c0.y;
+        h1[a].x = p1.x + s * c1.x; h1[a].y = p1.y + s * c1.y;
     }
-    T m0[3], m1[3];
+    const R ws = w * s;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         T x0, x1;
         x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            T e = DAG ? u[b][a] : u[a][b];
+            const T e = DAG ? U[(size_t)(NU * 9 + 3 * b + a) * V + ls] : U[(size_t)(NU * 9 + 3 * a + b) * V + ls];
             R ey = DAG ? -e.y : e.y;
             x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
             x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
         }
-        m0[a] = x0; m1[a] = x1;
-    }
-    R ws = w * s;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        acc[0][a].x += w * m0[a].x; acc[0][a].y += w * m0[a].y;
-        acc[1][a].x += w * m1[a].x; acc[1][a].y += w * m1[a].y;
+        acc[0][a].x += w * x0.x; acc[0][a].y += w * x0.y;
+        acc[1][a].x += w * x1.x; acc[1][a].y += w * x1.y;
         T b0, b1;  // (B_nu m)_0, _1
-        if (NU == 0) { b0 = mul_i(m1[a]); b1 = mul_i(m0[a]); }
-        else if (NU == 1) { b0 = m1[a]; b1 = neg(m0[a]); }
-        else if (NU == 2) { b0 = mul_i(m0[a]); b1 = mul_mi(m1[a]); }
-        else { b0 = m0[a]; b1 = m1[a]; }
+        if (NU == 0) { b0 = mul_i(x1); b1 = mul_i(x0); }
+        else if (NU == 1) { b0 = x1; b1 = neg(x0); }
+        else if (NU == 2) { b0 = mul_i(x0); b1 = mul_mi(x1); }
+        else { b0 = x0; b1 = x1; }
         acc[2][a].x += ws * b0.x; acc[2][a].y += ws * b0.y;
         acc[3][a].x += ws * b1.x; acc[3][a].y += ws * b1.y;
     }
@@ -99,20 +94,14 @@ template <int NU, typename R>
 __device__ __forceinline__ void dir(typename C2<R>::T acc[4][3], const typename C2<R>::T* __restrict__ U,
                                     const typename C2<R>::T* __restrict__ in, const Geom& g, int site,
                                     int coord, int L, int stride, R wplus, R wminus) {
-    typedef typename C2<R>::T T;
-    T u[3][3], p[4][3];
     // backward neighbour y - nu: (1 + gamma) U_{y-nu,+nu} psi_{y-nu}
-    int sb = coord == 0 ? site + (L - 1) * stride : site - stride;
-    R fb = (NU == 3 && g.antiperiodic && coord == 0) ? R(-1) : R(1);
-    load_link<R>(U, g.V, NU, sb, u);
-    load_spinor<R>(in, g.V, sb, p);
-    hop<NU, false, R>(acc, p, u, R(1), wplus * fb);
+    const int sb = coord == 0 ? site + (L - 1) * stride : site - stride;
+    const R fb = (NU == 3 && g.antiperiodic && coord == 0) ? R(-1) : R(1);
+    hop<NU, false, R>(acc, in, g.V, sb, U, sb, R(1), wplus * fb);
     // forward neighbour y + nu: (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}
-    int sf = coord == L - 1 ? site - (L - 1) * stride : site + stride;
-    R ff = (NU == 3 && g.antiperiodic && coord == L - 1) ? R(-1) : R(1);
-    load_link<R>(U, g.V, NU, site, u);
-    load_spinor<R>(in, g.V, sf, p);
-    hop<NU, true, R>(acc, p, u, R(-1), wminus * ff);
+    const int sf = coord == L - 1 ? site - (L - 1) * stride : site + stride;
+    const R ff = (NU == 3 && g.antiperiodic && coord == L - 1) ? R(-1) : R(1);
+    hop<NU, true, R>(acc, in, g.V, sf, U, site, R(-1), wminus * ff);
 }
 
 // precision-generic conversions (float via the integer pipe, see nk_common.cuh)
@@ -228,8 +217,15 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
 // output on, everything is FP64.  The blocks of side 0 reduce H(j,j) with the
 // deterministic two-stage scheme.  In double-pass mode side 0 also
 // accumulates y += c'_j q_j at its own site.
+// Minimum resident CTAs of kStencilMaxThreads threads per SM for the fused
+// stencil: the two-float instantiation is latency bound on long dependent
+// FP32 chains and gains from more resident warps than its unconstrained
+// register count (about 160) allows.
+template <typename R> struct StencilMinBlocks { static constexpr int value = 1; };
+template <> struct StencilMinBlocks<df> { static constexpr int value = 2; };
+
 template <typename R, bool TS, bool PASS2>
-__global__ void __launch_bounds__(kStencilMaxThreads) k_dslash_step1(
+__global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value) k_dslash_step1(
     const typename C2<R>::T* __restrict__ U, Geom g, Outer o, int j, R kappa, R emu, R emu_inv,
     const typename C2<R>::T* __restrict__ qin, long qin_stride, const typename C2<R>::T* __restrict__ pin,
     long pin_stride) {
@@ -333,19 +329,25 @@ template <typename R, typename T>
 static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R kappa, R emu, R emu_inv, const T* qin,
                            long qs, const T* pin, long ps, cudaStream_t st) {
     const int nvec = o.two_sided ? 2 * o.n_rhs : o.n_rhs;
-    dim3 grid((unsigned)(dslash_step1_blocks(g, o.st_threads) * nvec));
-    const int threads = o.st_threads;
+    // launch shape of this precision (the kernel reads the grid order from o)
+    Outer o2 = o;
+    if (std::is_same<R, df>::value) {
+        o2.st_threads = o.st_threads_df;
+        o2.st_order = o.st_order_df;
+    }
+    const int threads = o2.st_threads;
+    dim3 grid((unsigned)(dslash_step1_blocks(g, threads) * nvec));
     const bool pass2 = o.y != nullptr;
     if (o.two_sided) {
         if (pass2)
-            k_dslash_step1<R, true, true><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, true, true><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
         else
-            k_dslash_step1<R, true, false><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, true, false><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
     } else {
         if (pass2)
-            k_dslash_step1<R, false, true><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, false, true><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
         else
-            k_dslash_step1<R, false, false><<<grid, threads, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+            k_dslash_step1<R, false, false><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
     }
 }
 

@@ -134,7 +134,9 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.N = N; o.n_rhs = n_rhs; o.k = k; o.nblk = nblk; o.two_sided = two_sided;
     o.st_threads = lc.stencil_threads;
     o.st_order = lc.stencil_order;
-    o.npart = std::max(nblk, nk::dslash_step1_blocks(g, lc.stencil_threads));
+    o.st_threads_df = lc.early_threads;
+    o.st_order_df = lc.early_order;
+    o.npart = std::max(nblk, nk::dslash_step1_blocks(g, std::min(lc.stencil_threads, lc.early_threads)));
     o.q_ring = double_pass ? 1 : 0;
     o.qcols = double_pass ? 3 : k + 1;   // single pass: k basis vectors + one scratch column
     o.Q = (double2*)take(vec * (size_t)o.qcols * n_rhs);
@@ -194,12 +196,16 @@ nk_launch launch_cfg(const nk_ctx* c, int n_rhs, bool ts, bool mixed) {
     d.stencil_threads = 128;
     d.stencil_order = 0;
     d.step2_blocks = blocks_per_rhs(c->N, n_rhs);
+    d.early_threads = 128;
+    d.early_order = 0;
     return d;
 }
 
 bool valid_launch(const nk_launch& l) {
-    return (l.stencil_threads == 64 || l.stencil_threads == 128 || l.stencil_threads == 256) &&
-           (l.stencil_order == 0 || l.stencil_order == 1) && l.step2_blocks >= 1 && l.step2_blocks <= 4096;
+    auto threads_ok = [](int t) { return t == 64 || t == 128 || t == 256; };
+    auto order_ok = [](int o) { return o == 0 || o == 1; };
+    return threads_ok(l.stencil_threads) && order_ok(l.stencil_order) && threads_ok(l.early_threads) &&
+           order_ok(l.early_order) && l.step2_blocks >= 1 && l.step2_blocks <= 4096;
 }
 
 int check_solve_args(nk_ctx* c, int n_rhs, int k, int ell, double tol) {
@@ -671,8 +677,8 @@ int nk_get_launch(nk_ctx* c, int n_rhs, unsigned flags, nk_launch* l) {
 
 // Time of `steps` outer steps (init included) of n_rhs copies of the source
 // in `src` with launch shape lc: the minimum over three runs after a warm-up.
-static int time_shape(nk_ctx* c, const double* src, int n_rhs, bool mixed, const nk_launch& lc, int steps,
-                      cudaStream_t st, float* best) {
+static int time_shape(nk_ctx* c, const double* src, int n_rhs, bool mixed, int j0, const nk_launch& lc,
+                      int steps, cudaStream_t st, float* best) {
     const bool ts = c->mu != 0.0;
     Layout dry = carve(nullptr, geom_of(c), n_rhs, steps, 2, ts, false, lc);
     int rc = ensure(c, c->ws, dry.total);
@@ -688,7 +694,7 @@ static int time_shape(nk_ctx* c, const double* src, int n_rhs, bool mixed, const
         L.st = st;
         enqueue_load_sources(c, Lw.o, src, n_rhs, L);
         NK_CUDA(c, cudaEventRecord(e0, st));
-        enqueue_outer(c, Lw.o, mixed, 0, L);   // mixed: the FP32 stencil throughout
+        enqueue_outer(c, Lw.o, mixed, j0, L);   // mixed: two-float before j0, FP32 after
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());
         NK_CUDA(c, cudaEventSynchronize(e1));
@@ -712,18 +718,20 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "r")) {
             char tag[32];
-            int d[4], nr, t2, mx, th, od, bl;
+            int d[4], nr, t2, mx, th, od, bl, eth, eod;
             double ms;
             bool found = false;
             nk_launch hit;
-            while (std::fscanf(f, "%31s %d %d %d %d %d %d %d %d %d %d %lf", tag, &d[0], &d[1], &d[2], &d[3], &nr,
-                               &t2, &mx, &th, &od, &bl, &ms) == 12) {
+            while (std::fscanf(f, "%31s %d %d %d %d %d %d %d %d %d %d %d %d %lf", tag, &d[0], &d[1], &d[2], &d[3],
+                               &nr, &t2, &mx, &th, &od, &bl, &eth, &eod, &ms) == 14) {
                 if (std::strcmp(tag, "nk_launch") != 0) break;
                 if (d[0] == c->dims[0] && d[1] == c->dims[1] && d[2] == c->dims[2] && d[3] == c->dims[3] &&
                     nr == n_rhs && t2 == ts && mx == mixed) {
                     hit.stencil_threads = th;
                     hit.stencil_order = od;
                     hit.step2_blocks = bl;
+                    hit.early_threads = eth;
+                    hit.early_order = eod;
                     if (valid_launch(hit)) {
                         found = true;
                         if (ms_per_step) *ms_per_step = ms;
@@ -750,8 +758,14 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     nk_launch best = launch_cfg(c, n_rhs, ts != 0, mixed != 0);
     best.stencil_threads = 128;
     best.stencil_order = 0;
+    best.early_threads = 128;
+    best.early_order = 0;
     const int b0 = blocks_per_rhs(c->N, n_rhs);
     best.step2_blocks = b0;
+    auto timed = [&](const nk_launch& l, int j0, float* t) {
+        return time_shape(c, src, n_rhs, mixed != 0, j0, l, steps, st, t);
+    };
+    // FP64 mode: the FP64 stencil; mixed: the FP32 stencil (all steps after j0 = 0)
     float t_best = 1e30f;
     for (int th : {64, 128, 256})
         for (int od : {0, 1}) {
@@ -759,15 +773,30 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
             l.stencil_threads = th;
             l.stencil_order = od;
             float t;
-            rc = time_shape(c, src, n_rhs, mixed != 0, l, steps, st, &t);
+            rc = timed(l, 0, &t);
             if (rc) { cudaStreamDestroy(st); return rc; }
             if (t < t_best) { t_best = t; best = l; }
         }
+    if (mixed) {   // the two-float stencil of the early steps (all steps before j0 = steps)
+        float te_best = 1e30f;
+        nk_launch b2 = best;
+        for (int th : {64, 128, 256})
+            for (int od : {0, 1}) {
+                nk_launch l = best;
+                l.early_threads = th;
+                l.early_order = od;
+                float t;
+                rc = timed(l, steps, &t);
+                if (rc) { cudaStreamDestroy(st); return rc; }
+                if (t < te_best) { te_best = t; b2 = l; }
+            }
+        best = b2;
+    }
     for (int bl : {std::max(1, b0 / 2), 2 * b0, 4 * b0}) {
         nk_launch l = best;
         l.step2_blocks = std::min(bl, 4096);
         float t;
-        rc = time_shape(c, src, n_rhs, mixed != 0, l, steps, st, &t);
+        rc = timed(l, 0, &t);
         if (rc) { cudaStreamDestroy(st); return rc; }
         if (t < t_best) { t_best = t; best = l; }
     }
@@ -779,9 +808,9 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     if (ms_per_step) *ms_per_step = per_step;
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "a")) {
-            std::fprintf(f, "nk_launch %d %d %d %d %d %d %d %d %d %d %.6g\n", c->dims[0], c->dims[1], c->dims[2],
-                         c->dims[3], n_rhs, ts, mixed, best.stencil_threads, best.stencil_order, best.step2_blocks,
-                         per_step);
+            std::fprintf(f, "nk_launch %d %d %d %d %d %d %d %d %d %d %d %d %.6g\n", c->dims[0], c->dims[1],
+                         c->dims[2], c->dims[3], n_rhs, ts, mixed, best.stencil_threads, best.stencil_order,
+                         best.step2_blocks, best.early_threads, best.early_order, per_step);
             std::fclose(f);
         } else {
             return fail(c, NK_EINVAL, "cannot append to the tuning cache file");
@@ -924,6 +953,8 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     one.stencil_threads = 64;
     one.stencil_order = 0;
     one.step2_blocks = 1;
+    one.early_threads = 64;
+    one.early_order = 0;
     Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one);
     int rc = ensure(c, c->staging, std::max(dry.total, c->staging.bytes));
     if (rc) return rc;

@@ -93,10 +93,11 @@ class NkStats(ctypes.Structure):
 
 
 class NkLaunch(ctypes.Structure):
-    _fields_ = [("stencil_threads", ctypes.c_int), ("stencil_order", ctypes.c_int), ("step2_blocks", ctypes.c_int)]
+    _fields_ = [("stencil_threads", ctypes.c_int), ("stencil_order", ctypes.c_int), ("step2_blocks", ctypes.c_int),
+                ("early_threads", ctypes.c_int), ("early_order", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.stencil_threads, self.stencil_order, self.step2_blocks)
+        return (self.stencil_threads, self.stencil_order, self.step2_blocks, self.early_threads, self.early_order)
 
 
 class NkError(RuntimeError):
@@ -318,8 +319,10 @@ class Context:
         return c, st.as_dict(), rc
 
     # -- launch shape / autotuner -------------------------------------------
-    def set_launch(self, n_rhs, flags, stencil_threads, stencil_order, step2_blocks):
-        lc = NkLaunch(int(stencil_threads), int(stencil_order), int(step2_blocks))
+    def set_launch(self, n_rhs, flags, stencil_threads, stencil_order, step2_blocks, early_threads=128,
+                   early_order=0):
+        lc = NkLaunch(int(stencil_threads), int(stencil_order), int(step2_blocks), int(early_threads),
+                      int(early_order))
         self._check(self._lib.nk_set_launch(self.h, int(n_rhs), int(flags), ctypes.byref(lc)))
 
     def get_launch(self, n_rhs, flags=NK_FP64):
@@ -328,7 +331,8 @@ class Context:
         return lc.as_tuple()
 
     def autotune(self, n_rhs, flags=NK_FP64, cache_path=None):
-        """nk_autotune: returns ((stencil_threads, stencil_order, step2_blocks), ms per outer step)."""
+        """nk_autotune: returns ((stencil_threads, stencil_order, step2_blocks, early_threads, early_order),
+        ms per outer step)."""
         lc = NkLaunch()
         ms = ctypes.c_double()
         path = cache_path.encode() if cache_path else None

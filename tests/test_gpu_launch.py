@@ -45,7 +45,7 @@ def ctx_for(U, mu):
     return ctx
 
 
-SHAPES = [(64, 1, 1), (256, 0, 7), (128, 1, 40), (64, 0, 3)]
+SHAPES = [(64, 1, 1, 256, 1), (256, 0, 7, 64, 0), (128, 1, 40, 128, 1), (64, 0, 3, 64, 1)]
 
 
 @pytest.mark.parametrize("mu", [0.0, 0.3])
@@ -77,9 +77,10 @@ def test_autotune_and_cache(case, tmp_path):
     path = str(tmp_path / "tune.txt")
     ctx = ctx_for(U, 0.3)
     default = ctx.get_launch(3, NK_MIXED)
-    assert default[0] == 128 and default[1] == 0
+    assert default[:2] == (128, 0) and default[3:] == (128, 0)
     shape, ms = ctx.autotune(3, NK_MIXED, path)
     assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] >= 1
+    assert shape[3] in (64, 128, 256) and shape[4] in (0, 1)
     assert 0.0 < ms < 10.0
     assert ctx.get_launch(3, NK_MIXED) == shape
     lines = open(path).read().split("\n")
@@ -101,7 +102,7 @@ def test_autotune_and_cache(case, tmp_path):
 def test_invalid_shapes(case):
     U, _, _ = case
     ctx = ctx_for(U, 0.0)
-    for bad in [(96, 0, 4), (128, 2, 4), (128, 0, 0), (128, 0, 5000)]:
+    for bad in [(96, 0, 4), (128, 2, 4), (128, 0, 0), (128, 0, 5000), (128, 0, 4, 32, 0), (128, 0, 4, 64, 3)]:
         with pytest.raises(NkError) as e:
             ctx.set_launch(1, NK_FP64, *bad)
         assert e.value.code == NK_EINVAL
