@@ -156,11 +156,13 @@ typedef struct nk_launch {
 } nk_launch;
 int nk_set_launch(nk_ctx* ctx, int n_rhs, unsigned flags, const nk_launch* shape);
 int nk_get_launch(nk_ctx* ctx, int n_rhs, unsigned flags, nk_launch* shape);
-/* Times 16 outer steps of every stencil shape (3 x 2) with the FP32 stencil
- * (NK_MIXED) or the FP64 one, in NK_MIXED mode also every early shape with
- * the two-float stencil, then step2_blocks in {b/2, b, 2b, 4b} (b the
- * default) with the fastest stencil shape, on a synthetic constant source,
- * and keeps the fastest (written to *best and its time per outer step to
+/* Tunes each kernel of an outer step on its own, on a synthetic constant
+ * source after 8 outer steps, by CUDA-event timing of 20 repeated launches:
+ * the fused stencil (FP32 stencil in NK_MIXED mode, FP64 otherwise) over the
+ * 3 x 2 stencil shapes; in NK_MIXED mode the two-float stencil over the same
+ * shapes (early_threads, early_order); step 2 over step2_blocks in
+ * {b/2, b, 2b, 4b, 8b} (b the default).  Keeps the fastest of each (written
+ * to *best, and the time of one late outer step, stencil plus step 2, to
  * *ms_per_step; both nullable).  cache_path (nullable): a text file of lines
  *   nk_launch Lx Ly Lz Lt n_rhs two_sided mixed threads order blocks
  *             early_threads early_order ms_per_step

@@ -44,27 +44,22 @@ template <typename T> __device__ __forceinline__ T mul_mi(T z) { T r; r.x = z.y;
 template <typename T> __device__ __forceinline__ T neg(T z) { T r; r.x = -z.x; r.y = -z.y; return r; }
 
 // One hop: acc += w * (1 + s gamma_nu) M psi_n with M = U (dag = false) or
-// U^dagger, U the link of direction NU at site ls and psi the input at site
-// sn.  The spin projection is applied as the components arrive and each row
-// of M psi is accumulated as soon as it is formed, so that neither the whole
-// neighbour spinor nor the whole link is held in registers (this matters
-// most for the two-float instantiation).
+// U^dagger, from a neighbour spinor and link already loaded into registers
+// (FP32 and FP64; the two-float stencil has its own form below).
 template <int NU, bool DAG, typename R>
-__device__ __forceinline__ void hop(typename C2<R>::T acc[4][3], const typename C2<R>::T* __restrict__ in, int V,
-                                    int sn, const typename C2<R>::T* __restrict__ U, int ls, R s, R w) {
+__device__ __forceinline__ void hop_regs(typename C2<R>::T acc[4][3], const typename C2<R>::T psi[4][3],
+                                         const typename C2<R>::T u[3][3], R s, R w) {
     typedef typename C2<R>::T T;
     T h0[3], h1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const T p0 = in[(size_t)a * V + sn], p1 = in[(size_t)(3 + a) * V + sn];
-        const T p2 = in[(size_t)(6 + a) * V + sn], p3 = in[(size_t)(9 + a) * V + sn];
         T c0, c1;  // (C_nu psi_dn)_0, _1
-        if (NU == 0) { c0 = mul_mi(p3); c1 = mul_mi(p2); }
-        else if (NU == 1) { c0 = neg(p3); c1 = p2; }
-        else if (NU == 2) { c0 = mul_mi(p2); c1 = mul_i(p3); }
-        else { c0 = p2; c1 = p3; }
-        h0[a].x = p0.x + s * c0.x; h0[a].y = p0.y + s * c0.y;
-        h1[a].x = p1.x + s * c1.x; h1[a].y = p1.y + s * c1.y;
+        if (NU == 0) { c0 = mul_mi(psi[3][a]); c1 = mul_mi(psi[2][a]); }
+        else if (NU == 1) { c0 = neg(psi[3][a]); c1 = psi[2][a]; }
+        else if (NU == 2) { c0 = mul_mi(psi[2][a]); c1 = mul_i(psi[3][a]); }
+        else { c0 = psi[2][a]; c1 = psi[3][a]; }
+        h0[a].x = psi[0][a].x + s * c0.x; h0[a].y = psi[0][a].y + s * c0.y;
+        h1[a].x = psi[1][a].x + s * c1.x; h1[a].y = psi[1][a].y + s * c1.y;
     }
     const R ws = w * s;
 #pragma unroll
@@ -73,7 +68,7 @@ __device__ __forceinline__ void hop(typename C2<R>::T acc[4][3], const typename 
         x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            const T e = DAG ? U[(size_t)(NU * 9 + 3 * b + a) * V + ls] : U[(size_t)(NU * 9 + 3 * a + b) * V + ls];
+            const T e = DAG ? u[b][a] : u[a][b];
             R ey = DAG ? -e.y : e.y;
             x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
             x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
@@ -90,18 +85,118 @@ __device__ __forceinline__ void hop(typename C2<R>::T acc[4][3], const typename 
     }
 }
 
+template <typename R>
+__device__ __forceinline__ void load_link(const typename C2<R>::T* __restrict__ U, int V, int nu, int site,
+                                          typename C2<R>::T u[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) u[a][b] = U[(size_t)(nu * 9 + 3 * a + b) * V + site];
+}
+
 template <int NU, typename R>
 __device__ __forceinline__ void dir(typename C2<R>::T acc[4][3], const typename C2<R>::T* __restrict__ U,
                                     const typename C2<R>::T* __restrict__ in, const Geom& g, int site,
                                     int coord, int L, int stride, R wplus, R wminus) {
     // backward neighbour y - nu: (1 + gamma) U_{y-nu,+nu} psi_{y-nu}
+    typedef typename C2<R>::T T;
     const int sb = coord == 0 ? site + (L - 1) * stride : site - stride;
     const R fb = (NU == 3 && g.antiperiodic && coord == 0) ? R(-1) : R(1);
-    hop<NU, false, R>(acc, in, g.V, sb, U, sb, R(1), wplus * fb);
-    // forward neighbour y + nu: (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}
     const int sf = coord == L - 1 ? site - (L - 1) * stride : site + stride;
     const R ff = (NU == 3 && g.antiperiodic && coord == L - 1) ? R(-1) : R(1);
-    hop<NU, true, R>(acc, in, g.V, sf, U, site, R(-1), wminus * ff);
+    T u[3][3], p[4][3];
+    load_link<R>(U, g.V, NU, sb, u);
+    load_spinor<R>(in, g.V, sb, p);
+    hop_regs<NU, false, R>(acc, p, u, R(1), wplus * fb);
+    // forward neighbour y + nu: (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}
+    load_link<R>(U, g.V, NU, site, u);
+    load_spinor<R>(in, g.V, sf, p);
+    hop_regs<NU, true, R>(acc, p, u, R(-1), wminus * ff);
+}
+
+// ---- the two-float stencil: one copy of the hop body --------------------------
+// Two-float arithmetic turns every flop into 7-11 FP32 instructions; the
+// eight hops unrolled with compile-time gamma structure then overflow the
+// instruction cache (ncu: most stalls "no instruction").  Here the eight hops
+// run as a loop over one hop body: the direction is a warp-uniform run-time
+// value and the gamma matrices act through multiplications by i^q (exact:
+// swaps and sign changes), so the values are those of the unrolled form.
+__device__ __forceinline__ dfc rot_q(dfc z, int q) {   // z * i^q
+    dfc r;
+    switch (q & 3) {
+        case 0: r = z; break;
+        case 1: r.x = -z.y; r.y = z.x; break;
+        case 2: r.x = -z.x; r.y = -z.y; break;
+        default: r.x = z.y; r.y = -z.x; break;
+    }
+    return r;
+}
+// (C_nu psi)_0 = i^q0 psi_{i0}, (C_nu psi)_1 = i^q1 psi_{i1}; (B_nu m)_0 = i^r0q m_{r0},
+// (B_nu m)_1 = i^r1q m_{r1} -- the chiral-basis structure of the unrolled hop
+struct HopSpin { int i0, q0, i1, q1, r0, r0q, r1, r1q; };
+__device__ __forceinline__ HopSpin hop_spin(int nu) {
+    switch (nu) {
+        case 0: return {3, 3, 2, 3, 1, 1, 0, 1};
+        case 1: return {3, 2, 2, 0, 1, 0, 0, 2};
+        case 2: return {2, 3, 3, 1, 0, 1, 1, 3};
+        default: return {2, 0, 3, 0, 0, 0, 1, 0};
+    }
+}
+
+__device__ __forceinline__ void stencil_hops_df(dfc acc[4][3], const dfc* __restrict__ U, const dfc* __restrict__ in,
+                                                const Geom& g, int site, const int coord[4], df wp_t, df wm_t) {
+    const int V = g.V;
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+        const int nu = h >> 1;
+        const bool fwd = (h & 1) != 0;   // forward neighbour: (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}
+        int L, stride;
+        switch (nu) {
+            case 0: L = g.Lx; stride = 1; break;
+            case 1: L = g.Ly; stride = g.Lx; break;
+            case 2: L = g.Lz; stride = g.Lx * g.Ly; break;
+            default: L = g.Lt; stride = g.Lx * g.Ly * g.Lz; break;
+        }
+        const int c = coord[nu];
+        int sn, ls;
+        bool wrap;
+        if (fwd) { wrap = c == L - 1; sn = wrap ? site - (L - 1) * stride : site + stride; ls = site; }
+        else { wrap = c == 0; sn = wrap ? site + (L - 1) * stride : site - stride; ls = sn; }
+        const df flip = (nu == 3 && g.antiperiodic && wrap) ? df(-1) : df(1);
+        const df w = (nu == 3 ? (fwd ? wm_t : wp_t) : df(1)) * flip;
+        const df sgn = fwd ? df(-1) : df(1);
+        const HopSpin hs = hop_spin(nu);
+        dfc h0[3], h1[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const dfc p0 = in[(size_t)a * V + sn], p1 = in[(size_t)(3 + a) * V + sn];
+            const dfc p2 = in[(size_t)(6 + a) * V + sn], p3 = in[(size_t)(9 + a) * V + sn];
+            const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, hs.q0);
+            const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, hs.q1);
+            h0[a].x = p0.x + sgn * c0.x; h0[a].y = p0.y + sgn * c0.y;
+            h1[a].x = p1.x + sgn * c1.x; h1[a].y = p1.y + sgn * c1.y;
+        }
+        const df ws = w * sgn;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dfc x0, x1;
+            x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int e_idx = fwd ? nu * 9 + 3 * b + a : nu * 9 + 3 * a + b;
+                const dfc e = U[(size_t)e_idx * V + ls];
+                const df ey = fwd ? -e.y : e.y;
+                x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
+                x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
+            }
+            acc[0][a].x += w * x0.x; acc[0][a].y += w * x0.y;
+            acc[1][a].x += w * x1.x; acc[1][a].y += w * x1.y;
+            const dfc b0 = rot_q(hs.r0 == 1 ? x1 : x0, hs.r0q);
+            const dfc b1 = rot_q(hs.r1 == 1 ? x1 : x0, hs.r1q);
+            acc[2][a].x += ws * b0.x; acc[2][a].y += ws * b0.y;
+            acc[3][a].x += ws * b1.x; acc[3][a].y += ws * b1.y;
+        }
+    }
 }
 
 // precision-generic conversions (float via the integer pipe, see nk_common.cuh)
@@ -148,10 +243,15 @@ __device__ __forceinline__ void stencil_site(const typename C2<R>::T* __restrict
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
         for (int a = 0; a < 3; ++a) { acc[sp][a].x = 0; acc[sp][a].y = 0; }
-    dir<0, R>(acc, U, in, g, site, x, g.Lx, 1, R(1), R(1));
-    dir<1, R>(acc, U, in, g, site, y, g.Ly, g.Lx, R(1), R(1));
-    dir<2, R>(acc, U, in, g, site, z, g.Lz, g.Lx * g.Ly, R(1), R(1));
-    dir<3, R>(acc, U, in, g, site, t, g.Lt, g.Lx * g.Ly * g.Lz, wp_t, wm_t);
+    if constexpr (std::is_same<R, df>::value) {
+        const int coord[4] = {x, y, z, t};
+        stencil_hops_df(acc, U, in, g, site, coord, wp_t, wm_t);
+    } else {
+        dir<0, R>(acc, U, in, g, site, x, g.Lx, 1, R(1), R(1));
+        dir<1, R>(acc, U, in, g, site, y, g.Ly, g.Lx, R(1), R(1));
+        dir<2, R>(acc, U, in, g, site, z, g.Lz, g.Lx * g.Ly, R(1), R(1));
+        dir<3, R>(acc, U, in, g, site, t, g.Lt, g.Lx * g.Ly * g.Lz, wp_t, wm_t);
+    }
     T p[4][3];
     load_spinor<R>(in, g.V, site, p);
 #pragma unroll
@@ -218,11 +318,12 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
 // deterministic two-stage scheme.  In double-pass mode side 0 also
 // accumulates y += c'_j q_j at its own site.
 // Minimum resident CTAs of kStencilMaxThreads threads per SM for the fused
-// stencil: the two-float instantiation is latency bound on long dependent
-// FP32 chains and gains from more resident warps than its unconstrained
-// register count (about 160) allows.
+// stencil (a register cap): the FP32 and two-float instantiations are
+// latency bound (loads; long dependent FP32 chains) and gain from more
+// resident warps than their unconstrained register counts (about 160) allow.
 template <typename R> struct StencilMinBlocks { static constexpr int value = 1; };
 template <> struct StencilMinBlocks<df> { static constexpr int value = 2; };
+template <> struct StencilMinBlocks<float> { static constexpr int value = 3; };
 
 template <typename R, bool TS, bool PASS2>
 __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value) k_dslash_step1(

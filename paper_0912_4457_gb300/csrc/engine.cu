@@ -675,35 +675,50 @@ int nk_get_launch(nk_ctx* c, int n_rhs, unsigned flags, nk_launch* l) {
     return NK_OK;
 }
 
-// Time of `steps` outer steps (init included) of n_rhs copies of the source
-// in `src` with launch shape lc: the minimum over three runs after a warm-up.
-static int time_shape(nk_ctx* c, const double* src, int n_rhs, bool mixed, int j0, const nk_launch& lc,
-                      int steps, cudaStream_t st, float* best) {
+// Autotuner timing: the outer recurrence is run for kTuneWarm steps from the
+// synthetic source in `src` with launch shape lc, then one kernel of step
+// kTuneWarm is launched kTuneReps times in a row and timed with CUDA events
+// (the minimum over two rounds): the fused stencil in precision `prec` (32,
+// 48 or 64), or step 2 (prec = 0).  Repeating a launch recomputes the same
+// step (step 2 subtracts once more), which leaves the timing representative.
+constexpr int kTuneWarm = 8, kTuneReps = 20;
+static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int prec, const nk_launch& lc,
+                       cudaStream_t st, float* per_launch_ms) {
     const bool ts = c->mu != 0.0;
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, steps, 2, ts, false, lc);
+    const int k = 2 * kTuneWarm;
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, lc);
     int rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, steps, 2, ts, false, lc);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, lc);
+    NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
+    Launcher L;
+    L.st = st;
+    enqueue_load_sources(c, Lw.o, src, n_rhs, L);
+    // the copies of the stencil input that `prec` reads are made by the last warm step
+    const int j0 = prec == 48 ? k : 0;
+    enqueue_outer(c, Lw.o, mixed, j0, L, kTuneWarm);
+    const Geom g = geom_of(c);
+    const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
     cudaEvent_t e0, e1;
     NK_CUDA(c, cudaEventCreate(&e0));
     NK_CUDA(c, cudaEventCreate(&e1));
-    *best = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
-        NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
-        Launcher L;
-        L.st = st;
-        enqueue_load_sources(c, Lw.o, src, n_rhs, L);
+    float best = 1e30f;
+    for (int round = 0; round < 2; ++round) {
         NK_CUDA(c, cudaEventRecord(e0, st));
-        enqueue_outer(c, Lw.o, mixed, j0, L);   // mixed: two-float before j0, FP32 after
+        for (int r = 0; r < kTuneReps; ++r) {
+            if (prec == 0) nk::launch_outer_step2(Lw.o, kTuneWarm, copy_mode_for(mixed, j0, kTuneWarm + 1), st);
+            else nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
+        }
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());
         NK_CUDA(c, cudaEventSynchronize(e1));
         float ms = 0.f;
         NK_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0) *best = std::min(*best, ms);
+        best = std::min(best, ms / kTuneReps);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    *per_launch_ms = best;
     return NK_OK;
 }
 
@@ -714,7 +729,6 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     NK_CUDA(c, cudaSetDevice(c->device));
     const int ts = c->mu != 0.0 ? 1 : 0;
     const int mixed = (flags & NK_MIXED) ? 1 : 0;
-    const int steps = 16;
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "r")) {
             char tag[32];
@@ -762,48 +776,43 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     best.early_order = 0;
     const int b0 = blocks_per_rhs(c->N, n_rhs);
     best.step2_blocks = b0;
-    auto timed = [&](const nk_launch& l, int j0, float* t) {
-        return time_shape(c, src, n_rhs, mixed != 0, j0, l, steps, st, t);
-    };
-    // FP64 mode: the FP64 stencil; mixed: the FP32 stencil (all steps after j0 = 0)
-    float t_best = 1e30f;
+    // each kernel of an outer step is tuned on its own
+    auto fail_out = [&](int code) { cudaStreamDestroy(st); return code; };
+    float t_st = 1e30f, t_early = 1e30f, t_s2 = 1e30f;
+    nk_launch cand = best;
     for (int th : {64, 128, 256})
         for (int od : {0, 1}) {
             nk_launch l = best;
             l.stencil_threads = th;
             l.stencil_order = od;
             float t;
-            rc = timed(l, 0, &t);
-            if (rc) { cudaStreamDestroy(st); return rc; }
-            if (t < t_best) { t_best = t; best = l; }
-        }
-    if (mixed) {   // the two-float stencil of the early steps (all steps before j0 = steps)
-        float te_best = 1e30f;
-        nk_launch b2 = best;
-        for (int th : {64, 128, 256})
-            for (int od : {0, 1}) {
-                nk_launch l = best;
-                l.early_threads = th;
-                l.early_order = od;
-                float t;
-                rc = timed(l, steps, &t);
-                if (rc) { cudaStreamDestroy(st); return rc; }
-                if (t < te_best) { te_best = t; b2 = l; }
+            rc = time_kernel(c, src, n_rhs, mixed != 0, mixed ? 32 : 64, l, st, &t);
+            if (rc) return fail_out(rc);
+            if (t < t_st) { t_st = t; cand.stencil_threads = th; cand.stencil_order = od; }
+            if (mixed) {
+                nk_launch e = best;
+                e.early_threads = th;
+                e.early_order = od;
+                rc = time_kernel(c, src, n_rhs, true, 48, e, st, &t);
+                if (rc) return fail_out(rc);
+                if (t < t_early) { t_early = t; cand.early_threads = th; cand.early_order = od; }
             }
-        best = b2;
-    }
-    for (int bl : {std::max(1, b0 / 2), 2 * b0, 4 * b0}) {
+        }
+    for (int bl : {std::max(1, b0 / 2), b0, 2 * b0, 4 * b0, 8 * b0}) {
         nk_launch l = best;
         l.step2_blocks = std::min(bl, 4096);
         float t;
-        rc = timed(l, 0, &t);
-        if (rc) { cudaStreamDestroy(st); return rc; }
-        if (t < t_best) { t_best = t; best = l; }
+        rc = time_kernel(c, src, n_rhs, mixed != 0, 0, l, st, &t);
+        if (rc) return fail_out(rc);
+        if (t < t_s2) { t_s2 = t; cand.step2_blocks = l.step2_blocks; }
     }
+    best = cand;
+    // reported: the time of one outer step after j0 (stencil + step 2)
+    const float t_best = t_st + t_s2;
     cudaStreamDestroy(st);
     c->tune[std::make_tuple(n_rhs, ts, mixed)] = best;
     clear_graphs(c);
-    const double per_step = t_best / steps;
+    const double per_step = t_best;
     if (out) *out = best;
     if (ms_per_step) *ms_per_step = per_step;
     if (cache_path) {
