@@ -156,14 +156,15 @@ typedef struct nk_launch {
 } nk_launch;
 int nk_set_launch(nk_ctx* ctx, int n_rhs, unsigned flags, const nk_launch* shape);
 int nk_get_launch(nk_ctx* ctx, int n_rhs, unsigned flags, nk_launch* shape);
-/* Tunes each kernel of an outer step on its own, on a synthetic constant
- * source after 8 outer steps, by CUDA-event timing of 20 repeated launches:
- * the fused stencil (FP32 stencil in NK_MIXED mode, FP64 otherwise) over the
- * 3 x 2 stencil shapes; in NK_MIXED mode the two-float stencil over the same
- * shapes (early_threads, early_order); step 2 over step2_blocks in
- * {b/2, b, 2b, 4b, 8b} (b the default).  Keeps the fastest of each (written
- * to *best, and the time of one late outer step, stencil plus step 2, to
- * *ms_per_step; both nullable).  cache_path (nullable): a text file of lines
+/* Tunes the launch shape on a synthetic constant source: after 8 outer steps,
+ * 20 repetitions of one outer step (fused stencil, then step 2, as in a
+ * solve) are timed with CUDA events for each candidate -- the 3 x 2 stencil
+ * shapes with the FP32 stencil (NK_MIXED) or the FP64 one; in NK_MIXED mode
+ * the same shapes with the two-float stencil (early_threads, early_order);
+ * then step2_blocks in {b/2, b, 2b, 4b, 8b} (b the default) with the fastest
+ * late stencil shape.  Keeps the fastest of each (written to *best, and the
+ * time of one late outer step to *ms_per_step; both nullable).
+ * cache_path (nullable): a text file of lines
  *   nk_launch Lx Ly Lz Lt n_rhs two_sided mixed threads order blocks
  *             early_threads early_order ms_per_step
  * read first (a matching line is used without timing) and appended to after
@@ -300,7 +301,7 @@ int nk_predict_sizes(nk_ctx* ctx, nk_mlp* m, const double* b_dev, int k_max, int
  * arrays owned by the caller (alpha_dev, beta_dev, gamma_dev, c_dev in the
  * nk_outer_lanczos_dev layout, complex doubles [r*k + j]) and every other
  * buffer it needs lives in one static device array of the library (about
- * 5.4 MB, held by every GPU that loads the library until the process exits).
+ * 5.9 MB, held by every GPU that loads the library until the process exits).
  * It calls no cudaMalloc/cudaFree and needs no context.
  * Limits: n_rhs <= NK_NOALLOC_MAX_RHS, k <= NK_NOALLOC_MAX_K,
  * l <= NK_NOALLOC_MAX_ELL; larger sizes return NK_EINVAL with a message.

@@ -676,11 +676,14 @@ int nk_get_launch(nk_ctx* c, int n_rhs, unsigned flags, nk_launch* l) {
 }
 
 // Autotuner timing: the outer recurrence is run for kTuneWarm steps from the
-// synthetic source in `src` with launch shape lc, then one kernel of step
-// kTuneWarm is launched kTuneReps times in a row and timed with CUDA events
-// (the minimum over two rounds): the fused stencil in precision `prec` (32,
-// 48 or 64), or step 2 (prec = 0).  Repeating a launch recomputes the same
-// step (step 2 subtracts once more), which leaves the timing representative.
+// synthetic source in `src` with launch shape lc, then the two kernels of
+// step kTuneWarm -- the fused stencil in precision `prec` (32, 48 or 64) and
+// step 2 -- are launched kTuneReps times in turn and timed with CUDA events
+// (the minimum over two rounds, per step).  Alternating the two keeps the
+// dependency between them that a solve has (timing one kernel alone lets
+// consecutive launches overlap and favours other shapes); repeating a step
+// recomputes it (step 2 subtracts once more), which leaves the timing
+// representative.
 constexpr int kTuneWarm = 8, kTuneReps = 20;
 static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int prec, const nk_launch& lc,
                        cudaStream_t st, float* per_launch_ms) {
@@ -706,8 +709,8 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
     for (int round = 0; round < 2; ++round) {
         NK_CUDA(c, cudaEventRecord(e0, st));
         for (int r = 0; r < kTuneReps; ++r) {
-            if (prec == 0) nk::launch_outer_step2(Lw.o, kTuneWarm, copy_mode_for(mixed, j0, kTuneWarm + 1), st);
-            else nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
+            nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
+            nk::launch_outer_step2(Lw.o, kTuneWarm, copy_mode_for(mixed, j0, kTuneWarm + 1), st);
         }
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());
@@ -800,15 +803,17 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
         }
     for (int bl : {std::max(1, b0 / 2), b0, 2 * b0, 4 * b0, 8 * b0}) {
         nk_launch l = best;
+        l.stencil_threads = cand.stencil_threads;
+        l.stencil_order = cand.stencil_order;
         l.step2_blocks = std::min(bl, 4096);
         float t;
-        rc = time_kernel(c, src, n_rhs, mixed != 0, 0, l, st, &t);
+        rc = time_kernel(c, src, n_rhs, mixed != 0, mixed ? 32 : 64, l, st, &t);
         if (rc) return fail_out(rc);
         if (t < t_s2) { t_s2 = t; cand.step2_blocks = l.step2_blocks; }
     }
     best = cand;
     // reported: the time of one outer step after j0 (stencil + step 2)
-    const float t_best = t_st + t_s2;
+    const float t_best = t_s2;
     cudaStreamDestroy(st);
     c->tune[std::make_tuple(n_rhs, ts, mixed)] = best;
     clear_graphs(c);

@@ -13,9 +13,10 @@
 //
 // The inner Lanczos runs one CTA per RHS: the band products, inner products
 // and axpys are spread over the CTA; the two O(k) substitution sweeps of each
-// solve are parallel prefix scans on one warp (two warps in the two-sided
-// case: H_k' v and H_k'^dagger w are independent), with the parts of the
-// scans that depend on the LU factors alone tabulated once per LU.
+// solve are parallel prefix scans on a group of warps (all 8; two groups of 4
+// in the two-sided case, where H_k' v and H_k'^dagger w are independent),
+// with the parts of the scans that depend on the LU factors alone tabulated
+// once per LU.
 //
 // RHi runs one thread-block cluster per RHS: the rows of the l x l matrix
 // being inverted (in-place Gauss-Jordan with partial pivoting and row
@@ -154,12 +155,12 @@ __device__ double bnorm(int n, const T* a, double* sh) {
     return sqrt(block_sum(acc, sh));
 }
 
-// ---- tridiagonal solves as warp-level scans of affine maps ---------------------
+// ---- tridiagonal solves as scans of affine maps ---------------------------------
 //
 // The substitution sweeps of gttrs are linear recurrences.  A sequential chain
 // leaves GB300's FP64 pipe 31/32 idle (a warp instruction with one active lane
 // costs the pipe as much as a full one) and is latency bound, so each sweep
-// runs on one warp as a parallel prefix over affine maps:
+// runs as a parallel prefix over affine maps:
 //   first order  (L sweep with interchanges):  s <- a s + c
 //   second order (U sweep, two super-diagonals): X <- M X + v, X = (x_i, x_{i+1})
 // Each lane composes the maps of its contiguous chunk, an exclusive shuffle
@@ -189,125 +190,243 @@ __device__ __forceinline__ double2 t_fma(double2 a, double2 b, double2 c) {
 
 // The maps of a sweep split into a part that depends on the LU factors only
 // (a of s <- a s + c; M of X <- M X + v) and a part that depends on the
-// right-hand side (c; v).  The factor parts of the lane chunks and of every
-// level of the lane scan are composed once per LU (sweep_tables) and kept in
-// a per-RHS table; a solve then composes only the right-hand-side parts:
-// first order 1 complex product per element, second order 3 (the companion
-// matrix [[e, f], [1, 0]] is sparse), and the lane scan 1 (4) products per
-// level.  Composition rules (g after f):
+// right-hand side (c; v).  The factor parts are composed once per LU
+// (sweep_tables) and kept in a per-RHS table; a solve then composes only the
+// right-hand-side parts: first order 1 complex product per element, second
+// order 3 (the companion matrix [[e, f], [1, 0]] is sparse).
+// Composition rules (g after f):
 //   first order   (a, c): a = a_g a_f,  c = a_g c_f + c_g;
 //   second order  (M, v): M = M_g M_f,  v = M_g v_f + v_g.
-// Table rows (row-major [row][lane]): L 0-5, L^dagger 6-11 (a before each of
-// the 5 scan levels, then the exclusive prefix a), U 12-31, U^dagger 32-51
-// (the 4 entries of M before each scan level).
-constexpr int kTabL = 0, kTabLH = 6, kTabU = 12, kTabUH = 32;
+//
+// A solve runs on a group of W warps (W = 8 in the Hermitian case, where
+// there is one solve at a time; W = 4 per side in the two-sided case, where
+// H' v and H'^dagger w are solved side by side), so all four SM sub-partitions
+// issue its FP64 work.  Each of the 32 W lanes takes a contiguous chunk; the
+// chunk maps are composed by a shuffle scan inside each warp and by a short
+// sequential composition of the W warp aggregates (exchanged through shared
+// memory between two group barriers).  Positions run in the order the maps
+// are applied: ascending sweeps from chunk 0, descending ones from the last.
+//
+// Table rows ([row][group lane], NL = 32 W lanes per row):
+//   first order:  0-4 a before each shuffle level, 5 a of the intra-warp
+//                 exclusive prefix, 6 a of the whole exclusive prefix,
+//                 7 a of each warp's aggregate (indexed by warp position);
+//   second order: 0-19 M before each level (4 entries per level), 20-23 M of
+//                 the intra-warp exclusive prefix, 24-27 M of each warp's
+//                 aggregate (indexed by warp position).
+constexpr int kRowsFirst = 8, kRowsSecond = 28;
+constexpr int kTabL = 0, kTabLH = kRowsFirst, kTabU = 2 * kRowsFirst, kTabUH = 2 * kRowsFirst + kRowsSecond;
+constexpr int kTabRows = 2 * kRowsFirst + 2 * kRowsSecond;
+static_assert(kTabRows * 256 <= kSweepTableElems, "sweep tables do not fit the work area");
+
+// The warp group of the calling thread.  Group g uses named barrier 1 + g.
+struct Grp {
+    int W;      // warps in the group
+    int gw;     // this warp's index in the group
+    int lane;
+    int bar;    // named barrier id
+    int g;      // group index
+};
+__device__ __forceinline__ Grp grp_of(bool two_sided) {
+    const int warp = threadIdx.x >> 5;
+    const int W = two_sided ? 4 : 8;
+    return {W, warp % W, (int)(threadIdx.x & 31), 1 + warp / W, warp / W};
+}
+__device__ __forceinline__ void grp_sync(const Grp& G) {
+    asm volatile("bar.sync %0, %1;" ::"r"(G.bar), "r"(G.W * 32) : "memory");
+}
+// chunk [lo, hi) of group lane gw*32 + lane over n elements
+__device__ __forceinline__ void grp_chunk(const Grp& G, int n, int& lo, int& hi) {
+    const int NL = 32 * G.W;
+    const int C = (n + NL - 1) / NL;
+    lo = min((G.gw * 32 + G.lane) * C, n);
+    hi = min(lo + C, n);
+}
 
 template <typename T> struct Mat2 { T m00, m01, m10, m11; };
 template <typename T> __device__ __forceinline__ Mat2<T> mat_mul(const Mat2<T>& g, const Mat2<T>& f) {
     return {t_fma(g.m00, f.m00, t_mul(g.m01, f.m10)), t_fma(g.m00, f.m01, t_mul(g.m01, f.m11)),
             t_fma(g.m10, f.m00, t_mul(g.m11, f.m10)), t_fma(g.m10, f.m01, t_mul(g.m11, f.m11))};
 }
-template <typename T> __device__ __forceinline__ Mat2<T> shfl_mat(const Mat2<T>& a, int o, bool up) {
-    return up ? Mat2<T>{shup(a.m00, o), shup(a.m01, o), shup(a.m10, o), shup(a.m11, o)}
-              : Mat2<T>{shdn(a.m00, o), shdn(a.m01, o), shdn(a.m10, o), shdn(a.m11, o)};
+template <typename T> __device__ __forceinline__ T shfl_dir(T v, int o, bool asc) { return asc ? shup(v, o) : shdn(v, o); }
+template <typename T> __device__ __forceinline__ Mat2<T> shfl_mat(const Mat2<T>& a, int o, bool asc) {
+    return {shfl_dir(a.m00, o, asc), shfl_dir(a.m01, o, asc), shfl_dir(a.m10, o, asc), shfl_dir(a.m11, o, asc)};
 }
-// lane chunk [lo, hi) of n elements
-__device__ __forceinline__ void lane_chunk(int n, int& lo, int& hi) {
-    const int lane = threadIdx.x & 31;
-    const int C = (n + 31) / 32;
-    lo = min(lane * C, n);
-    hi = min(lo + C, n);
+template <typename T> __device__ __forceinline__ T shfl_from(T v, int src) {
+    return t_from(mk(__shfl_sync(kFull, t_to2(v).x, src), __shfl_sync(kFull, t_to2(v).y, src)), T());
 }
+__device__ __forceinline__ double shfl_from(double v, int src) { return __shfl_sync(kFull, v, src); }
+// partner exists at shuffle distance o; first / last position lanes
+__device__ __forceinline__ bool has_partner(int lane, int o, bool asc) { return asc ? lane >= o : lane + o < 32; }
+__device__ __forceinline__ int last_lane(bool asc) { return asc ? 31 : 0; }
+__device__ __forceinline__ bool first_lane(int lane, bool asc) { return asc ? lane == 0 : lane == 31; }
+__device__ __forceinline__ int warp_pos(const Grp& G, bool asc) { return asc ? G.gw : G.W - 1 - G.gw; }
 
-// first-order factor table: a_i over the chunk steps, then the scan levels
-// (ascending: lower lanes first; descending: higher lanes first)
+// first-order factor table (a_i = -dl_i, or -conj(dl_i) for the dagger sweep,
+// where row i was not interchanged, 1 where it was); all warps of the group
 template <typename T>
-__device__ void table_first_order(int n, const T* __restrict__ dl, const int* __restrict__ ipiv, bool dagger,
-                                  T* __restrict__ tab) {
-    const int lane = threadIdx.x & 31;
+__device__ void table_first_order(const Grp& G, int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
+                                  bool dagger, T* __restrict__ tab, double2* s_agg) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
+    const bool asc = !dagger;
     int lo, hi;
-    lane_chunk(n, lo, hi);
+    grp_chunk(G, n, lo, hi);
     const int shi = min(hi, n - 1);
     T A = t_one(T());
     for (int i = lo; i < shi; ++i)
         if (ipiv[i] == i) A = t_mul(t_scale(dagger ? t_conj(dl[i]) : dl[i], -1.0), A);
     for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
-        tab[lv * 32 + lane] = A;
-        const T pa = dagger ? shdn(A, o) : shup(A, o);
-        if (dagger ? lane + o < 32 : lane >= o) A = t_mul(A, pa);
+        tab[lv * NL + gl] = A;
+        const T pa = shfl_dir(A, o, asc);
+        if (has_partner(G.lane, o, asc)) A = t_mul(A, pa);
     }
-    const T ex = dagger ? shdn(A, 1) : shup(A, 1);
-    tab[5 * 32 + lane] = (dagger ? lane == 31 : lane == 0) ? t_one(T()) : ex;
+    const T ex = shfl_dir(A, 1, asc);
+    const T a_ex = first_lane(G.lane, asc) ? t_one(T()) : ex;
+    tab[5 * NL + gl] = a_ex;
+    const T agg = shfl_from(A, last_lane(asc));
+    const int pw = warp_pos(G, asc);
+    if (G.lane == 0) { tab[7 * NL + pw] = agg; s_agg[G.gw] = t_to2(agg); }
+    grp_sync(G);
+    T P = t_one(T());
+    for (int q = 0; q < G.W; ++q) {
+        const int qw = asc ? q : G.W - 1 - q;    // group warp at position q
+        if (q < pw) P = t_mul(t_from(s_agg[qw], T()), P);
+    }
+    tab[6 * NL + gl] = t_mul(a_ex, P);
+    grp_sync(G);
 }
 
-// second-order factor table: M_i = [[e_i, f_i], [1, 0]] over the chunk
-// (descending for U, ascending for U^dagger), then the scan levels
+// second-order factor table: M_i = [[e_i, f_i], [1, 0]] (descending for U,
+// ascending for U^dagger); all warps of the group
 template <typename T>
-__device__ void table_second_order(int n, const T* __restrict__ e, const T* __restrict__ f, bool ascending,
+__device__ void table_second_order(const Grp& G, int n, const T* __restrict__ e, const T* __restrict__ f, bool asc,
                                    T* __restrict__ tab) {
-    const int lane = threadIdx.x & 31;
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     int lo, hi;
-    lane_chunk(n, lo, hi);
+    grp_chunk(G, n, lo, hi);
     Mat2<T> F = {t_one(T()), t_zero(T()), t_zero(T()), t_one(T())};
     auto step = [&](int i) {
         F = {t_fma(e[i], F.m00, t_mul(f[i], F.m10)), t_fma(e[i], F.m01, t_mul(f[i], F.m11)), F.m00, F.m01};
     };
-    if (ascending) for (int i = lo; i < hi; ++i) step(i);
+    if (asc) for (int i = lo; i < hi; ++i) step(i);
     else for (int i = hi - 1; i >= lo; --i) step(i);
     for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
-        tab[(4 * lv + 0) * 32 + lane] = F.m00;
-        tab[(4 * lv + 1) * 32 + lane] = F.m01;
-        tab[(4 * lv + 2) * 32 + lane] = F.m10;
-        tab[(4 * lv + 3) * 32 + lane] = F.m11;
-        const Mat2<T> P = shfl_mat(F, o, ascending);
-        if (ascending ? lane >= o : lane + o < 32) F = mat_mul(F, P);
+        tab[(4 * lv + 0) * NL + gl] = F.m00;
+        tab[(4 * lv + 1) * NL + gl] = F.m01;
+        tab[(4 * lv + 2) * NL + gl] = F.m10;
+        tab[(4 * lv + 3) * NL + gl] = F.m11;
+        const Mat2<T> Pm = shfl_mat(F, o, asc);
+        if (has_partner(G.lane, o, asc)) F = mat_mul(F, Pm);
+    }
+    const Mat2<T> ex = shfl_mat(F, 1, asc);
+    const bool first = first_lane(G.lane, asc);
+    tab[20 * NL + gl] = first ? t_one(T()) : ex.m00;
+    tab[21 * NL + gl] = first ? t_zero(T()) : ex.m01;
+    tab[22 * NL + gl] = first ? t_zero(T()) : ex.m10;
+    tab[23 * NL + gl] = first ? t_one(T()) : ex.m11;
+    const int ll = last_lane(asc);
+    const T a00 = shfl_from(F.m00, ll), a01 = shfl_from(F.m01, ll);
+    const T a10 = shfl_from(F.m10, ll), a11 = shfl_from(F.m11, ll);
+    if (G.lane == 0) {
+        const int pw = warp_pos(G, asc);
+        tab[24 * NL + pw] = a00;
+        tab[25 * NL + pw] = a01;
+        tab[26 * NL + pw] = a10;
+        tab[27 * NL + pw] = a11;
     }
 }
 
-// The four tables of one LU: warps 0-1 (L, U), and 2-3 (the dagger sweeps)
-// when two-sided.  Caller synchronises the block afterwards.
+// The tables of one LU.  Hermitian: the one group builds L then U; two-sided:
+// group 0 builds L and U, group 1 the dagger sweeps.  Ends with a block barrier.
 template <typename T>
 __device__ void sweep_tables(int n, const T* dl, const int* ipiv, const T* e, const T* f, const T* eh,
-                             const T* fh, bool two_sided, T* tab) {
-    const int warp = threadIdx.x >> 5;
-    if (warp == 0) table_first_order<T>(n, dl, ipiv, false, tab + kTabL * 32);
-    else if (warp == 1) table_second_order<T>(n, e, f, false, tab + kTabU * 32);
-    else if (two_sided && warp == 2) table_first_order<T>(n, dl, ipiv, true, tab + kTabLH * 32);
-    else if (two_sided && warp == 3) table_second_order<T>(n, eh, fh, true, tab + kTabUH * 32);
+                             const T* fh, bool two_sided, T* tab, double2* s_agg) {
+    const Grp G = grp_of(two_sided);
+    const int NL = 32 * G.W;
+    double2* agg = s_agg + 16 * G.g;
+    if (G.g == 0) {
+        table_first_order<T>(G, n, dl, ipiv, false, tab + kTabL * NL, agg);
+        table_second_order<T>(G, n, e, f, false, tab + kTabU * NL);
+    } else {
+        table_first_order<T>(G, n, dl, ipiv, true, tab + kTabLH * NL, agg);
+        table_second_order<T>(G, n, eh, fh, true, tab + kTabUH * NL);
+    }
+    __syncthreads();
 }
 
-// exclusive lane scan of right-hand-side parts with tabulated factor parts
+// intra-warp inclusive scans of right-hand-side parts with tabulated factor parts
 template <typename T>
-__device__ __forceinline__ T scan_first_order(T c, const T* __restrict__ tab, bool descending) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ T scan_first_order(const Grp& G, T c, const T* __restrict__ tab, bool asc) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
 #pragma unroll
     for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
-        const T pc = descending ? shdn(c, o) : shup(c, o);
-        if (descending ? lane + o < 32 : lane >= o) c = t_fma(tab[lv * 32 + lane], pc, c);
+        const T pc = shfl_dir(c, o, asc);
+        if (has_partner(G.lane, o, asc)) c = t_fma(tab[lv * NL + gl], pc, c);
     }
-    const T ex = descending ? shdn(c, 1) : shup(c, 1);
-    return (descending ? lane == 31 : lane == 0) ? t_zero(T()) : ex;
+    return c;
 }
 template <typename T>
-__device__ __forceinline__ void scan_second_order(T& v0, T& v1, const T* __restrict__ tab, bool ascending) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void scan_second_order(const Grp& G, T& v0, T& v1, const T* __restrict__ tab, bool asc) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
 #pragma unroll
     for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
-        const T p0 = ascending ? shup(v0, o) : shdn(v0, o);
-        const T p1 = ascending ? shup(v1, o) : shdn(v1, o);
-        if (ascending ? lane >= o : lane + o < 32) {
-            const T m00 = tab[(4 * lv + 0) * 32 + lane], m01 = tab[(4 * lv + 1) * 32 + lane];
-            const T m10 = tab[(4 * lv + 2) * 32 + lane], m11 = tab[(4 * lv + 3) * 32 + lane];
+        const T p0 = shfl_dir(v0, o, asc);
+        const T p1 = shfl_dir(v1, o, asc);
+        if (has_partner(G.lane, o, asc)) {
+            const T m00 = tab[(4 * lv + 0) * NL + gl], m01 = tab[(4 * lv + 1) * NL + gl];
+            const T m10 = tab[(4 * lv + 2) * NL + gl], m11 = tab[(4 * lv + 3) * NL + gl];
             const T n0 = t_fma(m00, p0, t_fma(m01, p1, v0));
             v1 = t_fma(m10, p0, t_fma(m11, p1, v1));
             v0 = n0;
         }
     }
-    const T e0 = ascending ? shup(v0, 1) : shdn(v0, 1);
-    const T e1 = ascending ? shup(v1, 1) : shdn(v1, 1);
-    const bool first = ascending ? lane == 0 : lane == 31;
-    v0 = first ? t_zero(T()) : e0;
-    v1 = first ? t_zero(T()) : e1;
+}
+
+// The right-hand-side part of the exclusive prefix of this lane's chunk,
+// from its intra-warp inclusive value: intra-warp exclusive part, warp
+// aggregates through shared memory, composition.  Two group barriers.
+template <typename T>
+__device__ __forceinline__ T prefix_first_order(const Grp& G, T c_incl, const T* __restrict__ tab, bool asc,
+                                                double2* s_agg) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
+    const T ex = shfl_dir(c_incl, 1, asc);
+    const T c_ex = first_lane(G.lane, asc) ? t_zero(T()) : ex;
+    const T agg = shfl_from(c_incl, last_lane(asc));
+    if (G.lane == 0) s_agg[G.gw] = t_to2(agg);
+    grp_sync(G);
+    const int pw = warp_pos(G, asc);
+    T P = t_zero(T());
+    for (int q = 0; q < pw; ++q) {
+        const int qw = asc ? q : G.W - 1 - q;
+        P = t_fma(tab[7 * NL + q], P, t_from(s_agg[qw], T()));
+    }
+    grp_sync(G);   // the aggregates may be rewritten by the next solve
+    return t_fma(tab[5 * NL + gl], P, c_ex);
+}
+template <typename T>
+__device__ __forceinline__ void prefix_second_order(const Grp& G, T& v0, T& v1, const T* __restrict__ tab, bool asc,
+                                                    double2* s_agg) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
+    const T e0 = shfl_dir(v0, 1, asc), e1 = shfl_dir(v1, 1, asc);
+    const bool first = first_lane(G.lane, asc);
+    const T x0 = first ? t_zero(T()) : e0, x1 = first ? t_zero(T()) : e1;
+    const int ll = last_lane(asc);
+    const T a0 = shfl_from(v0, ll), a1 = shfl_from(v1, ll);
+    if (G.lane == 0) { s_agg[2 * G.gw] = t_to2(a0); s_agg[2 * G.gw + 1] = t_to2(a1); }
+    grp_sync(G);
+    const int pw = warp_pos(G, asc);
+    T p0 = t_zero(T()), p1 = t_zero(T());
+    for (int q = 0; q < pw; ++q) {
+        const int qw = asc ? q : G.W - 1 - q;
+        const T m00 = tab[24 * NL + q], m01 = tab[25 * NL + q], m10 = tab[26 * NL + q], m11 = tab[27 * NL + q];
+        const T n0 = t_fma(m00, p0, t_fma(m01, p1, t_from(s_agg[2 * qw], T())));
+        p1 = t_fma(m10, p0, t_fma(m11, p1, t_from(s_agg[2 * qw + 1], T())));
+        p0 = n0;
+    }
+    grp_sync(G);
+    const T m00 = tab[20 * NL + gl], m01 = tab[21 * NL + gl], m10 = tab[22 * NL + gl], m11 = tab[23 * NL + gl];
+    v0 = t_fma(m00, p0, t_fma(m01, p1, x0));
+    v1 = t_fma(m10, p0, t_fma(m11, p1, x1));
 }
 
 // Output of a sweep: plain store, or out = (out + x)/2 (the H' combination).
@@ -316,19 +435,23 @@ template <typename T> __device__ __forceinline__ void put(T* out, int i, T x, bo
 }
 
 // L sweep of (LU)^{-1}: y <- L^{-1} P b (forward, with the recorded interchanges).  in != out.
+// All warps of the calling group; s_agg: this group's 16-entry aggregate area.
 template <typename T>
-__device__ void warp_L_fwd(int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                           const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tab) {
+__device__ void grp_L_fwd(const Grp& G, int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
+                          const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tab, double2* s_agg) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
+    const T* tb = tab + kTabL * NL;
     int lo, hi;
-    lane_chunk(n, lo, hi);
+    grp_chunk(G, n, lo, hi);
     const int shi = min(hi, n - 1);   // steps i in [lo, shi)
     T c = t_zero(T());
     for (int i = lo; i < shi; ++i) {
         const T bn = in[i + 1];
         c = ipiv[i] == i ? t_fma(t_scale(dl[i], -1.0), c, bn) : t_fma(t_scale(dl[i], -1.0), bn, c);
     }
-    c = scan_first_order(c, tab + kTabL * 32, false);
-    T st = t_fma(tab[(kTabL + 5) * 32 + (threadIdx.x & 31)], in[0], c);
+    c = scan_first_order(G, c, tb, true);
+    c = prefix_first_order(G, c, tb, true, s_agg);
+    T st = t_fma(tb[6 * NL + gl], in[0], c);
     for (int i = lo; i < shi; ++i) {
         const T bn = in[i + 1];
         if (ipiv[i] == i) {
@@ -344,17 +467,20 @@ __device__ void warp_L_fwd(int n, const T* __restrict__ dl, const int* __restric
 
 // U sweep: x_i = e_i x_{i+1} + f_i x_{i+2} + y_i dinv_i (descending).
 template <typename T>
-__device__ void warp_U_bwd(int n, const T* __restrict__ e, const T* __restrict__ f, const T* __restrict__ dinv,
-                           const T* __restrict__ y, T* __restrict__ out, bool half_add, const T* __restrict__ tab) {
+__device__ void grp_U_bwd(const Grp& G, int n, const T* __restrict__ e, const T* __restrict__ f,
+                          const T* __restrict__ dinv, const T* __restrict__ y, T* __restrict__ out, bool half_add,
+                          const T* __restrict__ tab, double2* s_agg) {
+    const T* tb = tab + kTabU * 32 * G.W;
     int lo, hi;
-    lane_chunk(n, lo, hi);
+    grp_chunk(G, n, lo, hi);
     T v0 = t_zero(T()), v1 = t_zero(T());
     for (int i = hi - 1; i >= lo; --i) {
         const T n0 = t_fma(e[i], v0, t_fma(f[i], v1, t_mul(y[i], dinv[i])));
         v1 = v0;
         v0 = n0;
     }
-    scan_second_order(v0, v1, tab + kTabU * 32, false);
+    scan_second_order(G, v0, v1, tb, false);
+    prefix_second_order(G, v0, v1, tb, false, s_agg);
     T x1 = v0, x2 = v1;   // (x_{hi}, x_{hi+1})
     for (int i = hi - 1; i >= lo; --i) {
         const T x0 = t_fma(e[i], x1, t_fma(f[i], x2, t_mul(y[i], dinv[i])));
@@ -366,17 +492,20 @@ __device__ void warp_U_bwd(int n, const T* __restrict__ e, const T* __restrict__
 
 // U^dagger sweep: x_i = eh_i x_{i-1} + fh_i x_{i-2} + b_i conj(dinv_i) (ascending).  in != out.
 template <typename T>
-__device__ void warp_UH_fwd(int n, const T* __restrict__ eh, const T* __restrict__ fh, const T* __restrict__ dinv,
-                            const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tab) {
+__device__ void grp_UH_fwd(const Grp& G, int n, const T* __restrict__ eh, const T* __restrict__ fh,
+                           const T* __restrict__ dinv, const T* __restrict__ in, T* __restrict__ out,
+                           const T* __restrict__ tab, double2* s_agg) {
+    const T* tb = tab + kTabUH * 32 * G.W;
     int lo, hi;
-    lane_chunk(n, lo, hi);
+    grp_chunk(G, n, lo, hi);
     T v0 = t_zero(T()), v1 = t_zero(T());
     for (int i = lo; i < hi; ++i) {
         const T n0 = t_fma(eh[i], v0, t_fma(fh[i], v1, t_mul(in[i], t_conj(dinv[i]))));
         v1 = v0;
         v0 = n0;
     }
-    scan_second_order(v0, v1, tab + kTabUH * 32, true);
+    scan_second_order(G, v0, v1, tb, true);
+    prefix_second_order(G, v0, v1, tb, true, s_agg);
     T x1 = v0, x2 = v1;   // (x_{lo-1}, x_{lo-2})
     for (int i = lo; i < hi; ++i) {
         const T x0 = t_fma(eh[i], x1, t_fma(fh[i], x2, t_mul(in[i], t_conj(dinv[i]))));
@@ -388,16 +517,20 @@ __device__ void warp_UH_fwd(int n, const T* __restrict__ eh, const T* __restrict
 
 // L^dagger sweep of ((LU)^dagger)^{-1} (descending, interchanges undone).  in != out.
 template <typename T>
-__device__ void warp_LH_bwd(int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                            const T* __restrict__ in, T* __restrict__ out, bool half_add, const T* __restrict__ tab) {
+__device__ void grp_LH_bwd(const Grp& G, int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
+                           const T* __restrict__ in, T* __restrict__ out, bool half_add, const T* __restrict__ tab,
+                           double2* s_agg) {
+    const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
+    const T* tb = tab + kTabLH * NL;
     int lo, hi;
-    lane_chunk(n, lo, hi);
+    grp_chunk(G, n, lo, hi);
     const int shi = min(hi, n - 1);   // steps i in [lo, shi), walked downwards
     T c = t_zero(T());
     for (int i = shi - 1; i >= lo; --i)
         if (ipiv[i] == i) c = t_fma(t_scale(t_conj(dl[i]), -1.0), c, in[i]);
-    c = scan_first_order(c, tab + kTabLH * 32, true);
-    T st = t_fma(tab[(kTabLH + 5) * 32 + (threadIdx.x & 31)], in[n - 1], c);   // s_{shi}
+    c = scan_first_order(G, c, tb, false);
+    c = prefix_first_order(G, c, tb, false, s_agg);
+    T st = t_fma(tb[6 * NL + gl], in[n - 1], c);   // s_{shi}
     for (int i = shi - 1; i >= lo; --i) {
         const T cdl = t_conj(dl[i]);
         if (ipiv[i] == i) {
@@ -430,6 +563,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_inner(Inner in) {
     __shared__ double2 sh2[33];
     __shared__ double sh1[32];
+    __shared__ double2 s_agg[32];   // warp aggregates of the group scans, 16 per group
     __shared__ int s_info;
     const int rhs = blockIdx.x;
     const int k = in.k, L = in.ell;
@@ -461,7 +595,8 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     T* w = W + 11 * (size_t)k;
     T* l = W + 12 * (size_t)k;
     const bool TS = sizeof(T) == sizeof(double2);
-    const int warp = threadIdx.x >> 5;
+    const Grp G = grp_of(TS);
+    double2* gagg = s_agg + 16 * G.g;
 
     // LU of s * H in gttrf form, then the solve coefficients
     auto factor = [&](double sc) {
@@ -473,8 +608,7 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         if (threadIdx.x == 0) s_info = gttrf<T>(k, dl, t1, e, f, ipiv, dinv);
         __syncthreads();
         lu_coefficients<T>(k, e, f, eh, fh, dinv);
-        sweep_tables<T>(k, dl, ipiv, e, f, eh, fh, TS, tab);
-        __syncthreads();
+        sweep_tables<T>(k, dl, ipiv, e, f, eh, fh, TS, tab, s_agg);
     };
 
     // ---- p (Eq. popt) --------------------------------------------------------
@@ -498,10 +632,10 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         __syncthreads();
         double tn = 1.0;
         for (int it = 0; it < 30; ++it) {
-            if (warp == 0) {
-                warp_L_fwd<T>(k, dl, ipiv, x, t1, tab);
-                __syncwarp();
-                warp_U_bwd<T>(k, e, f, dinv, t1, y, false, tab);
+            if (G.g == 0) {
+                grp_L_fwd<T>(G, k, dl, ipiv, x, t1, tab, gagg);
+                grp_sync(G);
+                grp_U_bwd<T>(G, k, e, f, dinv, t1, y, false, tab, gagg);
             }
             __syncthreads();
             tn = bnorm<T>(k, y, sh1);
@@ -525,10 +659,10 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
             for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_scale(x[i], 1.0 / xn);
             __syncthreads();
             for (int it = 0; it < 30; ++it) {
-                if (warp == 0) {
-                    warp_L_fwd<T>(k, dl, ipiv, x, t1, tab);
-                    __syncwarp();
-                    warp_U_bwd<T>(k, e, f, dinv, t1, y, false, tab);
+                if (G.g == 0) {
+                    grp_L_fwd<T>(G, k, dl, ipiv, x, t1, tab, gagg);
+                    grp_sync(G);
+                    grp_U_bwd<T>(G, k, e, f, dinv, t1, y, false, tab, gagg);
                 }
                 __syncthreads();
                 project_out<T>(k, x1, y, sh2);
@@ -575,14 +709,14 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         band_mv<T>(k, p, al, be, ga, src_r, out_r, false);
         if (TS) band_mv<T>(k, p, al, be, ga, src_l, out_l, true);
         __syncthreads();
-        if (warp == 0) {
-            warp_L_fwd<T>(k, dl, ipiv, src_r, t1, tab);
-            __syncwarp();
-            warp_U_bwd<T>(k, e, f, dinv, t1, out_r, true, tab);
-        } else if (TS && warp == 1) {
-            warp_UH_fwd<T>(k, eh, fh, dinv, src_l, t2, tab);
-            __syncwarp();
-            warp_LH_bwd<T>(k, dl, ipiv, t2, out_l, true, tab);
+        if (G.g == 0) {
+            grp_L_fwd<T>(G, k, dl, ipiv, src_r, t1, tab, gagg);
+            grp_sync(G);
+            grp_U_bwd<T>(G, k, e, f, dinv, t1, out_r, true, tab, gagg);
+        } else {
+            grp_UH_fwd<T>(G, k, eh, fh, dinv, src_l, t2, tab, gagg);
+            grp_sync(G);
+            grp_LH_bwd<T>(G, k, dl, ipiv, t2, out_l, true, tab, gagg);
         }
         __syncthreads();
     };

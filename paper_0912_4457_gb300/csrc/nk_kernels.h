@@ -142,7 +142,7 @@ struct Inner {
 };
 constexpr int kInnerWorkVecs = 16;
 // per RHS: kInnerWorkVecs vectors of length k, then the sweep tables of the LU
-constexpr int kSweepTableElems = 64 * 32;
+constexpr int kSweepTableElems = 72 * 256;   // 72 table rows x up to 256 group lanes
 __host__ __device__ constexpr size_t inner_work_elems(int k) { return (size_t)kInnerWorkVecs * k + kSweepTableElems; }
 // Largest outer size k the inner kernel supports (its LU factors and solve
 // vectors, 8 complex vectors of length k plus the pivots, fill shared memory).

@@ -204,6 +204,26 @@ def oracle_inner_sensitivity(alpha, beta, gamma, ell, p, herm, c_ref, seed=0):
     return worst
 
 
+@pytest.mark.parametrize("mu,k,ell", [(0.0, 6, 4), (0.3, 6, 6), (0.3, 130, 32), (0.0, 300, 48), (0.3, 1000, 160)])
+def test_inner_sign_chunking_edge_sizes(mu, k, ell):
+    """Sizes around the scan layout of the tridiagonal solves (k smaller than
+    the lanes of a warp group, k just above a multiple of 128, k large): the
+    same H_k on both sides, fixed p, compared within the oracle's own
+    sensitivity to rounding-level changes of H_k."""
+    dims = (4, 4, 4, 4)
+    U = links(dims, 101)
+    b = inputs.gaussian_sources(dims, 203)[0]
+    A, Ad, herm = nested.operator(U, dims, mu, M_W)
+    ref = nested.outer_basis(A, Ad, b, k, herm)
+    p = 0.9
+    c_ref, info = nested.inner_sign(ref.alpha, ref.beta, ref.gamma, ell, p, herm)
+    sens = oracle_inner_sensitivity(ref.alpha, ref.beta, ref.gamma, ell, p, herm, c_ref)
+    ctx = make_ctx(dims, 101, mu)
+    c, st, _ = ctx.inner_sign(ref.alpha, ref.beta, ref.gamma, ell, p=p, hermitian=herm)
+    assert rel(c[0], c_ref) < max(1e-11, 10 * sens)
+    ctx.close()
+
+
 def test_inner_sign_batched_and_fixed_p():
     dims = (4, 4, 4, 4)
     U = links(dims, 101)
