@@ -108,7 +108,7 @@ __device__ int gttrf(int n, T* dl, T* d, T* du, T* du2, int* ipiv, T* dinv) {
 // summation order (diag, sub, super) -- all threads of the block.
 template <typename T>
 __device__ void band_mv(int n, double p, const double2* al, const double2* be, const double2* ga,
-                        const T* __restrict__ x, T* __restrict__ y, bool dagger) {
+                        const T* x, T* y, bool dagger) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         T dg = t_from(al[i], T());
         if (dagger) dg = t_conj(dg);
@@ -266,7 +266,7 @@ __device__ __forceinline__ int warp_pos(const Grp& G, bool asc) { return asc ? G
 // where row i was not interchanged, 1 where it was); all warps of the group
 template <typename T>
 __device__ void table_first_order(const Grp& G, int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                                  bool dagger, T* __restrict__ tab, double2* s_agg) {
+                                  bool dagger, T* tab, double2* s_agg) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     const bool asc = !dagger;
     int lo, hi;
@@ -300,7 +300,7 @@ __device__ void table_first_order(const Grp& G, int n, const T* __restrict__ dl,
 // ascending for U^dagger); all warps of the group
 template <typename T>
 __device__ void table_second_order(const Grp& G, int n, const T* __restrict__ e, const T* __restrict__ f, bool asc,
-                                   T* __restrict__ tab) {
+                                   T* tab) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     int lo, hi;
     grp_chunk(G, n, lo, hi);
@@ -356,7 +356,7 @@ __device__ void sweep_tables(int n, const T* dl, const int* ipiv, const T* e, co
 
 // intra-warp inclusive scans of right-hand-side parts with tabulated factor parts
 template <typename T>
-__device__ __forceinline__ T scan_first_order(const Grp& G, T c, const T* __restrict__ tab, bool asc) {
+__device__ __forceinline__ T scan_first_order(const Grp& G, T c, const T* tab, bool asc) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
 #pragma unroll
     for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
@@ -366,7 +366,7 @@ __device__ __forceinline__ T scan_first_order(const Grp& G, T c, const T* __rest
     return c;
 }
 template <typename T>
-__device__ __forceinline__ void scan_second_order(const Grp& G, T& v0, T& v1, const T* __restrict__ tab, bool asc) {
+__device__ __forceinline__ void scan_second_order(const Grp& G, T& v0, T& v1, const T* tab, bool asc) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
 #pragma unroll
     for (int lv = 0, o = 1; o < 32; ++lv, o <<= 1) {
@@ -386,7 +386,7 @@ __device__ __forceinline__ void scan_second_order(const Grp& G, T& v0, T& v1, co
 // from its intra-warp inclusive value: intra-warp exclusive part, warp
 // aggregates through shared memory, composition.  Two group barriers.
 template <typename T>
-__device__ __forceinline__ T prefix_first_order(const Grp& G, T c_incl, const T* __restrict__ tab, bool asc,
+__device__ __forceinline__ T prefix_first_order(const Grp& G, T c_incl, const T* tab, bool asc,
                                                 double2* s_agg) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     const T ex = shfl_dir(c_incl, 1, asc);
@@ -404,7 +404,7 @@ __device__ __forceinline__ T prefix_first_order(const Grp& G, T c_incl, const T*
     return t_fma(tab[5 * NL + gl], P, c_ex);
 }
 template <typename T>
-__device__ __forceinline__ void prefix_second_order(const Grp& G, T& v0, T& v1, const T* __restrict__ tab, bool asc,
+__device__ __forceinline__ void prefix_second_order(const Grp& G, T& v0, T& v1, const T* tab, bool asc,
                                                     double2* s_agg) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     const T e0 = shfl_dir(v0, 1, asc), e1 = shfl_dir(v1, 1, asc);
@@ -438,7 +438,7 @@ template <typename T> __device__ __forceinline__ void put(T* out, int i, T x, bo
 // All warps of the calling group; s_agg: this group's 16-entry aggregate area.
 template <typename T>
 __device__ void grp_L_fwd(const Grp& G, int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                          const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tab, double2* s_agg) {
+                          const T* in, T* out, const T* tab, double2* s_agg) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     const T* tb = tab + kTabL * NL;
     int lo, hi;
@@ -468,8 +468,8 @@ __device__ void grp_L_fwd(const Grp& G, int n, const T* __restrict__ dl, const i
 // U sweep: x_i = e_i x_{i+1} + f_i x_{i+2} + y_i dinv_i (descending).
 template <typename T>
 __device__ void grp_U_bwd(const Grp& G, int n, const T* __restrict__ e, const T* __restrict__ f,
-                          const T* __restrict__ dinv, const T* __restrict__ y, T* __restrict__ out, bool half_add,
-                          const T* __restrict__ tab, double2* s_agg) {
+                          const T* __restrict__ dinv, const T* y, T* out, bool half_add,
+                          const T* tab, double2* s_agg) {
     const T* tb = tab + kTabU * 32 * G.W;
     int lo, hi;
     grp_chunk(G, n, lo, hi);
@@ -493,8 +493,8 @@ __device__ void grp_U_bwd(const Grp& G, int n, const T* __restrict__ e, const T*
 // U^dagger sweep: x_i = eh_i x_{i-1} + fh_i x_{i-2} + b_i conj(dinv_i) (ascending).  in != out.
 template <typename T>
 __device__ void grp_UH_fwd(const Grp& G, int n, const T* __restrict__ eh, const T* __restrict__ fh,
-                           const T* __restrict__ dinv, const T* __restrict__ in, T* __restrict__ out,
-                           const T* __restrict__ tab, double2* s_agg) {
+                           const T* __restrict__ dinv, const T* in, T* out,
+                           const T* tab, double2* s_agg) {
     const T* tb = tab + kTabUH * 32 * G.W;
     int lo, hi;
     grp_chunk(G, n, lo, hi);
@@ -518,7 +518,7 @@ __device__ void grp_UH_fwd(const Grp& G, int n, const T* __restrict__ eh, const 
 // L^dagger sweep of ((LU)^dagger)^{-1} (descending, interchanges undone).  in != out.
 template <typename T>
 __device__ void grp_LH_bwd(const Grp& G, int n, const T* __restrict__ dl, const int* __restrict__ ipiv,
-                           const T* __restrict__ in, T* __restrict__ out, bool half_add, const T* __restrict__ tab,
+                           const T* in, T* out, bool half_add, const T* tab,
                            double2* s_agg) {
     const int NL = 32 * G.W, gl = G.gw * 32 + G.lane;
     const T* tb = tab + kTabLH * NL;

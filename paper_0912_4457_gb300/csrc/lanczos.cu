@@ -82,6 +82,35 @@ __global__ void __launch_bounds__(kThreads) k_init(Outer o, int copy_mode) {
     }
 }
 
+// End of step 2: the deterministic reduction of the per-thread partial
+// (r^dag r, or r^dag l two-sided) and, in the last block, beta and gamma.
+template <bool TS>
+__device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, double2 acc, double2* sh) {
+    double2 part = block_sum(acc, sh);
+    if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, blockIdx.x, o.nblk)) {
+        double2 d = sum_partials(o.partials + (size_t)rhs * o.npart, o.nblk, sh);
+        if (threadIdx.x == 0) {
+            const size_t at = (size_t)rhs * o.k + j;
+            if (!TS) {
+                double b = sqrt(d.x);                   // beta <- sqrt(r^dag r)
+                o.beta[at] = mk(b, 0.0);
+                o.gamma[at] = mk(b, 0.0);
+                if (!(b > 0.0) || !isfinite(b)) o.status[rhs] = kStatusBreakdown;
+            } else if ((d.x == 0.0 && d.y == 0.0) || !isfinite(d.x) || !isfinite(d.y)) {
+                // serious breakdown: delta = 0 (App. B); a non-finite delta is treated alike
+                o.status[rhs] = kStatusBreakdown;
+                o.beta[at] = mk(0.0, 0.0);
+                o.gamma[at] = mk(0.0, 0.0);
+            } else {
+                double2 b = csqrt_principal(d);         // beta <- sqrt(delta)
+                o.beta[at] = b;
+                o.gamma[at] = cdiv(cconj(d), b);        // gamma <- delta^* / beta
+            }
+            o.counters[rhs] = 0u;
+        }
+    }
+}
+
 template <bool TS>
 __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mode) {
     __shared__ double2 sh[33];
@@ -122,29 +151,74 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
             acc.x = fma(rr.x, rr.x, fma(rr.y, rr.y, acc.x));
         }
     }
-    double2 part = block_sum(acc, sh);
-    if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, blockIdx.x, o.nblk)) {
-        double2 d = sum_partials(o.partials + (size_t)rhs * o.npart, o.nblk, sh);
-        if (threadIdx.x == 0) {
-            const size_t at = hb + j;
-            if (!TS) {
-                double b = sqrt(d.x);                   // beta <- sqrt(r^dag r)
-                o.beta[at] = mk(b, 0.0);
-                o.gamma[at] = mk(b, 0.0);
-                if (!(b > 0.0) || !isfinite(b)) o.status[rhs] = kStatusBreakdown;
-            } else if ((d.x == 0.0 && d.y == 0.0) || !isfinite(d.x) || !isfinite(d.y)) {
-                // serious breakdown: delta = 0 (App. B); a non-finite delta is treated alike
-                o.status[rhs] = kStatusBreakdown;
-                o.beta[at] = mk(0.0, 0.0);
-                o.gamma[at] = mk(0.0, 0.0);
-            } else {
-                double2 b = csqrt_principal(d);         // beta <- sqrt(delta)
-                o.beta[at] = b;
-                o.gamma[at] = cdiv(cconj(d), b);        // gamma <- delta^* / beta
-            }
-            o.counters[rhs] = 0u;
+    step2_finish<TS>(o, rhs, j, acc, sh);
+}
+
+// Step 2 of the mixed-precision schedule (NK_MIXED) in two-float arithmetic
+// on the FP32 pipe: the same updates and reduction as k_step2, each element
+// read from FP64, updated and reduced in two-float (about 48-bit) arithmetic
+// and written back to FP64 (one FP64 addition per component instead of four
+// FP64 FMAs), with the next stencil's input copy taken from the two-float
+// value.  The FP32 stencil of these steps already perturbs the recurrence
+// at 1e-7; the 48-bit updates add a perturbation of about 1e-14.  The all-
+// FP64 schedule (NK_FP64) keeps k_step2.
+__device__ __forceinline__ dfc dfc_of(double2 v) {
+    dfc r;
+    r.x = df_from_double(v.x);
+    r.y = df_from_double(v.y);
+    return r;
+}
+__device__ __forceinline__ double2 double2_of(dfc v) { return mk(df_to_double(v.x), df_to_double(v.y)); }
+
+template <bool TS>
+__global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_mode) {
+    __shared__ double2 sh[33];
+    __shared__ double2 coef[2];
+    const int rhs = blockIdx.y;
+    if (o.status[rhs] != kStatusOK) return;
+    const size_t hb = (size_t)rhs * o.k;
+    if (threadIdx.x == 0) {
+        const double2 a = o.alpha[hb + j];
+        coef[0] = cdiv(a, scale_n(o, rhs, j));                 // H(j,j) / n_j
+        coef[1] = TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0);   // H(j,j)^* / m_j
+    }
+    __syncthreads();
+    const dfc c3 = dfc_of(coef[0]), c4 = dfc_of(coef[1]);
+    const double2* __restrict__ qj = outer_q(o, rhs, j);
+    double2* __restrict__ r = outer_q(o, rhs, j + 1);
+    const double2* __restrict__ pj = TS ? outer_p(o, rhs, j) : nullptr;
+    double2* __restrict__ l = TS ? outer_p(o, rhs, j + 1) : nullptr;
+    const size_t vb = (size_t)rhs * o.N;
+    df ax(0), ay(0);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
+        const dfc q = dfc_of(qj[i]);
+        dfc rr = dfc_of(r[i]);
+        // r <- r - c3 q, l <- l - c4 p
+        if (TS) {
+            rr.x = rr.x - (c3.x * q.x - c3.y * q.y);
+            rr.y = rr.y - (c3.x * q.y + c3.y * q.x);
+        } else {
+            rr.x = rr.x - c3.x * q.x;
+            rr.y = rr.y - c3.x * q.y;
+        }
+        r[i] = double2_of(rr);
+        if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(rr.x.hi, rr.y.hi);
+        else o.qdf[vb + i] = rr;
+        if (TS) {
+            const dfc pv = dfc_of(pj[i]);
+            dfc ll = dfc_of(l[i]);
+            ll.x = ll.x - (c4.x * pv.x - c4.y * pv.y);
+            ll.y = ll.y - (c4.x * pv.y + c4.y * pv.x);
+            l[i] = double2_of(ll);
+            if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(ll.x.hi, ll.y.hi);
+            else o.pdf[vb + i] = ll;
+            ax += rr.x * ll.x + rr.y * ll.y;   // conj(r) l
+            ay += rr.x * ll.y - rr.y * ll.x;
+        } else {
+            ax += rr.x * rr.x + rr.y * rr.y;
         }
     }
+    step2_finish<TS>(o, rhs, j, mk(df_to_double(ax), df_to_double(ay)), sh);
 }
 
 // c'_j = |x| c_j / n_j: the lift coefficients on the unnormalised basis
@@ -217,8 +291,13 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st) {
 
 void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
-    if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
-    else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
+    if (copy_mode == kCopyNone) {   // the all-FP64 schedule
+        if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
+        else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
+    } else {
+        if (o.two_sided) k_step2_df<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
+        else k_step2_df<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
+    }
 }
 
 void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st) {
