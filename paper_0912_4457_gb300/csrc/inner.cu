@@ -13,8 +13,8 @@
 //
 // The inner Lanczos runs one CTA per RHS: the band products, inner products
 // and axpys are spread over the CTA; the two O(k) substitution sweeps of each
-// solve are parallel prefix scans on a group of warps (all 8; two groups of 4
-// in the two-sided case, where H_k' v and H_k'^dagger w are independent),
+// solve are parallel prefix scans on a group of 4 warps (two groups in the
+// two-sided case, where H_k' v and H_k'^dagger w are independent),
 // with the parts of the scans that depend on the LU factors alone tabulated
 // once per LU.
 //
@@ -198,9 +198,8 @@ __device__ __forceinline__ double2 t_fma(double2 a, double2 b, double2 c) {
 //   first order   (a, c): a = a_g a_f,  c = a_g c_f + c_g;
 //   second order  (M, v): M = M_g M_f,  v = M_g v_f + v_g.
 //
-// A solve runs on a group of W warps (W = 8 in the Hermitian case, where
-// there is one solve at a time; W = 4 per side in the two-sided case, where
-// H' v and H'^dagger w are solved side by side), so all four SM sub-partitions
+// A solve runs on a group of W = 4 warps (warps 0-3; in the two-sided case
+// warps 4-7 solve with H'^dagger side by side), so all four SM sub-partitions
 // issue its FP64 work.  Each of the 32 W lanes takes a contiguous chunk; the
 // chunk maps are composed by a shuffle scan inside each warp and by a short
 // sequential composition of the W warp aggregates (exchanged through shared
@@ -227,9 +226,9 @@ struct Grp {
     int bar;    // named barrier id
     int g;      // group index
 };
-__device__ __forceinline__ Grp grp_of(bool two_sided) {
+__device__ __forceinline__ Grp grp_of(bool) {
     const int warp = threadIdx.x >> 5;
-    const int W = two_sided ? 4 : 8;
+    const int W = 4;
     return {W, warp % W, (int)(threadIdx.x & 31), 1 + warp / W, warp / W};
 }
 __device__ __forceinline__ void grp_sync(const Grp& G) {
@@ -347,7 +346,7 @@ __device__ void sweep_tables(int n, const T* dl, const int* ipiv, const T* e, co
     if (G.g == 0) {
         table_first_order<T>(G, n, dl, ipiv, false, tab + kTabL * NL, agg);
         table_second_order<T>(G, n, e, f, false, tab + kTabU * NL);
-    } else {
+    } else if (two_sided) {
         table_first_order<T>(G, n, dl, ipiv, true, tab + kTabLH * NL, agg);
         table_second_order<T>(G, n, eh, fh, true, tab + kTabUH * NL);
     }
@@ -713,7 +712,7 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
             grp_L_fwd<T>(G, k, dl, ipiv, src_r, t1, tab, gagg);
             grp_sync(G);
             grp_U_bwd<T>(G, k, e, f, dinv, t1, out_r, true, tab, gagg);
-        } else {
+        } else if (TS) {
             grp_UH_fwd<T>(G, k, eh, fh, dinv, src_l, t2, tab, gagg);
             grp_sync(G);
             grp_LH_bwd<T>(G, k, dl, ipiv, t2, out_l, true, tab, gagg);

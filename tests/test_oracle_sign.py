@@ -13,7 +13,7 @@ import pytest
 import scipy.linalg
 
 import inputs
-from oracle import dirac, krylov, nested, signfun
+from oracle import dirac, freefield, krylov, nested, signfun
 
 DIMS2 = (2, 2, 2, 2)
 
@@ -159,3 +159,33 @@ def test_overlap_unit_circle_via_nested(lattice2):
     # <z, (g5 D + D g5 - D g5 D) x> = 0
     lhs = g5(d(x)) + d(g5(x)) - d(g5(d(x)))
     assert np.linalg.norm(lhs) < 1e-8 * np.linalg.norm(x)
+
+
+# ---- free field and pure gauge: exact answers at any size (oracle/freefield.py)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_free_field_sign_matches_dense_sign(mu):
+    """Momentum-space sgn(A) b equals the dense spectral sgn of the
+    real-space operator (a separate construction: the stencil's matrix and
+    its eigendecomposition) on a lattice with four different extents."""
+    dims = (2, 3, 2, 4)
+    U = inputs.unit_links(dims)
+    b = inputs.gaussian_sources(dims, seed=7)[0]
+    exact = freefield.free_sign_apply(b, dims, mu, -1.5)
+    dense = nested.sign_apply(U, dims, mu, -1.5, b, method="dense")[0]
+    assert np.abs(exact - dense).max() < 1e-11 * np.abs(dense).max()
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_pure_gauge_sign_is_the_rotated_free_sign(mu):
+    """sgn(A_U) W b = W sgn(A_1) b for U_nu(x) = W(x+nu) W(x)^+."""
+    dims = (2, 2, 3, 4)
+    W = inputs.gauge_transform(dims, seed=8)
+    U = freefield.pure_gauge_links(W)
+    b = inputs.gaussian_sources(dims, seed=9)[0]
+    want = freefield.rotate(W, freefield.free_sign_apply(b, dims, mu, -1.5), dims)
+    got = nested.sign_apply(U, dims, mu, -1.5, freefield.rotate(W, b, dims), method="dense")[0]
+    assert np.abs(got - want).max() < 1e-11 * np.abs(want).max()
+    # the links are far from the identity
+    assert np.abs(U - inputs.unit_links(dims)).max() > 0.5
