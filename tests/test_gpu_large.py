@@ -1,0 +1,81 @@
+"""Large lattices (the 10^4 and 16^3 x 32 configurations), where the oracle
+cannot run the method: checked against answers that hold at any size.
+
+* 16^3 x 32, mu = 0.2, mixed schedule with double pass (the basis of 12
+  sources at this k would not fit in memory): pure-gauge links
+  U_nu(x) = W(x + nu) W(x)^+ with W random SU(3), for which
+  sgn(A_U) (W b) = W sgn(A_1) b exactly, and sgn(A_1) acts in momentum space
+  (oracle/freefield.py).  Bar: 1e-8 relative, the workload tolerance; at
+  k = 1024, j0 = 384 the measured error is about 2e-10.
+* 10^4, mu = 0.2, random links (plaquette 0.59): the sgn^2 estimate of
+  Sec. 3 (apply the solve to its own result) and gauge covariance of the
+  whole solve, each to the workload tolerance.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import freefield
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_0912_4457_gb300.nksign import NK_DOUBLE_PASS, NK_MIXED, Context  # noqa: E402
+
+TOL = 1e-8
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_16x16x16x32_pure_gauge_double_pass_mixed():
+    dims = (16, 16, 16, 32)
+    mu, m_w = 0.2, -2.0
+    W = inputs.gauge_transform(dims, seed=105)
+    U = freefield.pure_gauge_links(W)
+    n = 12
+    V = int(np.prod(dims))
+    b = np.zeros((n, 12 * V), complex)
+    b[:, :12] = np.eye(12)
+    exact = freefield.rotate(W, freefield.free_sign_apply(b, dims, mu, m_w), dims)
+    ctx = Context(dims)
+    ctx.load_links(U)
+    ctx.set_mu_mw(mu, m_w)
+    ctx.set_precision(384)
+    bd = torch.from_numpy(freefield.rotate(W, b, dims)).cuda()
+    y = torch.zeros_like(bd)
+    st, _ = ctx.sign_apply_dev(bd, y, n, 1024, 160, flags=NK_MIXED | NK_DOUBLE_PASS)
+    yh = y.cpu().numpy()
+    errs = [rel(yh[i], exact[i]) for i in range(n)]
+    assert max(errs) <= TOL, errs
+    ctx.close()
+
+
+def test_10x10x10x10_sgn2_and_gauge_covariance():
+    dims = (10, 10, 10, 10)
+    mu, m_w = 0.2, -2.0
+    U = inputs.su3_links(dims, 104)[0]
+    b = inputs.point_sources(dims)[:4]
+    ctx = Context(dims)
+    ctx.load_links(U)
+    ctx.set_mu_mw(mu, m_w)
+    k, ell = 1536, 256
+    ctx.set_precision(512)
+    y, st, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
+    x2, _, _ = ctx.sign_apply(y, k, ell, flags=NK_MIXED)
+    eps = [float(np.linalg.norm(x2[i] - b[i]) / (2 * np.linalg.norm(b[i]))) for i in range(len(b))]
+    assert max(eps) <= TOL, eps
+    # gauge covariance of the whole solve: links W(x+nu) U W(x)^+, source W b
+    Wg = inputs.gauge_transform(dims, seed=204)
+    Ug = np.empty_like(U)
+    for nu in range(4):
+        Ug[..., nu, :, :] = np.roll(Wg, -1, axis=3 - nu) @ U[..., nu, :, :] @ np.conj(np.swapaxes(Wg, -1, -2))
+    ctx.load_links(Ug)
+    yg, _, _ = ctx.sign_apply(freefield.rotate(Wg, b, dims), k, ell, flags=NK_MIXED)
+    want = freefield.rotate(Wg, y, dims)
+    assert max(rel(yg[i], want[i]) for i in range(len(b))) <= TOL
+    ctx.close()
