@@ -207,6 +207,20 @@ template <typename R> __device__ __forceinline__ R from_double(double d);
 template <> __device__ __forceinline__ float from_double<float>(double d) { return d2f_int(d); }
 template <> __device__ __forceinline__ double from_double<double>(double d) { return d; }
 template <> __device__ __forceinline__ df from_double<df>(double d) { return df_from_double(d); }
+// two-float complex values for the mixed-schedule epilogue
+__device__ __forceinline__ dfc to_dfc(float2 v) {
+    dfc r;
+    r.x = df(v.x, 0.0f);
+    r.y = df(v.y, 0.0f);
+    return r;
+}
+__device__ __forceinline__ dfc to_dfc(dfc v) { return v; }
+__device__ __forceinline__ dfc dfc_of2(double2 v) {
+    dfc r;
+    r.x = df_from_double(v.x);
+    r.y = df_from_double(v.y);
+    return r;
+}
 // a two-float kernel argument from a host double
 static df df_host(double d) {
     df r;
@@ -362,11 +376,47 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
         T out[4][3];
         stencil_site<R>(U, in, g, site, side, kappa, emu, emu_inv, out);
         const double2 c1 = coef[1];   // zero at j = 0 (the previous vector is then any valid one)
+        const int jp = j > 0 ? j - 1 : j;
+        if constexpr (!std::is_same<R, double>::value) {
+            // mixed schedule: the epilogue in two-float arithmetic on the rings
+            const dfc scr = dfc_of2(coef[0]), c1d = dfc_of2(c1);
+            df ax(0), ay(0);
+            const dfc* __restrict__ prv = side == 0 ? ring_q(o, rhs, jp) : ring_p(o, rhs, jp);
+            dfc* __restrict__ nxt = side == 0 ? ring_q(o, rhs, j + 1) : ring_p(o, rhs, j + 1);
+            const dfc* __restrict__ dotv = TS ? ring_p(o, rhs, j) : ring_q(o, rhs, j);
+            double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
+            const double2 cpj = PASS2 ? o.cp[hb + j] : make_double2(0.0, 0.0);
+            const double2* __restrict__ qj = outer_q(o, rhs, j);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const size_t idx = (size_t)(3 * sp + a) * g.V + site;
+                    const dfc v = to_dfc(out[sp][a]);
+                    const dfc pv = prv[idx];
+                    dfc rr;
+                    if (TS || side == 1) {
+                        rr.x = (v.x * scr.x - v.y * scr.y) - (c1d.x * pv.x - c1d.y * pv.y);   // s - c1 q_{j-1}
+                        rr.y = (v.x * scr.y + v.y * scr.x) - (c1d.x * pv.y + c1d.y * pv.x);
+                    } else {
+                        rr.x = v.x * scr.x - c1d.x * pv.x;
+                        rr.y = v.y * scr.x - c1d.x * pv.y;
+                    }
+                    nxt[idx] = rr;
+                    if (side == 0) {
+                        const dfc d = dotv[idx];
+                        ax += d.x * rr.x + d.y * rr.y;            // conj(d) r
+                        if (TS) ay += d.x * rr.y - d.y * rr.x;
+                        if (PASS2) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
+                    }
+                }
+            }
+            acc = make_double2(df_to_double(ax), df_to_double(ay));
+        } else {
         // the scale 1/n_j (1/m_j) in the stencil's precision
         T scr;
         scr.x = from_double<R>(coef[0].x);
         scr.y = from_double<R>(coef[0].y);
-        const int jp = j > 0 ? j - 1 : j;
         if (side == 0) {
             const double2* __restrict__ prv = outer_q(o, rhs, jp);
             double2* __restrict__ nxt = outer_q(o, rhs, j + 1);   // at j = k-1 a scratch column
@@ -409,6 +459,7 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
                     nxt[idx] = caxpy_neg(ll, c1, prv[idx]);             // l - c1 p_{j-1}
                 }
             }
+        }
         }
     }
     if (side == 0) {
@@ -457,9 +508,9 @@ void launch_dslash_step1(int precision, const void* U, const Geom& g, const Oute
     if (precision == 32) {
         launch_step1_t<float, float2>((const float2*)U, g, o, j, (float)kappa, (float)exp(mu), (float)exp(-mu), o.q32,
                                       o.N, o.p32, o.N, st);
-    } else if (precision == 48) {
-        launch_step1_t<df, dfc>((const dfc*)U, g, o, j, df_host(kappa), df_host(exp(mu)), df_host(exp(-mu)), o.qdf,
-                                o.N, o.pdf, o.N, st);
+    } else if (precision == 48) {   // the two-float stencil reads the two-float rings
+        launch_step1_t<df, dfc>((const dfc*)U, g, o, j, df_host(kappa), df_host(exp(mu)), df_host(exp(-mu)),
+                                ring_q(o, 0, j), 3 * o.N, o.two_sided ? ring_p(o, 0, j) : nullptr, 3 * o.N, st);
     } else {
         const long qs = (long)o.qcols * o.N;
         launch_step1_t<double, double2>((const double2*)U, g, o, j, kappa, exp(mu), exp(-mu), outer_q(o, 0, j), qs,

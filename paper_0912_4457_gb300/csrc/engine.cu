@@ -117,7 +117,7 @@ struct Layout {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_sided, bool double_pass,
-             const nk_launch& lc) {
+             const nk_launch& lc, bool mixed) {
     const int nblk = lc.step2_blocks;
     Layout L;
     std::memset(&L, 0, sizeof(L));
@@ -145,6 +145,10 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     if (two_sided) o.p32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
     o.qdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     if (two_sided) o.pdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
+    if (mixed) {
+        o.qr = (nk::dfc*)take((size_t)N * 16 * 3 * n_rhs);
+        if (two_sided) o.pr = (nk::dfc*)take((size_t)N * 16 * 3 * n_rhs);
+    }
     o.alpha = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     o.beta = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     o.gamma = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
@@ -457,10 +461,11 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     const bool ts = c->mu != 0.0;
     const bool dp = (flags & NK_DOUBLE_PASS) != 0;
     const nk_launch lc = launch_cfg(c, n_rhs, ts, (flags & NK_MIXED) != 0);
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, lc);
+    const bool mixed = (flags & NK_MIXED) != 0;
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, lc);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed);
     // counters must start at zero; status is (re)set by the norm kernel
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
     NK_CUDA(c, cudaMemsetAsync(Lw.in.timeout, 0, sizeof(int), st));
@@ -689,10 +694,10 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
                        cudaStream_t st, float* per_launch_ms) {
     const bool ts = c->mu != 0.0;
     const int k = 2 * kTuneWarm;
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, lc);
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, lc, mixed);
     int rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, lc);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, lc, mixed);
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
     Launcher L;
     L.st = st;
@@ -927,10 +932,11 @@ int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsig
     cudaStream_t st = (cudaStream_t)stream;
     const bool ts = c->mu != 0.0;
     const nk_launch lc = launch_cfg(c, n_rhs, ts, (flags & NK_MIXED) != 0);
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, lc);
+    const bool mixed = (flags & NK_MIXED) != 0;
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, 2, ts, false, lc, mixed);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, lc);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, 2, ts, false, lc, mixed);
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
     Launcher L;
     L.st = st;
@@ -969,10 +975,10 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     one.step2_blocks = 1;
     one.early_threads = 64;
     one.early_order = 0;
-    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one);
+    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one, false);
     int rc = ensure(c, c->staging, std::max(dry.total, c->staging.bytes));
     if (rc) return rc;
-    Layout Lw = carve((char*)c->staging.p, tiny, n_rhs, k, ell, ts, true, one);
+    Layout Lw = carve((char*)c->staging.p, tiny, n_rhs, k, ell, ts, true, one, false);
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpy(Lw.o.alpha, alpha, cb, cudaMemcpyHostToDevice));
     NK_CUDA(c, cudaMemcpy(Lw.o.beta, beta, cb, cudaMemcpyHostToDevice));

@@ -54,6 +54,14 @@ __global__ void __launch_bounds__(kThreads) k_norm(Outer o) {
     }
 }
 
+__device__ __forceinline__ dfc dfc_of(double2 v) {
+    dfc r;
+    r.x = df_from_double(v.x);
+    r.y = df_from_double(v.y);
+    return r;
+}
+__device__ __forceinline__ double2 double2_of(dfc v) { return mk(df_to_double(v.x), df_to_double(v.y)); }
+
 // The next stencil's input copy of one element (FP32 or two-float), made on
 // the integer pipe.
 __device__ __forceinline__ void put_copy(const Outer& o, int mode, bool left, size_t at, double2 v) {
@@ -69,13 +77,26 @@ __device__ __forceinline__ void put_copy(const Outer& o, int mode, bool left, si
 }
 
 // q_0 = x is already in place; p_0 = x, and the copies the first stencil reads.
+// Mixed schedule: the two-float rings hold q_0 and p_0, and a two-float
+// stencil reads the ring itself.
 __global__ void __launch_bounds__(kThreads) k_init(Outer o, int copy_mode) {
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
     const double2* x = outer_q(o, rhs, 0);
-    double2* p = o.two_sided ? outer_p(o, rhs, 0) : nullptr;
+    double2* p = (o.two_sided && !o.qr) ? outer_p(o, rhs, 0) : nullptr;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
         double2 a = x[i];
+        if (o.qr) {
+            const dfc d = dfc_of(a);
+            ring_q(o, rhs, 0)[i] = d;
+            if (o.two_sided) ring_p(o, rhs, 0)[i] = d;
+            if (copy_mode == kCopy32) {
+                const float2 f = make_float2(d.x.hi, d.y.hi);
+                o.q32[(size_t)rhs * o.N + i] = f;
+                if (o.two_sided) o.p32[(size_t)rhs * o.N + i] = f;
+            }
+            continue;
+        }
         if (p) p[i] = a;
         put_copy(o, copy_mode, false, (size_t)rhs * o.N + i, a);
         if (p) put_copy(o, copy_mode, true, (size_t)rhs * o.N + i, a);
@@ -155,21 +176,13 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
 }
 
 // Step 2 of the mixed-precision schedule (NK_MIXED) in two-float arithmetic
-// on the FP32 pipe: the same updates and reduction as k_step2, each element
-// read from FP64, updated and reduced in two-float (about 48-bit) arithmetic
-// and written back to FP64 (one FP64 addition per component instead of four
-// FP64 FMAs), with the next stencil's input copy taken from the two-float
-// value.  The FP32 stencil of these steps already perturbs the recurrence
-// at 1e-7; the 48-bit updates add a perturbation of about 1e-14.  The all-
-// FP64 schedule (NK_FP64) keeps k_step2.
-__device__ __forceinline__ dfc dfc_of(double2 v) {
-    dfc r;
-    r.x = df_from_double(v.x);
-    r.y = df_from_double(v.y);
-    return r;
-}
-__device__ __forceinline__ double2 double2_of(dfc v) { return mk(df_to_double(v.x), df_to_double(v.y)); }
-
+// on the FP32 pipe, on the two-float rings: r and l (left in ring slot j + 1
+// by the stencil kernel) are updated with q_j and p_j from the rings; r is
+// also written to the FP64 basis (one FP64 addition per component), and the
+// FP32 copy the next FP32 stencil reads is the high part (a two-float
+// stencil reads the ring).  The FP32 stencil of the late steps perturbs the
+// recurrence at 1e-7; 48-bit arithmetic adds about 1e-14.  The all-FP64
+// schedule (NK_FP64) keeps k_step2.
 template <bool TS>
 __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_mode) {
     __shared__ double2 sh[33];
@@ -184,15 +197,16 @@ __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_
     }
     __syncthreads();
     const dfc c3 = dfc_of(coef[0]), c4 = dfc_of(coef[1]);
-    const double2* __restrict__ qj = outer_q(o, rhs, j);
-    double2* __restrict__ r = outer_q(o, rhs, j + 1);
-    const double2* __restrict__ pj = TS ? outer_p(o, rhs, j) : nullptr;
-    double2* __restrict__ l = TS ? outer_p(o, rhs, j + 1) : nullptr;
+    const dfc* __restrict__ qj = ring_q(o, rhs, j);
+    dfc* __restrict__ r = ring_q(o, rhs, j + 1);
+    double2* __restrict__ rq = outer_q(o, rhs, j + 1);
+    const dfc* __restrict__ pj = TS ? ring_p(o, rhs, j) : nullptr;
+    dfc* __restrict__ l = TS ? ring_p(o, rhs, j + 1) : nullptr;
     const size_t vb = (size_t)rhs * o.N;
     df ax(0), ay(0);
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
-        const dfc q = dfc_of(qj[i]);
-        dfc rr = dfc_of(r[i]);
+        const dfc q = qj[i];
+        dfc rr = r[i];
         // r <- r - c3 q, l <- l - c4 p
         if (TS) {
             rr.x = rr.x - (c3.x * q.x - c3.y * q.y);
@@ -201,17 +215,16 @@ __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_
             rr.x = rr.x - c3.x * q.x;
             rr.y = rr.y - c3.x * q.y;
         }
-        r[i] = double2_of(rr);
+        r[i] = rr;
+        rq[i] = double2_of(rr);
         if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(rr.x.hi, rr.y.hi);
-        else o.qdf[vb + i] = rr;
         if (TS) {
-            const dfc pv = dfc_of(pj[i]);
-            dfc ll = dfc_of(l[i]);
+            const dfc pv = pj[i];
+            dfc ll = l[i];
             ll.x = ll.x - (c4.x * pv.x - c4.y * pv.y);
             ll.y = ll.y - (c4.x * pv.y + c4.y * pv.x);
-            l[i] = double2_of(ll);
+            l[i] = ll;
             if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(ll.x.hi, ll.y.hi);
-            else o.pdf[vb + i] = ll;
             ax += rr.x * ll.x + rr.y * ll.y;   // conj(r) l
             ay += rr.x * ll.y - rr.y * ll.x;
         } else {
@@ -291,7 +304,7 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st) {
 
 void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
-    if (copy_mode == kCopyNone) {   // the all-FP64 schedule
+    if (!o.qr) {   // the all-FP64 schedule
         if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
         else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
     } else {

@@ -234,6 +234,7 @@ struct __align__(16) dfc {
     df x, y;
 };
 template <> struct C2<df> { typedef dfc T; };
+static_assert(sizeof(dfc) == 16, "two-float complex is 16 bytes");
 
 // Upper bound on spin iterations of any device-side wait (each iteration
 // sleeps ~100 ns), about one second; a wait that runs out sets an error flag.

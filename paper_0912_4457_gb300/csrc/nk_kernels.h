@@ -68,6 +68,12 @@ struct Outer {
     double* xnorm;      // [rhs]
     double2* y;         // double pass: accumulation y = sum_j c'_j q_j, [rhs][N]
     const double2* cp;  // double pass: lift coefficients c'_j, [rhs][k]
+    // Mixed schedule (NK_MIXED): two-float rings of the newest three right and
+    // left vectors, [rhs][3][N] (slot j % 3).  The outer recurrence then runs in
+    // two-float arithmetic from these; only the right basis is also kept in
+    // FP64 (Q, for the lift).  nullptr in the all-FP64 schedule.
+    dfc* qr;
+    dfc* pr;
 };
 
 __host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {
@@ -75,6 +81,13 @@ __host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {
 }
 __host__ __device__ inline double2* outer_p(const Outer& o, int rhs, int j) {
     return o.P + ((size_t)rhs * 3 + j % 3) * o.N;
+}
+// (byte arithmetic: dfc, a two-float complex of 16 bytes, may be incomplete here)
+__host__ __device__ inline dfc* ring_q(const Outer& o, int rhs, int j) {
+    return reinterpret_cast<dfc*>(reinterpret_cast<char*>(o.qr) + ((size_t)rhs * 3 + j % 3) * o.N * 16);
+}
+__host__ __device__ inline dfc* ring_p(const Outer& o, int rhs, int j) {
+    return reinterpret_cast<dfc*>(reinterpret_cast<char*>(o.pr) + ((size_t)rhs * 3 + j % 3) * o.N * 16);
 }
 // n_j (q_j = n_j v_j) and m_j (p_j = m_j w_j)
 __device__ inline double2 scale_n(const Outer& o, int rhs, int j) {
