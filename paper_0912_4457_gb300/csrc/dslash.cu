@@ -377,8 +377,9 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
         stencil_site<R>(U, in, g, site, side, kappa, emu, emu_inv, out);
         const double2 c1 = coef[1];   // zero at j = 0 (the previous vector is then any valid one)
         const int jp = j > 0 ? j - 1 : j;
-        if constexpr (!std::is_same<R, double>::value) {
-            // mixed schedule: the epilogue in two-float arithmetic on the rings
+        if constexpr (std::is_same<R, float>::value) {
+            // late steps of the mixed schedule: the epilogue in two-float
+            // arithmetic on the rings
             const dfc scr = dfc_of2(coef[0]), c1d = dfc_of2(c1);
             df ax(0), ay(0);
             const dfc* __restrict__ prv = side == 0 ? ring_q(o, rhs, jp) : ring_p(o, rhs, jp);

@@ -285,7 +285,9 @@ void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int 
         const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
         L.run(cls, 1, [&] { nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
         if (j < o.k - 1)
-            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), st); });
+            L.run(NK_CLASS_STEP2, 1, [&] {
+                nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), mixed && j >= j0, st);
+            });
     }
 }
 
@@ -715,7 +717,7 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
         NK_CUDA(c, cudaEventRecord(e0, st));
         for (int r = 0; r < kTuneReps; ++r) {
             nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
-            nk::launch_outer_step2(Lw.o, kTuneWarm, copy_mode_for(mixed, j0, kTuneWarm + 1), st);
+            nk::launch_outer_step2(Lw.o, kTuneWarm, copy_mode_for(mixed, j0, kTuneWarm + 1), mixed && prec == 32, st);
         }
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());

@@ -63,12 +63,14 @@ __device__ __forceinline__ dfc dfc_of(double2 v) {
 __device__ __forceinline__ double2 double2_of(dfc v) { return mk(df_to_double(v.x), df_to_double(v.y)); }
 
 // The next stencil's input copy of one element (FP32 or two-float), made on
-// the integer pipe.
+// the integer pipe.  With the mixed schedule's rings the two-float copy is not
+// made here (the FP64 steps write the rings themselves, which the two-float
+// stencil reads).
 __device__ __forceinline__ void put_copy(const Outer& o, int mode, bool left, size_t at, double2 v) {
     if (mode == kCopy32) {
         float2 f = make_float2(d2f_int(v.x), d2f_int(v.y));
         (left ? o.p32 : o.q32)[at] = f;
-    } else if (mode == kCopyDF) {
+    } else if (mode == kCopyDF && !o.qr) {
         dfc w;
         w.x = df_from_double(v.x);
         w.y = df_from_double(v.y);
@@ -83,23 +85,17 @@ __global__ void __launch_bounds__(kThreads) k_init(Outer o, int copy_mode) {
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
     const double2* x = outer_q(o, rhs, 0);
-    double2* p = (o.two_sided && !o.qr) ? outer_p(o, rhs, 0) : nullptr;
+    double2* p = o.two_sided ? outer_p(o, rhs, 0) : nullptr;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
         double2 a = x[i];
+        if (p) p[i] = a;
+        put_copy(o, copy_mode, false, (size_t)rhs * o.N + i, a);
+        if (p) put_copy(o, copy_mode, true, (size_t)rhs * o.N + i, a);
         if (o.qr) {
             const dfc d = dfc_of(a);
             ring_q(o, rhs, 0)[i] = d;
             if (o.two_sided) ring_p(o, rhs, 0)[i] = d;
-            if (copy_mode == kCopy32) {
-                const float2 f = make_float2(d.x.hi, d.y.hi);
-                o.q32[(size_t)rhs * o.N + i] = f;
-                if (o.two_sided) o.p32[(size_t)rhs * o.N + i] = f;
-            }
-            continue;
         }
-        if (p) p[i] = a;
-        put_copy(o, copy_mode, false, (size_t)rhs * o.N + i, a);
-        if (p) put_copy(o, copy_mode, true, (size_t)rhs * o.N + i, a);
     }
 }
 
@@ -160,12 +156,14 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
         else rr = mk(fma(-c3.x, q.x, rr.x), fma(-c3.x, q.y, rr.y));
         r[i] = rr;
         put_copy(o, copy_mode, false, vb + i, rr);
+        if (o.qr) ring_q(o, rhs, j + 1)[i] = dfc_of(rr);
         if (TS) {
             const double2 pv = pj[i];
             double2 ll = l[i];
             ll = mk(fma(-c4.x, pv.x, fma(c4.y, pv.y, ll.x)), fma(-c4.x, pv.y, fma(-c4.y, pv.x, ll.y)));
             l[i] = ll;
             put_copy(o, copy_mode, true, vb + i, ll);
+            if (o.qr) ring_p(o, rhs, j + 1)[i] = dfc_of(ll);
             acc.x = fma(rr.x, ll.x, fma(rr.y, ll.y, acc.x));   // conj(r) l
             acc.y = fma(rr.x, ll.y, fma(-rr.y, ll.x, acc.y));
         } else {
@@ -175,8 +173,8 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
     step2_finish<TS>(o, rhs, j, acc, sh);
 }
 
-// Step 2 of the mixed-precision schedule (NK_MIXED) in two-float arithmetic
-// on the FP32 pipe, on the two-float rings: r and l (left in ring slot j + 1
+// Step 2 of the late (FP32-stencil) steps of the mixed schedule in two-float
+// arithmetic on the FP32 pipe, on the two-float rings: r and l (left in ring slot j + 1
 // by the stencil kernel) are updated with q_j and p_j from the rings; r is
 // also written to the FP64 basis (one FP64 addition per component), and the
 // FP32 copy the next FP32 stencil reads is the high part (a two-float
@@ -302,9 +300,9 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st) {
     k_init<<<grid, kThreads, 0, st>>>(o, copy_mode);
 }
 
-void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st) {
+void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
-    if (!o.qr) {   // the all-FP64 schedule
+    if (!ring || !o.qr) {   // FP64 step
         if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
         else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
     } else {

@@ -69,9 +69,11 @@ struct Outer {
     double2* y;         // double pass: accumulation y = sum_j c'_j q_j, [rhs][N]
     const double2* cp;  // double pass: lift coefficients c'_j, [rhs][k]
     // Mixed schedule (NK_MIXED): two-float rings of the newest three right and
-    // left vectors, [rhs][3][N] (slot j % 3).  The outer recurrence then runs in
-    // two-float arithmetic from these; only the right basis is also kept in
-    // FP64 (Q, for the lift).  nullptr in the all-FP64 schedule.
+    // left vectors, [rhs][3][N] (slot j % 3).  The early (two-float stencil)
+    // steps run in FP64 and copy their new vectors into the rings, which the
+    // two-float stencil reads; the late (FP32 stencil) steps run in two-float
+    // arithmetic from the rings, keeping only the right basis also in FP64
+    // (Q, for the lift).  nullptr in the all-FP64 schedule.
     dfc* qr;
     dfc* pr;
 };
@@ -117,7 +119,10 @@ void launch_dslash_step1(int precision, const void* U, const Geom& g, const Oute
                          double kappa, double mu, cudaStream_t st);
 int dslash_step1_blocks(const Geom& g, int threads);
 constexpr int kStencilMaxThreads = 256;
-void launch_outer_step2(const Outer& o, int j, int copy_mode, cudaStream_t st);
+// ring: the step belongs to the late (FP32-stencil) part of the mixed schedule,
+// which runs on the two-float rings; otherwise FP64 (the rings, if present,
+// still receive two-float copies of the new vectors).
+void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, cudaStream_t st);
 // kused[rhs]: outer steps whose basis vectors enter the lift of that RHS (k or,
 // adaptive, the converged size); coefficients beyond it are zero.
 void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st);
