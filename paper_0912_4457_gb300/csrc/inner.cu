@@ -786,13 +786,13 @@ __global__ void __launch_bounds__(kRhiThreads) k_rhi(Inner in, int C, int maxit,
     T* M = reinterpret_cast<T*>(smem);              // [nmax][L]
     T* prow = M + (size_t)nmax * L;                 // [L]
     T* tmp = prow + L;                              // [L]
-    T* fcol = tmp + L;                              // [nmax]
+    T* cand_row = tmp + L;                          // [2][L] published candidate pivot row
+    T* rowc = cand_row + 2 * L;                     // [2][L] published row c
+    T* fcol = rowc + 2 * L;                         // [nmax]
     int* piv = reinterpret_cast<int*>(fcol + nmax); // [L]
-    __shared__ double cand_val;
-    __shared__ int cand_idx;
+    __shared__ double cand_val[2];
+    __shared__ int cand_idx[2];
     __shared__ double part[2];
-    __shared__ double red_v[kRhiThreads / 32];
-    __shared__ int red_i[kRhiThreads / 32];
     __shared__ double sh1[32];
     __shared__ int s_stop;
 
@@ -802,6 +802,7 @@ __global__ void __launch_bounds__(kRhiThreads) k_rhi(Inner in, int C, int maxit,
     const double2* blo = in.bl + (size_t)rhs * L;
     const double2* glo = in.gl + (size_t)rhs * L;
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
 
     // S_0 = H_l (own rows)
     for (int e = tid; e < nloc * L; e += blockDim.x) {
@@ -825,83 +826,87 @@ __global__ void __launch_bounds__(kRhiThreads) k_rhi(Inner in, int C, int maxit,
         }
         __syncthreads();
         // ---- in-place Gauss-Jordan inverse of M with partial pivoting ----
+        // One cluster barrier per pivot: each CTA publishes its candidate pivot
+        // row (and the owner of row c that row) in a buffer of parity c & 1
+        // before the barrier; after it every CTA reads the pivot row and row c
+        // from those buffers, which their owners rewrite only two pivots later,
+        // after every CTA has passed the next barrier.
         for (int c = 0; c < L; ++c) {
-            // (a) local candidate: largest |M(i,c)|^2 over own rows i >= c (lowest i on ties)
-            double bv = -1.0;
-            int bi = 0x7fffffff;
-            for (int li = tid; li < nloc; li += blockDim.x) {
-                int i = rank + C * li;
-                if (i < c) continue;
-                double m = t_norm2(M[(size_t)li * L + c]);
-                if (m > bv || (m == bv && i < bi)) { bv = m; bi = i; }
-            }
+            const int par = c & 1;
+            // (a) local candidate: largest |M(i,c)|^2 over own rows i >= c (lowest i on ties);
+            // nloc <= 32, so warp 0 holds one row per lane
+            if (warp == 0) {
+                double bv = -1.0;
+                int bi = 0x7fffffff;
+                if (lane < nloc) {
+                    const int i = rank + C * lane;
+                    if (i >= c) { bv = t_norm2(M[(size_t)lane * L + c]); bi = i; }
+                }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                }
+                if (lane == 0) { cand_val[par] = bv; cand_idx[par] = bi; }
             }
-            if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_i[tid >> 5] = bi; }
             __syncthreads();
-            if (tid == 0) {
-                for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
-                    if (red_v[q] > bv || (red_v[q] == bv && red_i[q] < bi)) { bv = red_v[q]; bi = red_i[q]; }
-                cand_val = bv;
-                cand_idx = bi;
+            if (cand_val[par] >= 0.0) {
+                const T* src = M + (size_t)((cand_idx[par] - rank) / C) * L;
+                for (int col = tid; col < L; col += blockDim.x) cand_row[par * L + col] = src[col];
             }
-            cl.sync();                                                  // barrier A
-            // (b) pivot row over the cluster, ranks in fixed order
+            if (c % C == rank) {
+                const T* src = M + (size_t)(c / C) * L;
+                for (int col = tid; col < L; col += blockDim.x) rowc[par * L + col] = src[col];
+            }
+            cl.sync();                                                  // the one barrier of the pivot
+            // (b) pivot row over the cluster, ranks in fixed order (same decision everywhere)
             double pv = -1.0;
             int pi = 0x7fffffff;
             for (int q = 0; q < C; ++q) {
-                double qv = *cl.map_shared_rank(&cand_val, q);
-                int qi = *cl.map_shared_rank(&cand_idx, q);
+                double qv = cl.map_shared_rank(cand_val, q)[par];
+                int qi = cl.map_shared_rank(cand_idx, q)[par];
                 if (qv > pv || (qv == pv && qi < pi)) { pv = qv; pi = qi; }
             }
             if (!(pv > 0.0)) {              // singular (same decision in every CTA)
                 ok = false;
-                cl.sync();
+                cl.sync();                  // no CTA leaves while others read its buffers
                 break;
             }
             if (tid == 0) piv[c] = pi;
-            // (c) fetch the pivot row (and, for its owner, old row c)
+            // (c) fetch the pivot row and, for the owner of row pi, old row c
             {
-                T* src = cl.map_shared_rank(M, pi % C) + (size_t)(pi / C) * L;
+                const T* src = cl.map_shared_rank(cand_row, pi % C) + par * L;
                 for (int col = tid; col < L; col += blockDim.x) prow[col] = src[col];
                 if (pi != c && pi % C == rank) {
-                    T* srcc = cl.map_shared_rank(M, c % C) + (size_t)(c / C) * L;
+                    const T* srcc = cl.map_shared_rank(rowc, c % C) + par * L;
                     for (int col = tid; col < L; col += blockDim.x) tmp[col] = srcc[col];
                 }
             }
-            cl.sync();                                                  // barrier B
-            // (d) interchange and scale the pivot row
-            if (pi != c && pi % C == rank) {
-                T* dst = M + (size_t)(pi / C) * L;
-                for (int col = tid; col < L; col += blockDim.x) dst[col] = tmp[col];
-            }
+            __syncthreads();
             const T pinv = t_inv(prow[c]);
-            __syncthreads();
-            for (int col = tid; col < L; col += blockDim.x)
-                if (col != c) prow[col] = t_mul(prow[col], pinv);
-            __syncthreads();
-            if (tid == 0) prow[c] = pinv;
-            __syncthreads();
-            if (c % C == rank) {
-                T* dst = M + (size_t)(c / C) * L;
-                for (int col = tid; col < L; col += blockDim.x) dst[col] = prow[col];
+            // (d) multipliers of the own rows other than the pivot row, already
+            // divided by the pivot (the row in slot pi now holds old row c)
+            for (int li = tid; li < nloc; li += blockDim.x) {
+                const int i = rank + C * li;
+                const T f = (i == pi && pi != c) ? tmp[c] : M[(size_t)li * L + c];
+                fcol[li] = i == c ? t_zero(T()) : t_mul(f, pinv);
             }
-            // (e) eliminate column c from every other own row: M(i,:) -= M(i,c) prow,
-            // then M(i,c) = -M(i,c) pinv (the multipliers, read first)
-            for (int li = tid; li < nloc; li += blockDim.x) fcol[li] = M[(size_t)li * L + c];
             __syncthreads();
-            for (int e = tid; e < nloc * L; e += blockDim.x) {
-                const int li = e / L, col = e % L;
-                if (rank + C * li == c || col == c) continue;
-                T& m = M[(size_t)li * L + col];
-                m = t_fma(t_neg(fcol[li]), prow[col], m);
+            // (e) rows by warp, columns by lane: the pivot row scaled into slot c;
+            // every other row: M(i,:) -= f' prow, M(i,c) = -f'
+            for (int li = warp; li < nloc; li += nwarps) {
+                const int i = rank + C * li;
+                T* row = M + (size_t)li * L;
+                if (i == c) {
+                    for (int col = lane; col < L; col += 32) row[col] = col == c ? pinv : t_mul(prow[col], pinv);
+                } else {
+                    const T* src = (i == pi && pi != c) ? tmp : row;
+                    const T f = fcol[li];
+                    for (int col = lane; col < L; col += 32)
+                        row[col] = col == c ? t_neg(f) : t_fma(t_neg(f), prow[col], src[col]);
+                }
             }
-            for (int li = tid; li < nloc; li += blockDim.x)
-                if (rank + C * li != c) M[(size_t)li * L + c] = t_mul(t_neg(fcol[li]), pinv);
             __syncthreads();
         }
         if (!ok) break;
@@ -1000,7 +1005,7 @@ static int rhi_cluster_size(int ell) { return ell >= 64 ? 8 : (ell >= 16 ? 4 : 1
 template <typename T>
 static size_t rhi_smem(int ell, int C) {
     int nmax = (ell + C - 1) / C;
-    return (size_t)nmax * ell * sizeof(T) + 2 * (size_t)ell * sizeof(T) + (size_t)nmax * sizeof(T) +
+    return (size_t)nmax * ell * sizeof(T) + 6 * (size_t)ell * sizeof(T) + (size_t)nmax * sizeof(T) +
            (size_t)ell * sizeof(int) + 16;
 }
 
