@@ -381,7 +381,9 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
             // late steps of the mixed schedule: the epilogue in two-float
             // arithmetic on the rings
             const dfc scr = dfc_of2(coef[0]), c1d = dfc_of2(c1);
-            df ax(0), ay(0);
+            // one accumulator per spin component: four short dependency chains
+            // of two-float additions instead of one of twelve
+            df ax[4] = {df(0), df(0), df(0), df(0)}, ay[4] = {df(0), df(0), df(0), df(0)};
             const dfc* __restrict__ prv = side == 0 ? ring_q(o, rhs, jp) : ring_p(o, rhs, jp);
             dfc* __restrict__ nxt = side == 0 ? ring_q(o, rhs, j + 1) : ring_p(o, rhs, j + 1);
             const dfc* __restrict__ dotv = TS ? ring_p(o, rhs, j) : ring_q(o, rhs, j);
@@ -406,13 +408,14 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
                     nxt[idx] = rr;
                     if (side == 0) {
                         const dfc d = dotv[idx];
-                        ax += d.x * rr.x + d.y * rr.y;            // conj(d) r
-                        if (TS) ay += d.x * rr.y - d.y * rr.x;
+                        ax[sp] += d.x * rr.x + d.y * rr.y;        // conj(d) r
+                        if (TS) ay[sp] += d.x * rr.y - d.y * rr.x;
                         if (PASS2) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
                     }
                 }
             }
-            acc = make_double2(df_to_double(ax), df_to_double(ay));
+            acc = make_double2(df_to_double((ax[0] + ax[1]) + (ax[2] + ax[3])),
+                               df_to_double((ay[0] + ay[1]) + (ay[2] + ay[3])));
         } else {
         // the scale 1/n_j (1/m_j) in the stencil's precision
         T scr;

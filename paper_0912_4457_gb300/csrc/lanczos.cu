@@ -201,35 +201,43 @@ __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_
     const dfc* __restrict__ pj = TS ? ring_p(o, rhs, j) : nullptr;
     dfc* __restrict__ l = TS ? ring_p(o, rhs, j + 1) : nullptr;
     const size_t vb = (size_t)rhs * o.N;
-    df ax(0), ay(0);
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
-        const dfc q = qj[i];
-        dfc rr = r[i];
-        // r <- r - c3 q, l <- l - c4 p
-        if (TS) {
-            rr.x = rr.x - (c3.x * q.x - c3.y * q.y);
-            rr.y = rr.y - (c3.x * q.y + c3.y * q.x);
-        } else {
-            rr.x = rr.x - c3.x * q.x;
-            rr.y = rr.y - c3.x * q.y;
-        }
-        r[i] = rr;
-        rq[i] = double2_of(rr);
-        if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(rr.x.hi, rr.y.hi);
-        if (TS) {
-            const dfc pv = pj[i];
-            dfc ll = l[i];
-            ll.x = ll.x - (c4.x * pv.x - c4.y * pv.y);
-            ll.y = ll.y - (c4.x * pv.y + c4.y * pv.x);
-            l[i] = ll;
-            if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(ll.x.hi, ll.y.hi);
-            ax += rr.x * ll.x + rr.y * ll.y;   // conj(r) l
-            ay += rr.x * ll.y - rr.y * ll.x;
-        } else {
-            ax += rr.x * rr.x + rr.y * rr.y;
+    // two elements per iteration with separate accumulators: independent
+    // loads and two-float dependency chains in flight
+    df ax[2] = {df(0), df(0)}, ay[2] = {df(0), df(0)};
+    const long stride = (long)o.nblk * blockDim.x;
+    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < o.N; i0 += 2 * stride) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long i = i0 + u * stride;
+            if (i >= o.N) break;
+            const dfc q = qj[i];
+            dfc rr = r[i];
+            // r <- r - c3 q, l <- l - c4 p
+            if (TS) {
+                rr.x = rr.x - (c3.x * q.x - c3.y * q.y);
+                rr.y = rr.y - (c3.x * q.y + c3.y * q.x);
+            } else {
+                rr.x = rr.x - c3.x * q.x;
+                rr.y = rr.y - c3.x * q.y;
+            }
+            r[i] = rr;
+            rq[i] = double2_of(rr);
+            if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(rr.x.hi, rr.y.hi);
+            if (TS) {
+                const dfc pv = pj[i];
+                dfc ll = l[i];
+                ll.x = ll.x - (c4.x * pv.x - c4.y * pv.y);
+                ll.y = ll.y - (c4.x * pv.y + c4.y * pv.x);
+                l[i] = ll;
+                if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(ll.x.hi, ll.y.hi);
+                ax[u] += rr.x * ll.x + rr.y * ll.y;   // conj(r) l
+                ay[u] += rr.x * ll.y - rr.y * ll.x;
+            } else {
+                ax[u] += rr.x * rr.x + rr.y * rr.y;
+            }
         }
     }
-    step2_finish<TS>(o, rhs, j, mk(df_to_double(ax), df_to_double(ay)), sh);
+    step2_finish<TS>(o, rhs, j, mk(df_to_double(ax[0] + ax[1]), df_to_double(ay[0] + ay[1])), sh);
 }
 
 // c'_j = |x| c_j / n_j: the lift coefficients on the unnormalised basis
