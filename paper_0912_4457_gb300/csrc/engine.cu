@@ -178,6 +178,7 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     L.kused = (int*)take(sizeof(int) * n_rhs);
     in.status = o.status;
     in.timeout = (int*)take(sizeof(int));
+    in.df_inner = mixed ? 1 : 0;
     L.total = off;
     return L;
 }

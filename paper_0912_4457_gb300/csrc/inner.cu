@@ -66,6 +66,72 @@ __device__ __forceinline__ bool t_iszero(double2 a) { return a.x == 0.0 && a.y =
 __device__ __forceinline__ double2 t_dotc(double a, double b) { return mk(a * b, 0.0); }
 __device__ __forceinline__ double2 t_dotc(double2 a, double2 b) { return cmulc(a, b); }
 
+// ---- the same on T = df (real) or dfc (complex): two-float arithmetic on the
+// FP32 pipe, for the inner part of the mixed schedule ---------------------------
+__device__ __forceinline__ df t_zero(df) { return df(0); }
+__device__ __forceinline__ dfc t_zero(dfc) { dfc r; r.x = df(0); r.y = df(0); return r; }
+__device__ __forceinline__ df t_from(double2 a, df) { return df_from_double(a.x); }
+__device__ __forceinline__ dfc t_from(double2 a, dfc) { dfc r; r.x = df_from_double(a.x); r.y = df_from_double(a.y); return r; }
+__device__ __forceinline__ double2 t_to2(df a) { return mk(df_to_double(a), 0.0); }
+__device__ __forceinline__ double2 t_to2(dfc a) { return mk(df_to_double(a.x), df_to_double(a.y)); }
+__device__ __forceinline__ df t_conj(df a) { return a; }
+__device__ __forceinline__ dfc t_conj(dfc a) { dfc r; r.x = a.x; r.y = -a.y; return r; }
+__device__ __forceinline__ df t_mul(df a, df b) { return a * b; }
+__device__ __forceinline__ dfc t_mul(dfc a, dfc b) {
+    dfc r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+__device__ __forceinline__ df t_add(df a, df b) { return a + b; }
+__device__ __forceinline__ dfc t_add(dfc a, dfc b) { dfc r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+__device__ __forceinline__ df t_sub(df a, df b) { return a - b; }
+__device__ __forceinline__ dfc t_sub(dfc a, dfc b) { dfc r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// scaling by -1 and 1/2 is exact; other factors go through a two-float product
+__device__ __forceinline__ df t_scale(df a, double s) {
+    if (s == -1.0) return -a;
+    if (s == 0.5) return df(a.hi * 0.5f, a.lo * 0.5f);
+    return a * df_from_double(s);
+}
+__device__ __forceinline__ dfc t_scale(dfc a, double s) { dfc r; r.x = t_scale(a.x, s); r.y = t_scale(a.y, s); return r; }
+__device__ __forceinline__ df t_neg(df a) { return -a; }
+__device__ __forceinline__ dfc t_neg(dfc a) { dfc r; r.x = -a.x; r.y = -a.y; return r; }
+// 1/a: the FP32 reciprocal refined by one Newton step in two-float arithmetic
+__device__ __forceinline__ df t_inv(df a) {
+    const df y0(__frcp_rn(a.hi), 0.0f);
+    const df e = df(1) - a * y0;
+    return y0 + y0 * e;
+}
+__device__ __forceinline__ dfc t_inv(dfc a) {
+    const df ninv = t_inv(a.x * a.x + a.y * a.y);
+    dfc r;
+    r.x = a.x * ninv;
+    r.y = -(a.y * ninv);
+    return r;
+}
+// pivot magnitudes (gttrf's choice only): from the high parts
+__device__ __forceinline__ double t_abs1(df a) { return fabsf(a.hi); }
+__device__ __forceinline__ double t_abs1(dfc a) { return fabsf(a.x.hi) + fabsf(a.y.hi); }
+__device__ __forceinline__ double t_norm2(df a) { return df_to_double(a * a); }
+__device__ __forceinline__ double t_norm2(dfc a) { return df_to_double(a.x * a.x + a.y * a.y); }
+__device__ __forceinline__ bool t_iszero(df a) { return a.hi == 0.0f && a.lo == 0.0f; }
+__device__ __forceinline__ bool t_iszero(dfc a) { return t_iszero(a.x) && t_iszero(a.y); }
+__device__ __forceinline__ double2 t_dotc(df a, df b) { return mk(df_to_double(a * b), 0.0); }
+__device__ __forceinline__ double2 t_dotc(dfc a, dfc b) {
+    return mk(df_to_double(a.x * b.x + a.y * b.y), df_to_double(a.x * b.y - a.y * b.x));
+}
+template <typename T> struct IsDF { static constexpr bool value = false; };
+template <> struct IsDF<df> { static constexpr bool value = true; };
+template <> struct IsDF<dfc> { static constexpr bool value = true; };
+// two-float partial sums of conj(a) b and |a|^2, converted once per thread
+__device__ __forceinline__ void dotc_acc(df a, df b, df& sx, df&) { sx += a * b; }
+__device__ __forceinline__ void dotc_acc(dfc a, dfc b, df& sx, df& sy) {
+    sx += a.x * b.x + a.y * b.y;
+    sy += a.x * b.y - a.y * b.x;
+}
+__device__ __forceinline__ df norm2_df(df a) { return a * a; }
+__device__ __forceinline__ df norm2_df(dfc a) { return a.x * a.x + a.y * a.y; }
+
 // Tridiagonal LU with partial pivoting, LAPACK gttrf semantics (row i and
 // i+1 are interchanged when |d_i| < |dl_i|, |.| = |re| + |im| for complex).
 // On return dl holds the multipliers, d, du, du2 the rows of U, ipiv the
@@ -105,20 +171,21 @@ __device__ int gttrf(int n, T* dl, T* d, T* du, T* du2, int* ipiv, T* dinv) {
 }
 
 // y = p * H x (dagger: p * H^dagger x) for the outer tridiagonal, in the
-// summation order (diag, sub, super) -- all threads of the block.
+// summation order (diag, sub, super) -- all threads of the block.  The
+// diagonals come as T arrays (converted once per kernel).
 template <typename T>
-__device__ void band_mv(int n, double p, const double2* al, const double2* be, const double2* ga,
+__device__ void band_mv(int n, double p, const T* al, const T* be, const T* ga,
                         const T* x, T* y, bool dagger) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        T dg = t_from(al[i], T());
+        T dg = al[i];
         if (dagger) dg = t_conj(dg);
         T acc = t_mul(dg, x[i]);
         if (i > 0) {
-            T sub = dagger ? t_conj(t_from(ga[i - 1], T())) : t_from(be[i - 1], T());
+            T sub = dagger ? t_conj(ga[i - 1]) : be[i - 1];
             acc = t_add(acc, t_mul(sub, x[i - 1]));
         }
         if (i < n - 1) {
-            T sup = dagger ? t_conj(t_from(be[i], T())) : t_from(ga[i], T());
+            T sup = dagger ? t_conj(be[i]) : ga[i];
             acc = t_add(acc, t_mul(sup, x[i + 1]));
         }
         y[i] = t_scale(acc, p);
@@ -129,16 +196,20 @@ __device__ void band_mv(int n, double p, const double2* al, const double2* be, c
 template <typename T>
 __device__ double2 bdot(int n, const T* a, const T* b, double2* sh) {
     double2 acc = mk(0.0, 0.0);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cadd(acc, t_dotc(a[i], b[i]));
+    if constexpr (IsDF<T>::value) {
+        df sx(0), sy(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dotc_acc(a[i], b[i], sx, sy);
+        acc = mk(df_to_double(sx), df_to_double(sy));
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cadd(acc, t_dotc(a[i], b[i]));
+    }
     return block_sum(acc, sh);
 }
 
 // a <- a - (u^dag a) u, u of unit norm (all threads of the block)
 template <typename T>
 __device__ void project_out(int n, const T* u, T* a, double2* sh) {
-    double2 d = make_double2(0.0, 0.0);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) d = cadd(d, t_dotc(u[i], a[i]));
-    d = block_sum(d, sh);
+    double2 d = bdot<T>(n, u, a, sh);
     const T dc = t_from(d, T());
     for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = t_sub(a[i], t_mul(dc, u[i]));
     __syncthreads();
@@ -151,7 +222,13 @@ constexpr double kPResidTol = 0.1;
 template <typename T>
 __device__ double bnorm(int n, const T* a, double* sh) {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += t_norm2(a[i]);
+    if constexpr (IsDF<T>::value) {
+        df sx(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sx += norm2_df(a[i]);
+        acc = df_to_double(sx);
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) acc += t_norm2(a[i]);
+    }
     return sqrt(block_sum(acc, sh));
 }
 
@@ -187,6 +264,14 @@ __device__ __forceinline__ double t_fma(double a, double b, double c) { return f
 __device__ __forceinline__ double2 t_fma(double2 a, double2 b, double2 c) {
     return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
+__device__ __forceinline__ df shup(df v, int o) { return df(__shfl_up_sync(kFull, v.hi, o), __shfl_up_sync(kFull, v.lo, o)); }
+__device__ __forceinline__ df shdn(df v, int o) { return df(__shfl_down_sync(kFull, v.hi, o), __shfl_down_sync(kFull, v.lo, o)); }
+__device__ __forceinline__ dfc shup(dfc v, int o) { dfc r; r.x = shup(v.x, o); r.y = shup(v.y, o); return r; }
+__device__ __forceinline__ dfc shdn(dfc v, int o) { dfc r; r.x = shdn(v.x, o); r.y = shdn(v.y, o); return r; }
+__device__ __forceinline__ df t_one(df) { return df(1); }
+__device__ __forceinline__ dfc t_one(dfc) { dfc r; r.x = df(1); r.y = df(0); return r; }
+__device__ __forceinline__ df t_fma(df a, df b, df c) { return a * b + c; }
+__device__ __forceinline__ dfc t_fma(dfc a, dfc b, dfc c) { return t_add(t_mul(a, b), c); }
 
 // The maps of a sweep split into a part that depends on the LU factors only
 // (a of s <- a s + c; M of X <- M X + v) and a part that depends on the
@@ -585,6 +670,15 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     int* ipiv = reinterpret_cast<int*>(t2 + k);
     T* W = reinterpret_cast<T*>(in.work + (size_t)rhs * inner_work_elems(k));
     T* tab = W + (size_t)kInnerWorkVecs * k;   // sweep tables of the current LU
+    T* alT = W;                                 // H_k's diagonals as T (W[0..3k) is free)
+    T* beT = W + (size_t)k;
+    T* gaT = W + 2 * (size_t)k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        alT[i] = t_from(al[i], T());
+        beT[i] = t_from(be[i], T());
+        gaT[i] = t_from(ga[i], T());
+    }
+    __syncthreads();
     T* x = W + 5 * (size_t)k;
     T* y = W + 6 * (size_t)k;
     T* vprev = W + 7 * (size_t)k;
@@ -618,7 +712,7 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         __syncthreads();
         double zmax = 0.0;
         for (int it = 0; it < 30; ++it) {
-            band_mv<T>(k, 1.0, al, be, ga, x, y, false);
+            band_mv<T>(k, 1.0, alT, beT, gaT, x, y, false);
             __syncthreads();
             zmax = bnorm<T>(k, y, sh1);
             const double inv = 1.0 / zmax;
@@ -705,8 +799,8 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
     // out_l = H'^dagger src_l: band products by the whole block, then the
     // (pH)^{-1} solve on warp 0 and the ((pH)^dagger)^{-1} solve on warp 1.
     auto apply_hp = [&](const T* src_r, T* out_r, const T* src_l, T* out_l) {
-        band_mv<T>(k, p, al, be, ga, src_r, out_r, false);
-        if (TS) band_mv<T>(k, p, al, be, ga, src_l, out_l, true);
+        band_mv<T>(k, p, alT, beT, gaT, src_r, out_r, false);
+        if (TS) band_mv<T>(k, p, alT, beT, gaT, src_l, out_l, true);
         __syncthreads();
         if (G.g == 0) {
             grp_L_fwd<T>(G, k, dl, ipiv, src_r, t1, tab, gagg);
@@ -980,9 +1074,14 @@ size_t inner_smem_bytes(int k, bool two_sided) {
 }
 
 void launch_inner_lanczos(const Inner& in, cudaStream_t st) {
-    size_t smem = inner_smem_bytes(in.k, in.two_sided);
-    if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, smem, st>>>(in);
-    else k_inner<double><<<in.n_rhs, 256, smem, st>>>(in);
+    size_t smem = inner_smem_bytes(in.k, in.two_sided);   // the same for the two-float types
+    if (in.df_inner) {
+        if (in.two_sided) k_inner<dfc><<<in.n_rhs, 256, smem, st>>>(in);
+        else k_inner<df><<<in.n_rhs, 256, smem, st>>>(in);
+    } else {
+        if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, smem, st>>>(in);
+        else k_inner<double><<<in.n_rhs, 256, smem, st>>>(in);
+    }
 }
 
 // Largest dynamic shared memory any RHi launch needs (l <= 256, complex, 8 CTAs).
@@ -993,6 +1092,10 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(k_inner<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)inner_smem_bytes(kMaxInnerK, false));
     cudaFuncSetAttribute(k_inner<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)inner_smem_bytes(kMaxInnerK, true));
+    cudaFuncSetAttribute(k_inner<df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)inner_smem_bytes(kMaxInnerK, false));
+    cudaFuncSetAttribute(k_inner<dfc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)inner_smem_bytes(kMaxInnerK, true));
     cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());
     cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());

@@ -157,6 +157,8 @@ struct Inner {
     double2* c;            // V_l s, [rhs][k]
     int* status;           // [rhs]
     int* timeout;          // device flag: a bounded wait ran out
+    int df_inner;          // 1: p estimate, LU, sweeps and inner Lanczos in two-float
+                           // arithmetic (the mixed schedule); 0: FP64
 };
 constexpr int kInnerWorkVecs = 16;
 // per RHS: kInnerWorkVecs vectors of length k, then the sweep tables of the LU
