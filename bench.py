@@ -52,6 +52,20 @@ DEFAULT_WORKLOAD = "8^4-mu0.3-12pt"
 STENCIL_DIMS = (16, 16, 16, 32)
 
 
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries
+    (a line 'traffic_bytes_per_launch <kernel>: <bytes>'), else None."""
+    import glob
+    import re
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                m = re.match(r"\s*traffic_bytes_per_launch\s+(\S+):\s*([0-9.eE+]+)", line)
+                if m and m.group(1) == kernel:
+                    return float(m.group(2))
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -449,20 +463,22 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
         tf = flops / (ms * 1e-3) / 1e12
         peak = 152 * 128 * (sm_mhz or 2070.0) * 1e6 / 9.0 / 1e12
         return {"kernel": "k_dslash_step1<df> (two-float stencil fused with step 1)", "bound": "alu",
-                "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "traffic": None,
+                "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                "traffic": profiled_traffic("k_dslash_step1<df>"),
                 "ms_per_launch": ms, "flops_per_launch": flops,
                 "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
     if dom == "step2":
         flops = (24 if two else 8) * N * n_rhs
         tf = flops / (ms * 1e-3) / 1e12
         return {"kernel": "k_step2", "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": tf / fp64_peak, "traffic": None, "ms_per_launch": ms,
+                "frac": tf / fp64_peak, "traffic": profiled_traffic("k_step2_df"), "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": (112 if two else 56) * N * n_rhs}
     if dom in ("dslash", "dslash64"):
         b = V * (288 + nv * (96 + 192)) + V * n_rhs * 2 * 192
         gbs = b / (ms * 1e-3) / 1e9
         return {"kernel": "k_dslash_step1", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "ms_per_launch": ms}
+                "unit": "GB/s", "frac": gbs / hbm, "traffic": profiled_traffic("k_dslash_step1<float>"),
+                "ms_per_launch": ms}
     if dom == "lift":
         b = n_rhs * w["k"] * N * 16
         gbs = b / (ms * 1e-3) / 1e9

@@ -157,8 +157,8 @@ typedef struct nk_launch {
 int nk_set_launch(nk_ctx* ctx, int n_rhs, unsigned flags, const nk_launch* shape);
 int nk_get_launch(nk_ctx* ctx, int n_rhs, unsigned flags, nk_launch* shape);
 /* Tunes the launch shape on a synthetic constant source: after 8 outer steps,
- * 20 repetitions of one outer step (fused stencil, then step 2, as in a
- * solve) are timed with CUDA events for each candidate -- the 3 x 2 stencil
+ * 50 repetitions of one outer step (fused stencil, then step 2, as in a
+ * solve; best of 3 rounds) are timed with CUDA events for each candidate -- the 3 x 2 stencil
  * shapes with the FP32 stencil (NK_MIXED) or the FP64 one; in NK_MIXED mode
  * the same shapes with the two-float stencil (early_threads, early_order);
  * then step2_blocks in {b/2, b, 2b, 4b, 8b} (b the default) with the fastest

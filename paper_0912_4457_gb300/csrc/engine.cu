@@ -687,12 +687,12 @@ int nk_get_launch(nk_ctx* c, int n_rhs, unsigned flags, nk_launch* l) {
 // synthetic source in `src` with launch shape lc, then the two kernels of
 // step kTuneWarm -- the fused stencil in precision `prec` (32, 48 or 64) and
 // step 2 -- are launched kTuneReps times in turn and timed with CUDA events
-// (the minimum over two rounds, per step).  Alternating the two keeps the
+// (the minimum over kTuneRounds rounds, per step).  Alternating the two keeps the
 // dependency between them that a solve has (timing one kernel alone lets
 // consecutive launches overlap and favours other shapes); repeating a step
 // recomputes it (step 2 subtracts once more), which leaves the timing
 // representative.
-constexpr int kTuneWarm = 8, kTuneReps = 20;
+constexpr int kTuneWarm = 8, kTuneReps = 50, kTuneRounds = 3;
 static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int prec, const nk_launch& lc,
                        cudaStream_t st, float* per_launch_ms) {
     const bool ts = c->mu != 0.0;
@@ -714,7 +714,7 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
     NK_CUDA(c, cudaEventCreate(&e0));
     NK_CUDA(c, cudaEventCreate(&e1));
     float best = 1e30f;
-    for (int round = 0; round < 2; ++round) {
+    for (int round = 0; round < kTuneRounds; ++round) {
         NK_CUDA(c, cudaEventRecord(e0, st));
         for (int r = 0; r < kTuneReps; ++r) {
             nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);

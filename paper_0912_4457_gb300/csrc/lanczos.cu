@@ -292,6 +292,37 @@ __global__ void __launch_bounds__(kThreads) k_lift(Outer o, const double2* __res
     yo[i] = acc;
 }
 
+// The same lift in two-float arithmetic for the mixed schedule: the
+// coefficients are converted once per block into shared memory, each basis
+// element on load, and the sum runs in two accumulators (even and odd j).
+__global__ void __launch_bounds__(kThreads) k_lift_df(Outer o, const double2* __restrict__ cp,
+                                                       const int* __restrict__ kused, double2* __restrict__ y) {
+    extern __shared__ dfc cs[];   // [kused]
+    const int rhs = blockIdx.y;
+    const int ku = kused[rhs];
+    const double2* cr = cp + (size_t)rhs * o.k;
+    for (int j = threadIdx.x; j < ku; j += blockDim.x) cs[j] = dfc_of(cr[j]);
+    __syncthreads();
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= o.N) return;
+    double2* yo = y + (size_t)rhs * o.N;
+    if (o.status[rhs] != kStatusOK) { yo[i] = mk(0.0, 0.0); return; }
+    const double2* Qr = o.Q + (size_t)rhs * o.qcols * o.N;
+    dfc acc[2];
+    acc[0].x = df(0); acc[0].y = df(0); acc[1] = acc[0];
+    for (int j = 0; j < ku; ++j) {
+        const dfc c = cs[j];
+        const dfc v = dfc_of(Qr[(size_t)j * o.N + i]);
+        dfc& a = acc[j & 1];
+        a.x += c.x * v.x - c.y * v.y;
+        a.y += c.x * v.y + c.y * v.x;
+    }
+    dfc t;
+    t.x = acc[0].x + acc[1].x;
+    t.y = acc[0].y + acc[1].y;
+    yo[i] = double2_of(t);
+}
+
 // double pass: zero the status of sources that are exactly zero
 __global__ void k_zero_bad(Outer o, double2* y) {
     const int rhs = blockIdx.y;
@@ -327,6 +358,7 @@ void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double
 void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y, cudaStream_t st) {
     dim3 grid((unsigned)((o.N + kThreads - 1) / kThreads), o.n_rhs);
     if (o.q_ring) k_zero_bad<<<grid, kThreads, 0, st>>>(o, y);
+    else if (o.qr) k_lift_df<<<grid, kThreads, sizeof(dfc) * (size_t)o.k, st>>>(o, cp, kused, y);
     else k_lift<<<grid, kThreads, 0, st>>>(o, cp, kused, y);
 }
 
