@@ -164,19 +164,19 @@ __device__ __forceinline__ void stencil_hops_df(dfc acc[4][3], const dfc* __rest
         else { wrap = c == 0; sn = wrap ? site + (L - 1) * stride : site - stride; ls = sn; }
         const df flip = (nu == 3 && g.antiperiodic && wrap) ? df(-1) : df(1);
         const df w = (nu == 3 ? (fwd ? wm_t : wp_t) : df(1)) * flip;
-        const df sgn = fwd ? df(-1) : df(1);
         const HopSpin hs = hop_spin(nu);
+        // the projection and the weights of the spatial hops are +-1: additions
+        // and subtractions, not two-float products (exact either way)
         dfc h0[3], h1[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const dfc p0 = in[(size_t)a * V + sn], p1 = in[(size_t)(3 + a) * V + sn];
             const dfc p2 = in[(size_t)(6 + a) * V + sn], p3 = in[(size_t)(9 + a) * V + sn];
-            const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, hs.q0);
-            const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, hs.q1);
-            h0[a].x = p0.x + sgn * c0.x; h0[a].y = p0.y + sgn * c0.y;
-            h1[a].x = p1.x + sgn * c1.x; h1[a].y = p1.y + sgn * c1.y;
+            const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, fwd ? hs.q0 + 2 : hs.q0);   // -c for the forward hop
+            const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, fwd ? hs.q1 + 2 : hs.q1);
+            h0[a].x = p0.x + c0.x; h0[a].y = p0.y + c0.y;
+            h1[a].x = p1.x + c1.x; h1[a].y = p1.y + c1.y;
         }
-        const df ws = w * sgn;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             dfc x0, x1;
@@ -189,12 +189,16 @@ __device__ __forceinline__ void stencil_hops_df(dfc acc[4][3], const dfc* __rest
                 x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
                 x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
             }
-            acc[0][a].x += w * x0.x; acc[0][a].y += w * x0.y;
-            acc[1][a].x += w * x1.x; acc[1][a].y += w * x1.y;
-            const dfc b0 = rot_q(hs.r0 == 1 ? x1 : x0, hs.r0q);
-            const dfc b1 = rot_q(hs.r1 == 1 ? x1 : x0, hs.r1q);
-            acc[2][a].x += ws * b0.x; acc[2][a].y += ws * b0.y;
-            acc[3][a].x += ws * b1.x; acc[3][a].y += ws * b1.y;
+            if (nu == 3) {   // temporal weights e^{+-mu} and the boundary sign
+                x0.x = w * x0.x; x0.y = w * x0.y;
+                x1.x = w * x1.x; x1.y = w * x1.y;
+            }
+            acc[0][a].x += x0.x; acc[0][a].y += x0.y;
+            acc[1][a].x += x1.x; acc[1][a].y += x1.y;
+            const dfc b0 = rot_q(hs.r0 == 1 ? x1 : x0, fwd ? hs.r0q + 2 : hs.r0q);   // times -1 forward
+            const dfc b1 = rot_q(hs.r1 == 1 ? x1 : x0, fwd ? hs.r1q + 2 : hs.r1q);
+            acc[2][a].x += b0.x; acc[2][a].y += b0.y;
+            acc[3][a].x += b1.x; acc[3][a].y += b1.y;
         }
     }
 }

@@ -691,7 +691,8 @@ int nk_get_launch(nk_ctx* c, int n_rhs, unsigned flags, nk_launch* l) {
 // dependency between them that a solve has (timing one kernel alone lets
 // consecutive launches overlap and favours other shapes); repeating a step
 // recomputes it (step 2 subtracts once more), which leaves the timing
-// representative.
+// representative.  Step 2 skips the copy for the next stencil there (the next
+// repetition's stencil must read q_j again), a small part of its traffic.
 constexpr int kTuneWarm = 8, kTuneReps = 50, kTuneRounds = 3;
 static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int prec, const nk_launch& lc,
                        cudaStream_t st, float* per_launch_ms) {
@@ -718,7 +719,9 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
         NK_CUDA(c, cudaEventRecord(e0, st));
         for (int r = 0; r < kTuneReps; ++r) {
             nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
-            nk::launch_outer_step2(Lw.o, kTuneWarm, copy_mode_for(mixed, j0, kTuneWarm + 1), mixed && prec == 32, st);
+            // no copy for the next stencil: the stencil of the next repetition
+            // must read q_j again, so that every repetition recomputes the same step
+            nk::launch_outer_step2(Lw.o, kTuneWarm, nk::kCopyNone, mixed && prec == 32, st);
         }
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());

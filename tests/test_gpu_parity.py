@@ -361,7 +361,9 @@ def test_double_pass_graph_and_determinism(c1):
     y4, _, _ = ctx.sign_apply(b, 256, 64, flags=NK_MIXED | NK_DOUBLE_PASS)
     assert np.array_equal(y1, y2)
     assert np.array_equal(y1, y3)
-    assert rel(y4, y1) < 1e-14
+    # the same basis; the single-pass lift of the mixed schedule sums in
+    # two-float (about 48-bit) arithmetic, the double pass in FP64
+    assert rel(y4, y1) < 1e-13
     ctx.close()
 
 
