@@ -448,6 +448,8 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
              FP64 output 192 B -- HBM;
       step2: 24 (8) FP64 flops per element -- FP64 ALU, 1.0 TFLOP/s measured
              DFMA rate;
+      step2_df: reads q_j, r, p_j, l and writes r, l (two-float rings), r in
+             FP64 and the FP32 copies: 128 (64) B per element -- HBM;
       lift: reads V_k once, 16 B x k per element -- HBM.
     """
     V = int(np.prod(w["dims"]))
@@ -467,11 +469,18 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
                 "traffic": profiled_traffic("k_dslash_step1<df>"),
                 "ms_per_launch": ms, "flops_per_launch": flops,
                 "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
+    if dom == "step2_df":
+        b = (128 if two else 64) * N * n_rhs
+        gbs = b / (ms * 1e-3) / 1e9
+        return {"kernel": "k_step2_df (step 2 of the FP32-stencil steps, two-float)", "bound": "hbm",
+                "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": profiled_traffic("k_step2_df"), "ms_per_launch": ms,
+                "algorithmic_bytes_per_launch": b}
     if dom == "step2":
         flops = (24 if two else 8) * N * n_rhs
         tf = flops / (ms * 1e-3) / 1e12
         return {"kernel": "k_step2", "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": tf / fp64_peak, "traffic": profiled_traffic("k_step2_df"), "ms_per_launch": ms,
+                "frac": tf / fp64_peak, "traffic": profiled_traffic("k_step2"), "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": (112 if two else 56) * N * n_rhs}
     if dom in ("dslash", "dslash64"):
         b = V * (288 + nv * (96 + 192)) + V * n_rhs * 2 * 192

@@ -69,13 +69,14 @@ extern "C" {
 #define NK_CLASS_DSLASH 0     /* FP32 Wilson stencil A v (and A^dagger w) fused with
                                  r = Av - c v_prev and the H(j,j) reduction */
 #define NK_CLASS_DSLASH_DF 1  /* the same with the two-float (about 48-bit) stencil */
-#define NK_CLASS_STEP2 2      /* r -= H(j,j) v, beta / delta, stencil input copies */
+#define NK_CLASS_STEP2 2      /* r -= H(j,j) v, beta / delta, stencil input copies (FP64) */
 #define NK_CLASS_DSLASH64 3   /* the same with the FP64 stencil */
 #define NK_CLASS_INNER 4    /* p estimate, LU of p H_k, inner Lanczos */
 #define NK_CLASS_RHI 5      /* Roberts-Higham iteration */
 #define NK_CLASS_LIFT 6     /* V_l s and |x| V_k c */
 #define NK_CLASS_OTHER 7    /* layout conversion, norms */
-#define NK_NCLASS 8
+#define NK_CLASS_STEP2_DF 8 /* step 2 of the FP32-stencil steps of NK_MIXED (two-float) */
+#define NK_NCLASS 9
 
 typedef struct nk_ctx nk_ctx;
 

@@ -285,10 +285,12 @@ void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int 
         const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
         const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
         L.run(cls, 1, [&] { nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
-        if (j < o.k - 1)
-            L.run(NK_CLASS_STEP2, 1, [&] {
-                nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), mixed && j >= j0, st);
+        if (j < o.k - 1) {
+            const bool ring = mixed && j >= j0;
+            L.run(ring ? NK_CLASS_STEP2_DF : NK_CLASS_STEP2, 1, [&] {
+                nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), ring, st);
             });
+        }
     }
 }
 

@@ -33,8 +33,8 @@ NK_DOUBLE_PASS = 0x2
 NK_NO_GRAPH = 0x10
 NK_PROFILE = 0x20
 NK_MAX_RHS = 12
-NK_NCLASS = 8
-CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other"]
+NK_NCLASS = 9
+CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other", "step2_df"]
 
 ERROR_NAMES = {
     NK_EINVAL: "NK_EINVAL", NK_ENOMEM: "NK_ENOMEM", NK_EBREAKDOWN: "NK_EBREAKDOWN",
