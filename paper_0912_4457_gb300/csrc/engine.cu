@@ -269,9 +269,9 @@ int copy_mode_for(bool mixed, int j0, int j) {
     return !mixed ? nk::kCopyNone : (j < j0 ? nk::kCopyDF : nk::kCopy32);
 }
 
-void enqueue_outer_init(const nk::Outer& o, bool mixed, int j0, Launcher& L) {
+void enqueue_outer_init(const nk::Outer& o, bool mixed, int j0, Launcher& L, bool keep_status = false) {
     cudaStream_t st = L.st;
-    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_mode_for(mixed, j0, 0), st); });
+    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_mode_for(mixed, j0, 0), st, keep_status); });
 }
 
 // steps j in [j_begin, j_end); step 2 runs for every step but the last of the
@@ -294,8 +294,9 @@ void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int 
     }
 }
 
-void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& L, int steps = -1) {
-    enqueue_outer_init(o, mixed, j0, L);
+void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& L, int steps = -1,
+                   bool keep_status = false) {
+    enqueue_outer_init(o, mixed, j0, L, keep_status);
     enqueue_outer_steps(c, o, mixed, j0, 0, steps < 0 ? o.k : steps, L);
 }
 
@@ -336,7 +337,7 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
         o.cp = Lw.cp;
         cudaMemsetAsync(Lw.y_soa, 0, sizeof(double2) * (size_t)c->N * n_rhs, st);
         enqueue_load_sources(c, o, b_dev, n_rhs, L);
-        enqueue_outer(c, o, mixed, j0, L);
+        enqueue_outer(c, o, mixed, j0, L, -1, true);
     }
     L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, Lw.cp, Lw.kused, Lw.y_soa, st); });
     L.run(NK_CLASS_OTHER, 1, [&] {

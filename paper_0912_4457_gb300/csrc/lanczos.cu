@@ -33,7 +33,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) k_norm(Outer o) {
+__global__ void __launch_bounds__(kThreads) k_norm(Outer o, int keep_status) {
     __shared__ double2 sh[33];
     const int rhs = blockIdx.y;
     const double2* x = outer_q(o, rhs, 0);
@@ -48,7 +48,11 @@ __global__ void __launch_bounds__(kThreads) k_norm(Outer o) {
         if (threadIdx.x == 0) {
             double nrm = sqrt(tot.x);
             o.xnorm[rhs] = nrm;
-            o.status[rhs] = nrm > 0.0 ? kStatusOK : kStatusZeroSource;
+            // the second pass of NK_DOUBLE_PASS keeps a failure of the first
+            // (breakdown, RHi): that source is not recomputed
+            const int prev = o.status[rhs];
+            const bool keep = keep_status && prev != kStatusOK && prev != kStatusZeroSource;
+            o.status[rhs] = keep ? prev : (nrm > 0.0 ? kStatusOK : kStatusZeroSource);
             o.counters[rhs] = 0u;
         }
     }
@@ -333,9 +337,9 @@ __global__ void k_zero_bad(Outer o, double2* y) {
 
 }  // namespace
 
-void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st) {
+void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep_status) {
     dim3 grid(o.nblk, o.n_rhs);
-    k_norm<<<grid, kThreads, 0, st>>>(o);
+    k_norm<<<grid, kThreads, 0, st>>>(o, keep_status ? 1 : 0);
     k_init<<<grid, kThreads, 0, st>>>(o, copy_mode);
 }
 

@@ -112,7 +112,8 @@ constexpr int kStatusInnerBreakdown = 6;  // inner (two-sided) Lanczos on H_k': 
 
 // Copy modes for the next stencil's input: none, FP32, two-float.
 constexpr int kCopyNone = 0, kCopy32 = 1, kCopyDF = 2;
-void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st);
+// keep_status: the second pass of NK_DOUBLE_PASS (a failure of the first pass stays)
+void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep_status = false);
 // Fused stencil + first half of step j (dslash.cu); precision 32 (FP32),
 // 48 (two-float) or 64 (FP64).
 void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
