@@ -140,13 +140,16 @@ int nk_set_adapt_start(nk_ctx* ctx, int k_first);
  *  step2_blocks     CTAs per RHS of the step-2 and norm kernels (grid-stride),
  *                   1..4096; also the number of partial sums of their
  *                   deterministic reductions;
- *  early_threads, early_order
+ *  stencil_split    threads per site of the fused stencil: 1, or 3 (one per
+ *                   colour: each projects the neighbour spinors and forms one
+ *                   colour row, with a third of the accumulators);
+ *  early_threads, early_order, early_split
  *                   the stencil shape of the two-float steps before j0 in
  *                   NK_MIXED mode (unused in NK_FP64 mode).
  * A shape belongs to (n_rhs, sidedness of the current mu (mu != 0), the
  * NK_MIXED bit of flags).  Different shapes sum in different orders, so
  * results differ at rounding level; one shape is bitwise reproducible.
- * Unset shapes use 128 / 0 / min(ceil(12 V / 2048), 608 / n_rhs) / 128 / 0.
+ * Unset shapes use 128 / 0 / min(ceil(12 V / 2048), 608 / n_rhs) / 128 / 0 / 1 / 1.
  */
 typedef struct nk_launch {
     int stencil_threads;
@@ -154,20 +157,22 @@ typedef struct nk_launch {
     int step2_blocks;
     int early_threads;
     int early_order;
+    int stencil_split;
+    int early_split;
 } nk_launch;
 int nk_set_launch(nk_ctx* ctx, int n_rhs, unsigned flags, const nk_launch* shape);
 int nk_get_launch(nk_ctx* ctx, int n_rhs, unsigned flags, nk_launch* shape);
 /* Tunes the launch shape on a synthetic constant source: after 8 outer steps,
  * 50 repetitions of one outer step (fused stencil, then step 2, as in a
- * solve; best of 3 rounds) are timed with CUDA events for each candidate -- the 3 x 2 stencil
- * shapes with the FP32 stencil (NK_MIXED) or the FP64 one; in NK_MIXED mode
+ * solve; best of 3 rounds) are timed with CUDA events for each candidate -- the 3 x 2 x 2
+ * stencil shapes with the FP32 stencil (NK_MIXED) or the FP64 one; in NK_MIXED mode
  * the same shapes with the two-float stencil (early_threads, early_order);
  * then step2_blocks in {b/2, b, 2b, 4b, 8b} (b the default) with the fastest
  * late stencil shape.  Keeps the fastest of each (written to *best, and the
  * time of one late outer step to *ms_per_step; both nullable).
  * cache_path (nullable): a text file of lines
  *   nk_launch Lx Ly Lz Lt n_rhs two_sided mixed threads order blocks
- *             early_threads early_order ms_per_step
+ *             early_threads early_order split early_split ms_per_step
  * read first (a matching line is used without timing) and appended to after
  * timing.  Blocks. */
 int nk_autotune(nk_ctx* ctx, int n_rhs, unsigned flags, const char* cache_path, nk_launch* best,

@@ -114,6 +114,66 @@ __device__ __forceinline__ void dir(typename C2<R>::T acc[4][3], const typename 
     hop_regs<NU, true, R>(acc, p, u, R(-1), wminus * ff);
 }
 
+// ---- colour split: one thread per (site, colour a) -----------------------------
+// The same hop restricted to row a of M psi: the thread projects the whole
+// neighbour spinor (all three colours) but forms and accumulates only the a-th
+// row, so it holds a quarter of the accumulators; three threads share a site.
+template <int NU, bool DAG, typename R>
+__device__ __forceinline__ void hop_regs_a(typename C2<R>::T acc[4], const typename C2<R>::T psi[4][3],
+                                           const typename C2<R>::T urow[3], R s, R w) {
+    typedef typename C2<R>::T T;
+    T h0[3], h1[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        T c0, c1;
+        if (NU == 0) { c0 = mul_mi(psi[3][b]); c1 = mul_mi(psi[2][b]); }
+        else if (NU == 1) { c0 = neg(psi[3][b]); c1 = psi[2][b]; }
+        else if (NU == 2) { c0 = mul_mi(psi[2][b]); c1 = mul_i(psi[3][b]); }
+        else { c0 = psi[2][b]; c1 = psi[3][b]; }
+        h0[b].x = psi[0][b].x + s * c0.x; h0[b].y = psi[0][b].y + s * c0.y;
+        h1[b].x = psi[1][b].x + s * c1.x; h1[b].y = psi[1][b].y + s * c1.y;
+    }
+    const R ws = w * s;
+    T x0, x1;
+    x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const T e = urow[b];
+        R ey = DAG ? -e.y : e.y;
+        x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
+        x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
+    }
+    acc[0].x += w * x0.x; acc[0].y += w * x0.y;
+    acc[1].x += w * x1.x; acc[1].y += w * x1.y;
+    T b0, b1;
+    if (NU == 0) { b0 = mul_i(x1); b1 = mul_i(x0); }
+    else if (NU == 1) { b0 = x1; b1 = neg(x0); }
+    else if (NU == 2) { b0 = mul_i(x0); b1 = mul_mi(x1); }
+    else { b0 = x0; b1 = x1; }
+    acc[2].x += ws * b0.x; acc[2].y += ws * b0.y;
+    acc[3].x += ws * b1.x; acc[3].y += ws * b1.y;
+}
+
+template <int NU, typename R>
+__device__ __forceinline__ void dir_a(typename C2<R>::T acc[4], const typename C2<R>::T* __restrict__ U,
+                                      const typename C2<R>::T* __restrict__ in, const Geom& g, int site, int a,
+                                      int coord, int L, int stride, R wplus, R wminus) {
+    typedef typename C2<R>::T T;
+    const int sb = coord == 0 ? site + (L - 1) * stride : site - stride;
+    const R fb = (NU == 3 && g.antiperiodic && coord == 0) ? R(-1) : R(1);
+    const int sf = coord == L - 1 ? site - (L - 1) * stride : site + stride;
+    const R ff = (NU == 3 && g.antiperiodic && coord == L - 1) ? R(-1) : R(1);
+    T urow[3], p[4][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) urow[b] = U[(size_t)(NU * 9 + 3 * a + b) * g.V + sb];   // row a of U
+    load_spinor<R>(in, g.V, sb, p);
+    hop_regs_a<NU, false, R>(acc, p, urow, R(1), wplus * fb);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) urow[b] = U[(size_t)(NU * 9 + 3 * b + a) * g.V + site]; // column a: row a of U^dagger
+    load_spinor<R>(in, g.V, sf, p);
+    hop_regs_a<NU, true, R>(acc, p, urow, R(-1), wminus * ff);
+}
+
 // ---- the two-float stencil: one copy of the hop body --------------------------
 // Two-float arithmetic turns every flop into 7-11 FP32 instructions; the
 // eight hops unrolled with compile-time gamma structure then overflow the
@@ -203,6 +263,62 @@ __device__ __forceinline__ void stencil_hops_df(dfc acc[4][3], const dfc* __rest
     }
 }
 
+__device__ __forceinline__ void stencil_hops_df_a(dfc acc[4], const dfc* __restrict__ U, const dfc* __restrict__ in,
+                                                  const Geom& g, int site, int a, const int coord[4], df wp_t,
+                                                  df wm_t) {
+    const int V = g.V;
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+        const int nu = h >> 1;
+        const bool fwd = (h & 1) != 0;
+        int L, stride;
+        switch (nu) {
+            case 0: L = g.Lx; stride = 1; break;
+            case 1: L = g.Ly; stride = g.Lx; break;
+            case 2: L = g.Lz; stride = g.Lx * g.Ly; break;
+            default: L = g.Lt; stride = g.Lx * g.Ly * g.Lz; break;
+        }
+        const int c = coord[nu];
+        int sn, ls;
+        bool wrap;
+        if (fwd) { wrap = c == L - 1; sn = wrap ? site - (L - 1) * stride : site + stride; ls = site; }
+        else { wrap = c == 0; sn = wrap ? site + (L - 1) * stride : site - stride; ls = sn; }
+        const df flip = (nu == 3 && g.antiperiodic && wrap) ? df(-1) : df(1);
+        const df w = (nu == 3 ? (fwd ? wm_t : wp_t) : df(1)) * flip;
+        const HopSpin hs = hop_spin(nu);
+        dfc h0[3], h1[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const dfc p0 = in[(size_t)b * V + sn], p1 = in[(size_t)(3 + b) * V + sn];
+            const dfc p2 = in[(size_t)(6 + b) * V + sn], p3 = in[(size_t)(9 + b) * V + sn];
+            const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, fwd ? hs.q0 + 2 : hs.q0);
+            const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, fwd ? hs.q1 + 2 : hs.q1);
+            h0[b].x = p0.x + c0.x; h0[b].y = p0.y + c0.y;
+            h1[b].x = p1.x + c1.x; h1[b].y = p1.y + c1.y;
+        }
+        dfc x0, x1;
+        x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int e_idx = fwd ? nu * 9 + 3 * b + a : nu * 9 + 3 * a + b;
+            const dfc e = U[(size_t)e_idx * V + ls];
+            const df ey = fwd ? -e.y : e.y;
+            x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
+            x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
+        }
+        if (nu == 3) {
+            x0.x = w * x0.x; x0.y = w * x0.y;
+            x1.x = w * x1.x; x1.y = w * x1.y;
+        }
+        acc[0].x += x0.x; acc[0].y += x0.y;
+        acc[1].x += x1.x; acc[1].y += x1.y;
+        const dfc b0 = rot_q(hs.r0 == 1 ? x1 : x0, fwd ? hs.r0q + 2 : hs.r0q);
+        const dfc b1 = rot_q(hs.r1 == 1 ? x1 : x0, fwd ? hs.r1q + 2 : hs.r1q);
+        acc[2].x += b0.x; acc[2].y += b0.y;
+        acc[3].x += b1.x; acc[3].y += b1.y;
+    }
+}
+
 // precision-generic conversions (float via the integer pipe, see nk_common.cuh)
 __device__ __forceinline__ double to_double(float a) { return f2d_int(a); }
 __device__ __forceinline__ double to_double(double a) { return a; }
@@ -283,6 +399,41 @@ __device__ __forceinline__ void stencil_site(const typename C2<R>::T* __restrict
     }
 }
 
+// The colour-a components of gamma5 (psi - kappa * hops)(site): out[sp] for colour a.
+template <typename R>
+__device__ __forceinline__ void stencil_site_a(const typename C2<R>::T* __restrict__ U,
+                                               const typename C2<R>::T* __restrict__ in, const Geom& g,
+                                               int site, int a, int dag, R kappa, R emu, R emu_inv,
+                                               typename C2<R>::T out[4]) {
+    typedef typename C2<R>::T T;
+    const R wp_t = dag ? emu_inv : emu;
+    const R wm_t = dag ? emu : emu_inv;
+    int x = site % g.Lx;
+    int r = site / g.Lx;
+    int y = r % g.Ly; r /= g.Ly;
+    int z = r % g.Lz;
+    int t = r / g.Lz;
+    T acc[4];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) { acc[sp].x = 0; acc[sp].y = 0; }
+    if constexpr (std::is_same<R, df>::value) {
+        const int coord[4] = {x, y, z, t};
+        stencil_hops_df_a(acc, U, in, g, site, a, coord, wp_t, wm_t);
+    } else {
+        dir_a<0, R>(acc, U, in, g, site, a, x, g.Lx, 1, R(1), R(1));
+        dir_a<1, R>(acc, U, in, g, site, a, y, g.Ly, g.Lx, R(1), R(1));
+        dir_a<2, R>(acc, U, in, g, site, a, z, g.Lz, g.Lx * g.Ly, R(1), R(1));
+        dir_a<3, R>(acc, U, in, g, site, a, t, g.Lt, g.Lx * g.Ly * g.Lz, wp_t, wm_t);
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const R sg = sp < 2 ? R(1) : R(-1);
+        const T p = in[(size_t)(3 * sp + a) * g.V + site];
+        out[sp].x = sg * (p.x - kappa * acc[sp].x);
+        out[sp].y = sg * (p.y - kappa * acc[sp].y);
+    }
+}
+
 // One thread per (site, vector). Vectors [0, n0) come from set 0, [n0, n0+n1)
 // from set 1; set s applies A (dag = 0) or A^dagger (dag = 1).
 template <typename R>
@@ -343,8 +494,9 @@ template <typename R> struct StencilMinBlocks { static constexpr int value = 1; 
 template <> struct StencilMinBlocks<df> { static constexpr int value = 2; };
 template <> struct StencilMinBlocks<float> { static constexpr int value = 3; };
 
-template <typename R, bool TS, bool PASS2>
-__global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value) k_dslash_step1(
+// CS: threads per site (1, or 3 with one colour each; blockDim = (sites, CS)).
+template <typename R, bool TS, bool PASS2, int CS>
+__global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinBlocks<R>::value : 1) k_dslash_step1(
     const typename C2<R>::T* __restrict__ U, Geom g, Outer o, int j, R kappa, R emu, R emu_inv,
     const typename C2<R>::T* __restrict__ qin, long qin_stride, const typename C2<R>::T* __restrict__ pin,
     long pin_stride) {
@@ -360,7 +512,7 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
     if (o.status[rhs] != kStatusOK) return;
     if (side == 1 && j == o.k - 1) return;   // the last step needs no left vector
     const size_t hb = (size_t)rhs * o.k;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
         const double2 zero = make_double2(0.0, 0.0);
         if (side == 0) {
             coef[0] = cinv(scale_n(o, rhs, j));
@@ -377,8 +529,23 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
     double2 acc = make_double2(0.0, 0.0);
     if (site < g.V) {
         const T* __restrict__ in = side == 0 ? qin + (size_t)rhs * qin_stride : pin + (size_t)rhs * pin_stride;
-        T out[4][3];
-        stencil_site<R>(U, in, g, site, side, kappa, emu, emu_inv, out);
+        // the stencil output of this thread's components, handed to epi(sp, a, value)
+        auto for_each_out = [&](auto&& epi) {
+            if constexpr (CS == 1) {
+                T out[4][3];
+                stencil_site<R>(U, in, g, site, side, kappa, emu, emu_inv, out);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) epi(sp, a, out[sp][a]);
+            } else {
+                const int a = threadIdx.y;
+                T out[4];
+                stencil_site_a<R>(U, in, g, site, a, side, kappa, emu, emu_inv, out);
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) epi(sp, a, out[sp]);
+            }
+        };
         const double2 c1 = coef[1];   // zero at j = 0 (the previous vector is then any valid one)
         const int jp = j > 0 ? j - 1 : j;
         if constexpr (std::is_same<R, float>::value) {
@@ -394,50 +561,42 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
             double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
             const double2 cpj = PASS2 ? o.cp[hb + j] : make_double2(0.0, 0.0);
             const double2* __restrict__ qj = outer_q(o, rhs, j);
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const size_t idx = (size_t)(3 * sp + a) * g.V + site;
-                    const dfc v = to_dfc(out[sp][a]);
-                    const dfc pv = prv[idx];
-                    dfc rr;
-                    if (TS || side == 1) {
-                        rr.x = (v.x * scr.x - v.y * scr.y) - (c1d.x * pv.x - c1d.y * pv.y);   // s - c1 q_{j-1}
-                        rr.y = (v.x * scr.y + v.y * scr.x) - (c1d.x * pv.y + c1d.y * pv.x);
-                    } else {
-                        rr.x = v.x * scr.x - c1d.x * pv.x;
-                        rr.y = v.y * scr.x - c1d.x * pv.y;
-                    }
-                    nxt[idx] = rr;
-                    if (side == 0) {
-                        const dfc d = dotv[idx];
-                        ax[sp] += d.x * rr.x + d.y * rr.y;        // conj(d) r
-                        if (TS) ay[sp] += d.x * rr.y - d.y * rr.x;
-                        if (PASS2) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
-                    }
+            for_each_out([&](int sp, int a, const T& vout) {
+                const size_t idx = (size_t)(3 * sp + a) * g.V + site;
+                const dfc v = to_dfc(vout);
+                const dfc pv = prv[idx];
+                dfc rr;
+                if (TS || side == 1) {
+                    rr.x = (v.x * scr.x - v.y * scr.y) - (c1d.x * pv.x - c1d.y * pv.y);   // s - c1 q_{j-1}
+                    rr.y = (v.x * scr.y + v.y * scr.x) - (c1d.x * pv.y + c1d.y * pv.x);
+                } else {
+                    rr.x = v.x * scr.x - c1d.x * pv.x;
+                    rr.y = v.y * scr.x - c1d.x * pv.y;
                 }
-            }
+                nxt[idx] = rr;
+                if (side == 0) {
+                    const dfc d = dotv[idx];
+                    ax[sp] += d.x * rr.x + d.y * rr.y;        // conj(d) r
+                    if (TS) ay[sp] += d.x * rr.y - d.y * rr.x;
+                    if (PASS2) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
+                }
+            });
             acc = make_double2(df_to_double((ax[0] + ax[1]) + (ax[2] + ax[3])),
                                df_to_double((ay[0] + ay[1]) + (ay[2] + ay[3])));
         } else {
-        // the scale 1/n_j (1/m_j) in the stencil's precision
-        T scr;
-        scr.x = from_double<R>(coef[0].x);
-        scr.y = from_double<R>(coef[0].y);
-        if (side == 0) {
-            const double2* __restrict__ prv = outer_q(o, rhs, jp);
-            double2* __restrict__ nxt = outer_q(o, rhs, j + 1);   // at j = k-1 a scratch column
-            const double2* __restrict__ dotv = TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j);
-            double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
-            const double2 cpj = PASS2 ? o.cp[hb + j] : make_double2(0.0, 0.0);
-            const double2* __restrict__ qj = outer_q(o, rhs, j);
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
+            // the scale 1/n_j (1/m_j) in the stencil's precision
+            T scr;
+            scr.x = from_double<R>(coef[0].x);
+            scr.y = from_double<R>(coef[0].y);
+            if (side == 0) {
+                const double2* __restrict__ prv = outer_q(o, rhs, jp);
+                double2* __restrict__ nxt = outer_q(o, rhs, j + 1);   // at j = k-1 a scratch column
+                const double2* __restrict__ dotv = TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j);
+                double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
+                const double2 cpj = PASS2 ? o.cp[hb + j] : make_double2(0.0, 0.0);
+                const double2* __restrict__ qj = outer_q(o, rhs, j);
+                for_each_out([&](int sp, int a, const T& v) {
                     const size_t idx = (size_t)(3 * sp + a) * g.V + site;
-                    const T v = out[sp][a];
                     double2 rr;
                     if (TS) {
                         rr = make_double2(to_double(v.x * scr.x - v.y * scr.y), to_double(v.x * scr.y + v.y * scr.x));
@@ -452,29 +611,23 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
                     acc.x = fma(d.x, rr.x, fma(d.y, rr.y, acc.x));          // conj(d) r
                     if (TS) acc.y = fma(d.x, rr.y, fma(-d.y, rr.x, acc.y));
                     if (PASS2) yacc[idx] = caxpy_pos(yacc[idx], cpj, qj[idx]);
-                }
-            }
-        } else {
-            const double2* __restrict__ prv = outer_p(o, rhs, jp);
-            double2* __restrict__ nxt = outer_p(o, rhs, j + 1);
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
+                });
+            } else {
+                const double2* __restrict__ prv = outer_p(o, rhs, jp);
+                double2* __restrict__ nxt = outer_p(o, rhs, j + 1);
+                for_each_out([&](int sp, int a, const T& v) {
                     const size_t idx = (size_t)(3 * sp + a) * g.V + site;
-                    const T v = out[sp][a];
                     double2 ll = make_double2(to_double(v.x * scr.x - v.y * scr.y), to_double(v.x * scr.y + v.y * scr.x));
                     nxt[idx] = caxpy_neg(ll, c1, prv[idx]);             // l - c1 p_{j-1}
-                }
+                });
             }
-        }
         }
     }
     if (side == 0) {
         double2 part = block_sum(acc, sh);
         if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, sb, nsb)) {
             double2 tot = sum_partials(o.partials + (size_t)rhs * o.npart, nsb, sh);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && threadIdx.y == 0) {
                 // Hermitian: H(j,j) = Re(q_j^dag r) / n_j, real (App. C); two-sided: (p_j^dag r) / m_j^*
                 o.alpha[hb + j] = TS ? cmul(coef[2], tot) : make_double2(tot.x * coef[2].x, 0.0);
                 o.counters[rhs] = 0u;
@@ -485,30 +638,41 @@ __global__ void __launch_bounds__(kStencilMaxThreads, StencilMinBlocks<R>::value
 
 int dslash_step1_blocks(const Geom& g, int threads) { return (g.V + threads - 1) / threads; }
 
+template <typename R, typename T, int CS>
+static void launch_step1_cs(dim3 grid, dim3 block, const T* U, const Geom& g, const Outer& o, int j, R kappa,
+                            R emu, R emu_inv, const T* qin, long qs, const T* pin, long ps, cudaStream_t st) {
+    const bool pass2 = o.y != nullptr;
+    if (o.two_sided) {
+        if (pass2)
+            k_dslash_step1<R, true, true, CS><<<grid, block, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+        else
+            k_dslash_step1<R, true, false, CS><<<grid, block, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+    } else {
+        if (pass2)
+            k_dslash_step1<R, false, true, CS><<<grid, block, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+        else
+            k_dslash_step1<R, false, false, CS><<<grid, block, 0, st>>>(U, g, o, j, kappa, emu, emu_inv, qin, qs, pin, ps);
+    }
+}
+
 template <typename R, typename T>
 static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R kappa, R emu, R emu_inv, const T* qin,
                            long qs, const T* pin, long ps, cudaStream_t st) {
     const int nvec = o.two_sided ? 2 * o.n_rhs : o.n_rhs;
     // launch shape of this precision (the kernel reads the grid order from o)
     Outer o2 = o;
+    int split = o.st_split;
     if (std::is_same<R, df>::value) {
         o2.st_threads = o.st_threads_df;
         o2.st_order = o.st_order_df;
+        split = o.st_split_df;
     }
     const int threads = o2.st_threads;
     dim3 grid((unsigned)(dslash_step1_blocks(g, threads) * nvec));
-    const bool pass2 = o.y != nullptr;
-    if (o.two_sided) {
-        if (pass2)
-            k_dslash_step1<R, true, true><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
-        else
-            k_dslash_step1<R, true, false><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
-    } else {
-        if (pass2)
-            k_dslash_step1<R, false, true><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
-        else
-            k_dslash_step1<R, false, false><<<grid, threads, 0, st>>>(U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps);
-    }
+    if (split == 3)
+        launch_step1_cs<R, T, 3>(grid, dim3(threads, 3), U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps, st);
+    else
+        launch_step1_cs<R, T, 1>(grid, dim3(threads, 1), U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps, st);
 }
 
 void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,

@@ -49,7 +49,8 @@ struct Outer {
     int n_rhs, k, nblk, npart;
     int st_threads;  // fused stencil: sites (threads) per CTA, 64 / 128 / 256
     int st_order;    // fused stencil grid: 0 vector-fastest (link reuse in L2), 1 site-block-fastest
-    int st_threads_df, st_order_df;   // the same for the two-float stencil steps
+    int st_split;    // fused stencil: threads per site, 1 or 3 (one colour each)
+    int st_threads_df, st_order_df, st_split_df;   // the same for the two-float stencil steps
     int two_sided;
     int q_ring;      // 0: Q holds all k vectors (+1 scratch) [rhs][k+1][N]; 1: ring [rhs][3][N] (double pass)
     int qcols;       // vectors per RHS in Q: k + 1 or 3

@@ -94,10 +94,12 @@ class NkStats(ctypes.Structure):
 
 class NkLaunch(ctypes.Structure):
     _fields_ = [("stencil_threads", ctypes.c_int), ("stencil_order", ctypes.c_int), ("step2_blocks", ctypes.c_int),
-                ("early_threads", ctypes.c_int), ("early_order", ctypes.c_int)]
+                ("early_threads", ctypes.c_int), ("early_order", ctypes.c_int), ("stencil_split", ctypes.c_int),
+                ("early_split", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.stencil_threads, self.stencil_order, self.step2_blocks, self.early_threads, self.early_order)
+        return (self.stencil_threads, self.stencil_order, self.step2_blocks, self.early_threads, self.early_order,
+                self.stencil_split, self.early_split)
 
 
 class NkError(RuntimeError):
@@ -320,9 +322,9 @@ class Context:
 
     # -- launch shape / autotuner -------------------------------------------
     def set_launch(self, n_rhs, flags, stencil_threads, stencil_order, step2_blocks, early_threads=128,
-                   early_order=0):
+                   early_order=0, stencil_split=1, early_split=1):
         lc = NkLaunch(int(stencil_threads), int(stencil_order), int(step2_blocks), int(early_threads),
-                      int(early_order))
+                      int(early_order), int(stencil_split), int(early_split))
         self._check(self._lib.nk_set_launch(self.h, int(n_rhs), int(flags), ctypes.byref(lc)))
 
     def get_launch(self, n_rhs, flags=NK_FP64):
