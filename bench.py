@@ -377,7 +377,8 @@ def run_gpu(args, w, rank, world, local_rank):
         "speedup_vs_fp64_plain": (value / world) / (1.0 / (fp64_ms * 1e-3)),
         "gpu_launches": launches,
         "launch_shape": {"stencil_threads": shape[0], "stencil_order": shape[1], "step2_blocks": shape[2],
-                         "early_threads": shape[3], "early_order": shape[4],
+                         "early_threads": shape[3], "early_order": shape[4], "stencil_split": shape[5],
+                         "early_split": shape[6],
                          "autotune_ms_per_outer_step": tune_ms},
         "rhi_iters": stp["rhi_iters"],
         "kernel_class_ms": {kk: round(v, 3) for kk, v in tc.items()},

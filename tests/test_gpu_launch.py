@@ -45,7 +45,8 @@ def ctx_for(U, mu):
     return ctx
 
 
-SHAPES = [(64, 1, 1, 256, 1), (256, 0, 7, 64, 0), (128, 1, 40, 128, 1), (64, 0, 3, 64, 1)]
+# (stencil threads, order, step-2 blocks, early threads, early order, split, early split)
+SHAPES = [(64, 1, 1, 256, 1, 1, 3), (256, 0, 7, 64, 0, 3, 1), (128, 1, 40, 128, 1, 3, 3), (64, 0, 3, 64, 1, 1, 1)]
 
 
 @pytest.mark.parametrize("mu", [0.0, 0.3])
@@ -77,10 +78,10 @@ def test_autotune_and_cache(case, tmp_path):
     path = str(tmp_path / "tune.txt")
     ctx = ctx_for(U, 0.3)
     default = ctx.get_launch(3, NK_MIXED)
-    assert default[:2] == (128, 0) and default[3:] == (128, 0)
+    assert default[:2] == (128, 0) and default[3:] == (128, 0, 1, 1)
     shape, ms = ctx.autotune(3, NK_MIXED, path)
     assert shape[0] in (64, 128, 256) and shape[1] in (0, 1) and shape[2] >= 1
-    assert shape[3] in (64, 128, 256) and shape[4] in (0, 1)
+    assert shape[3] in (64, 128, 256) and shape[4] in (0, 1) and shape[5] in (1, 3) and shape[6] in (1, 3)
     assert 0.0 < ms < 10.0
     assert ctx.get_launch(3, NK_MIXED) == shape
     lines = open(path).read().split("\n")
@@ -102,7 +103,8 @@ def test_autotune_and_cache(case, tmp_path):
 def test_invalid_shapes(case):
     U, _, _ = case
     ctx = ctx_for(U, 0.0)
-    for bad in [(96, 0, 4), (128, 2, 4), (128, 0, 0), (128, 0, 5000), (128, 0, 4, 32, 0), (128, 0, 4, 64, 3)]:
+    for bad in [(96, 0, 4), (128, 2, 4), (128, 0, 0), (128, 0, 5000), (128, 0, 4, 32, 0), (128, 0, 4, 64, 3),
+                (128, 0, 4, 64, 0, 2, 1), (128, 0, 4, 64, 0, 1, 4)]:
         with pytest.raises(NkError) as e:
             ctx.set_launch(1, NK_FP64, *bad)
         assert e.value.code == NK_EINVAL
