@@ -74,13 +74,20 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Block sum of a double2 (blockDim.x a multiple of 32, <= 1024). Every thread
-// of the block receives the same value; the summation order is fixed.
-// Only warp 0 does the second level (FP64 adds are scarce on GB300); the
-// result is broadcast through shared memory.
+// Linear thread index and thread count of the block (blocks may be 2-D with
+// blockDim.x a multiple of 32: warps are then runs of 32 linear indices).
+__device__ __forceinline__ int block_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
+__device__ __forceinline__ int block_threads() { return blockDim.x * blockDim.y * blockDim.z; }
+
+// Block sum of a double2 (<= 1024 threads in whole warps). Every thread of the
+// block receives the same value; the summation order is fixed.  Only warp 0
+// does the second level (FP64 adds are scarce on GB300); the result is
+// broadcast through shared memory.  The butterfly of the second level stops at
+// the number of warps (lanes beyond it hold zeros).
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh /* >= 33 */) {
     v = warp_sum(v);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tid = block_tid();
+    int lane = tid & 31, w = tid >> 5, nw = block_threads() >> 5;
     __syncthreads();
     if (lane == 0) sh[w] = v;
     __syncthreads();
@@ -88,7 +95,7 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* sh /* >= 33 */)
         double2 t = lane < nw ? sh[lane] : mk(0.0, 0.0);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            if (o < nw) {   // nw is a power of two: only the levels that combine real partials
+            if (o < nw) {   // only the levels that combine real partials
                 t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
                 t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
             }
@@ -100,7 +107,8 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* sh /* >= 33 */)
 }
 __device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
     v = warp_sum(v);
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tid = block_tid();
+    int lane = tid & 31, w = tid >> 5, nw = block_threads() >> 5;
     __syncthreads();
     if (lane == 0) sh[w] = v;
     __syncthreads();
@@ -115,7 +123,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh /* >= 32 */) {
 __device__ __forceinline__ bool finish_partial(double2 part, double2* partials, unsigned* counter,
                                                int slot, int nslots) {
     __shared__ bool last;
-    if (threadIdx.x == 0) {
+    if (block_tid() == 0) {
         partials[slot] = part;
         __threadfence();
         unsigned ticket = atomicAdd(counter, 1u);
@@ -129,7 +137,7 @@ __device__ __forceinline__ bool finish_partial(double2 part, double2* partials, 
 __device__ __forceinline__ double2 sum_partials(const double2* partials, int nslots, double2* sh) {
     __threadfence();
     double2 a = mk(0.0, 0.0);
-    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+    for (int i = block_tid(); i < nslots; i += block_threads()) {
         double2 v = __ldcg(partials + i);
         a.x += v.x; a.y += v.y;
     }
