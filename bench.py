@@ -52,6 +52,25 @@ DEFAULT_WORKLOAD = "8^4-mu0.3-12pt"
 STENCIL_DIMS = (16, 16, 16, 32)
 
 
+def max_over_ranks(ms, dist=None):
+    """The timed region's length: the maximum over the ranks (replicas: each rank
+    solves its own batch; this reduction and the barriers are the only
+    collectives)."""
+    if not dist:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(solves_per_step, steps, ms, world):
+    """Solves/s of the whole job: every rank solves solves_per_step sources per
+    step (weak scaling), over the slowest rank's time."""
+    return world * solves_per_step * steps / (ms * 1e-3)
+
+
 def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summaries
     (a line 'traffic_bytes_per_launch <kernel>: <bytes>'), else None."""
@@ -295,11 +314,7 @@ def run_gpu(args, w, rank, world, local_rank):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     y = y_dev.cpu().numpy()
 
     # e2e: host buffers in pinned memory, through the host-pointer C entry point
@@ -354,7 +369,7 @@ def run_gpu(args, w, rank, world, local_rank):
         ok = 0
     solves_per_step = ok
 
-    value = world * solves_per_step * args.steps / (ms * 1e-3)
+    value = whole_job_value(solves_per_step, args.steps, ms, world)
     e2e_value = solves_per_step / e2e_s
     tc = stp["t_class_ms"]
     nc = stp["n_class"]
