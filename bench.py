@@ -219,6 +219,7 @@ def config_of(w, args):
                           "inner products, preconditioning, inner Lanczos, RHi and lift FP64" % w["j0"])
                          if w["mixed"] else "FP64",
             "graph": True, "parallelism": "replicas" if args.gpus > 1 else "single",
+            "batches_in_flight": args.inflight,
             "l2": "working set (Krylov basis %.1f GB) larger than L2" % (
                 12 * w["n_rhs"] * np.prod(w["dims"]) * w["k"] * 16 / 1e9)}
 
@@ -293,8 +294,22 @@ def run_gpu(args, w, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     b_dev = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
     y_dev = torch.zeros_like(b_dev)
+    # Batches in flight: each step is one whole batched solve; with two contexts
+    # on two streams the next batch's outer recurrence (all SMs) runs while the
+    # previous batch's inner part and RHi (12 and 96 SMs) finish.
+    inflight = max(1, args.inflight)
+    ctxs, ys, streams = [ctx], [y_dev], [torch.cuda.Stream() for _ in range(inflight)]
+    for _ in range(1, inflight):
+        c2 = nk.Context(w["dims"])
+        c2.load_links(U)
+        c2.set_mu_mw(w["mu"], w["m_w"])
+        c2.set_precision(w.get("j0", -1))
+        c2.set_launch(n_rhs, flags, *shape)
+        ctxs.append(c2)
+        ys.append(torch.zeros_like(b_dev))
     for _ in range(args.warmup):
-        st, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
+        for c_, y_ in zip(ctxs, ys):
+            st, _ = c_.sign_apply_dev(b_dev, y_, n_rhs, k, ell, flags=flags)
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -305,10 +320,26 @@ def run_gpu(args, w, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    for s_ in streams:
+        s_.wait_stream(stream)
     launches = 0
-    for _ in range(args.steps):
-        st, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
-        launches += st["launches"]
+    for i in range(args.steps):
+        c_ = ctxs[i % inflight]
+        if inflight > 1:
+            if i >= inflight:       # the previous batch of this context
+                st, _ = c_.wait()
+                launches += st["launches"]
+            c_.sign_apply_dev(b_dev, ys[i % inflight], n_rhs, k, ell, flags=flags | nk.NK_ASYNC,
+                              stream=streams[i % inflight])
+        else:
+            st, _ = c_.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
+            launches += st["launches"]
+    if inflight > 1:
+        for c_ in ctxs:
+            st, rc_w = c_.wait()
+            launches += st["launches"]
+        for s_ in streams:
+            stream.wait_stream(s_)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -316,6 +347,8 @@ def run_gpu(args, w, rank, world, local_rank):
     clocks = sampler.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
     y = y_dev.cpu().numpy()
+    for c_ in ctxs[1:]:
+        c_.close()
 
     # e2e: host buffers in pinned memory, through the host-pointer C entry point
     b_pin = torch.from_numpy(np.ascontiguousarray(b_host)).pin_memory()
@@ -524,6 +557,8 @@ def main():
                          "no output line), for launch lists and captures under ncu")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
+    ap.add_argument("--inflight", type=int, default=2,
+                    help="batches in flight (contexts on their own streams); 1: one synchronous solve per step")
     ap.add_argument("--tune-cache", default=None,
                     help="launch-shape cache file (read if it has the workload's shape, else written)")
     args = ap.parse_args()

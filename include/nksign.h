@@ -60,6 +60,10 @@ extern "C" {
 #define NK_MIXED 0x1u       /* FP32 stencil after the first j0 outer steps (nk_set_precision) */
 #define NK_DOUBLE_PASS 0x2u /* regenerate V_k in a second pass instead of storing it (Sec. 4.4) */
 #define NK_NO_GRAPH 0x10u   /* launch kernel by kernel instead of replaying a CUDA graph */
+#define NK_ASYNC 0x40u      /* nk_sign_apply_dev / nk_overlap_apply_dev with tol = 0: enqueue the
+                               solve and return without waiting; nk_wait collects its outcome.
+                               One pending solve per context (its workspace); two contexts on two
+                               streams keep two batches in flight. */
 #define NK_PROFILE 0x20u    /* kernel by kernel, with CUDA events around every launch; fills
                                nk_stats.t_class_ms / n_class (implies NK_NO_GRAPH) */
 
@@ -219,6 +223,10 @@ int nk_overlap_apply(nk_ctx* ctx, const double* b, int n_rhs, int k, int ell, do
                      unsigned flags, double* y, nk_stats* st);
 int nk_overlap_apply_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, int ell,
                          double tol, unsigned flags, double* y_dev, nk_stats* st, void* stream);
+
+/* Waits for the pending NK_ASYNC solve of the context and returns its result
+ * code; st (nullable) receives its statistics.  NK_OK if none is pending. */
+int nk_wait(nk_ctx* ctx, nk_stats* st);
 
 /* The Wilson stencil alone: out_r = A in_r (dagger = 0) or A^dagger in_r
  * (dagger = 1; A^dagger = gamma5 D_w(-mu)) for n_vec DEVICE vectors in the

@@ -54,6 +54,14 @@ struct nk_ctx {
     DevBuf links_tmp;
     std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;  // exec, kernels per replay
     std::map<std::tuple<int, int, int>, nk_launch> tune;  // (n_rhs, two_sided, mixed) -> launch shape
+    struct Pending {                 // an NK_ASYNC solve not yet collected
+        bool on = false;
+        cudaStream_t st = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int n_rhs = 0, k = 0, ell = 0, launches = 0;
+        const int *status = nullptr, *iters = nullptr;
+        const double *p = nullptr, *zmin = nullptr, *zmax = nullptr, *xnorm = nullptr;
+    } pending;
     std::string err = "no error";
 };
 
@@ -468,10 +476,52 @@ int status_to_code(int s) {
     }
 }
 
+// Per-RHS outcome of a finished solve (device arrays read after the stream
+// has been synchronised) into codes and stats.
+int collect_outcome(nk_ctx* c, int n_rhs, int k_used_max, const std::vector<int>& kused_h,
+                    const std::vector<int>& notconv, int checks, int ell, int launches, float ms,
+                    const std::vector<int>& status, const std::vector<int>& iters, const std::vector<double>& pv,
+                    const std::vector<double>& zmin, const std::vector<double>& zmax, const std::vector<double>& xn,
+                    nk_stats* stats) {
+    int worst = NK_OK;
+    std::vector<int> codes(n_rhs);
+    for (int r = 0; r < n_rhs; ++r) {
+        codes[r] = status_to_code(status[r]);
+        if (codes[r] == NK_OK && notconv[r]) codes[r] = NK_ENOTCONV;
+        if (codes[r] != NK_OK && worst == NK_OK) worst = codes[r];
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->n_rhs = n_rhs;
+        stats->k_used = k_used_max;
+        stats->ell_used = ell;
+        stats->checks = checks;
+        for (int r = 0; r < n_rhs; ++r) {
+            stats->k_rhs[r] = kused_h[r];
+            stats->rhi_iters[r] = iters[r];
+            stats->status[r] = codes[r];
+            stats->p[r] = pv[r];
+            stats->z_min[r] = zmin[r];
+            stats->z_max[r] = zmax[r];
+            stats->xnorm[r] = xn[r];
+        }
+        stats->t_total_ms = ms;
+        stats->launches = launches;
+    }
+    if (worst == NK_EBREAKDOWN) return fail(c, worst, "two-sided Lanczos: serious breakdown (delta = 0)");
+    if (worst == NK_ERHI) return fail(c, worst, "Roberts-Higham iteration did not converge (or p H_k singular)");
+    if (worst == NK_ENOTCONV) return fail(c, worst, "adaptive k: tolerance not met at k_max for some RHS");
+    return worst;
+}
+
 int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
               unsigned flags, double* y_dev, nk_stats* stats, cudaStream_t st, bool overlap) {
     int rc = check_solve_args(c, n_rhs, k, ell, tol);
     if (rc) return rc;
+    if (c->pending.on) return fail(c, NK_ESTATE, "an NK_ASYNC solve is pending on this context: nk_wait first");
+    const bool async = (flags & NK_ASYNC) != 0;
+    if (async && (tol > 0.0 || (flags & NK_PROFILE)))
+        return fail(c, NK_EINVAL, "NK_ASYNC needs a fixed k (tol = 0) and no NK_PROFILE");
     NK_CUDA(c, cudaSetDevice(c->device));
     const bool ts = c->mu != 0.0;
     const bool dp = (flags & NK_DOUBLE_PASS) != 0;
@@ -530,6 +580,24 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
         if (e != cudaSuccess) return cuda_fail(c, e, "enqueue_solve");
     }
     NK_CUDA(c, cudaEventRecord(e1, st));
+    if (async) {   // collected by nk_wait
+        nk_ctx::Pending& P = c->pending;
+        P.on = true;
+        P.st = st;
+        P.e0 = e0;
+        P.e1 = e1;
+        P.n_rhs = n_rhs;
+        P.k = k;
+        P.ell = ell;
+        P.launches = L.launches;
+        P.status = Lw.o.status;
+        P.iters = Lw.in.rhi_iters;
+        P.p = Lw.in.p;
+        P.zmin = Lw.in.zmin;
+        P.zmax = Lw.in.zmax;
+        P.xnorm = Lw.o.xnorm;
+        return NK_OK;
+    }
     // read back per-RHS outcome
     std::vector<int> status(n_rhs), iters(n_rhs);
     std::vector<double> pv(n_rhs), zmin(n_rhs), zmax(n_rhs), xn(n_rhs);
@@ -544,42 +612,19 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int worst = NK_OK;
-    std::vector<int> codes(n_rhs);
-    for (int r = 0; r < n_rhs; ++r) {
-        codes[r] = status_to_code(status[r]);
-        if (codes[r] == NK_OK && notconv[r]) codes[r] = NK_ENOTCONV;
-        if (codes[r] != NK_OK && worst == NK_OK) worst = codes[r];
+    double tcm[NK_NCLASS] = {0};   // NK_PROFILE: summed device time per class
+    int ncl[NK_NCLASS] = {0};
+    if (profile) {
+        L.collect(tcm);
+        for (int q = 0; q < NK_NCLASS; ++q) ncl[q] = L.n_class[q];
     }
-    if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->n_rhs = n_rhs;
-        stats->k_used = *std::max_element(kused_h.begin(), kused_h.end());
-        stats->ell_used = ell;
-        stats->checks = checks;
-        for (int r = 0; r < n_rhs; ++r) {
-            stats->k_rhs[r] = kused_h[r];
-            stats->rhi_iters[r] = iters[r];
-            stats->status[r] = codes[r];
-            stats->p[r] = pv[r];
-            stats->z_min[r] = zmin[r];
-            stats->z_max[r] = zmax[r];
-            stats->xnorm[r] = xn[r];
-        }
-        stats->t_total_ms = ms;
-        stats->launches = L.launches;
-        if (profile) {
-            L.collect(stats->t_class_ms);
-            for (int q = 0; q < NK_NCLASS; ++q) stats->n_class[q] = L.n_class[q];
-        }
-    } else if (profile) {
-        double tmp[NK_NCLASS] = {0};
-        L.collect(tmp);
+    rc = collect_outcome(c, n_rhs, *std::max_element(kused_h.begin(), kused_h.end()), kused_h, notconv, checks, ell,
+                         L.launches, ms, status, iters, pv, zmin, zmax, xn, stats);
+    if (stats && profile) {
+        std::memcpy(stats->t_class_ms, tcm, sizeof(tcm));
+        for (int q = 0; q < NK_NCLASS; ++q) stats->n_class[q] = ncl[q];
     }
-    if (worst == NK_EBREAKDOWN) return fail(c, worst, "two-sided Lanczos: serious breakdown (delta = 0)");
-    if (worst == NK_ERHI) return fail(c, worst, "Roberts-Higham iteration did not converge (or p H_k singular)");
-    if (worst == NK_ENOTCONV) return fail(c, worst, "adaptive k: tolerance not met at k_max for some RHS");
-    return worst;
+    return rc;
 }
 
 }  // namespace
@@ -1147,11 +1192,40 @@ int nk_predict_sizes(nk_ctx* c, nk_mlp* m, const double* b_dev, int k_max, int* 
     return NK_OK;
 }
 
+int nk_wait(nk_ctx* c, nk_stats* stats) {
+    if (!c) return NK_EINVAL;
+    if (!c->pending.on) return NK_OK;
+    nk_ctx::Pending P = c->pending;
+    c->pending.on = false;
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const int n = P.n_rhs;
+    std::vector<int> status(n), iters(n), kused(n, P.k), notconv(n, 0);
+    std::vector<double> pv(n), zmin(n), zmax(n), xn(n);
+    NK_CUDA(c, cudaMemcpyAsync(status.data(), P.status, sizeof(int) * n, cudaMemcpyDeviceToHost, P.st));
+    NK_CUDA(c, cudaMemcpyAsync(iters.data(), P.iters, sizeof(int) * n, cudaMemcpyDeviceToHost, P.st));
+    NK_CUDA(c, cudaMemcpyAsync(pv.data(), P.p, sizeof(double) * n, cudaMemcpyDeviceToHost, P.st));
+    NK_CUDA(c, cudaMemcpyAsync(zmin.data(), P.zmin, sizeof(double) * n, cudaMemcpyDeviceToHost, P.st));
+    NK_CUDA(c, cudaMemcpyAsync(zmax.data(), P.zmax, sizeof(double) * n, cudaMemcpyDeviceToHost, P.st));
+    NK_CUDA(c, cudaMemcpyAsync(xn.data(), P.xnorm, sizeof(double) * n, cudaMemcpyDeviceToHost, P.st));
+    NK_CUDA(c, cudaStreamSynchronize(P.st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, P.e0, P.e1);
+    cudaEventDestroy(P.e0);
+    cudaEventDestroy(P.e1);
+    return collect_outcome(c, n, P.k, kused, notconv, 0, P.ell, P.launches, ms, status, iters, pv, zmin, zmax, xn,
+                           stats);
+}
+
 const char* nk_last_error(const nk_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void nk_destroy(nk_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    if (c->pending.on) {
+        cudaStreamSynchronize(c->pending.st);
+        cudaEventDestroy(c->pending.e0);
+        cudaEventDestroy(c->pending.e1);
+    }
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.first);
     if (c->ws.p) cudaFree(c->ws.p);
     if (c->staging.p) cudaFree(c->staging.p);

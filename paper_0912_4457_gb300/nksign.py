@@ -32,6 +32,7 @@ NK_MIXED = 0x1
 NK_DOUBLE_PASS = 0x2
 NK_NO_GRAPH = 0x10
 NK_PROFILE = 0x20
+NK_ASYNC = 0x40
 NK_MAX_RHS = 12
 NK_NCLASS = 9
 CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other", "step2_df"]
@@ -50,7 +51,7 @@ EXPORTED = [
     "nk_destroy",
     "nk_mlp_create", "nk_mlp_set_norm", "nk_mlp_set_weight_decay", "nk_mlp_get_params", "nk_mlp_set_params", "nk_mlp_loss_grad",
     "nk_mlp_train", "nk_mlp_forward", "nk_mlp_last_error", "nk_mlp_destroy", "nk_features",
-    "nk_predict_sizes", "nk_set_launch", "nk_get_launch", "nk_autotune",
+    "nk_predict_sizes", "nk_set_launch", "nk_get_launch", "nk_autotune", "nk_wait",
 ]
 
 NK_MLP_IN = 16
@@ -154,6 +155,7 @@ def load_library(path: str = LIB_PATH):
         "nk_set_launch": ([P, I, U, ctypes.POINTER(NkLaunch)], I),
         "nk_get_launch": ([P, I, U, ctypes.POINTER(NkLaunch)], I),
         "nk_autotune": ([P, I, U, ctypes.c_char_p, ctypes.POINTER(NkLaunch), dp], I),
+        "nk_wait": ([P, ctypes.POINTER(NkStats)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -281,6 +283,14 @@ class Context:
             self._check(rc)
         return st.as_dict(), rc
 
+    def wait(self, check=True):
+        """nk_wait: collect the pending NK_ASYNC solve (statistics dict, rc)."""
+        st = NkStats()
+        rc = self._lib.nk_wait(self.h, ctypes.byref(st))
+        if check:
+            self._check(rc)
+        return st.as_dict(), rc
+
     def overlap_apply_dev(self, b_dev, y_dev, n_rhs, k, ell, tol=0.0, flags=NK_FP64, stream=None):
         st = NkStats()
         rc = self._lib.nk_overlap_apply_dev(self.h, _dev_ptr(b_dev), int(n_rhs), int(k), int(ell),
@@ -333,8 +343,8 @@ class Context:
         return lc.as_tuple()
 
     def autotune(self, n_rhs, flags=NK_FP64, cache_path=None):
-        """nk_autotune: returns ((stencil_threads, stencil_order, step2_blocks, early_threads, early_order),
-        ms per outer step)."""
+        """nk_autotune: returns ((stencil_threads, stencil_order, step2_blocks, early_threads, early_order,
+        stencil_split, early_split), ms per outer step)."""
         lc = NkLaunch()
         ms = ctypes.c_double()
         path = cache_path.encode() if cache_path else None

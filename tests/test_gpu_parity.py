@@ -427,3 +427,37 @@ def test_invalid_arguments(k, ell, n_rhs):
     assert rc == NK_EINVAL
     assert len(ctx._lib.nk_last_error(ctx.h)) > 0
     ctx.close()
+
+
+def test_async_two_contexts_match_sync(c1):
+    """NK_ASYNC: two contexts on two streams with both batches in flight give
+    the synchronous result bit for bit; a second solve on a context with one
+    pending is refused (NK_ESTATE), and nk_wait with nothing pending is a no-op."""
+    dims, U, b, truth = c1
+    k, ell = 256, 64
+    ctx_a, ctx_b = make_ctx(dims, 101, 0.3), make_ctx(dims, 101, 0.3)
+    bd = to_dev(np.concatenate([b, inputs.gaussian_sources(dims, 31, n_rhs=2)]))
+    ref = torch.zeros_like(bd)
+    ctx_a.sign_apply_dev(bd, ref, 3, k, ell, flags=NK_MIXED)
+    torch.cuda.synchronize()
+    st_idle, rc_idle = ctx_b.wait()
+    assert rc_idle == 0
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    ya, yb = torch.zeros_like(bd), torch.zeros_like(bd)
+    for _ in range(2):
+        ctx_a.sign_apply_dev(bd, ya, 3, k, ell, flags=NK_MIXED | nksign.NK_ASYNC, stream=sa)
+        ctx_b.sign_apply_dev(bd, yb, 3, k, ell, flags=NK_MIXED | nksign.NK_ASYNC, stream=sb)
+        _, rc = ctx_a.sign_apply_dev(bd, ya, 3, k, ell, flags=NK_MIXED | nksign.NK_ASYNC, stream=sa,
+                                     check=False)
+        assert rc == nksign.NK_ESTATE
+        st_a, rc_a = ctx_a.wait()
+        st_b, rc_b = ctx_b.wait()
+        assert rc_a == 0 and rc_b == 0
+        assert st_a["launches"] > 0 and st_a["n_rhs"] == 3
+        torch.cuda.synchronize()
+        assert torch.equal(ya, ref) and torch.equal(yb, ref)
+    # NK_ASYNC with an adaptive k is refused
+    _, rc = ctx_a.sign_apply_dev(bd, ya, 3, k, ell, tol=1e-8, flags=NK_MIXED | nksign.NK_ASYNC, check=False)
+    assert rc == NK_EINVAL
+    ctx_a.close()
+    ctx_b.close()
