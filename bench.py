@@ -218,6 +218,8 @@ def config_of(w, args):
             "precision": ("two-float (48-bit) stencil for outer steps < %d, FP32 stencil after; recurrences, "
                           "inner products, preconditioning, inner Lanczos, RHi and lift FP64" % w["j0"])
                          if w["mixed"] else "FP64",
+            "p": "one p per batch: Eq. popt with z_min, z_max of A estimated as the extremes over the "
+                 "batch's H_k (power / inverse iteration)",
             "graph": True, "parallelism": "replicas" if args.gpus > 1 else "single",
             "batches_in_flight": args.inflight,
             "l2": "working set (Krylov basis %.1f GB) larger than L2" % (
@@ -284,7 +286,7 @@ def run_gpu(args, w, rank, world, local_rank):
     peaks = measured_peaks()
     U, b_host = make_inputs(w)
     n_rhs, k, ell = w["n_rhs"], w["k"], w["ell"]
-    flags = nk.NK_MIXED if w["mixed"] else nk.NK_FP64
+    flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_SHARED_P
     ctx = nk.Context(w["dims"])
     ctx.load_links(U)
     ctx.set_mu_mw(w["mu"], w["m_w"])
@@ -349,6 +351,15 @@ def run_gpu(args, w, rank, world, local_rank):
     y = y_dev.cpu().numpy()
     for c_ in ctxs[1:]:
         c_.close()
+    # latency of one batch with nothing else in flight
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    l0.record(stream)
+    for _ in range(2):
+        ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
+    l1.record(stream)
+    torch.cuda.synchronize()
+    latency_ms = l0.elapsed_time(l1) / 2
 
     # e2e: host buffers in pinned memory, through the host-pointer C entry point
     b_pin = torch.from_numpy(np.ascontiguousarray(b_host)).pin_memory()
@@ -413,7 +424,7 @@ def run_gpu(args, w, rank, world, local_rank):
     sten = stencil_roofline(nk, torch, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "latency_ms_one_batch": latency_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": config_of(w, args),
         "accuracy": {"rel_err_vs_oracle_src0": err0, "eps_sgn2_max": max(eps), "solves_meeting_tol": ok,
                      "tol": TOL},
@@ -458,7 +469,7 @@ def run_ncu(args, w):
     ctx.load_links(U)
     ctx.set_mu_mw(w["mu"], w["m_w"])
     ctx.set_precision(w.get("j0", -1))
-    flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_NO_GRAPH
+    flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_SHARED_P | nk.NK_NO_GRAPH
     # with --tune-cache from a plain bench run the shape is read, not timed
     ctx.autotune(w["n_rhs"], flags, args.tune_cache)
     b_dev = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
@@ -549,7 +560,7 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--mode", choices=["bench", "ncu"], default="bench",
@@ -557,7 +568,7 @@ def main():
                          "no output line), for launch lists and captures under ncu")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
-    ap.add_argument("--inflight", type=int, default=2,
+    ap.add_argument("--inflight", type=int, default=4,
                     help="batches in flight (contexts on their own streams); 1: one synchronous solve per step")
     ap.add_argument("--tune-cache", default=None,
                     help="launch-shape cache file (read if it has the workload's shape, else written)")

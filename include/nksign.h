@@ -64,6 +64,9 @@ extern "C" {
                                solve and return without waiting; nk_wait collects its outcome.
                                One pending solve per context (its workspace); two contexts on two
                                streams keep two batches in flight. */
+#define NK_SHARED_P 0x80u   /* one p for the whole batch (Eq. popt with z_min and z_max of A taken as
+                               the extremes of the per-RHS estimates over the batch: every RHS
+                               shares A), instead of one per RHS; p > 0 overrides both */
 #define NK_PROFILE 0x20u    /* kernel by kernel, with CUDA events around every launch; fills
                                nk_stats.t_class_ms / n_class (implies NK_NO_GRAPH) */
 

@@ -75,6 +75,25 @@ def estimate_p(alpha, beta, gamma, iters: int = P_EST_ITERS, resid_tol: float = 
     return 1.0 / np.sqrt(z_min * z_max), z_min, z_max
 
 
+def shared_p(estimates):
+    """One p for a batch of right-hand sides that share A (Eq. popt).
+
+    The footnote to Eq. popt takes z_min and z_max from spectral information
+    of A.  Each RHS's H_k gives estimates (z_min, z_max) (``estimate_p``);
+    their extremes over the batch, min z_min and max z_max, are the batch's
+    estimates of A's.  ``estimates`` is a sequence of (p, z_min, z_max); entries
+    without a positive finite z_min and z_max are skipped.
+    """
+    zmn, zmx = None, 0.0
+    for _, a, b in estimates:
+        if a > 0.0 and b > 0.0 and np.isfinite(a) and np.isfinite(b):
+            zmn = a if zmn is None else min(zmn, a)
+            zmx = max(zmx, b)
+    if zmn is None:
+        return 1.0
+    return 1.0 / np.sqrt(zmn * zmx)
+
+
 def inner_sign(alpha, beta, gamma, ell: int, p: float, hermitian: bool):
     """App. C steps 3-5 and the inner half of step 6: c = V_l sgn(H_l) e_1 (a k-vector).
 

@@ -6,6 +6,6 @@ the CUDA library ``libnksign.so`` (sources in ``csrc/``, C ABI in
 ``include/nksign.h``); ``nksign`` is its thin ctypes binding.
 """
 from .nksign import (  # noqa: F401
-    NK_ASYNC, NK_DOUBLE_PASS, NK_FP64, NK_MIXED, NK_NO_GRAPH, NK_PROFILE, NK_MAX_RHS, Context, Mlp, NkError,
+    NK_ASYNC, NK_DOUBLE_PASS, NK_SHARED_P, NK_FP64, NK_MIXED, NK_NO_GRAPH, NK_PROFILE, NK_MAX_RHS, Context, Mlp, NkError,
     load_library,
 )

@@ -203,120 +203,153 @@ __device__ __forceinline__ HopSpin hop_spin(int nu) {
     }
 }
 
-__device__ __forceinline__ void stencil_hops_df(dfc acc[4][3], const dfc* __restrict__ U, const dfc* __restrict__ in,
-                                                const Geom& g, int site, const int coord[4], df wp_t, df wm_t) {
-    const int V = g.V;
-#pragma unroll 1
-    for (int h = 0; h < 8; ++h) {
-        const int nu = h >> 1;
-        const bool fwd = (h & 1) != 0;   // forward neighbour: (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}
-        int L, stride;
-        switch (nu) {
-            case 0: L = g.Lx; stride = 1; break;
-            case 1: L = g.Ly; stride = g.Lx; break;
-            case 2: L = g.Lz; stride = g.Lx * g.Ly; break;
-            default: L = g.Lt; stride = g.Lx * g.Ly * g.Lz; break;
-        }
-        const int c = coord[nu];
-        int sn, ls;
-        bool wrap;
-        if (fwd) { wrap = c == L - 1; sn = wrap ? site - (L - 1) * stride : site + stride; ls = site; }
-        else { wrap = c == 0; sn = wrap ? site + (L - 1) * stride : site - stride; ls = sn; }
-        const df flip = (nu == 3 && g.antiperiodic && wrap) ? df(-1) : df(1);
-        const df w = (nu == 3 ? (fwd ? wm_t : wp_t) : df(1)) * flip;
-        const HopSpin hs = hop_spin(nu);
-        // the projection and the weights of the spatial hops are +-1: additions
-        // and subtractions, not two-float products (exact either way)
-        dfc h0[3], h1[3];
+__device__ __forceinline__ dfac rot_q(dfac z, int q) {   // z * i^q
+    dfac r;
+    switch (q & 3) {
+        case 0: r = z; break;
+        case 1: r.x = dfa_neg(z.y); r.y = z.x; break;
+        case 2: r.x = dfa_neg(z.x); r.y = dfa_neg(z.y); break;
+        default: r.x = z.y; r.y = dfa_neg(z.x); break;
+    }
+    return r;
+}
+
+// Neighbour index, link site and two-float weight of hop h (nu = h / 2; odd h:
+// forward neighbour, (1 - gamma) U^dagger_{y,+nu} psi_{y+nu}).
+struct HopGeo { int sn, ls; df w; };
+__device__ __forceinline__ HopGeo hop_geo(const Geom& g, int site, const int coord[4], int h, df wp_t,
+                                          df wm_t) {
+    const int nu = h >> 1;
+    const bool fwd = (h & 1) != 0;
+    int L, stride;
+    switch (nu) {
+        case 0: L = g.Lx; stride = 1; break;
+        case 1: L = g.Ly; stride = g.Lx; break;
+        case 2: L = g.Lz; stride = g.Lx * g.Ly; break;
+        default: L = g.Lt; stride = g.Lx * g.Ly * g.Lz; break;
+    }
+    const int c = coord[nu];
+    HopGeo r;
+    bool wrap;
+    if (fwd) { wrap = c == L - 1; r.sn = wrap ? site - (L - 1) * stride : site + stride; r.ls = site; }
+    else { wrap = c == 0; r.sn = wrap ? site + (L - 1) * stride : site - stride; r.ls = r.sn; }
+    const df flip = (nu == 3 && g.antiperiodic && wrap) ? df(-1) : df(1);
+    r.w = (nu == 3 ? (fwd ? wm_t : wp_t) : df(1)) * flip;
+    return r;
+}
+
+// Half spinors h0, h1 of one hop (the projection: additions of +-1 and +-i
+// multiples, exact up to the two-float rounding).
+__device__ __forceinline__ void hop_project(dfac h0[3], dfac h1[3], const dfc* __restrict__ in, int V, int sn,
+                                            const HopSpin& hs, bool fwd) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const dfc p0 = in[(size_t)a * V + sn], p1 = in[(size_t)(3 + a) * V + sn];
-            const dfc p2 = in[(size_t)(6 + a) * V + sn], p3 = in[(size_t)(9 + a) * V + sn];
-            const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, fwd ? hs.q0 + 2 : hs.q0);   // -c for the forward hop
-            const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, fwd ? hs.q1 + 2 : hs.q1);
-            h0[a].x = p0.x + c0.x; h0[a].y = p0.y + c0.y;
-            h1[a].x = p1.x + c1.x; h1[a].y = p1.y + c1.y;
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            dfc x0, x1;
-            x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const int e_idx = fwd ? nu * 9 + 3 * b + a : nu * 9 + 3 * a + b;
-                const dfc e = U[(size_t)e_idx * V + ls];
-                const df ey = fwd ? -e.y : e.y;
-                x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
-                x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
-            }
-            if (nu == 3) {   // temporal weights e^{+-mu} and the boundary sign
-                x0.x = w * x0.x; x0.y = w * x0.y;
-                x1.x = w * x1.x; x1.y = w * x1.y;
-            }
-            acc[0][a].x += x0.x; acc[0][a].y += x0.y;
-            acc[1][a].x += x1.x; acc[1][a].y += x1.y;
-            const dfc b0 = rot_q(hs.r0 == 1 ? x1 : x0, fwd ? hs.r0q + 2 : hs.r0q);   // times -1 forward
-            const dfc b1 = rot_q(hs.r1 == 1 ? x1 : x0, fwd ? hs.r1q + 2 : hs.r1q);
-            acc[2][a].x += b0.x; acc[2][a].y += b0.y;
-            acc[3][a].x += b1.x; acc[3][a].y += b1.y;
-        }
+    for (int b = 0; b < 3; ++b) {
+        const dfc p0 = in[(size_t)b * V + sn], p1 = in[(size_t)(3 + b) * V + sn];
+        const dfc p2 = in[(size_t)(6 + b) * V + sn], p3 = in[(size_t)(9 + b) * V + sn];
+        const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, fwd ? hs.q0 + 2 : hs.q0);   // -c for the forward hop
+        const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, fwd ? hs.q1 + 2 : hs.q1);
+        h0[b].x = dfa_of(p0.x); dfa_add(h0[b].x, c0.x.hi, c0.x.lo);
+        h0[b].y = dfa_of(p0.y); dfa_add(h0[b].y, c0.y.hi, c0.y.lo);
+        h1[b].x = dfa_of(p1.x); dfa_add(h1[b].x, c1.x.hi, c1.x.lo);
+        h1[b].y = dfa_of(p1.y); dfa_add(h1[b].y, c1.y.hi, c1.y.lo);
     }
 }
 
-__device__ __forceinline__ void stencil_hops_df_a(dfc acc[4], const dfc* __restrict__ U, const dfc* __restrict__ in,
-                                                  const Geom& g, int site, int a, const int coord[4], df wp_t,
-                                                  df wm_t) {
+// Row a of the link (or of its adjoint, forward hops) times h0 and h1: each
+// output component is a dot product of six two-float products, accumulated
+// unnormalised; nu = t multiplies by the temporal weight.  Adds the results
+// to the four spin components of acc (colour a).
+__device__ __forceinline__ void hop_row(dfac acc[4], const dfc* __restrict__ U, int V, int ls, int nu, bool fwd,
+                                        int a, const dfac h0[3], const dfac h1[3], const HopSpin& hs, df w) {
+    dfac x0, x1;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const int e_idx = fwd ? nu * 9 + 3 * b + a : nu * 9 + 3 * a + b;
+        const dfc e = U[(size_t)e_idx * V + ls];
+        const float eyh = fwd ? -e.y.hi : e.y.hi, eyl = fwd ? -e.y.lo : e.y.lo;
+        if (b == 0) {
+            x0.x = dfa_prod(e.x.hi, e.x.lo, h0[0].x.s, h0[0].x.e);
+            x0.y = dfa_prod(e.x.hi, e.x.lo, h0[0].y.s, h0[0].y.e);
+            x1.x = dfa_prod(e.x.hi, e.x.lo, h1[0].x.s, h1[0].x.e);
+            x1.y = dfa_prod(e.x.hi, e.x.lo, h1[0].y.s, h1[0].y.e);
+        } else {
+            dfa_add_prod(x0.x, e.x.hi, e.x.lo, h0[b].x.s, h0[b].x.e);
+            dfa_add_prod(x0.y, e.x.hi, e.x.lo, h0[b].y.s, h0[b].y.e);
+            dfa_add_prod(x1.x, e.x.hi, e.x.lo, h1[b].x.s, h1[b].x.e);
+            dfa_add_prod(x1.y, e.x.hi, e.x.lo, h1[b].y.s, h1[b].y.e);
+        }
+        dfa_add_prod(x0.x, -eyh, -eyl, h0[b].y.s, h0[b].y.e);
+        dfa_add_prod(x0.y, eyh, eyl, h0[b].x.s, h0[b].x.e);
+        dfa_add_prod(x1.x, -eyh, -eyl, h1[b].y.s, h1[b].y.e);
+        dfa_add_prod(x1.y, eyh, eyl, h1[b].x.s, h1[b].x.e);
+    }
+    if (nu == 3) {   // temporal weights e^{+-mu} and the boundary sign
+        x0.x = dfa_prod(x0.x.s, x0.x.e, w.hi, w.lo);
+        x0.y = dfa_prod(x0.y.s, x0.y.e, w.hi, w.lo);
+        x1.x = dfa_prod(x1.x.s, x1.x.e, w.hi, w.lo);
+        x1.y = dfa_prod(x1.y.s, x1.y.e, w.hi, w.lo);
+    }
+    dfa_add(acc[0].x, x0.x); dfa_add(acc[0].y, x0.y);
+    dfa_add(acc[1].x, x1.x); dfa_add(acc[1].y, x1.y);
+    const dfac b0 = rot_q(hs.r0 == 1 ? x1 : x0, fwd ? hs.r0q + 2 : hs.r0q);   // times -1 forward
+    const dfac b1 = rot_q(hs.r1 == 1 ? x1 : x0, fwd ? hs.r1q + 2 : hs.r1q);
+    dfa_add(acc[2].x, b0.x); dfa_add(acc[2].y, b0.y);
+    dfa_add(acc[3].x, b1.x); dfa_add(acc[3].y, b1.y);
+}
+
+__device__ __forceinline__ dfc dfc_value(dfac a) {
+    dfc r;
+    r.x = dfa_value(a.x);
+    r.y = dfa_value(a.y);
+    return r;
+}
+
+// The sum over the eight hops of one site, all colours (acc[spin][colour]).
+__device__ __forceinline__ void stencil_hops_df(dfc acc[4][3], const dfc* __restrict__ U, const dfc* __restrict__ in,
+                                                const Geom& g, int site, const int coord[4], df wp_t, df wm_t) {
     const int V = g.V;
+    dfac A[3][4];   // [colour][spin], unnormalised
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) A[a][sp].x = A[a][sp].y = dfa{0.0f, 0.0f};
 #pragma unroll 1
     for (int h = 0; h < 8; ++h) {
         const int nu = h >> 1;
         const bool fwd = (h & 1) != 0;
-        int L, stride;
-        switch (nu) {
-            case 0: L = g.Lx; stride = 1; break;
-            case 1: L = g.Ly; stride = g.Lx; break;
-            case 2: L = g.Lz; stride = g.Lx * g.Ly; break;
-            default: L = g.Lt; stride = g.Lx * g.Ly * g.Lz; break;
-        }
-        const int c = coord[nu];
-        int sn, ls;
-        bool wrap;
-        if (fwd) { wrap = c == L - 1; sn = wrap ? site - (L - 1) * stride : site + stride; ls = site; }
-        else { wrap = c == 0; sn = wrap ? site + (L - 1) * stride : site - stride; ls = sn; }
-        const df flip = (nu == 3 && g.antiperiodic && wrap) ? df(-1) : df(1);
-        const df w = (nu == 3 ? (fwd ? wm_t : wp_t) : df(1)) * flip;
+        const HopGeo hg = hop_geo(g, site, coord, h, wp_t, wm_t);
         const HopSpin hs = hop_spin(nu);
-        dfc h0[3], h1[3];
+        dfac h0[3], h1[3];
+        hop_project(h0, h1, in, V, hg.sn, hs, fwd);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const dfc p0 = in[(size_t)b * V + sn], p1 = in[(size_t)(3 + b) * V + sn];
-            const dfc p2 = in[(size_t)(6 + b) * V + sn], p3 = in[(size_t)(9 + b) * V + sn];
-            const dfc c0 = rot_q(hs.i0 == 3 ? p3 : p2, fwd ? hs.q0 + 2 : hs.q0);
-            const dfc c1 = rot_q(hs.i1 == 3 ? p3 : p2, fwd ? hs.q1 + 2 : hs.q1);
-            h0[b].x = p0.x + c0.x; h0[b].y = p0.y + c0.y;
-            h1[b].x = p1.x + c1.x; h1[b].y = p1.y + c1.y;
-        }
-        dfc x0, x1;
-        x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int e_idx = fwd ? nu * 9 + 3 * b + a : nu * 9 + 3 * a + b;
-            const dfc e = U[(size_t)e_idx * V + ls];
-            const df ey = fwd ? -e.y : e.y;
-            x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
-            x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
-        }
-        if (nu == 3) {
-            x0.x = w * x0.x; x0.y = w * x0.y;
-            x1.x = w * x1.x; x1.y = w * x1.y;
-        }
-        acc[0].x += x0.x; acc[0].y += x0.y;
-        acc[1].x += x1.x; acc[1].y += x1.y;
-        const dfc b0 = rot_q(hs.r0 == 1 ? x1 : x0, fwd ? hs.r0q + 2 : hs.r0q);
-        const dfc b1 = rot_q(hs.r1 == 1 ? x1 : x0, fwd ? hs.r1q + 2 : hs.r1q);
-        acc[2].x += b0.x; acc[2].y += b0.y;
-        acc[3].x += b1.x; acc[3].y += b1.y;
+        for (int a = 0; a < 3; ++a) hop_row(A[a], U, V, hg.ls, nu, fwd, a, h0, h1, hs, hg.w);
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) acc[sp][a] = dfc_value(A[a][sp]);
+}
+
+// The same for colour a only (three threads per site).
+__device__ __forceinline__ void stencil_hops_df_a(dfc acc[4], const dfc* __restrict__ U, const dfc* __restrict__ in,
+                                                  const Geom& g, int site, int a, const int coord[4], df wp_t,
+                                                  df wm_t) {
+    const int V = g.V;
+    dfac A[4];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) A[sp].x = A[sp].y = dfa{0.0f, 0.0f};
+#pragma unroll 1
+    for (int h = 0; h < 8; ++h) {
+        const int nu = h >> 1;
+        const bool fwd = (h & 1) != 0;
+        const HopGeo hg = hop_geo(g, site, coord, h, wp_t, wm_t);
+        const HopSpin hs = hop_spin(nu);
+        dfac h0[3], h1[3];
+        hop_project(h0, h1, in, V, hg.sn, hs, fwd);
+        hop_row(A, U, V, hg.ls, nu, fwd, a, h0, h1, hs, hg.w);
+    }
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) acc[sp] = dfc_value(A[sp]);
 }
 
 // precision-generic conversions (float via the integer pipe, see nk_common.cuh)

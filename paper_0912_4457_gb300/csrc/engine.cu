@@ -192,6 +192,7 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     // near the imaginary axis its sign is ill conditioned, and two-float
     // arithmetic there left single sources of the 16^3 x 32 test at 2.5e-8
     in.df_inner = 0;
+    in.p_shared = 0;
     L.total = off;
     return L;
 }
@@ -337,10 +338,11 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     nk::Outer o = Lw.o;
     nk::Inner in = Lw.in;
     in.p_fixed = p;
+    in.p_shared = (flags & NK_SHARED_P) ? 1 : 0;
     enqueue_load_sources(c, o, b_dev, n_rhs, L);
     L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_fill_int(Lw.kused, n_rhs, o.k, st); });
     enqueue_outer(c, o, mixed, j0, L);
-    L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_lanczos(in, st); });
+    L.run(NK_CLASS_INNER, nk::inner_launches(in), [&] { nk::launch_inner_lanczos(in, st); });
     cudaError_t e = cudaSuccess;
     L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(in, st); });
     if (e != cudaSuccess) return e;
@@ -377,6 +379,7 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
     nk::Outer o = Lw.o;
     nk::Inner in = Lw.in;
     in.p_fixed = p;
+    in.p_shared = (flags & NK_SHARED_P) ? 1 : 0;
     in.kstride = kmax;
     enqueue_load_sources(c, o, b_dev, n_rhs, L);
     enqueue_outer_init(o, mixed, j0, L);
@@ -394,7 +397,7 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
         nk::Inner ic = in;
         ic.k = kc;
         ic.ell = std::min(ell, kc);
-        L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_lanczos(ic, st); });
+        L.run(NK_CLASS_INNER, nk::inner_launches(ic), [&] { nk::launch_inner_lanczos(ic, st); });
         cudaError_t e = cudaSuccess;
         L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(ic, st); });
         if (e != cudaSuccess) return e;
@@ -898,7 +901,7 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     if (ms_per_step) *ms_per_step = per_step;
     if (cache_path) {
         if (FILE* f = std::fopen(cache_path, "a")) {
-            std::fprintf(f, "nk_launch %d %d %d %d %d %d %d %d %d %d %d %d %d %d %.6g\n", c->dims[0], c->dims[1],
+            std::fprintf(f, "nk_launch %d %d %d %d %d %d %d %d %d %d %d %d %d %d %.17g\n", c->dims[0], c->dims[1],
                          c->dims[2], c->dims[3], n_rhs, ts, mixed, best.stencil_threads, best.stencil_order,
                          best.step2_blocks, best.early_threads, best.early_order, best.stencil_split,
                          best.early_split, per_step);

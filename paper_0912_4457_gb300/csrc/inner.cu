@@ -643,15 +643,26 @@ __device__ void lu_coefficients(int n, T* e, T* f, T* eh, T* fh, const T* dinv) 
     __syncthreads();
 }
 
+// phase 0: p of this RHS, then steps 3-4.  With a p shared by the batch
+// (Inner::p_shared) two launches: phase 1 estimates z_min, z_max of every RHS
+// and stops; phase 2 takes p from the extremes over the batch and runs steps 3-4.
 template <typename T>
-__global__ void __launch_bounds__(256) k_inner(Inner in) {
+__global__ void __launch_bounds__(256) k_inner(Inner in, int phase) {
     __shared__ double2 sh2[33];
     __shared__ double sh1[32];
     __shared__ double2 s_agg[32];   // warp aggregates of the group scans, 16 per group
     __shared__ int s_info;
     const int rhs = blockIdx.x;
     const int k = in.k, L = in.ell;
-    if (in.status[rhs] != kStatusOK) return;
+    if (in.status[rhs] != kStatusOK) {
+        // no estimate from this RHS (a frozen RHS of adaptive k keeps the one
+        // from the H_k it converged with)
+        if (phase == 1 && threadIdx.x == 0 && in.status[rhs] != kStatusConverged) {
+            in.zmin[rhs] = 0.0;
+            in.zmax[rhs] = 0.0;
+        }
+        return;
+    }
     const int ks = in.kstride > 0 ? in.kstride : k;   // row stride of the outer H_k arrays and of c
     const double2* al = in.alpha + (size_t)rhs * ks;
     const double2* be = in.beta + (size_t)rhs * ks;
@@ -706,7 +717,20 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
 
     // ---- p (Eq. popt) --------------------------------------------------------
     double p = in.p_fixed;
-    if (!(p > 0.0)) {
+    if (!(p > 0.0) && phase == 2) {
+        // Eq. popt with z_min = min |z| and z_max = max |z| of A, estimated as
+        // the extremes over the batch's H_k (all RHS share A); every CTA forms
+        // the same value in the same order
+        double zmn = 0.0, zmx = 0.0;
+        for (int r = 0; r < in.n_rhs; ++r) {
+            const double a = in.zmin[r], b = in.zmax[r];
+            if (a > 0.0 && b > 0.0 && isfinite(a) && isfinite(b)) {
+                zmn = zmn > 0.0 ? fmin(zmn, a) : a;
+                zmx = fmax(zmx, b);
+            }
+        }
+        p = zmn > 0.0 ? 1.0 / sqrt(zmn * zmx) : 1.0;
+    } else if (!(p > 0.0)) {
         const double x0 = 1.0 / sqrt((double)k);
         for (int i = threadIdx.x; i < k; i += blockDim.x) x[i] = t_from(mk(x0, 0.0), T());
         __syncthreads();
@@ -768,6 +792,7 @@ __global__ void __launch_bounds__(256) k_inner(Inner in) {
         }
         p = 1.0 / sqrt(zmin * zmax);
         if (threadIdx.x == 0) { in.zmin[rhs] = zmin; in.zmax[rhs] = zmax; }
+        if (phase == 1) return;
     } else if (threadIdx.x == 0) {
         in.zmin[rhs] = 0.0; in.zmax[rhs] = 0.0;
     }
@@ -1075,12 +1100,15 @@ size_t inner_smem_bytes(int k, bool two_sided) {
 
 void launch_inner_lanczos(const Inner& in, cudaStream_t st) {
     size_t smem = inner_smem_bytes(in.k, in.two_sided);   // the same for the two-float types
-    if (in.df_inner) {
-        if (in.two_sided) k_inner<dfc><<<in.n_rhs, 256, smem, st>>>(in);
-        else k_inner<df><<<in.n_rhs, 256, smem, st>>>(in);
-    } else {
-        if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, smem, st>>>(in);
-        else k_inner<double><<<in.n_rhs, 256, smem, st>>>(in);
+    const bool shared = in.p_shared && !(in.p_fixed > 0.0);
+    for (int phase = shared ? 1 : 0; phase <= (shared ? 2 : 0); ++phase) {
+        if (in.df_inner) {
+            if (in.two_sided) k_inner<dfc><<<in.n_rhs, 256, smem, st>>>(in, phase);
+            else k_inner<df><<<in.n_rhs, 256, smem, st>>>(in, phase);
+        } else {
+            if (in.two_sided) k_inner<double2><<<in.n_rhs, 256, smem, st>>>(in, phase);
+            else k_inner<double><<<in.n_rhs, 256, smem, st>>>(in, phase);
+        }
     }
 }
 

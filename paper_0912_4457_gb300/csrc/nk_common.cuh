@@ -241,6 +241,45 @@ __device__ __forceinline__ double df_to_double(df a) { return f2d_int(a.hi) + f2
 struct __align__(16) dfc {
     df x, y;
 };
+
+// Unnormalised two-float accumulator: the value is s + e, with |e| small
+// against |s| but not renormalised after each step.  Adding an exact product
+// (TwoProd via FMA, including the cross terms of two-float operands) or
+// another value is TwoSum on the leading parts and a plain FP32 sum of the
+// trailing parts: 12 and 8 FP32 instructions, against 18 and 11 for the
+// normalised product and sum (the accumulation of Ogita, Rump and Oishi's
+// compensated dot product, applied to two-float operands).  dfa_value
+// renormalises once at the end.
+struct dfa {
+    float s, e;
+};
+__device__ __forceinline__ dfa dfa_of(df a) { return {a.hi, a.lo}; }
+__device__ __forceinline__ dfa dfa_neg(dfa a) { return {-a.s, -a.e}; }
+// (ah + al) (bh + bl) up to the al bl term
+__device__ __forceinline__ dfa dfa_prod(float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    return {p, e};
+}
+// a += s + e
+__device__ __forceinline__ void dfa_add(dfa& a, float s, float e) {
+    const float t = __fadd_rn(a.s, s);
+    const float v = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, v)), __fsub_rn(s, v));
+    a.s = t;
+    a.e = __fadd_rn(a.e, __fadd_rn(e, err));
+}
+__device__ __forceinline__ void dfa_add(dfa& a, dfa b) { dfa_add(a, b.s, b.e); }
+__device__ __forceinline__ void dfa_add_prod(dfa& a, float ah, float al, float bh, float bl) {
+    const dfa p = dfa_prod(ah, al, bh, bl);
+    dfa_add(a, p.s, p.e);
+}
+__device__ __forceinline__ df dfa_value(dfa a) { return df_fast_two_sum(a.s, a.e); }
+struct dfac {
+    dfa x, y;
+};
 template <> struct C2<df> { typedef dfc T; };
 static_assert(sizeof(dfc) == 16, "two-float complex is 16 bytes");
 

@@ -144,6 +144,8 @@ struct Inner {
     const double2* beta;
     const double2* gamma;
     double p_fixed;        // > 0: use it; else estimate
+    int p_shared;          // 1: one p for the batch, from the extremes of the z_min, z_max
+                           // estimates over its RHS (all RHS share A); 0: p per RHS
     double* p;             // [rhs] out
     double* zmin;          // [rhs] out
     double* zmax;          // [rhs] out
@@ -171,6 +173,8 @@ __host__ __device__ constexpr size_t inner_work_elems(int k) { return (size_t)kI
 constexpr int kMaxInnerK = 1536;
 
 void launch_inner_lanczos(const Inner& in, cudaStream_t st);
+// kernels launch_inner_lanczos launches: two with a p shared by the batch
+inline int inner_launches(const Inner& in) { return in.p_shared && !(in.p_fixed > 0.0) ? 2 : 1; }
 int launch_rhi(const Inner& in, cudaStream_t st);  // returns cudaError_t
 void launch_inner_combine(const Inner& in, cudaStream_t st);
 // Kernel attributes that must be set outside stream capture (once per device).

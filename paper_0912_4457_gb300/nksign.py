@@ -33,6 +33,7 @@ NK_DOUBLE_PASS = 0x2
 NK_NO_GRAPH = 0x10
 NK_PROFILE = 0x20
 NK_ASYNC = 0x40
+NK_SHARED_P = 0x80
 NK_MAX_RHS = 12
 NK_NCLASS = 9
 CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other", "step2_df"]

@@ -461,3 +461,29 @@ def test_async_two_contexts_match_sync(c1):
     assert rc == NK_EINVAL
     ctx_a.close()
     ctx_b.close()
+
+
+def test_shared_p_batch_matches_oracle(c1):
+    """NK_SHARED_P: one p for the batch from the extremes of the per-RHS
+    z_min, z_max estimates (Eq. popt, footnote: spectral information of A);
+    each RHS equals the oracle's nested solve with that p."""
+    dims, U, b, truth = c1
+    mu, k, ell = 0.3, 512, 128
+    srcs = np.concatenate([b, inputs.gaussian_sources(dims, 41, n_rhs=1), inputs.point_sources(dims)[5:6]])
+    est = [nested.sign_apply(U, dims, mu, M_W, srcs[i], k, ell)[1] for i in range(3)]
+    p_sh = nested.shared_p([(e["p"], e["z_min"], e["z_max"]) for e in est])
+    ctx = make_ctx(dims, 101, mu)
+    y, st, rc = ctx.sign_apply(srcs, k, ell, flags=NK_FP64 | nksign.NK_SHARED_P)
+    assert rc == 0
+    assert st["launches"] > 0
+    for i in range(3):
+        assert st["z_min"][i] == pytest.approx(est[i]["z_min"], rel=1e-9)
+        assert st["z_max"][i] == pytest.approx(est[i]["z_max"], rel=1e-9)
+        assert st["p"][i] == pytest.approx(p_sh, rel=1e-9)
+        y_or, _ = nested.sign_apply(U, dims, mu, M_W, srcs[i], k, ell, p=p_sh)
+        assert rel(y[i], y_or) < 1e-10
+    # without the flag each RHS keeps its own estimate
+    _, st1, _ = ctx.sign_apply(srcs, k, ell, flags=NK_FP64)
+    for i in range(3):
+        assert st1["p"][i] == pytest.approx(est[i]["p"], rel=1e-9)
+    ctx.close()

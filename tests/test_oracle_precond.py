@@ -169,3 +169,35 @@ def test_spectral_estimates_hermitian():
     assert zmax == pytest.approx(z[-1], rel=1e-10)
     assert zmin == pytest.approx(z[0], rel=1e-10)
     assert p == pytest.approx(precond.p_opt(z[0], z[-1]), rel=1e-10)
+
+
+@pytest.mark.parametrize("hermitian", [True, False])
+def test_shared_p_is_p_opt_of_the_batch_spectrum(hermitian):
+    """Two sources that each excite part of the spectrum of A = diag(w): each
+    H_k (k = the size of its part, so its Ritz values are exact) sees only
+    its part, and the batch's p (Eq. popt with z_min, z_max of A, footnote)
+    is p_opt(min |w|, max |w|) over the whole spectrum."""
+    from oracle import krylov
+    lam1 = np.array([0.4, -0.55, 0.8, -1.1, 1.5])
+    lam2 = np.array([1.0, -1.7, 2.2, -2.6, 3.0])
+    w = np.concatenate([lam1, lam2]).astype(np.complex128)
+    if not hermitian:
+        w = w * np.exp(0.15j * np.arange(w.size))     # |w| unchanged, off the real axis
+    rng = np.random.default_rng(4)
+    wt = rng.uniform(0.5, 1.5, w.size)
+    est = []
+    for part in (slice(0, 5), slice(5, 10)):
+        x = np.zeros(w.size, np.complex128)
+        x[part] = wt[part]
+        if hermitian:
+            res = krylov.lanczos(lambda v: w.real * v, x.real, 5)
+        else:
+            res = krylov.two_sided_lanczos(lambda v: w * v, lambda v: np.conj(w) * v, x, 5)
+        # exact Ritz values: no screening of unconverged ones needed
+        est.append(nested.estimate_p(res.alpha, res.beta, res.gamma, iters=400, resid_tol=np.inf))
+    assert est[0][1] == pytest.approx(0.4, rel=1e-8) and est[0][2] == pytest.approx(1.5, rel=1e-8)
+    assert est[1][1] == pytest.approx(1.0, rel=1e-8) and est[1][2] == pytest.approx(3.0, rel=1e-8)
+    assert nested.shared_p(est) == pytest.approx(precond.p_opt(0.4, 3.0), rel=1e-8)
+    # one RHS: its own estimate; entries without an estimate are skipped
+    assert nested.shared_p(est[:1]) == pytest.approx(est[0][0], rel=1e-15)
+    assert nested.shared_p([(1.0, 0.0, 0.0)] + est) == nested.shared_p(est)
