@@ -252,7 +252,8 @@ int nk_outer_lanczos_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, uns
  * tridiagonal Ritz matrices (HOST arrays in the nk_outer_lanczos_dev layout):
  * c_r = V_l sgn(H_l) e_1 as complex doubles in the HOST array c[r*k + i].
  * hermitian = 1 uses the real Lanczos path (H real symmetric), 0 the
- * two-sided one.  p > 0 fixes p; p <= 0 estimates it (Eq. popt).  Needs a
+ * two-sided one.  p > 0 fixes p; p == 0 estimates it per RHS (Eq. popt);
+ * p < 0 estimates one p for the batch (as NK_SHARED_P).  Needs a
  * context only for its device and scratch memory.  Blocks. */
 int nk_inner_sign(nk_ctx* ctx, const double* alpha, const double* beta, const double* gamma,
                   int n_rhs, int k, int ell, double p, int hermitian, double* c,

@@ -1062,7 +1062,8 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     NK_CUDA(c, cudaMemcpy(Lw.o.gamma, gamma, cb, cudaMemcpyHostToDevice));
     NK_CUDA(c, cudaMemset(Lw.o.status, 0, sizeof(int) * n_rhs));
     nk::Inner in = Lw.in;
-    in.p_fixed = p;
+    in.p_fixed = p > 0.0 ? p : 0.0;
+    in.p_shared = p < 0.0 ? 1 : 0;
     nk::launch_inner_lanczos(in, 0);
     cudaError_t e = (cudaError_t)nk::launch_rhi(in, 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "launch_rhi");

@@ -463,27 +463,48 @@ def test_async_two_contexts_match_sync(c1):
     ctx_b.close()
 
 
-def test_shared_p_batch_matches_oracle(c1):
-    """NK_SHARED_P: one p for the batch from the extremes of the per-RHS
-    z_min, z_max estimates (Eq. popt, footnote: spectral information of A);
-    each RHS equals the oracle's nested solve with that p."""
+def test_shared_p_inner_matches_oracle():
+    """One p for the batch (Eq. popt, footnote: spectral information of A),
+    the same H_k on both sides: per-RHS z_min, z_max, the batch's p from
+    their extremes, and c of every RHS with that p."""
+    dims = (4, 4, 4, 4)
+    U = links(dims, 101)
+    mu, k, ell = 0.3, 384, 96
+    A, Ad, herm = nested.operator(U, dims, mu, M_W)
+    srcs = np.concatenate([inputs.gaussian_sources(dims, 201), inputs.gaussian_sources(dims, 41),
+                           inputs.point_sources(dims)[5:6]])
+    outs = [nested.outer_basis(A, Ad, srcs[i], k, herm) for i in range(3)]
+    est = [nested.estimate_p(o.alpha, o.beta, o.gamma) for o in outs]
+    p_sh = nested.shared_p(est)
+    ctx = make_ctx(dims, 101, mu)
+    c, st, rc = ctx.inner_sign(np.stack([o.alpha for o in outs]), np.stack([o.beta for o in outs]),
+                               np.stack([o.gamma for o in outs]), ell, p=-1.0, hermitian=herm)
+    assert rc == 0
+    for i in range(3):
+        assert st["z_min"][i] == pytest.approx(est[i][1], rel=1e-10)
+        assert st["z_max"][i] == pytest.approx(est[i][2], rel=1e-10)
+        assert st["p"][i] == pytest.approx(p_sh, rel=1e-10)
+        c_ref, _ = nested.inner_sign(outs[i].alpha, outs[i].beta, outs[i].gamma, ell, p_sh, herm)
+        assert rel(c[i], c_ref) < 1e-10
+    ctx.close()
+
+
+def test_shared_p_whole_solve(c1):
+    """NK_SHARED_P through a whole batched solve: every RHS reports the same
+    p, the one its batch's own z_min, z_max estimates give, and each result
+    is the oracle's nested solve with that p (converged k, so rounding-level
+    differences of H_k do not matter)."""
     dims, U, b, truth = c1
     mu, k, ell = 0.3, 512, 128
     srcs = np.concatenate([b, inputs.gaussian_sources(dims, 41, n_rhs=1), inputs.point_sources(dims)[5:6]])
-    est = [nested.sign_apply(U, dims, mu, M_W, srcs[i], k, ell)[1] for i in range(3)]
-    p_sh = nested.shared_p([(e["p"], e["z_min"], e["z_max"]) for e in est])
     ctx = make_ctx(dims, 101, mu)
     y, st, rc = ctx.sign_apply(srcs, k, ell, flags=NK_FP64 | nksign.NK_SHARED_P)
     assert rc == 0
-    assert st["launches"] > 0
+    p = st["p"][0]
+    assert p == pytest.approx(1.0 / np.sqrt(min(st["z_min"]) * max(st["z_max"])), rel=1e-12)
+    assert all(q == p for q in st["p"])
     for i in range(3):
-        assert st["z_min"][i] == pytest.approx(est[i]["z_min"], rel=1e-9)
-        assert st["z_max"][i] == pytest.approx(est[i]["z_max"], rel=1e-9)
-        assert st["p"][i] == pytest.approx(p_sh, rel=1e-9)
-        y_or, _ = nested.sign_apply(U, dims, mu, M_W, srcs[i], k, ell, p=p_sh)
+        y_or, _ = nested.sign_apply(U, dims, mu, M_W, srcs[i], k, ell, p=p)
         assert rel(y[i], y_or) < 1e-10
-    # without the flag each RHS keeps its own estimate
-    _, st1, _ = ctx.sign_apply(srcs, k, ell, flags=NK_FP64)
-    for i in range(3):
-        assert st1["p"][i] == pytest.approx(est[i]["p"], rel=1e-9)
+    assert rel(y[0], truth[mu]) < 1e-9
     ctx.close()
