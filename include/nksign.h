@@ -124,11 +124,20 @@ int nk_load_links_dev(nk_ctx* ctx, const double* U_dev, void* stream);
  * mass m_w (kappa = 1/(8 + 2 m_w); requires 8 + 2 m_w > 0). */
 int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
 
-/* Precision schedule for NK_MIXED: outer steps j < j0 use the FP64 stencil,
- * j >= j0 the FP32 stencil.  j0 < 0 selects the default k/4.  Everything
- * other than the stencil (recurrence coefficients, inner products, basis,
- * preconditioning, inner projection, RHi, lift) stays FP64. */
+/* Precision schedule for NK_MIXED (the outer recurrence, App. A/B): outer
+ * steps j < j0 apply the stencil in two-float arithmetic (about 48 bits, on
+ * the FP32 pipe; FP32 links hi + lo), steps j >= j0 in FP32.  j0 < 0 selects
+ * the default k/4.  The recurrence itself (the update of r and l, their
+ * inner products, the basis) runs in FP64 before step j1 and in two-float
+ * arithmetic from j1 on (nk_set_df_recurrence; default j1 = j0).  The
+ * coefficients H_k, p, the LU of p H_k, the inner Lanczos and RHi are FP64
+ * in every schedule; the lift sums in two-float arithmetic. */
 int nk_set_precision(nk_ctx* ctx, int j0);
+
+/* The first outer step j1 of NK_MIXED whose recurrence runs in two-float
+ * arithmetic (see nk_set_precision); j1 < 0 selects j0, and j1 > j0 acts as
+ * j0.  Takes effect with the next solve. */
+int nk_set_df_recurrence(nk_ctx* ctx, int j1);
 
 /* Adaptive k: the outer size at the first convergence check (even; 0 selects
  * NK_ADAPT_FIRST(l)).  A predicted k (nk_predict_sizes) minus two check

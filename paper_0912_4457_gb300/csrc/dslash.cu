@@ -581,9 +581,11 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
         };
         const double2 c1 = coef[1];   // zero at j = 0 (the previous vector is then any valid one)
         const int jp = j > 0 ? j - 1 : j;
-        if constexpr (std::is_same<R, float>::value) {
-            // late steps of the mixed schedule: the epilogue in two-float
-            // arithmetic on the rings
+        bool ring_epilogue = std::is_same<R, float>::value;
+        if constexpr (std::is_same<R, df>::value) ring_epilogue = j >= o.ring_from;
+        if constexpr (!std::is_same<R, double>::value) if (ring_epilogue) {
+            // steps of the mixed schedule from ring_from on (every FP32 stencil
+            // step): the epilogue in two-float arithmetic on the rings
             const dfc scr = dfc_of2(coef[0]), c1d = dfc_of2(c1);
             // one accumulator per spin component: four short dependency chains
             // of two-float additions instead of one of twelve
@@ -616,7 +618,8 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
             });
             acc = make_double2(df_to_double((ax[0] + ax[1]) + (ax[2] + ax[3])),
                                df_to_double((ay[0] + ay[1]) + (ay[2] + ay[3])));
-        } else {
+        }
+        if (!ring_epilogue) {
             // the scale 1/n_j (1/m_j) in the stencil's precision
             T scr;
             scr.x = from_double<R>(coef[0].x);

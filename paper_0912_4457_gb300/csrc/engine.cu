@@ -25,13 +25,13 @@ struct DevBuf {
 struct GraphKey {
     const void* b;
     void* y;
-    int n_rhs, k, ell, j0;
+    int n_rhs, k, ell, j0, j1;
     unsigned flags;
     double p, mu, mw;
     int overlap;
     bool operator<(const GraphKey& o) const {
-        return std::tie(b, y, n_rhs, k, ell, j0, flags, p, mu, mw, overlap) <
-               std::tie(o.b, o.y, o.n_rhs, o.k, o.ell, o.j0, o.flags, o.p, o.mu, o.mw, o.overlap);
+        return std::tie(b, y, n_rhs, k, ell, j0, j1, flags, p, mu, mw, overlap) <
+               std::tie(o.b, o.y, o.n_rhs, o.k, o.ell, o.j0, o.j1, o.flags, o.p, o.mu, o.mw, o.overlap);
     }
 };
 
@@ -44,6 +44,7 @@ struct nk_ctx {
     double mu = 0.0, m_w = 0.0;
     bool mu_set = false;
     int j0 = -1;
+    int j1 = -1;   // first outer step whose recurrence runs in two-float arithmetic (< 0: j0)
     int adapt_start = 0;   // adaptive k: first check (0: NK_ADAPT_FIRST(l))
     bool links = false;
     double2* U64 = nullptr;
@@ -155,6 +156,8 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     if (two_sided) o.p32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
     o.qdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     if (two_sided) o.pdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
+    o.q_df_from = 1 << 30;
+    o.ring_from = 1 << 30;
     if (mixed) {
         o.qr = (nk::dfc*)take((size_t)N * 16 * 3 * n_rhs);
         if (two_sided) o.pr = (nk::dfc*)take((size_t)N * 16 * 3 * n_rhs);
@@ -293,7 +296,8 @@ void enqueue_outer_init(const nk::Outer& o, bool mixed, int j0, Launcher& L, boo
 }
 
 // steps j in [j_begin, j_end); step 2 runs for every step but the last of the
-// whole recurrence (j = o.k - 1)
+// whole recurrence (j = o.k - 1).  Mixed schedule: steps j >= o.ring_from
+// (<= j0) run the recurrence in two-float arithmetic on the rings.
 void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int j_begin, int j_end, Launcher& L) {
     const Geom g = geom_of(c);
     const double kap = kappa_of(c);
@@ -304,7 +308,7 @@ void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int 
         const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
         L.run(cls, 1, [&] { nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
         if (j < o.k - 1) {
-            const bool ring = mixed && j >= j0;
+            const bool ring = mixed && j >= o.ring_from;
             L.run(ring ? NK_CLASS_STEP2_DF : NK_CLASS_STEP2, 1, [&] {
                 nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), ring, st);
             });
@@ -327,6 +331,7 @@ void enqueue_load_sources(nk_ctx* c, const nk::Outer& o, const double* b_dev, in
 }
 
 int effective_j0(const nk_ctx* c, int k) { return c->j0 < 0 ? k / 4 : std::min(c->j0, k); }
+int effective_j1(const nk_ctx* c, int j0) { return c->j1 < 0 ? j0 : std::min(c->j1, j0); }
 
 // Enqueues a whole solve (device pointers in ABI layout). Returns cudaError_t of launches.
 cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_dev, int n_rhs,
@@ -336,6 +341,8 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     const int j0 = effective_j0(c, Lw.o.k);
     cudaStream_t st = L.st;
     nk::Outer o = Lw.o;
+    if (mixed) o.ring_from = effective_j1(c, j0);
+    if (mixed && o.qr && !o.q_ring) o.q_df_from = o.ring_from + 1;   // written by the two-float step 2
     nk::Inner in = Lw.in;
     in.p_fixed = p;
     in.p_shared = (flags & NK_SHARED_P) ? 1 : 0;
@@ -377,6 +384,8 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
     const bool mixed = (flags & NK_MIXED) != 0;
     const int j0 = effective_j0(c, kmax);
     nk::Outer o = Lw.o;
+    if (mixed) o.ring_from = effective_j1(c, j0);
+    if (mixed && o.qr && !o.q_ring) o.q_df_from = o.ring_from + 1;
     nk::Inner in = Lw.in;
     in.p_fixed = p;
     in.p_shared = (flags & NK_SHARED_P) ? 1 : 0;
@@ -556,7 +565,7 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
                                        notconv, checks);
         if (e != cudaSuccess) return cuda_fail(c, e, "adaptive solve");
     } else if (use_graph) {
-        GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, flags, p, c->mu, c->m_w, overlap ? 1 : 0};
+        GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, c->j1, flags, p, c->mu, c->m_w, overlap ? 1 : 0};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             cudaStream_t cs;
@@ -708,6 +717,12 @@ int nk_set_precision(nk_ctx* c, int j0) {
     return NK_OK;
 }
 
+int nk_set_df_recurrence(nk_ctx* c, int j1) {
+    if (!c) return NK_EINVAL;
+    c->j1 = j1;
+    return NK_OK;
+}
+
 int nk_set_adapt_start(nk_ctx* c, int k_first) {
     if (!c || k_first < 0) return NK_EINVAL;
     c->adapt_start = k_first;
@@ -768,6 +783,9 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
     enqueue_load_sources(c, Lw.o, src, n_rhs, L);
     // the copies of the stencil input that `prec` reads are made by the last warm step
     const int j0 = prec == 48 ? k : 0;
+    // the two-float stencil steps with the epilogue the solves will use
+    if (mixed) Lw.o.ring_from = prec == 48 && c->j1 != 0 ? k : 0;
+    const bool ring = mixed && Lw.o.ring_from == 0;
     enqueue_outer(c, Lw.o, mixed, j0, L, kTuneWarm);
     const Geom g = geom_of(c);
     const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
@@ -781,7 +799,7 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
             nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
             // no copy for the next stencil: the stencil of the next repetition
             // must read q_j again, so that every repetition recomputes the same step
-            nk::launch_outer_step2(Lw.o, kTuneWarm, nk::kCopyNone, mixed && prec == 32, st);
+            nk::launch_outer_step2(Lw.o, kTuneWarm, nk::kCopyNone, ring, st);
         }
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
 // Step 2 of the late (FP32-stencil) steps of the mixed schedule in two-float
 // arithmetic on the FP32 pipe, on the two-float rings: r and l (left in ring slot j + 1
 // by the stencil kernel) are updated with q_j and p_j from the rings; r is
-// also written to the FP64 basis (one FP64 addition per component), and the
+// also written to the basis Q (as two-float values in a single-pass solve,
+// else FP64: one FP64 addition per component), and the
 // FP32 copy the next FP32 stencil reads is the high part (a two-float
 // stencil reads the ring).  The FP32 stencil of the late steps perturbs the
 // recurrence at 1e-7; 48-bit arithmetic adds about 1e-14.  The all-FP64
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_
     const dfc* __restrict__ qj = ring_q(o, rhs, j);
     dfc* __restrict__ r = ring_q(o, rhs, j + 1);
     double2* __restrict__ rq = outer_q(o, rhs, j + 1);
+    const bool qdf = j + 1 >= o.q_df_from;   // the basis column is kept in two-float form
     const dfc* __restrict__ pj = TS ? ring_p(o, rhs, j) : nullptr;
     dfc* __restrict__ l = TS ? ring_p(o, rhs, j + 1) : nullptr;
     const size_t vb = (size_t)rhs * o.N;
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_
                 rr.y = rr.y - c3.x * q.y;
             }
             r[i] = rr;
-            rq[i] = double2_of(rr);
+            if (qdf) reinterpret_cast<dfc*>(rq)[i] = rr;
+            else rq[i] = double2_of(rr);
             if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(rr.x.hi, rr.y.hi);
             if (TS) {
                 const dfc pv = pj[i];
@@ -314,9 +317,10 @@ __global__ void __launch_bounds__(kThreads) k_lift_df(Outer o, const double2* __
     const double2* Qr = o.Q + (size_t)rhs * o.qcols * o.N;
     dfc acc[2];
     acc[0].x = df(0); acc[0].y = df(0); acc[1] = acc[0];
+    const int j1 = min(ku, o.q_df_from);   // columns [j1, ku) are two-float already
     for (int j = 0; j < ku; ++j) {
         const dfc c = cs[j];
-        const dfc v = dfc_of(Qr[(size_t)j * o.N + i]);
+        const dfc v = j < j1 ? dfc_of(Qr[(size_t)j * o.N + i]) : reinterpret_cast<const dfc*>(Qr)[(size_t)j * o.N + i];
         dfc& a = acc[j & 1];
         a.x += c.x * v.x - c.y * v.y;
         a.y += c.x * v.y + c.y * v.x;

@@ -77,6 +77,16 @@ struct Outer {
     // (Q, for the lift).  nullptr in the all-FP64 schedule.
     dfc* qr;
     dfc* pr;
+    // Q columns from q_df_from on hold two-float values (dfc, 16 bytes like
+    // double2): the late steps of the mixed schedule, whose recurrence runs in
+    // two-float arithmetic, write them without an FP64 conversion, and the
+    // two-float lift reads them as they are.  Larger than k otherwise.
+    int q_df_from;
+    // Mixed schedule: steps j >= ring_from run the recurrence (the stencil
+    // kernel's epilogue and step 2) in two-float arithmetic on the rings;
+    // the steps before it in FP64.  ring_from <= j0 (the FP32 stencil steps
+    // always run on the rings).  Larger than k otherwise.
+    int ring_from;
 };
 
 __host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {

@@ -45,7 +45,7 @@ ERROR_NAMES = {
 }
 
 EXPORTED = [
-    "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision",
+    "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision", "nk_set_df_recurrence",
     "nk_set_adapt_start",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
@@ -130,6 +130,7 @@ def load_library(path: str = LIB_PATH):
         "nk_load_links_dev": ([P, P, P], I),
         "nk_set_mu_mw": ([P, D, D], I),
         "nk_set_precision": ([P, I], I),
+        "nk_set_df_recurrence": ([P, I], I),
         "nk_set_adapt_start": ([P, I], I),
         "nk_sign_apply": ([P, dp, I, I, I, D, D, U, dp, ctypes.POINTER(NkStats)], I),
         "nk_sign_apply_dev": ([P, P, I, I, I, D, D, U, P, ctypes.POINTER(NkStats), P], I),
@@ -242,6 +243,9 @@ class Context:
 
     def set_precision(self, j0: int):
         self._check(self._lib.nk_set_precision(self.h, int(j0)))
+
+    def set_df_recurrence(self, j1: int):
+        self._check(self._lib.nk_set_df_recurrence(self.h, int(j1)))
 
     def set_adapt_start(self, k_first: int):
         self._check(self._lib.nk_set_adapt_start(self.h, int(k_first)))
