@@ -210,14 +210,21 @@ def run_reference(args, w, rank):
     return 0
 
 
+def j1_of(w, args):
+    """First outer step whose recurrence runs in two-float arithmetic."""
+    j1 = args.j1 if args.j1 is not None else w.get("j1", -1)
+    return w["j0"] if j1 < 0 else min(j1, w["j0"])
+
+
 def config_of(w, args):
     return {"workload": args.workload, "lattice": "x".join(str(d) for d in w["dims"]), "mu": w["mu"],
             "m_w": w["m_w"], "k": w["k"], "ell": w["ell"], "n_rhs": w["n_rhs"],
             "sources": "12 spin-colour point sources at the origin" if w["source"] == "point" else "gaussian",
             "links": "U = exp(i eps X), plaquette 0.59, seed %d" % w["link_seed"],
-            "precision": ("two-float (48-bit) stencil for outer steps < %d, FP32 stencil after; recurrences, "
-                          "inner products, preconditioning, inner Lanczos, RHi and lift FP64" % w["j0"])
-                         if w["mixed"] else "FP64",
+            "precision": ("two-float (48-bit) stencil for outer steps < %d, FP32 stencil after; the recurrence "
+                          "(vector updates, inner products, basis) FP64 before step %d and two-float from it on; "
+                          "H_k, p, LU of pH_k, inner Lanczos and RHi FP64; lift two-float"
+                          % (w["j0"], j1_of(w, args))) if w["mixed"] else "FP64",
             "p": "one p per batch: Eq. popt with z_min, z_max of A estimated as the extremes over the "
                  "batch's H_k (power / inverse iteration)",
             "graph": True, "parallelism": "replicas" if args.gpus > 1 else "single",
@@ -291,6 +298,7 @@ def run_gpu(args, w, rank, world, local_rank):
     ctx.load_links(U)
     ctx.set_mu_mw(w["mu"], w["m_w"])
     ctx.set_precision(w.get("j0", -1))
+    ctx.set_df_recurrence(j1_of(w, args))
     # launch shape of the outer recurrence: timed on 16 synthetic steps, kept
     shape, tune_ms = ctx.autotune(n_rhs, flags, args.tune_cache)
     stream = torch.cuda.current_stream()
@@ -306,6 +314,7 @@ def run_gpu(args, w, rank, world, local_rank):
         c2.load_links(U)
         c2.set_mu_mw(w["mu"], w["m_w"])
         c2.set_precision(w.get("j0", -1))
+        c2.set_df_recurrence(j1_of(w, args))
         c2.set_launch(n_rhs, flags, *shape)
         ctxs.append(c2)
         ys.append(torch.zeros_like(b_dev))
@@ -469,6 +478,7 @@ def run_ncu(args, w):
     ctx.load_links(U)
     ctx.set_mu_mw(w["mu"], w["m_w"])
     ctx.set_precision(w.get("j0", -1))
+    ctx.set_df_recurrence(j1_of(w, args))
     flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_SHARED_P | nk.NK_NO_GRAPH
     # with --tune-cache from a plain bench run the shape is read, not timed
     ctx.autotune(w["n_rhs"], flags, args.tune_cache)
@@ -568,6 +578,8 @@ def main():
                          "no output line), for launch lists and captures under ncu")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
+    ap.add_argument("--j1", type=int, default=None,
+                    help="first outer step with a two-float recurrence (default: the workload's)")
     ap.add_argument("--inflight", type=int, default=4,
                     help="batches in flight (contexts on their own streams); 1: one synchronous solve per step")
     ap.add_argument("--tune-cache", default=None,

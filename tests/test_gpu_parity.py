@@ -292,6 +292,25 @@ def test_mixed_precision_within_1e8(c1, mu, k, ell):
     ctx.close()
 
 
+@pytest.mark.parametrize("mu,k,ell", [(0.0, 384, 96), (0.3, 512, 128)])
+def test_df_recurrence_start(c1, mu, k, ell):
+    """nk_set_df_recurrence: the whole recurrence in two-float arithmetic
+    (j1 = 0) stays within the workload tolerance of the dense truth; j1 past
+    j0 is the default schedule (j1 = j0) bit for bit."""
+    dims, U, b, truth = c1
+    ctx = make_ctx(dims, 101, mu)
+    ctx.set_precision(k // 4)
+    y_def, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
+    ctx.set_df_recurrence(k)
+    y_big, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
+    assert np.array_equal(y_def, y_big)
+    ctx.set_df_recurrence(0)
+    y0, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
+    assert rel(y0[0], truth[mu]) <= 1e-8
+    assert not np.array_equal(y0, y_def)
+    ctx.close()
+
+
 @pytest.fixture(scope="module")
 def c2():
     dims = (6, 6, 6, 6)
