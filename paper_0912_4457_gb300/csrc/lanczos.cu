@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
 // recurrence at 1e-7; 48-bit arithmetic adds about 1e-14.  The all-FP64
 // schedule (NK_FP64) keeps k_step2.
 template <bool TS>
-__global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_mode) {
+__global__ void __launch_bounds__(kThreads, 2) k_step2_df(Outer o, int j, int copy_mode) {
     __shared__ double2 sh[33];
     __shared__ double2 coef[2];
     const int rhs = blockIdx.y;
@@ -216,44 +216,57 @@ __global__ void __launch_bounds__(kThreads) k_step2_df(Outer o, int j, int copy_
     const dfc* __restrict__ pj = TS ? ring_p(o, rhs, j) : nullptr;
     dfc* __restrict__ l = TS ? ring_p(o, rhs, j + 1) : nullptr;
     const size_t vb = (size_t)rhs * o.N;
-    // two elements per iteration with separate accumulators: independent
-    // loads and two-float dependency chains in flight
-    df ax[2] = {df(0), df(0)}, ay[2] = {df(0), df(0)};
-    const long stride = (long)o.nblk * blockDim.x;
-    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < o.N; i0 += 2 * stride) {
+    // U elements per thread and iteration, all their loads issued before any
+    // arithmetic (the kernel is bound by the latency of these L2 reads), one
+    // accumulator each
+    constexpr int U = 4;
+    df ax[U], ay[U];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < U; ++u) ax[u] = ay[u] = df(0);
+    const long stride = (long)o.nblk * blockDim.x;
+    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < o.N; i0 += U * stride) {
+        dfc q[U], rr[U], pv[U], ll[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long i = i0 + u * stride;
+            if (i < o.N) {
+                q[u] = qj[i];
+                rr[u] = r[i];
+                if (TS) { pv[u] = pj[i]; ll[u] = l[i]; }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
             const long i = i0 + u * stride;
             if (i >= o.N) break;
-            const dfc q = qj[i];
-            dfc rr = r[i];
             // r <- r - c3 q, l <- l - c4 p
+            dfc& a = rr[u];
             if (TS) {
-                rr.x = rr.x - (c3.x * q.x - c3.y * q.y);
-                rr.y = rr.y - (c3.x * q.y + c3.y * q.x);
+                a.x = a.x - (c3.x * q[u].x - c3.y * q[u].y);
+                a.y = a.y - (c3.x * q[u].y + c3.y * q[u].x);
             } else {
-                rr.x = rr.x - c3.x * q.x;
-                rr.y = rr.y - c3.x * q.y;
+                a.x = a.x - c3.x * q[u].x;
+                a.y = a.y - c3.x * q[u].y;
             }
-            r[i] = rr;
-            if (qdf) reinterpret_cast<dfc*>(rq)[i] = rr;
-            else rq[i] = double2_of(rr);
-            if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(rr.x.hi, rr.y.hi);
+            r[i] = a;
+            if (qdf) reinterpret_cast<dfc*>(rq)[i] = a;
+            else rq[i] = double2_of(a);
+            if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(a.x.hi, a.y.hi);
             if (TS) {
-                const dfc pv = pj[i];
-                dfc ll = l[i];
-                ll.x = ll.x - (c4.x * pv.x - c4.y * pv.y);
-                ll.y = ll.y - (c4.x * pv.y + c4.y * pv.x);
-                l[i] = ll;
-                if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(ll.x.hi, ll.y.hi);
-                ax[u] += rr.x * ll.x + rr.y * ll.y;   // conj(r) l
-                ay[u] += rr.x * ll.y - rr.y * ll.x;
+                dfc& b = ll[u];
+                b.x = b.x - (c4.x * pv[u].x - c4.y * pv[u].y);
+                b.y = b.y - (c4.x * pv[u].y + c4.y * pv[u].x);
+                l[i] = b;
+                if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(b.x.hi, b.y.hi);
+                ax[u] += a.x * b.x + a.y * b.y;   // conj(r) l
+                ay[u] += a.x * b.y - a.y * b.x;
             } else {
-                ax[u] += rr.x * rr.x + rr.y * rr.y;
+                ax[u] += a.x * a.x + a.y * a.y;
             }
         }
     }
-    step2_finish<TS>(o, rhs, j, mk(df_to_double(ax[0] + ax[1]), df_to_double(ay[0] + ay[1])), sh);
+    step2_finish<TS>(o, rhs, j, mk(df_to_double((ax[0] + ax[1]) + (ax[2] + ax[3])),
+                                   df_to_double((ay[0] + ay[1]) + (ay[2] + ay[3]))), sh);
 }
 
 // c'_j = |x| c_j / n_j: the lift coefficients on the unnormalised basis
