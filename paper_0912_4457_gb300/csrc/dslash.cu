@@ -545,10 +545,24 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
     if (o.status[rhs] != kStatusOK) return;
     if (side == 1 && j == o.k - 1) return;   // the last step needs no left vector
     const size_t hb = (size_t)rhs * o.k;
-    // the scalars of this step, formed by the kernel that finished the last reduction
-    if (threadIdx.y == 0 && threadIdx.x < 3) {
-        const double2* sc = step_coefs(o, rhs, j);
-        coef[threadIdx.x] = side == 0 ? sc[threadIdx.x] : (threadIdx.x < 2 ? sc[3 + threadIdx.x] : make_double2(0.0, 0.0));
+    // the scalars of this step (a complex FP64 division or inverse each), one
+    // per warp so that they run side by side instead of one after another
+    if ((block_tid() & 31) == 0) {
+        const int nw = block_threads() >> 5;   // 2 warps or more
+        for (int t = block_tid() >> 5; t < 3; t += nw) {
+            const double2 zero = make_double2(0.0, 0.0);
+            double2 v;
+            if (side == 0) {
+                if (t == 0) v = cinv(scale_n(o, rhs, j));
+                else if (t == 1) v = j > 0 ? cdiv(TS ? o.gamma[hb + j - 1] : o.beta[hb + j - 1], scale_n(o, rhs, j - 1)) : zero;
+                else v = TS ? cinv(cconj(scale_m(o, rhs, j))) : cinv(scale_n(o, rhs, j));
+            } else {
+                if (t == 0) v = cinv(scale_m(o, rhs, j));
+                else if (t == 1) v = j > 0 ? cdiv(cconj(o.beta[hb + j - 1]), scale_m(o, rhs, j - 1)) : zero;
+                else v = zero;
+            }
+            coef[t] = v;
+        }
     }
     __syncthreads();
     const int site = sb * blockDim.x + threadIdx.x;
@@ -658,12 +672,7 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
             double2 tot = sum_partials(o.partials + (size_t)rhs * o.npart, nsb, sh);
             if (threadIdx.x == 0 && threadIdx.y == 0) {
                 // Hermitian: H(j,j) = Re(q_j^dag r) / n_j, real (App. C); two-sided: (p_j^dag r) / m_j^*
-                const double2 a = TS ? cmul(coef[2], tot) : make_double2(tot.x * coef[2].x, 0.0);
-                o.alpha[hb + j] = a;
-                // step 2's scalars: H(j,j) / n_j and H(j,j)^* / m_j
-                double2* sc = step_coefs(o, rhs, j);
-                sc[5] = cdiv(a, scale_n(o, rhs, j));
-                sc[6] = TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : make_double2(0.0, 0.0);
+                o.alpha[hb + j] = TS ? cmul(coef[2], tot) : make_double2(tot.x * coef[2].x, 0.0);
                 o.counters[rhs] = 0u;
             }
         }

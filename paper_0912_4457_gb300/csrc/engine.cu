@@ -169,7 +169,6 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.counters = (unsigned*)take(sizeof(unsigned) * n_rhs);
     o.status = (int*)take(sizeof(int) * n_rhs);
     o.xnorm = (double*)take(sizeof(double) * n_rhs);
-    o.sc = (double2*)take(sizeof(double2) * nk::kStepCoefs * (size_t)k * n_rhs);
     L.cp = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     nk::Inner& in = L.in;
     in.n_rhs = n_rhs; in.k = k; in.ell = ell; in.two_sided = two_sided;

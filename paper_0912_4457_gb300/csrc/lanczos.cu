@@ -33,20 +33,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// The stencil kernel's scalars of step j (entries 0-4 of step_coefs), from
-// n_j, m_j and the coefficients of step j - 1.
-__device__ void put_stencil_coefs(const Outer& o, int rhs, int j) {
-    const size_t hb = (size_t)rhs * o.k;
-    const double2 zero = mk(0.0, 0.0);
-    double2* sc = step_coefs(o, rhs, j);
-    sc[0] = cinv(scale_n(o, rhs, j));
-    sc[1] = j > 0 ? cdiv(o.two_sided ? o.gamma[hb + j - 1] : o.beta[hb + j - 1], scale_n(o, rhs, j - 1)) : zero;
-    sc[2] = o.two_sided ? cinv(cconj(scale_m(o, rhs, j))) : cinv(scale_n(o, rhs, j));
-    if (o.two_sided) {
-        sc[3] = cinv(scale_m(o, rhs, j));
-        sc[4] = j > 0 ? cdiv(cconj(o.beta[hb + j - 1]), scale_m(o, rhs, j - 1)) : zero;
-    }
-}
 
 __global__ void __launch_bounds__(kThreads) k_norm(Outer o, int keep_status) {
     __shared__ double2 sh[33];
@@ -68,7 +54,6 @@ __global__ void __launch_bounds__(kThreads) k_norm(Outer o, int keep_status) {
             const int prev = o.status[rhs];
             const bool keep = keep_status && prev != kStatusOK && prev != kStatusZeroSource;
             o.status[rhs] = keep ? prev : (nrm > 0.0 ? kStatusOK : kStatusZeroSource);
-            if (nrm > 0.0) put_stencil_coefs(o, rhs, 0);
             o.counters[rhs] = 0u;
         }
     }
@@ -143,7 +128,6 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
                 o.beta[at] = b;
                 o.gamma[at] = cdiv(cconj(d), b);        // gamma <- delta^* / beta
             }
-            if (o.status[rhs] == kStatusOK && j + 1 < o.k) put_stencil_coefs(o, rhs, j + 1);
             o.counters[rhs] = 0u;
         }
     }
@@ -156,7 +140,13 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
     const size_t hb = (size_t)rhs * o.k;
-    if (threadIdx.x < 2) coef[threadIdx.x] = step_coefs(o, rhs, j)[5 + threadIdx.x];   // H(j,j)/n_j, H(j,j)^*/m_j
+    // H(j,j)/n_j and H(j,j)^*/m_j, one FP64 division each, by lane 0 of two
+    // warps (on two SM sub-partitions) at the same time
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+        const double2 a = o.alpha[hb + j];
+        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv(a, scale_n(o, rhs, j))
+                                                  : (TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
+    }
     __syncthreads();
     const double2 c3 = coef[0], c4 = coef[1];
     const double2* __restrict__ qj = outer_q(o, rhs, j);
@@ -206,7 +196,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_step2_df(Outer o, int j, int co
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
     const size_t hb = (size_t)rhs * o.k;
-    if (threadIdx.x < 2) coef[threadIdx.x] = step_coefs(o, rhs, j)[5 + threadIdx.x];   // H(j,j)/n_j, H(j,j)^*/m_j
+    // H(j,j)/n_j and H(j,j)^*/m_j, one FP64 division each, by lane 0 of two
+    // warps (on two SM sub-partitions) at the same time
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+        const double2 a = o.alpha[hb + j];
+        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv(a, scale_n(o, rhs, j))
+                                                  : (TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
+    }
     __syncthreads();
     const dfc c3 = dfc_of(coef[0]), c4 = dfc_of(coef[1]);
     const dfc* __restrict__ qj = ring_q(o, rhs, j);

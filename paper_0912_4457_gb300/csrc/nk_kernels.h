@@ -87,18 +87,7 @@ struct Outer {
     // the steps before it in FP64.  ring_from <= j0 (the FP32 stencil steps
     // always run on the rings).  Larger than k otherwise.
     int ring_from;
-    // Scalars of each step, formed once by the thread that finishes the
-    // reduction they depend on (so that the CTAs of the next kernel load them
-    // instead of each dividing in FP64 first), [rhs][k][kStepCoefs]:
-    //   0: 1/n_j   1: c_{j-1}/n_{j-1} (c = beta, two-sided gamma)   2: the scale of H(j,j)
-    //   3: 1/m_j   4: beta^*_{j-1}/m_{j-1}                            (left recurrence)
-    //   5: H(j,j)/n_j   6: H(j,j)^*/m_j                               (step 2)
-    double2* sc;
 };
-constexpr int kStepCoefs = 8;
-__host__ __device__ inline double2* step_coefs(const Outer& o, int rhs, int j) {
-    return o.sc + ((size_t)rhs * o.k + j) * kStepCoefs;
-}
 
 __host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {
     return o.Q + ((size_t)rhs * o.qcols + (o.q_ring ? j % 3 : j)) * o.N;
