@@ -519,8 +519,9 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
              FP64 output 192 B -- HBM;
       step2: 24 (8) FP64 flops per element -- FP64 ALU, 1.0 TFLOP/s measured
              DFMA rate;
-      step2_df: reads q_j, r, p_j, l and writes r, l (two-float rings), r in
-             FP64 and the FP32 copies: 128 (64) B per element -- HBM;
+      step2_df: reads q_j, r, p_j, l and writes r, l (two-float rings), the
+             basis column and, before an FP32 stencil, the FP32 copies: 128
+             (64) B per element, 112 (56) without the copies -- HBM;
       lift: reads V_k once, 16 B x k per element -- HBM.
     """
     V = int(np.prod(w["dims"]))
@@ -541,9 +542,17 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
                 "ms_per_launch": ms, "flops_per_launch": flops,
                 "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
     if dom == "step2_df":
-        b = (128 if two else 64) * N * n_rhs
+        # launches j1 <= j <= k - 2; those with j + 1 >= j0 also write the FP32
+        # copy the next (FP32) stencil reads, the others do not
+        k, j0 = w["k"], w["j0"]
+        j1 = w.get("j1", -1)
+        j1 = j0 if j1 < 0 else min(j1, j0)
+        n_df = max(1, k - 1 - j1)
+        n_copy = min(n_df, k - j0)
+        per_el = ((n_copy * (128 if two else 64) + (n_df - n_copy) * (112 if two else 56)) / n_df)
+        b = per_el * N * n_rhs
         gbs = b / (ms * 1e-3) / 1e9
-        return {"kernel": "k_step2_df (step 2 of the FP32-stencil steps, two-float)", "bound": "hbm",
+        return {"kernel": "k_step2_df (two-float step 2 on the rings)", "bound": "hbm",
                 "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": gbs / hbm,
                 "traffic": profiled_traffic("k_step2_df"), "ms_per_launch": ms,
                 "algorithmic_bytes_per_launch": b}
