@@ -134,14 +134,6 @@ int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
  * in every schedule; the lift sums in two-float arithmetic. */
 int nk_set_precision(nk_ctx* ctx, int j0);
 
-/* The FP64 reciprocal and square root the recurrence uses for its per-step
- * scalars (1/n_j, beta = sqrt(delta), ...): an FP32 seed refined by
- * Newton-Raphson iteration in FP64, within a few ulp of the correctly rounded
- * results.  Evaluates them on the current device for n HOST values x:
- * out[2i] = 1/x_i, out[2i+1] = sqrt(x_i) (out holds 2n doubles).  For tests of
- * their error bound; blocks; no context needed. */
-int nk_scalar_math_check(const double* x, int n, double* out);
-
 /* The first outer step j1 of NK_MIXED whose recurrence runs in two-float
  * arithmetic (see nk_set_precision); j1 < 0 selects j0, and j1 > j0 acts as
  * j0.  Takes effect with the next solve. */

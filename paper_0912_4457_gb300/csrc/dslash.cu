@@ -553,12 +553,12 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
             const double2 zero = make_double2(0.0, 0.0);
             double2 v;
             if (side == 0) {
-                if (t == 0) v = cinv_nr(scale_n(o, rhs, j));
-                else if (t == 1) v = j > 0 ? cdiv_nr(TS ? o.gamma[hb + j - 1] : o.beta[hb + j - 1], scale_n(o, rhs, j - 1)) : zero;
-                else v = TS ? cinv_nr(cconj(scale_m(o, rhs, j))) : cinv_nr(scale_n(o, rhs, j));
+                if (t == 0) v = cinv(scale_n(o, rhs, j));
+                else if (t == 1) v = j > 0 ? cdiv(TS ? o.gamma[hb + j - 1] : o.beta[hb + j - 1], scale_n(o, rhs, j - 1)) : zero;
+                else v = TS ? cinv(cconj(scale_m(o, rhs, j))) : cinv(scale_n(o, rhs, j));
             } else {
-                if (t == 0) v = cinv_nr(scale_m(o, rhs, j));
-                else if (t == 1) v = j > 0 ? cdiv_nr(cconj(o.beta[hb + j - 1]), scale_m(o, rhs, j - 1)) : zero;
+                if (t == 0) v = cinv(scale_m(o, rhs, j));
+                else if (t == 1) v = j > 0 ? cdiv(cconj(o.beta[hb + j - 1]), scale_m(o, rhs, j - 1)) : zero;
                 else v = zero;
             }
             coef[t] = v;

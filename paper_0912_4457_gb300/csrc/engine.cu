@@ -717,23 +717,6 @@ int nk_set_precision(nk_ctx* c, int j0) {
     return NK_OK;
 }
 
-int nk_scalar_math_check(const double* x, int n, double* out) {
-    if (!x || !out || n < 0) return NK_EINVAL;
-    if (n == 0) return NK_OK;
-    double *dx = nullptr, *dout = nullptr;
-    if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return NK_ENOMEM;
-    if (cudaMalloc(&dout, sizeof(double) * 2 * n) != cudaSuccess) { cudaFree(dx); return NK_ENOMEM; }
-    cudaError_t e = cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        nk::launch_scalar_math(dx, dout, n, 0);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost);
-    cudaFree(dx);
-    cudaFree(dout);
-    return e == cudaSuccess ? NK_OK : NK_ECUDA;
-}
-
 int nk_set_df_recurrence(nk_ctx* c, int j1) {
     if (!c) return NK_EINVAL;
     c->j1 = j1;

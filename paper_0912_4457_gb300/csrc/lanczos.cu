@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kThreads) k_norm(Outer o, int keep_status) {
     if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, blockIdx.x, o.nblk)) {
         double2 tot = sum_partials(o.partials + (size_t)rhs * o.npart, o.nblk, sh);
         if (threadIdx.x == 0) {
-            double nrm = sqrt_nr(tot.x);
+            double nrm = sqrt(tot.x);
             o.xnorm[rhs] = nrm;
             // the second pass of NK_DOUBLE_PASS keeps a failure of the first
             // (breakdown, RHi): that source is not recomputed
@@ -114,7 +114,7 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
         if (threadIdx.x == 0) {
             const size_t at = (size_t)rhs * o.k + j;
             if (!TS) {
-                double b = sqrt_nr(d.x);                // beta <- sqrt(r^dag r)
+                double b = sqrt(d.x);                   // beta <- sqrt(r^dag r)
                 o.beta[at] = mk(b, 0.0);
                 o.gamma[at] = mk(b, 0.0);
                 if (!(b > 0.0) || !isfinite(b)) o.status[rhs] = kStatusBreakdown;
@@ -124,9 +124,9 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
                 o.beta[at] = mk(0.0, 0.0);
                 o.gamma[at] = mk(0.0, 0.0);
             } else {
-                double2 b = csqrt_nr(d);                // beta <- sqrt(delta)
+                double2 b = csqrt_principal(d);         // beta <- sqrt(delta)
                 o.beta[at] = b;
-                o.gamma[at] = cdiv_nr(cconj(d), b);     // gamma <- delta^* / beta
+                o.gamma[at] = cdiv(cconj(d), b);        // gamma <- delta^* / beta
             }
             o.counters[rhs] = 0u;
         }
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
     // warps (on two SM sub-partitions) at the same time
     if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
         const double2 a = o.alpha[hb + j];
-        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv_nr(a, scale_n(o, rhs, j))
-                                                  : (TS ? cdiv_nr(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
+        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv(a, scale_n(o, rhs, j))
+                                                  : (TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
     }
     __syncthreads();
     const double2 c3 = coef[0], c4 = coef[1];
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_step2_df(Outer o, int j, int co
     // warps (on two SM sub-partitions) at the same time
     if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
         const double2 a = o.alpha[hb + j];
-        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv_nr(a, scale_n(o, rhs, j))
-                                                  : (TS ? cdiv_nr(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
+        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv(a, scale_n(o, rhs, j))
+                                                  : (TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
     }
     __syncthreads();
     const dfc c3 = dfc_of(coef[0]), c4 = dfc_of(coef[1]);
@@ -391,18 +391,6 @@ void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y
 __global__ void k_fill_int(int* p, int n, int v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
-}
-
-// rcp_nr and sqrt_nr on n values: out[2i] = 1/x_i, out[2i+1] = sqrt(x_i) (for tests)
-__global__ void k_scalar_math(const double* x, double* out, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    out[2 * i] = rcp_nr(x[i]);
-    out[2 * i + 1] = sqrt_nr(x[i]);
-}
-
-void launch_scalar_math(const double* x, double* out, int n, cudaStream_t st) {
-    if (n > 0) k_scalar_math<<<(n + 127) / 128, 128, 0, st>>>(x, out, n);
 }
 
 void launch_fill_int(int* p, int n, int value, cudaStream_t st) {

@@ -283,58 +283,6 @@ struct dfac {
 template <> struct C2<df> { typedef dfc T; };
 static_assert(sizeof(dfc) == 16, "two-float complex is 16 bytes");
 
-// ---- FP64 reciprocal, square root and complex division for the recurrence's
-// scalars -------------------------------------------------------------------------
-// The scalars of each outer step (1/n_j, H(j,j)/n_j, beta = sqrt(delta), ...)
-// sit on the critical path between dependent kernels, and on GB300 an FP64
-// division or square root there is a long chain on the slow FP64 pipe.  These
-// take an FP32 seed (one MUFU operation on the FP32 pipe, conversions on the
-// integer pipe) and refine it by Newton-Raphson iteration in FP64: for 1/d,
-// r <- r + r (1 - d r); for 1/sqrt(x), y <- y + (y/2)(1 - x y^2); each step
-// squares the relative error (2^-22 -> 2^-44 -> below 2^-53), and sqrt(x) is
-// x y with one more correction s <- s + (y/2)(x - s^2) (Newton's method for
-// these functions; e.g. Markstein, IA-64 and Elementary Functions, 2000).
-// Results are within a few ulp of the correctly rounded ones, and
-// deterministic.  Arguments outside the range where the FP32 seed is a normal
-// number take the ordinary FP64 operations.
-__device__ __forceinline__ double rcp_nr(double d) {
-    const double a = fabs(d);
-    if (!(a > 0x1p-120 && a < 0x1p120)) return 1.0 / d;
-    double r = f2d_int(__frcp_rn(d2f_int(d)));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
-}
-__device__ __forceinline__ double sqrt_nr(double x) {
-    if (!(x > 0x1p-120 && x < 0x1p120)) return sqrt(x);
-    double y = f2d_int(__frsqrt_rn(d2f_int(x)));
-    double e = fma(-x * y, y, 1.0);
-    y = fma(0.5 * y, e, y);
-    e = fma(-x * y, y, 1.0);
-    y = fma(0.5 * y, e, y);
-    const double s = x * y;
-    return fma(0.5 * y, fma(-s, s, x), s);
-}
-// 1/a = conj(a) / |a|^2; |a| far from 1 takes Smith's form (cinv)
-__device__ __forceinline__ double2 cinv_nr(double2 a) {
-    const double m = fmax(fabs(a.x), fabs(a.y));
-    if (!(m > 0x1p-50 && m < 0x1p50)) return cinv(a);
-    const double r = rcp_nr(fma(a.x, a.x, a.y * a.y));
-    return mk(a.x * r, -a.y * r);
-}
-__device__ __forceinline__ double2 cdiv_nr(double2 a, double2 b) { return cmul(a, cinv_nr(b)); }
-// principal square root, as csqrt_principal
-__device__ __forceinline__ double2 csqrt_nr(double2 z) {
-    const double m = fmax(fabs(z.x), fabs(z.y));
-    if (!(m > 0x1p-50 && m < 0x1p50)) return csqrt_principal(z);
-    const double r = sqrt_nr(fma(z.x, z.x, z.y * z.y));
-    const double t = sqrt_nr(0.5 * (r + fabs(z.x)));
-    const double h = 0.5 * rcp_nr(t);
-    if (z.x >= 0.0) return mk(t, z.y * h);
-    return mk(fabs(z.y) * h, z.y >= 0.0 ? t : -t);
-}
-
 // Upper bound on spin iterations of any device-side wait (each iteration
 // sleeps ~100 ns), about one second; a wait that runs out sets an error flag.
 constexpr long long kSpinLimit = 10000000LL;

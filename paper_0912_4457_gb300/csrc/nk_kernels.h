@@ -140,8 +140,6 @@ void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, cudaStr
 void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st);
 void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y, cudaStream_t st);
 void launch_fill_int(int* p, int n, int value, cudaStream_t st);
-// the FP64 reciprocal and square root of the recurrence's scalars (for tests)
-void launch_scalar_math(const double* x, double* out, int n, cudaStream_t st);
 // Adaptive k: per RHS (|c - c_prev|, |c|) over the first k entries, then c_prev <- c.
 void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st);
 

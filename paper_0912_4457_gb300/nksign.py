@@ -45,7 +45,7 @@ ERROR_NAMES = {
 }
 
 EXPORTED = [
-    "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision", "nk_set_df_recurrence", "nk_scalar_math_check",
+    "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision", "nk_set_df_recurrence",
     "nk_set_adapt_start",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
@@ -131,7 +131,6 @@ def load_library(path: str = LIB_PATH):
         "nk_set_mu_mw": ([P, D, D], I),
         "nk_set_precision": ([P, I], I),
         "nk_set_df_recurrence": ([P, I], I),
-        "nk_scalar_math_check": ([P, I, P], I),
         "nk_set_adapt_start": ([P, I], I),
         "nk_sign_apply": ([P, dp, I, I, I, D, D, U, dp, ctypes.POINTER(NkStats)], I),
         "nk_sign_apply_dev": ([P, P, I, I, I, D, D, U, P, ctypes.POINTER(NkStats), P], I),
@@ -459,18 +458,6 @@ def inner_sign_noalloc(alpha_dev, beta_dev, gamma_dev, c_dev, n_rhs, k, ell, p=0
                                    int(k), int(ell), float(p), 1 if hermitian else 0, _dev_ptr(c_dev),
                                    _stream_ptr(stream), buf, 256)
     return rc, buf.value.decode()
-
-
-def scalar_math_check(x):
-    """nk_scalar_math_check: the library's FP64 reciprocal and square root of
-    the host values x on the current device; returns (1/x, sqrt(x))."""
-    lib = load_library()
-    x = np.ascontiguousarray(x, dtype=np.float64)
-    out = np.zeros(2 * x.size, np.float64)
-    rc = lib.nk_scalar_math_check(_dptr(x), int(x.size), _dptr(out))
-    if rc != NK_OK:
-        raise NkError(rc, "nk_scalar_math_check failed")
-    return out[0::2].copy(), out[1::2].copy()
 
 
 def _pad(x, n, k):
