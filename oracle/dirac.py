@@ -10,7 +10,7 @@ Written out per site y:
   (T_nu^+ psi)_y = (1 + gamma_nu) U_{y-nu,+nu} psi_{y-nu}
   (T_nu^- psi)_y = (1 - gamma_nu) U^dagger_{y,+nu} psi_{y+nu}
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent:
 * gamma basis: chiral, gamma_k = [[0, -i s_k], [i s_k, 0]], gamma_4 = [[0, 1], [1, 0]],
   so gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 = diag(1, 1, -1, -1);
 * boundary conditions: periodic in x, y, z, antiperiodic in t (a factor -1 on

@@ -10,7 +10,7 @@ H_k as its three diagonals:
 * ``beta[j]``  = H(j+1, j), j = 0..k-2   (sub-diagonal)
 * ``gamma[j]`` = H(j, j+1), j = 0..k-2   (super-diagonal)
 
-Readings (listed in DESIGN.md):
+Readings where the paper leaves a choice:
 * Hermitian case: H(j,j) = v_j^dagger r is real in exact arithmetic; its real
   part is used both in H and in the update r <- r - H(j,j) v_j, in line with
   "steps 3-5 are done in real arithmetic" (App. C).  The imaginary part is

@@ -15,7 +15,7 @@ Test infrastructure only (see ``oracle/__init__.py``).
   Steps 3-5 are real in the Hermitian case.
 * p: Eq. popt, p = (z_min z_max)^{-1/2}.  The paper takes z_min, z_max from
   spectral information of A (footnote to Eq. popt; p need only be
-  approximate).  Reading used here and on the GPU (listed in the design doc):
+  approximate).  Reading used here and on the GPU:
   z_max from P_EST_ITERS = 30 steps of power iteration with H_k and z_min
   from 30 steps of inverse iteration with the LU of H_k, both from the
   normalised all-ones start vector; the estimate is |H x| (resp. 1/|H^{-1} x|)

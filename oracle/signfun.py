@@ -7,8 +7,8 @@ Test infrastructure only (see ``oracle/__init__.py``).
   negative real axis  (Sec. 2, Eq. sgnz).  For Hermitian A the eigenvalues are
   real and sgn(x) = +-1.
 * Roberts-Higham iteration (RHi): S_0 = H, S_{n+1} = (S_n + S_n^{-1}) / 2
-  (Sec. 3, Eq. Roberts).  The paper iterates "to machine precision"; the
-  stopping rule here (a reading, listed in the design doc) stops once the relative
+  (Sec. 3, Eq. Roberts).  The paper iterates until the iterate is exact to
+  working precision; the stopping rule here (a reading of that) stops once the relative
   Frobenius change ||S_{n+1} - S_n|| / ||S_{n+1}|| falls below ``RHI_STOP``
   = 1e-10.  In the quadratic regime the error of S_{n+1} is of the order of
   the square of that change, i.e. at rounding level.  At most ``RHI_MAXIT``

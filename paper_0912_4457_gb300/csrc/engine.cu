@@ -1,5 +1,5 @@
-// Host engine and C ABI (include/nksign.h): context, device workspace, the
-// solve driver that sequences the kernels of one nested Krylov-Ritz
+// Host engine and C ABI (include/nksign.h): context, device workspace,
+// the host code that sequences the kernels of one nested Krylov-Ritz
 // evaluation, and CUDA-graph capture of whole solves.
 #include <cuda_runtime.h>
 
