@@ -3,11 +3,14 @@
 
 One step = one batched solve of the workload's n_rhs sources (12 spin-colour
 point sources at the origin) by the nested method: outer two-sided Lanczos
-(FP32 stencil after the first k/4 steps, FP64 everything else), p estimate,
-LU of p H_k, inner two-sided Lanczos with H_k', batched Roberts-Higham, lift.
-The whole solve replays one CUDA graph.
+(two-float stencil for the first j0 steps, FP32 stencil after; the
+recurrence itself two-float from step j1 on, FP64 before), one p for the
+batch, LU of p H_k, inner two-sided Lanczos with H_k', batched
+Roberts-Higham (FP64), two-float lift.  The whole solve replays one CUDA
+graph; --inflight batches (default 4) run at a time on their own streams.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                    [--inflight B] [--j1 J] [--tune-cache FILE] [--mode bench|ncu]
 
 Prints one JSON line on rank 0.  Under torchrun each rank runs an independent
 replica of the workload on its own GPU (the method has no exchange step:
