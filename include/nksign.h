@@ -57,7 +57,7 @@ extern "C" {
 
 /* Solve flags (bitwise or). */
 #define NK_FP64 0x0u        /* every stencil application in FP64 */
-#define NK_MIXED 0x1u       /* FP32 stencil after the first j0 outer steps (nk_set_precision) */
+#define NK_MIXED 0x1u       /* two-float stencil for the first j0 outer steps, FP32 after (nk_set_precision) */
 #define NK_DOUBLE_PASS 0x2u /* regenerate V_k in a second pass instead of storing it (Sec. 4.4) */
 #define NK_NO_GRAPH 0x10u   /* launch kernel by kernel instead of replaying a CUDA graph */
 #define NK_ASYNC 0x40u      /* nk_sign_apply_dev / nk_overlap_apply_dev with tol = 0: enqueue the
