@@ -53,3 +53,19 @@ def test_null_and_invalid_arguments_without_gpu(lib):
     bad = (ctypes.c_int * 4)(4, 4, 1, 4)
     assert lib.nk_create_lattice(bad, 1, ctypes.byref(out)) == -1
     assert lib.nk_create_lattice(None, 1, ctypes.byref(out)) == -1
+
+
+def test_null_context_is_rejected_by_every_setter_and_wait(lib):
+    """The schedule setters, the launch-shape calls and nk_wait check their
+    context before touching the device."""
+    P, I = ctypes.c_void_p, ctypes.c_int
+    for name in ("nk_set_precision", "nk_set_df_recurrence", "nk_set_adapt_start"):
+        f = getattr(lib, name)
+        f.argtypes, f.restype = [P, I], I
+        assert f(None, 0) == -1, name
+    lib.nk_set_mu_mw.argtypes, lib.nk_set_mu_mw.restype = [P, ctypes.c_double, ctypes.c_double], I
+    assert lib.nk_set_mu_mw(None, 0.3, -2.0) == -1
+    lib.nk_wait.argtypes, lib.nk_wait.restype = [P, P], I
+    assert lib.nk_wait(None, None) == -1
+    lib.nk_get_launch.argtypes, lib.nk_get_launch.restype = [P, I, ctypes.c_uint, P], I
+    assert lib.nk_get_launch(None, 12, 0, None) == -1
