@@ -515,10 +515,13 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
 //   left vectors (side 1, two-sided only):
 //     t = A^dag p_j / m_j;  l = t - (beta^*_{j-1}/m_{j-1}) p_{j-1};  l -> p_{j+1}
 // The stencil runs in precision R (FP32 reads the FP32 copies of q_j, p_j and
-// the FP32 links; the scale 1/n_j is applied in R too); from the stencil
-// output on, everything is FP64.  The blocks of side 0 reduce H(j,j) with the
-// deterministic two-stage scheme.  In double-pass mode side 0 also
-// accumulates y += c'_j q_j at its own site.
+// the FP32 links; the two-float stencil reads the two-float rings).  The
+// epilogue (the scale 1/n_j, the update and the H(j,j) partial) runs in
+// two-float arithmetic on the rings for the FP32 stencil and, from step
+// o.ring_from on, for the two-float stencil; otherwise in FP64 on the FP64
+// vectors.  The blocks of side 0 reduce H(j,j) with the deterministic
+// two-stage scheme.  In double-pass mode side 0 also accumulates
+// y += c'_j q_j at its own site.
 // Minimum resident CTAs of kStencilMaxThreads threads per SM for the fused
 // stencil (a register cap): the FP32 and two-float instantiations are
 // latency bound (loads; long dependent FP32 chains) and gain from more
