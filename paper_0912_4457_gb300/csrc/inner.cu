@@ -2,7 +2,9 @@
 // precond, innersign, Roberts):
 //   p      = (z_min z_max)^{-1/2}, z_max by power iteration with H_k and z_min
 //            by inverse iteration with the LU of H_k (30 steps each, from the
-//            normalised all-ones vector), unless p is given;
+//            normalised all-ones vector), unless p is given; with one p for
+//            the batch, z_min and z_max are the extremes over its RHS (two
+//            launches: the estimates of every RHS, then the rest);
 //   LU of p H_k in LAPACK gttrf form (partial pivoting; U with two super-diagonals);
 //   inner (two-sided) Lanczos of size l with H_k' = [p H_k + (p H_k)^{-1}]/2 and
 //            e_1, applying (p H_k)^{-1} by the gttrs back substitution and
@@ -22,8 +24,9 @@
 // being inverted (in-place Gauss-Jordan with partial pivoting and row
 // interchanges) are spread cyclically over the cluster's CTAs and held in
 // their shared memory; the pivot search, the pivot row broadcast and the row
-// interchange go through distributed shared memory between two cluster
-// barriers per pivot.
+// interchange go through distributed shared memory, with one cluster barrier
+// per pivot (candidate rows published in buffers that alternate between
+// pivots).
 #include <cooperative_groups.h>
 
 #include "nk_common.cuh"

@@ -18,6 +18,10 @@
 //          beta = |r| (two-sided: delta = r^dag l, beta = sqrt(delta),
 //          gamma = delta^*/beta; delta = 0 is a serious breakdown),
 //          plus the FP32 copies the next mixed-precision stencil reads.
+// In the mixed schedule, from the step where its recurrence turns two-float,
+// both kernels work in two-float arithmetic on rings of the newest three
+// right and left vectors (k_step2_df), and the basis columns they produce are
+// stored as two-float values.
 //
 // Reductions are deterministic: a fixed grid, a fixed per-thread order,
 // warp-shuffle and shared-memory block sums, per-block partials and a final
