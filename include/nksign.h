@@ -57,7 +57,8 @@ extern "C" {
 
 /* Solve flags (bitwise or). */
 #define NK_FP64 0x0u        /* every stencil application in FP64 */
-#define NK_MIXED 0x1u       /* two-float stencil for the first j0 outer steps, FP32 after (nk_set_precision) */
+#define NK_MIXED 0x1u       /* two-float stencil for the first j0 outer steps, FP32 after; FP64
+                               recurrence (nk_set_precision) */
 #define NK_DOUBLE_PASS 0x2u /* regenerate V_k in a second pass instead of storing it (Sec. 4.4) */
 #define NK_NO_GRAPH 0x10u   /* launch kernel by kernel instead of replaying a CUDA graph */
 #define NK_ASYNC 0x40u      /* nk_sign_apply_dev / nk_overlap_apply_dev with tol = 0: enqueue the
@@ -69,6 +70,8 @@ extern "C" {
                                shares A), instead of one per RHS; p > 0 overrides both */
 #define NK_PROFILE 0x20u    /* kernel by kernel, with CUDA events around every launch; fills
                                nk_stats.t_class_ms / n_class (implies NK_NO_GRAPH) */
+#define NK_PREFIX_FP64 0x100u /* with NK_MIXED: the outer steps before j0 apply the FP64 stencil
+                               instead of the two-float one (nk_set_precision) */
 
 #define NK_MAX_RHS 12
 
@@ -126,17 +129,21 @@ int nk_set_mu_mw(nk_ctx* ctx, double mu, double m_w);
 
 /* Precision schedule for NK_MIXED (the outer recurrence, App. A/B): outer
  * steps j < j0 apply the stencil in two-float arithmetic (about 48 bits, on
- * the FP32 pipe; FP32 links hi + lo), steps j >= j0 in FP32.  j0 < 0 selects
- * the default k/4.  The recurrence itself (the update of r and l, their
- * inner products, the basis) runs in FP64 before step j1 and in two-float
- * arithmetic from j1 on (nk_set_df_recurrence; default j1 = j0).  The
- * coefficients H_k, p, the LU of p H_k, the inner Lanczos and RHi are FP64
- * in every schedule; the lift sums in two-float arithmetic. */
+ * the FP32 pipe; FP32 links hi + lo) or, with NK_PREFIX_FP64, in FP64; steps
+ * j >= j0 in FP32 (input vector, links and arithmetic FP32, including the
+ * scale 1/|q_j| of the stencil output).  j0 < 0 selects the default k/4.
+ * The recurrence itself (the updates of r and l, their inner products and
+ * accumulation, the basis V_k) runs in FP64, and so do H_k, p, the LU of
+ * p H_k, the inner Lanczos, RHi and the lift; nk_set_df_recurrence can move
+ * the recurrence from a given step on to two-float arithmetic instead. */
 int nk_set_precision(nk_ctx* ctx, int j0);
 
-/* The first outer step j1 of NK_MIXED whose recurrence runs in two-float
- * arithmetic (see nk_set_precision); j1 < 0 selects j0, and j1 > j0 acts as
- * j0.  Takes effect with the next solve. */
+/* Optional two-float recurrence for NK_MIXED: from outer step j1 on the
+ * updates of r and l, their inner products and the basis columns run in
+ * two-float arithmetic (about 48 bits, on the FP32 pipe) on rings of the
+ * newest three vectors, and the lift sums in two-float arithmetic.  j1 < 0
+ * (the default) keeps the whole recurrence in FP64.  Takes effect with the
+ * next solve. */
 int nk_set_df_recurrence(nk_ctx* ctx, int j1);
 
 /* Adaptive k: the outer size at the first convergence check (even; 0 selects
@@ -324,7 +331,8 @@ int nk_predict_sizes(nk_ctx* ctx, nk_mlp* m, const double* b_dev, int k_max, int
  * must not allocate device memory -- code running where cudaMalloc is
  * forbidden or unsafe, such as inside another framework's memory budget or a
  * process whose allocator it does not own.  It computes the same c_r =
- * V_l sgn(H_l) e_1 as nk_inner_sign, but all inputs and outputs are DEVICE
+ * V_l sgn(H_l) e_1 as nk_inner_sign (p > 0 fixed, p == 0 one estimate per
+ * RHS, p < 0 one p for the batch), but all inputs and outputs are DEVICE
  * arrays owned by the caller (alpha_dev, beta_dev, gamma_dev, c_dev in the
  * nk_outer_lanczos_dev layout, complex doubles [r*k + j]) and every other
  * buffer it needs lives in one static device array of the library (about

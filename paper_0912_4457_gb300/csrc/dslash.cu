@@ -515,11 +515,12 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
 //   left vectors (side 1, two-sided only):
 //     t = A^dag p_j / m_j;  l = t - (beta^*_{j-1}/m_{j-1}) p_{j-1};  l -> p_{j+1}
 // The stencil runs in precision R (FP32 reads the FP32 copies of q_j, p_j and
-// the FP32 links; the two-float stencil reads the two-float rings).  The
-// epilogue (the scale 1/n_j, the update and the H(j,j) partial) runs in
-// two-float arithmetic on the rings for the FP32 stencil and, from step
-// o.ring_from on, for the two-float stencil; otherwise in FP64 on the FP64
-// vectors.  The blocks of side 0 reduce H(j,j) with the deterministic
+// the FP32 links; the two-float stencil reads the two-float rings); the scale
+// 1/n_j of its output is part of the stencil application (A v_j = A q_j / n_j)
+// and is applied in the same precision.  The rest of the epilogue (the
+// update with q_{j-1}, p_{j-1} and the H(j,j) partial) runs in FP64 on the
+// FP64 vectors, or, from step o.ring_from on (the optional two-float
+// recurrence of the mixed schedule), in two-float arithmetic on the rings.  The blocks of side 0 reduce H(j,j) with the deterministic
 // two-stage scheme.  In double-pass mode side 0 also accumulates
 // y += c'_j q_j at its own site.
 // Minimum resident CTAs of kStencilMaxThreads threads per SM for the fused
@@ -591,11 +592,11 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
         };
         const double2 c1 = coef[1];   // zero at j = 0 (the previous vector is then any valid one)
         const int jp = j > 0 ? j - 1 : j;
-        bool ring_epilogue = std::is_same<R, float>::value;
-        if constexpr (std::is_same<R, df>::value) ring_epilogue = j >= o.ring_from;
+        bool ring_epilogue = false;
+        if constexpr (!std::is_same<R, double>::value) ring_epilogue = j >= o.ring_from;
         if constexpr (!std::is_same<R, double>::value) if (ring_epilogue) {
-            // steps of the mixed schedule from ring_from on (every FP32 stencil
-            // step): the epilogue in two-float arithmetic on the rings
+            // steps of the mixed schedule from ring_from on (the two-float
+            // recurrence): the epilogue in two-float arithmetic on the rings
             const dfc scr = dfc_of2(coef[0]), c1d = dfc_of2(c1);
             // one accumulator per spin component: four short dependency chains
             // of two-float additions instead of one of twelve

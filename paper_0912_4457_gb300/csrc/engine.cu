@@ -44,7 +44,7 @@ struct nk_ctx {
     double mu = 0.0, m_w = 0.0;
     bool mu_set = false;
     int j0 = -1;
-    int j1 = -1;   // first outer step whose recurrence runs in two-float arithmetic (< 0: j0)
+    int j1 = -1;   // first outer step whose recurrence runs in two-float arithmetic (< 0: none)
     int adapt_start = 0;   // adaptive k: first check (0: NK_ADAPT_FIRST(l))
     bool links = false;
     double2* U64 = nullptr;
@@ -284,42 +284,57 @@ struct Launcher {
     }
 };
 
-// The outer recurrence: norm/init, then per step the fused stencil kernel and
-// step 2 (mixed mode: the two-float stencil before step j0, FP32 from j0 on).
-int copy_mode_for(bool mixed, int j0, int j) {
-    return !mixed ? nk::kCopyNone : (j < j0 ? nk::kCopyDF : nk::kCopy32);
+// The stencil precision of outer step j: FP64 (NK_FP64); in the mixed
+// schedule the two-float stencil (or, with NK_PREFIX_FP64, the FP64 one)
+// before step j0 and FP32 from j0 on.
+struct Schedule {
+    bool mixed = false;
+    bool prefix64 = false;
+    int j0 = 0;
+    int prec(int j) const { return !mixed ? 64 : (j < j0 ? (prefix64 ? 64 : 48) : 32); }
+};
+
+// The copy of the new vectors that the stencil of step j reads: none for the
+// FP64 stencil, FP32 for the FP32 one; a two-float stencil reads the rings.
+int copy_mode_for(const Schedule& s, int j) {
+    const int p = s.prec(j);
+    return p == 32 ? nk::kCopy32 : (p == 48 ? nk::kCopyDF : nk::kCopyNone);
 }
 
-void enqueue_outer_init(const nk::Outer& o, bool mixed, int j0, Launcher& L, bool keep_status = false) {
+void enqueue_outer_init(const nk::Outer& o, const Schedule& s, Launcher& L, bool keep_status = false) {
     cudaStream_t st = L.st;
-    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_mode_for(mixed, j0, 0), st, keep_status); });
+    L.run(NK_CLASS_OTHER, 2, [&] { nk::launch_outer_init(o, copy_mode_for(s, 0), st, keep_status); });
 }
 
 // steps j in [j_begin, j_end); step 2 runs for every step but the last of the
-// whole recurrence (j = o.k - 1).  Mixed schedule: steps j >= o.ring_from
-// (<= j0) run the recurrence in two-float arithmetic on the rings.
-void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, int j_begin, int j_end, Launcher& L) {
+// whole recurrence (j = o.k - 1).  Mixed schedule: steps j >= o.ring_from run
+// the recurrence in two-float arithmetic on the rings (the optional two-float
+// recurrence); an FP64 step 2 stores two-float copies of its new vectors only
+// when a two-float stencil (the next step) or a ring step (from ring_from - 1
+// on, the previous vector of the first ring step) reads them.
+void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, const Schedule& s, int j_begin, int j_end, Launcher& L) {
     const Geom g = geom_of(c);
     const double kap = kappa_of(c);
     cudaStream_t st = L.st;
     for (int j = j_begin; j < j_end; ++j) {
-        const int prec = !mixed ? 64 : (j < j0 ? 48 : 32);
+        const int prec = s.prec(j);
         const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
         const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
         L.run(cls, 1, [&] { nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
         if (j < o.k - 1) {
-            const bool ring = mixed && j >= o.ring_from;
+            const bool ring = s.mixed && j >= o.ring_from;
+            const bool write_ring = s.mixed && (s.prec(j + 1) == 48 || j + 1 >= o.ring_from - 1);
             L.run(ring ? NK_CLASS_STEP2_DF : NK_CLASS_STEP2, 1, [&] {
-                nk::launch_outer_step2(o, j, copy_mode_for(mixed, j0, j + 1), ring, st);
+                nk::launch_outer_step2(o, j, copy_mode_for(s, j + 1), ring, write_ring, st);
             });
         }
     }
 }
 
-void enqueue_outer(nk_ctx* c, const nk::Outer& o, bool mixed, int j0, Launcher& L, int steps = -1,
+void enqueue_outer(nk_ctx* c, const nk::Outer& o, const Schedule& s, Launcher& L, int steps = -1,
                    bool keep_status = false) {
-    enqueue_outer_init(o, mixed, j0, L, keep_status);
-    enqueue_outer_steps(c, o, mixed, j0, 0, steps < 0 ? o.k : steps, L);
+    enqueue_outer_init(o, s, L, keep_status);
+    enqueue_outer_steps(c, o, s, 0, steps < 0 ? o.k : steps, L);
 }
 
 // b (ABI layout, device) -> q_0 of every RHS
@@ -331,24 +346,33 @@ void enqueue_load_sources(nk_ctx* c, const nk::Outer& o, const double* b_dev, in
 }
 
 int effective_j0(const nk_ctx* c, int k) { return c->j0 < 0 ? k / 4 : std::min(c->j0, k); }
-int effective_j1(const nk_ctx* c, int j0) { return c->j1 < 0 ? j0 : std::min(c->j1, j0); }
+// first step of the two-float recurrence; none (FP64 throughout) unless set
+int effective_j1(const nk_ctx* c) { return c->j1 < 0 ? (1 << 30) : c->j1; }
+
+Schedule schedule_of(const nk_ctx* c, unsigned flags, int k) {
+    Schedule s;
+    s.mixed = (flags & NK_MIXED) != 0;
+    s.prefix64 = (flags & NK_PREFIX_FP64) != 0;
+    s.j0 = effective_j0(c, k);
+    return s;
+}
 
 // Enqueues a whole solve (device pointers in ABI layout). Returns cudaError_t of launches.
 cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_dev, int n_rhs,
                           double p, unsigned flags, bool overlap, Launcher& L) {
     const bool mixed = (flags & NK_MIXED) != 0;
     const bool dp = (flags & NK_DOUBLE_PASS) != 0;
-    const int j0 = effective_j0(c, Lw.o.k);
+    const Schedule sch = schedule_of(c, flags, Lw.o.k);
     cudaStream_t st = L.st;
     nk::Outer o = Lw.o;
-    if (mixed) o.ring_from = effective_j1(c, j0);
+    if (mixed) o.ring_from = effective_j1(c);
     if (mixed && o.qr && !o.q_ring) o.q_df_from = o.ring_from + 1;   // written by the two-float step 2
     nk::Inner in = Lw.in;
     in.p_fixed = p;
     in.p_shared = (flags & NK_SHARED_P) ? 1 : 0;
     enqueue_load_sources(c, o, b_dev, n_rhs, L);
     L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_fill_int(Lw.kused, n_rhs, o.k, st); });
-    enqueue_outer(c, o, mixed, j0, L);
+    enqueue_outer(c, o, sch, L);
     L.run(NK_CLASS_INNER, nk::inner_launches(in), [&] { nk::launch_inner_lanczos(in, st); });
     cudaError_t e = cudaSuccess;
     L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(in, st); });
@@ -363,7 +387,7 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
         o.cp = Lw.cp;
         cudaMemsetAsync(Lw.y_soa, 0, sizeof(double2) * (size_t)c->N * n_rhs, st);
         enqueue_load_sources(c, o, b_dev, n_rhs, L);
-        enqueue_outer(c, o, mixed, j0, L, -1, true);
+        enqueue_outer(c, o, sch, L, -1, true);
     }
     L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_lift(o, Lw.cp, Lw.kused, Lw.y_soa, st); });
     L.run(NK_CLASS_OTHER, 1, [&] {
@@ -382,16 +406,16 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
                            std::vector<int>& kused_h, std::vector<int>& notconv, int& checks) {
     cudaStream_t st = L.st;
     const bool mixed = (flags & NK_MIXED) != 0;
-    const int j0 = effective_j0(c, kmax);
+    const Schedule sch = schedule_of(c, flags, kmax);
     nk::Outer o = Lw.o;
-    if (mixed) o.ring_from = effective_j1(c, j0);
+    if (mixed) o.ring_from = effective_j1(c);
     if (mixed && o.qr && !o.q_ring) o.q_df_from = o.ring_from + 1;
     nk::Inner in = Lw.in;
     in.p_fixed = p;
     in.p_shared = (flags & NK_SHARED_P) ? 1 : 0;
     in.kstride = kmax;
     enqueue_load_sources(c, o, b_dev, n_rhs, L);
-    enqueue_outer_init(o, mixed, j0, L);
+    enqueue_outer_init(o, sch, L);
     cudaMemsetAsync(Lw.c_prev, 0, sizeof(double2) * (size_t)kmax * n_rhs, st);
     int first = c->adapt_start > 0 ? c->adapt_start : NK_ADAPT_FIRST(ell);
     first = std::max(2, std::min(kmax, first + (first & 1)));
@@ -402,7 +426,7 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
     checks = 0;
     int j = 0, kc = first;
     while (true) {
-        enqueue_outer_steps(c, o, mixed, j0, j, kc, L);
+        enqueue_outer_steps(c, o, sch, j, kc, L);
         nk::Inner ic = in;
         ic.k = kc;
         ic.ell = std::min(ell, kc);
@@ -782,11 +806,15 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
     L.st = st;
     enqueue_load_sources(c, Lw.o, src, n_rhs, L);
     // the copies of the stencil input that `prec` reads are made by the last warm step
-    const int j0 = prec == 48 ? k : 0;
-    // the two-float stencil steps with the epilogue the solves will use
-    if (mixed) Lw.o.ring_from = prec == 48 && c->j1 != 0 ? k : 0;
+    Schedule sch;
+    sch.mixed = mixed;
+    sch.j0 = prec == 48 ? k : 0;
+    // the epilogue the solves will use: the two-float recurrence where it is
+    // selected (nk_set_df_recurrence; for the two-float stencil only from step 0),
+    // else FP64
+    if (mixed) Lw.o.ring_from = (prec == 48 ? c->j1 == 0 : c->j1 >= 0) ? 0 : k;
     const bool ring = mixed && Lw.o.ring_from == 0;
-    enqueue_outer(c, Lw.o, mixed, j0, L, kTuneWarm);
+    enqueue_outer(c, Lw.o, sch, L, kTuneWarm);
     const Geom g = geom_of(c);
     const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
     cudaEvent_t e0, e1;
@@ -799,7 +827,7 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
             nk::launch_dslash_step1(prec, U, g, Lw.o, kTuneWarm, kappa_of(c), c->mu, st);
             // no copy for the next stencil: the stencil of the next repetition
             // must read q_j again, so that every repetition recomputes the same step
-            nk::launch_outer_step2(Lw.o, kTuneWarm, nk::kCopyNone, ring, st);
+            nk::launch_outer_step2(Lw.o, kTuneWarm, nk::kCopyNone, ring, false, st);
         }
         NK_CUDA(c, cudaEventRecord(e1, st));
         NK_CUDA(c, cudaGetLastError());
@@ -1034,7 +1062,8 @@ int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsig
     Launcher L;
     L.st = st;
     enqueue_load_sources(c, Lw.o, b_dev, n_rhs, L);
-    enqueue_outer(c, Lw.o, (flags & NK_MIXED) != 0, effective_j0(c, k), L);
+    if (mixed) Lw.o.ring_from = effective_j1(c);
+    enqueue_outer(c, Lw.o, schedule_of(c, flags, k), L);
     NK_CUDA(c, cudaGetLastError());
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpyAsync(alpha, Lw.o.alpha, cb, cudaMemcpyDeviceToHost, st));

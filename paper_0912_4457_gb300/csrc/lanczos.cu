@@ -137,8 +137,10 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
     }
 }
 
+// write_ring: also store two-float copies of the new vectors in the rings
+// (read by a two-float stencil or by the two-float recurrence later on).
 template <bool TS>
-__global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mode) {
+__global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mode, int write_ring) {
     __shared__ double2 sh[33];
     __shared__ double2 coef[2];
     const int rhs = blockIdx.y;
@@ -167,14 +169,14 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
         else rr = mk(fma(-c3.x, q.x, rr.x), fma(-c3.x, q.y, rr.y));
         r[i] = rr;
         put_copy(o, copy_mode, false, vb + i, rr);
-        if (o.qr) ring_q(o, rhs, j + 1)[i] = dfc_of(rr);
+        if (write_ring) ring_q(o, rhs, j + 1)[i] = dfc_of(rr);
         if (TS) {
             const double2 pv = pj[i];
             double2 ll = l[i];
             ll = mk(fma(-c4.x, pv.x, fma(c4.y, pv.y, ll.x)), fma(-c4.x, pv.y, fma(-c4.y, pv.x, ll.y)));
             l[i] = ll;
             put_copy(o, copy_mode, true, vb + i, ll);
-            if (o.qr) ring_p(o, rhs, j + 1)[i] = dfc_of(ll);
+            if (write_ring) ring_p(o, rhs, j + 1)[i] = dfc_of(ll);
             acc.x = fma(rr.x, ll.x, fma(rr.y, ll.y, acc.x));   // conj(r) l
             acc.y = fma(rr.x, ll.y, fma(-rr.y, ll.x, acc.y));
         } else {
@@ -369,11 +371,12 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep
     k_init<<<grid, kThreads, 0, st>>>(o, copy_mode);
 }
 
-void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, cudaStream_t st) {
+void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, bool write_ring, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
+    const int wr = (write_ring && o.qr) ? 1 : 0;
     if (!ring || !o.qr) {   // FP64 step
-        if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
-        else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
+        if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode, wr);
+        else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode, wr);
     } else {
         if (o.two_sided) k_step2_df<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
         else k_step2_df<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
@@ -387,8 +390,10 @@ void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double
 
 void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y, cudaStream_t st) {
     dim3 grid((unsigned)((o.N + kThreads - 1) / kThreads), o.n_rhs);
+    // the two-float lift only where the two-float recurrence wrote two-float
+    // basis columns; an FP64 recurrence is lifted in FP64
     if (o.q_ring) k_zero_bad<<<grid, kThreads, 0, st>>>(o, y);
-    else if (o.qr) k_lift_df<<<grid, kThreads, sizeof(dfc) * (size_t)o.k, st>>>(o, cp, kused, y);
+    else if (o.qr && o.q_df_from < o.k) k_lift_df<<<grid, kThreads, sizeof(dfc) * (size_t)o.k, st>>>(o, cp, kused, y);
     else k_lift<<<grid, kThreads, 0, st>>>(o, cp, kused, y);
 }
 

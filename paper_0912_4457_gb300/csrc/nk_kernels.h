@@ -84,8 +84,8 @@ struct Outer {
     int q_df_from;
     // Mixed schedule: steps j >= ring_from run the recurrence (the stencil
     // kernel's epilogue and step 2) in two-float arithmetic on the rings;
-    // the steps before it in FP64.  ring_from <= j0 (the FP32 stencil steps
-    // always run on the rings).  Larger than k otherwise.
+    // the steps before it in FP64.  Larger than k (the default): the whole
+    // recurrence in FP64.
     int ring_from;
 };
 
@@ -131,10 +131,11 @@ void launch_dslash_step1(int precision, const void* U, const Geom& g, const Oute
                          double kappa, double mu, cudaStream_t st);
 int dslash_step1_blocks(const Geom& g, int threads);
 constexpr int kStencilMaxThreads = 256;
-// ring: the step belongs to the late (FP32-stencil) part of the mixed schedule,
-// which runs on the two-float rings; otherwise FP64 (the rings, if present,
-// still receive two-float copies of the new vectors).
-void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, cudaStream_t st);
+// ring: the step belongs to the two-float recurrence of the mixed schedule
+// (j >= ring_from), which runs on the two-float rings; otherwise FP64, and
+// write_ring says whether the FP64 step also stores two-float copies of its
+// new vectors in the rings (for a two-float stencil or a later ring step).
+void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, bool write_ring, cudaStream_t st);
 // kused[rhs]: outer steps whose basis vectors enter the lift of that RHS (k or,
 // adaptive, the converged size); coefficients beyond it are zero.
 void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st);

@@ -8,7 +8,7 @@
 // allocate; the caller passes only its inputs and outputs.
 //
 // The array is a module global: every GPU that loads this library holds it
-// (about 5.3 MB) until the process exits.  All calls share it and it keeps the
+// (about 5.9 MB) until the process exits.  All calls share it and it keeps the
 // last call's contents, so calls whose work overlaps on the GPU (different
 // streams, or different host threads) race on it; serialise them.
 #include <cuda_runtime.h>
@@ -96,7 +96,10 @@ extern "C" int nk_inner_sign_noalloc(const double* alpha_dev, const double* beta
     in.alpha = (const double2*)alpha_dev;
     in.beta = (const double2*)beta_dev;
     in.gamma = (const double2*)gamma_dev;
-    in.p_fixed = p;
+    // p > 0 fixes p; p == 0 estimates one p per RHS; p < 0 one p for the
+    // batch, from the extremes of the per-RHS estimates (as nk_inner_sign)
+    in.p_fixed = p > 0.0 ? p : 0.0;
+    in.p_shared = p < 0.0 ? 1 : 0;
     in.work = base + kOffWork;
     in.Vl = base + kOffVl;
     in.S = base + kOffS;
@@ -128,10 +131,18 @@ extern "C" int nk_inner_sign_noalloc(const double* alpha_dev, const double* beta
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_err(err, err_len, NK_ECUDA, cudaGetErrorString(e));
     for (int r = 0; r < n_rhs; ++r) {
-        if (status[r] == nk::kStatusBreakdown || status[r] == nk::kStatusInnerBreakdown)
-            return set_err(err, err_len, NK_EBREAKDOWN, "inner two-sided Lanczos: serious breakdown");
-        if (status[r] == nk::kStatusRhi || status[r] == nk::kStatusLU)
-            return set_err(err, err_len, NK_ERHI, "Roberts-Higham did not converge or p H_k is singular");
+        switch (status[r]) {
+            case nk::kStatusOK:
+            case nk::kStatusZeroSource: break;
+            case nk::kStatusBreakdown:
+            case nk::kStatusInnerBreakdown:
+                return set_err(err, err_len, NK_EBREAKDOWN, "inner two-sided Lanczos: serious breakdown");
+            case nk::kStatusRhi:
+            case nk::kStatusLU:
+                return set_err(err, err_len, NK_ERHI, "Roberts-Higham did not converge or p H_k is singular");
+            default:
+                return set_err(err, err_len, NK_ECUDA, "unexpected per-RHS status code");
+        }
     }
     return set_err(err, err_len, NK_OK, "no error");
 }

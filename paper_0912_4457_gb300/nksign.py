@@ -34,6 +34,7 @@ NK_NO_GRAPH = 0x10
 NK_PROFILE = 0x20
 NK_ASYNC = 0x40
 NK_SHARED_P = 0x80
+NK_PREFIX_FP64 = 0x100
 NK_MAX_RHS = 12
 NK_NCLASS = 9
 CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other", "step2_df"]
@@ -448,10 +449,26 @@ class Mlp:
         return Y
 
 
+def _check_complex_extent(name, t, need):
+    """Raises ValueError unless tensor t holds at least `need` complex128
+    entries (a float64 tensor counts two of its entries per complex)."""
+    per = 2 if str(getattr(t, "dtype", "")) == "torch.float64" else 1
+    have = int(t.numel()) // per
+    if need > 0 and have < need:
+        raise ValueError("%s holds %d complex entries, the call needs %d" % (name, have, need))
+
+
 def inner_sign_noalloc(alpha_dev, beta_dev, gamma_dev, c_dev, n_rhs, k, ell, p=0.0, hermitian=True,
                        stream=None):
     """nk_inner_sign_noalloc on caller-owned device tensors (complex128, shape
-    (n_rhs, k)); returns (rc, message).  The library allocates nothing."""
+    (n_rhs, k)); returns (rc, message).  The library allocates nothing.
+
+    The C entry point reads n_rhs * k complex entries of alpha, beta and gamma
+    and writes as many to c, so a tensor holding fewer is refused here with
+    ValueError before anything is launched."""
+    need = int(n_rhs) * int(k)
+    for name, t in (("alpha", alpha_dev), ("beta", beta_dev), ("gamma", gamma_dev), ("c", c_dev)):
+        _check_complex_extent(name, t, need)
     lib = load_library()
     buf = ctypes.create_string_buffer(256)
     rc = lib.nk_inner_sign_noalloc(_dev_ptr(alpha_dev), _dev_ptr(beta_dev), _dev_ptr(gamma_dev), int(n_rhs),

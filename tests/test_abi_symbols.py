@@ -69,3 +69,25 @@ def test_null_context_is_rejected_by_every_setter_and_wait(lib):
     assert lib.nk_wait(None, None) == -1
     lib.nk_get_launch.argtypes, lib.nk_get_launch.restype = [P, I, ctypes.c_uint, P], I
     assert lib.nk_get_launch(None, 12, 0, None) == -1
+
+
+def test_noalloc_binding_refuses_undersized_tensors_before_any_launch():
+    """inner_sign_noalloc reads n_rhs * k complex entries of each input and
+    writes as many to c; a smaller tensor is refused in the binding with
+    ValueError before the library is called (here with CPU tensors: the
+    size check comes before the device-pointer check)."""
+    torch = pytest.importorskip("torch")
+    from paper_0912_4457_gb300 import nksign
+    k = 64
+    ok = torch.zeros((2, k), dtype=torch.complex128)
+    short = torch.zeros((1, k), dtype=torch.complex128)
+    for args in ((short, ok, ok, ok), (ok, short, ok, ok), (ok, ok, short, ok), (ok, ok, ok, short)):
+        with pytest.raises(ValueError):
+            nksign.inner_sign_noalloc(*args, 2, k, 16, 0.0, True)
+    # float64 with interleaved (re, im) counts two entries per complex
+    f64 = torch.zeros((2, 2 * k - 1), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        nksign.inner_sign_noalloc(ok, ok, ok, f64, 2, k, 16, 0.0, True)
+    # the right sizes pass the check and then need a CUDA tensor
+    with pytest.raises(TypeError):
+        nksign.inner_sign_noalloc(ok, ok, ok, ok, 2, k, 16, 0.0, True)

@@ -48,7 +48,10 @@ def test_16x16x16x32_pure_gauge_double_pass_mixed():
     ctx.set_precision(384)
     bd = torch.from_numpy(freefield.rotate(W, b, dims)).cuda()
     y = torch.zeros_like(bd)
-    st, _ = ctx.sign_apply_dev(bd, y, n, 1024, 256, flags=NK_MIXED | NK_DOUBLE_PASS)
+    # one p for the batch (Eq. popt takes z_min, z_max from the spectrum of A,
+    # which the 12 sources share): a per-source estimate can land on a
+    # spurious gap Ritz value under rounding-level changes of H_k
+    st, _ = ctx.sign_apply_dev(bd, y, n, 1024, 256, flags=NK_MIXED | NK_DOUBLE_PASS | NK_SHARED_P)
     yh = y.cpu().numpy()
     errs = [rel(yh[i], exact[i]) for i in range(n)]
     assert max(errs) <= TOL, (errs, st["p"])

@@ -294,20 +294,35 @@ def test_mixed_precision_within_1e8(c1, mu, k, ell):
 
 @pytest.mark.parametrize("mu,k,ell", [(0.0, 384, 96), (0.3, 512, 128)])
 def test_df_recurrence_start(c1, mu, k, ell):
-    """nk_set_df_recurrence: the whole recurrence in two-float arithmetic
-    (j1 = 0) stays within the workload tolerance of the dense truth; j1 past
-    j0 is the default schedule (j1 = j0) bit for bit."""
+    """nk_set_df_recurrence: the default schedule keeps the recurrence in FP64
+    (a start at or past k is the same schedule, bit for bit); the two-float
+    recurrence from step 0 or from the FP32 switch j0 stays within the
+    workload tolerance of the dense truth and differs from the FP64 one."""
     dims, U, b, truth = c1
     ctx = make_ctx(dims, 101, mu)
     ctx.set_precision(k // 4)
     y_def, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
+    assert rel(y_def[0], truth[mu]) <= 1e-8
     ctx.set_df_recurrence(k)
     y_big, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
     assert np.array_equal(y_def, y_big)
-    ctx.set_df_recurrence(0)
-    y0, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
-    assert rel(y0[0], truth[mu]) <= 1e-8
-    assert not np.array_equal(y0, y_def)
+    for j1 in (0, k // 4):
+        ctx.set_df_recurrence(j1)
+        y0, _, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED)
+        assert rel(y0[0], truth[mu]) <= 1e-8
+        assert not np.array_equal(y0, y_def)
+    ctx.close()
+
+
+@pytest.mark.parametrize("mu,k,ell", [(0.0, 384, 96), (0.3, 512, 128)])
+def test_fp64_prefix_stencil(c1, mu, k, ell):
+    """NK_PREFIX_FP64: the steps before j0 apply the FP64 stencil; the result
+    stays within the workload tolerance of the dense truth."""
+    dims, U, b, truth = c1
+    ctx = make_ctx(dims, 101, mu)
+    ctx.set_precision(k // 4)
+    y, st, _ = ctx.sign_apply(b, k, ell, flags=NK_MIXED | nksign.NK_PREFIX_FP64)
+    assert rel(y[0], truth[mu]) <= 1e-8
     ctx.close()
 
 
