@@ -2,15 +2,17 @@
 """Throughput of the nested Krylov-Ritz sign function sgn(gamma5 D_w(mu)) b on GB300.
 
 One step = one batched solve of the workload's n_rhs sources (12 spin-colour
-point sources at the origin) by the nested method: outer two-sided Lanczos
-(two-float stencil for the first j0 steps, FP32 stencil after; the
-recurrence itself two-float from step j1 on, FP64 before), one p for the
-batch, LU of p H_k, inner two-sided Lanczos with H_k', batched
-Roberts-Higham (FP64), two-float lift.  The whole solve replays one CUDA
-graph; --inflight batches (default 4) run at a time on their own streams.
+point sources at the origin) by the nested method (Eq. nested, App. C steps
+2-6): outer two-sided Lanczos (two-float stencil for the first j0 steps,
+FP32 stencil after; the recurrence -- vector updates, inner products and
+their accumulation, the basis -- in FP64), one p for the batch, LU of p H_k,
+inner two-sided Lanczos with H_k', batched Roberts-Higham and the lift, all
+FP64.  The whole solve replays one CUDA graph; --inflight batches (default 4)
+run at a time on their own streams.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                    [--inflight B] [--j1 J] [--tune-cache FILE] [--mode bench|ncu]
+                    [--workload NAME] [--inflight B] [--tune-cache FILE] [--mode bench|ncu]
+                    [--quick]
 
 Prints one JSON line on rank 0.  Under torchrun each rank runs an independent
 replica of the workload on its own GPU (the method has no exchange step:
@@ -20,8 +22,8 @@ from __future__ import annotations
 
 import os
 
-# The CPU oracle leg uses one host thread (numpy elementwise code is single
-# threaded; this keeps its BLAS calls single threaded too).
+# numpy in the oracle legs: one BLAS thread per process (the all-cores CPU
+# baseline runs one process per core instead)
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -40,19 +42,26 @@ sys.path.insert(0, ROOT)
 METRIC = "sgn(A)b solves/s at rel err ≤1e-8, mixed+batched vs FP64 plain; stencil %HBM"
 TOL = 1e-8
 REF_BUDGET_S = 120.0
+CPU_SAMPLE_S = 12.0
+# nominal FP64 rate of GB300 (dense, all SMs): the peak of the FP64-ALU-bound kernels
+FP64_PEAK_TFLOPS = 1.25
 
 WORKLOADS = {
-    # 8^4, mu = 0.3 (two-sided), 12 point sources, mixed precision, one graph
-    # k and the FP32 switch j0 are the smallest (from a sweep) that give rel err
-    # <= 1e-8 on all 12 sources with these links; the whole recurrence runs in
-    # two-float arithmetic (j1 = 0: the same errors as j1 = j0 here)
-    "8^4-mu0.3-12pt": dict(dims=(8, 8, 8, 8), mu=0.3, m_w=-2.0, link_seed=103, k=896, ell=160, j0=256, j1=0,
-                           n_rhs=12, source="point", mixed=True),
-    "8^4-mu0-12pt": dict(dims=(8, 8, 8, 8), mu=0.0, m_w=-2.0, link_seed=103, k=768, ell=160, j0=64,
-                         n_rhs=12, source="point", mixed=True),
+    # 10^4, mu = 0.2, 12 point sources: the largest lattice of the paper's
+    # range that holds the stored basis (k = 1024: 23.6 GB per batch).  FP64
+    # converges by k = 1024 (1e-11 against k = 1536); the FP32 switch j0 sets
+    # the error of the mixed schedule (j0 = 128: 2.9e-8, 256: 1.5e-9,
+    # 384: 6e-11 against FP64 k = 1536), l = 128 leaves it unchanged.
+    "10^4-mu0.2-12pt": dict(dims=(10, 10, 10, 10), mu=0.2, m_w=-2.0, link_seed=104, k=1024, ell=128, j0=256,
+                            j1=-1, n_rhs=12, source="point", mixed=True, k_ref=1536, ell_ref=256),
+    # 8^4, mu = 0.3 (two-sided), 12 point sources
+    "8^4-mu0.3-12pt": dict(dims=(8, 8, 8, 8), mu=0.3, m_w=-2.0, link_seed=103, k=896, ell=160, j0=256, j1=-1,
+                           n_rhs=12, source="point", mixed=True, k_ref=1280, ell_ref=256),
+    "8^4-mu0-12pt": dict(dims=(8, 8, 8, 8), mu=0.0, m_w=-2.0, link_seed=103, k=768, ell=160, j0=64, j1=-1,
+                         n_rhs=12, source="point", mixed=True, k_ref=1280, ell_ref=256),
 }
-DEFAULT_WORKLOAD = "8^4-mu0.3-12pt"
-# stencil roofline case: 16^3 x 32, FP32 stencil, 12 RHS in one launch (A and A^dagger)
+DEFAULT_WORKLOAD = "10^4-mu0.2-12pt"
+# stencil roofline case: 16^3 x 32 (vectors larger than L2), FP32, 12 RHS of A and 12 of A^dagger
 STENCIL_DIMS = (16, 16, 16, 32)
 
 
@@ -161,27 +170,72 @@ def make_inputs(w):
     return U, b
 
 
-def oracle_leg(w, U, b, budget_s=40.0):
-    """The CPU oracle, as it stands, on a bounded sample: the nested method for
-    the first source of the workload (same k, l), one host thread."""
+# ---- oracle legs (CPU; spawned processes, never forked after CUDA is up) ----------
+
+def _oracle_solve(args):
+    """The nested oracle on one source (same k, l and p as the GPU batch)."""
+    U, dims, mu, m_w, b0, k, ell, p = args
     from oracle import nested
     t0 = time.perf_counter()
-    y, info = nested.sign_apply(U, w["dims"], w["mu"], w["m_w"], b[0], w["k"], w["ell"])
-    t = time.perf_counter() - t0
-    return y, t
+    y, _ = nested.sign_apply(U, dims, mu, m_w, b0, k, ell, p=p)
+    return y, time.perf_counter() - t0
+
+
+def _oracle_steps(args):
+    """k_s steps of the oracle's outer recurrence (App. B) from one source: the
+    bulk of the oracle's time, linear in k."""
+    dims, mu, m_w, link_seed, src, k_s = args
+    from oracle import nested
+    import inputs
+    U, _ = inputs.su3_links(dims, link_seed)
+    b = inputs.point_sources(dims)[src]
+    a, adag, herm = nested.operator(U, dims, mu, m_w)
+    t0 = time.perf_counter()
+    nested.outer_basis(a, adag, b, k_s, herm)
+    return time.perf_counter() - t0
+
+
+def cpu_baselines(w, budget_s=CPU_SAMPLE_S):
+    """The oracle as it stands on the host cores, on a bounded sample: its outer
+    recurrence for k_s of the k steps per source (calibrated to about budget_s
+    seconds), (a) one source in one process (1 thread), (b) one source per
+    process on every host core.  Each counts k_s / k of a solve per source (the
+    inner part, a few percent of the oracle's time, is left out, which favours
+    the oracle).  Returns both as solves/s."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    with ctx.Pool(1) as pool:
+        per_step = pool.map(_oracle_steps, [(w["dims"], w["mu"], w["m_w"], w["link_seed"], 0, 8)])[0] / 8
+        k_s = int(np.clip(budget_s / per_step, 8, w["k"]))
+        t1 = pool.map(_oracle_steps, [(w["dims"], w["mu"], w["m_w"], w["link_seed"], 0, k_s)])[0]
+    one = (k_s / w["k"]) / t1
+    n_all = cores
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        pool.map(_oracle_steps, [(w["dims"], w["mu"], w["m_w"], w["link_seed"], i % w["n_rhs"], k_s)
+                                 for i in range(n_all)])
+        tall = time.perf_counter() - t0
+    allc = n_all * (k_s / w["k"]) / tall
+    sample = ("oracle outer recurrence (numpy FP64), %d of the k = %d steps of a point source per process; "
+              "counts %d/%d of a solve per source" % (k_s, w["k"], k_s, w["k"]))
+    return ({"value": one, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample + ", 1 process",
+             "seconds": t1},
+            {"value": allc, "unit": "solves/s", "cores": cores, "kind": "oracle",
+             "sample": sample + ", %d processes on %d cores" % (n_all, cores), "seconds": tall})
 
 
 def run_reference(args, w, rank):
     """The oracle as it stands, on the host cores, as the reference arm.
 
-    A full oracle solve of one source takes tens of seconds, so each step is
-    a bounded sample of the workload: the oracle's outer recurrence (App. B,
-    two-sided for mu != 0), which is the bulk of its time and linear in k,
-    for k_s of the k steps, from source (step mod n_rhs); the metric counts
-    k_s / k of a solve per step.  k_s is sized from a short calibration so
-    that warm-up plus timed steps take about REF_BUDGET_S seconds.  The
-    inner part (p estimate, LU, inner Lanczos, RHi: a few percent of the
-    oracle's time) is left out of the sample, which favours the reference."""
+    A full oracle solve of one 10^4 source takes minutes, so each step is a
+    bounded sample of the workload: the oracle's outer recurrence (App. B,
+    two-sided for mu != 0), the bulk of its time and linear in k, for k_s of
+    the k steps, from source (step mod n_rhs); the metric counts k_s / k of a
+    solve per step.  k_s is sized from a short calibration so that warm-up
+    plus timed steps take about REF_BUDGET_S seconds.  The inner part (p
+    estimate, LU, inner Lanczos, RHi: a few percent of the oracle's time) is
+    left out of the sample, which favours the reference."""
     if rank != 0:
         return 0
     from oracle import nested
@@ -215,39 +269,98 @@ def run_reference(args, w, rank):
 
 
 def j1_of(w, args):
-    """First outer step whose recurrence runs in two-float arithmetic."""
+    """First outer step whose recurrence runs in two-float arithmetic (-1: none,
+    the recurrence is FP64 throughout)."""
     j1 = args.j1 if args.j1 is not None else w.get("j1", -1)
-    return w["j0"] if j1 < 0 else min(j1, w["j0"])
+    return -1 if j1 < 0 else j1
+
+
+def precision_text(w, j1):
+    if not w["mixed"]:
+        return "FP64"
+    rec = ("the recurrence (vector updates, inner products and their accumulation, basis V_k) FP64"
+           if j1 < 0 else
+           "the recurrence FP64 before step %d and two-float (about 48-bit) from it on, lift two-float" % j1)
+    return ("two-float (about 48-bit) stencil for outer steps < %d, FP32 stencil after; %s; H_k, p, LU of "
+            "pH_k, inner Lanczos, RHi%s FP64" % (w["j0"], rec, " and lift" if j1 < 0 else ""))
 
 
 def config_of(w, args):
     return {"workload": args.workload, "lattice": "x".join(str(d) for d in w["dims"]), "mu": w["mu"],
-            "m_w": w["m_w"], "k": w["k"], "ell": w["ell"], "n_rhs": w["n_rhs"],
+            "m_w": w["m_w"], "k": w["k"], "ell": w["ell"], "j0": w["j0"], "n_rhs": w["n_rhs"],
             "sources": "12 spin-colour point sources at the origin" if w["source"] == "point" else "gaussian",
             "links": "U = exp(i eps X), plaquette 0.59, seed %d" % w["link_seed"],
-            "precision": ("two-float (48-bit) stencil for outer steps < %d, FP32 stencil after; the recurrence "
-                          "(vector updates, inner products, basis) FP64 before step %d and two-float from it on; "
-                          "H_k, p, LU of pH_k, inner Lanczos and RHi FP64; lift two-float"
-                          % (w["j0"], j1_of(w, args))) if w["mixed"] else "FP64",
+            "precision": precision_text(w, j1_of(w, args)),
             "p": "one p per batch: Eq. popt with z_min, z_max of A estimated as the extremes over the "
                  "batch's H_k (power / inverse iteration)",
             "graph": True, "parallelism": "replicas" if args.gpus > 1 else "single",
             "batches_in_flight": args.inflight,
-            "l2": "working set (Krylov basis %.1f GB) larger than L2" % (
+            "l2": "working set (Krylov basis %.1f GB per batch) larger than L2" % (
                 12 * w["n_rhs"] * np.prod(w["dims"]) * w["k"] * 16 / 1e9)}
 
 
-def stencil_roofline(nk, torch, peaks):
-    """The solver's stencil kernel (FP32 Wilson stencil for 12 RHS of A and 12
-    of A^dagger in one launch, fused with the first half of the Lanczos step)
-    on 16^3 x 32, a lattice whose vectors are larger than L2.  Achieved
-    algorithmic GB/s from CUDA events around each launch on the launch stream
-    (NK_PROFILE), over a 16-step mixed solve with every stencil in FP32.
+def new_context(nk, w, U, j1, shape=None, n_rhs=None, flags=0):
+    c = nk.Context(w["dims"])
+    c.load_links(U)
+    c.set_mu_mw(w["mu"], w["m_w"])
+    c.set_precision(w.get("j0", -1))
+    c.set_df_recurrence(j1)
+    if shape is not None:
+        c.set_launch(n_rhs, flags, *shape)
+    return c
 
-    Algorithmic bytes of launch j (each array moved once): FP32 links 288 B/site;
-    per right vector FP32 input 96, FP64 q_{j-1} 192 (j > 0), FP64 dot vector
-    p_j 192, FP64 output r 192 (j < k-1); per left vector (j < k-1) FP32 input
-    96, FP64 p_{j-1} 192 (j > 0), FP64 output 192."""
+
+def timed_batches(nk, torch, ctxs, b_dev, ys, streams, w, flags, steps, warmup):
+    """warmup then `steps` whole batched solves, len(ctxs) in flight on their own
+    streams (NK_ASYNC + nk_wait); returns (ms, launches) of the timed region
+    (CUDA events on the current stream, which waits for every stream)."""
+    n_rhs, k, ell = w["n_rhs"], w["k"], w["ell"]
+    inflight = len(ctxs)
+    for _ in range(warmup):
+        for c_, y_ in zip(ctxs, ys):
+            c_.sign_apply_dev(b_dev, y_, n_rhs, k, ell, flags=flags)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s_ in streams:
+        s_.wait_stream(stream)
+    launches = 0
+    for i in range(steps):
+        c_ = ctxs[i % inflight]
+        if inflight > 1:
+            if i >= inflight:
+                st, _ = c_.wait()
+                launches += st["launches"]
+            c_.sign_apply_dev(b_dev, ys[i % inflight], n_rhs, k, ell, flags=flags | nk.NK_ASYNC,
+                              stream=streams[i % inflight])
+        else:
+            st, _ = c_.sign_apply_dev(b_dev, ys[0], n_rhs, k, ell, flags=flags)
+            launches += st["launches"]
+    if inflight > 1:
+        for c_ in ctxs:
+            st, _ = c_.wait()
+            launches += st["launches"]
+        for s_ in streams:
+            stream.wait_stream(s_)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), launches
+
+
+def rel_errs(y, ref):
+    return [float(np.linalg.norm(y[i] - ref[i]) / np.linalg.norm(ref[i])) for i in range(len(ref))]
+
+
+def stencil_roofline(nk, torch, peaks):
+    """The solver's FP32 stencil kernel alone (12 RHS of A and 12 of A^dagger
+    per launch, FP32 vectors in and out) on 16^3 x 32, a lattice whose vectors
+    are larger than L2: achieved algorithmic GB/s from CUDA events around
+    repeated launches on the launch stream (nk_stencil32_dev), against the
+    measured HBM copy bandwidth.  Algorithmic bytes per launch (each array
+    moved once): FP32 links 288 B/site + per vector FP32 input 96 B and FP32
+    output 96 B per site."""
     import inputs
     dims = STENCIL_DIMS
     ctx = nk.Context(dims)
@@ -255,32 +368,127 @@ def stencil_roofline(nk, torch, peaks):
     ctx.set_mu_mw(0.2, -2.0)
     V = int(np.prod(dims))
     n = 12
-    ctx.autotune(n, nk.NK_MIXED)
-    b = torch.zeros((n, 12 * V), dtype=torch.complex128, device="cuda")
-    b[:, :12] = torch.eye(12, dtype=torch.complex128, device="cuda")
-    y = torch.zeros_like(b)
-    k = 16
-    ctx.set_precision(0)
-    ctx.sign_apply_dev(b, y, n, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
-    st, _ = ctx.sign_apply_dev(b, y, n, k, 4, flags=nk.NK_MIXED | nk.NK_PROFILE)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(2 * n * 24 * V, dtype=torch.float32, device="cuda", generator=g)
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.stencil32_dev(x, out, n)
     torch.cuda.synchronize()
-    t_ms = st["t_class_ms"]["dslash"]
-    launches = st["n_class"]["dslash"]
-    total = 0
-    for j in range(k):
-        bj = 288 + n * (96 + (192 if j > 0 else 0) + 192 + (192 if j < k - 1 else 0))
-        if j < k - 1:
-            bj += n * (96 + (192 if j > 0 else 0) + 192)
-        total += V * bj
-    gbs = total / (t_ms * 1e-3) / 1e9
+    reps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):     # input and output (302 MB each) are larger than L2
+        ctx.stencil32_dev(x, out, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    total = V * (288 + 2 * n * 192)
+    gbs = total / (ms * 1e-3) / 1e9
     ctx.close()
-    return {"kernel": "k_dslash_step1<float, two-sided> (12 RHS A + 12 RHS A^dagger per launch)",
+    return {"kernel": "k_stencil32 (FP32 Wilson stencil, 12 RHS of A + 12 of A^dagger per launch, links "
+                      "loaded once per site block for all 24 vectors)",
             "lattice": "16x16x16x32", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-            "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "ms_per_launch": t_ms / launches,
-            "bytes_per_launch": total / launches, "launches": launches}
+            "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "ms_per_launch": ms,
+            "bytes_per_launch": total, "launches": reps, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
+    """Roofline entry for the kernel class with the largest device time.
+
+    Algorithmic work per launch, n_rhs sources, two-sided (Hermitian in
+    parentheses); each array moved once, each flop of the method counted once:
+      step2 (FP64): r -= c3 q_j, l -= c4 p_j, delta += r^dag l: 24 (8) FP64
+             flops per element -- FP64 ALU, peak the nominal 1.25 TFLOP/s;
+      dslash (FP32 stencil fused with the FP64 step-1 epilogue): the FP64
+             part, r = s - c1 q_{j-1} and H(j,j) += p_j^dag r (16 (12) flops
+             per element) plus l = t - c1' p_{j-1} (8 flops), against the FP64
+             peak (the FP32 stencil part runs beside it on the FP32 pipe);
+      dslash_df: the two-float stencil, 1320 flops per site and vector;
+             two-float arithmetic costs 9 FP32 instructions per flop on
+             average, so its ALU peak is 152 x 128 x f_SM / 9;
+      lift (FP64): y += c_j q_j over k columns: 8 FP64 flops per element and
+             column -- FP64 ALU;
+      inner / rhi: FP64 ALU, latency bound on few SMs (not modelled).
+    """
+    V = int(np.prod(w["dims"]))
+    N = 12 * V
+    n_rhs = w["n_rhs"]
+    two = w["mu"] != 0.0
+    nv = (2 if two else 1) * n_rhs
+    ms = tc[dom] / max(1, nc[dom])
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    def alu64(kernel, flops, extra=None):
+        tf = flops / (ms * 1e-3) / 1e12
+        r = {"kernel": kernel, "bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "frac": tf / FP64_PEAK_TFLOPS, "ms_per_launch": ms, "flops_per_launch": flops,
+             "peak_derivation": "nominal dense FP64 rate of GB300 (1.25 TFLOP/s, 152 SMs)"}
+        r.update(extra or {})
+        return r
+
+    if dom == "step2":
+        return alu64("k_step2 (FP64)", (24 if two else 8) * N * n_rhs,
+                     {"traffic": profiled_traffic("k_step2"),
+                      "algorithmic_bytes_per_launch": (128 if two else 64) * N * n_rhs})
+    if dom == "dslash":
+        return alu64("k_dslash_step1<float> (FP32 stencil + FP64 step-1 epilogue)",
+                     ((16 + 8) if two else 12) * N * n_rhs,
+                     {"traffic": profiled_traffic("k_dslash_step1<float>")})
+    if dom == "lift":
+        return alu64("k_lift (FP64)", 8.0 * N * n_rhs * w["k"], {"traffic": None})
+    if dom == "dslash_df":
+        flops = 1320.0 * V * nv
+        tf = flops / (ms * 1e-3) / 1e12
+        peak = 152 * 128 * (sm_mhz or 2070.0) * 1e6 / 9.0 / 1e12
+        return {"kernel": "k_dslash_step1<df> (two-float stencil fused with step 1)", "bound": "alu",
+                "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                "traffic": profiled_traffic("k_dslash_step1<df>"), "ms_per_launch": ms, "flops_per_launch": flops,
+                "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": None, "traffic": None, "ms_per_launch": ms, "hbm_gbs": hbm}
+
+
+def learned_arm(nk, torch, ctx, b_dev, w, flags):
+    """Adaptive k (tol = TOL, NK_ADAPT_STEP = 64) on the batch, (a) from the
+    default start NK_ADAPT_FIRST(l) with the workload's l, (b) from the
+    predicted sizes: the predictor (predictor_weights.npz, trained on runs of
+    the method) gives (k, l) from the features of source 0; checks start at
+    k_pred - 128 with l = 1.5 l_pred.  Solves/s count the sources that the
+    adaptive stop accepted (NK_OK); each arm is timed on a warm repeat."""
+    from paper_0912_4457_gb300 import predictor
+    n_rhs = w["n_rhs"]
+    y = torch.zeros_like(b_dev)
+    k_max = predictor.K_MAX
+    out = {}
+    m = predictor.load_model()
+    t0 = time.perf_counter()
+    k_pred, l_pred = ctx.predict_sizes(m, b_dev[:1].contiguous(), k_max)
+    t_pred = time.perf_counter() - t0
+    l_use = min(256, k_pred, 2 * int(np.ceil(0.75 * l_pred)))
+    for name, start, ell in (("adaptive_default", 0, w["ell"]), ("adaptive_predicted", max(64, k_pred - 128), l_use)):
+        ctx.set_adapt_start(start)
+        try:
+            for rep in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, rc = ctx.sign_apply_dev(b_dev, y, n_rhs, k_max, ell, tol=TOL, flags=flags, check=False)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+        finally:
+            ctx.set_adapt_start(0)
+        ok = sum(1 for s in st["status"] if s == 0)
+        out[name] = {"value": ok / wall, "unit": "solves/s", "wall_ms": 1e3 * wall, "device_ms": st["t_total_ms"],
+                     "checks": st["checks"], "k_rhs": st["k_rhs"], "ell": ell, "start": start or None, "rc": rc,
+                     "y": y.cpu().numpy()}
+    out["prediction"] = {"k": k_pred, "ell": l_pred, "ms": 1e3 * t_pred}
+    m.close()
+    return out
 
 
 def run_gpu(args, w, rank, world, local_rank):
+    import multiprocessing as mp
     import torch
     import paper_0912_4457_gb300 as nk
     from paper_0912_4457_gb300 import build as nkbuild
@@ -290,83 +498,61 @@ def run_gpu(args, w, rank, world, local_rank):
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
-    torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
         import torch.distributed as dist
     peaks = measured_peaks()
     U, b_host = make_inputs(w)
     n_rhs, k, ell = w["n_rhs"], w["k"], w["ell"]
+    j1 = j1_of(w, args)
     flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_SHARED_P
-    ctx = nk.Context(w["dims"])
-    ctx.load_links(U)
-    ctx.set_mu_mw(w["mu"], w["m_w"])
-    ctx.set_precision(w.get("j0", -1))
-    ctx.set_df_recurrence(j1_of(w, args))
+    torch.cuda.set_device(local_rank)
+    ctx = new_context(nk, w, U, j1)
     # launch shape of the outer recurrence: timed on 16 synthetic steps, kept
     shape, tune_ms = ctx.autotune(n_rhs, flags, args.tune_cache)
-    stream = torch.cuda.current_stream()
     b_dev = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
-    y_dev = torch.zeros_like(b_dev)
-    # Batches in flight: each step is one whole batched solve; with two contexts
-    # on two streams the next batch's outer recurrence (all SMs) runs while the
-    # previous batch's inner part and RHi (12 and 96 SMs) finish.
-    inflight = max(1, args.inflight)
-    ctxs, ys, streams = [ctx], [y_dev], [torch.cuda.Stream() for _ in range(inflight)]
-    for _ in range(1, inflight):
-        c2 = nk.Context(w["dims"])
-        c2.load_links(U)
-        c2.set_mu_mw(w["mu"], w["m_w"])
-        c2.set_precision(w.get("j0", -1))
-        c2.set_df_recurrence(j1_of(w, args))
-        c2.set_launch(n_rhs, flags, *shape)
-        ctxs.append(c2)
-        ys.append(torch.zeros_like(b_dev))
-    for _ in range(args.warmup):
-        for c_, y_ in zip(ctxs, ys):
-            st, _ = c_.sign_apply_dev(b_dev, y_, n_rhs, k, ell, flags=flags)
+    st0, _ = ctx.sign_apply_dev(b_dev, torch.zeros_like(b_dev), n_rhs, k, ell, flags=flags)
     torch.cuda.synchronize()
+    p_batch = float(st0["p"][0])
+    # the oracle on source 0 (same k, l, p), in a spawned process beside the GPU work
+    pool = None
+    if rank == 0 and not args.quick:
+        pool = mp.get_context("spawn").Pool(1)
+        oracle_job = pool.apply_async(_oracle_solve, ((U, w["dims"], w["mu"], w["m_w"], b_host[0], k, ell, p_batch),))
+
+    # ---- headline: fixed k, batches in flight -----------------------------------
+    inflight = max(1, args.inflight)
+    ctxs = [ctx] + [new_context(nk, w, U, j1, shape, n_rhs, flags) for _ in range(1, inflight)]
+    ys = [torch.zeros_like(b_dev) for _ in range(inflight)]
+    streams = [torch.cuda.Stream() for _ in range(inflight)]
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.3)
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for s_ in streams:
-        s_.wait_stream(stream)
-    launches = 0
-    for i in range(args.steps):
-        c_ = ctxs[i % inflight]
-        if inflight > 1:
-            if i >= inflight:       # the previous batch of this context
-                st, _ = c_.wait()
-                launches += st["launches"]
-            c_.sign_apply_dev(b_dev, ys[i % inflight], n_rhs, k, ell, flags=flags | nk.NK_ASYNC,
-                              stream=streams[i % inflight])
-        else:
-            st, _ = c_.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
-            launches += st["launches"]
-    if inflight > 1:
-        for c_ in ctxs:
-            st, rc_w = c_.wait()
-            launches += st["launches"]
-        for s_ in streams:
-            stream.wait_stream(s_)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms_raw, launches = timed_batches(nk, torch, ctxs, b_dev, ys, streams, w, flags, args.steps, args.warmup)
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist)
-    y = y_dev.cpu().numpy()
+    ms = max_over_ranks(ms_raw, dist)
+    y = ys[(args.steps - 1) % inflight].cpu().numpy()
+    # the two-float recurrence (a second, labelled line of the same workload)
+    df = None
+    if not args.quick:
+        for c_ in ctxs:
+            c_.set_df_recurrence(0)
+        ms_df, _ = timed_batches(nk, torch, ctxs, b_dev, ys, streams, w, flags, max(4, args.steps // 2), 1)
+        y_df = ys[(max(4, args.steps // 2) - 1) % inflight].cpu().numpy()
+        for c_ in ctxs:
+            c_.set_df_recurrence(j1)
+        df = {"ms_per_step": ms_df / max(4, args.steps // 2), "y": y_df}
     for c_ in ctxs[1:]:
         c_.close()
     # latency of one batch with nothing else in flight
     l0 = torch.cuda.Event(enable_timing=True)
     l1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    y_dev = torch.zeros_like(b_dev)
     l0.record(stream)
     for _ in range(2):
         ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags)
@@ -374,94 +560,125 @@ def run_gpu(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     latency_ms = l0.elapsed_time(l1) / 2
 
-    # e2e: host buffers in pinned memory, through the host-pointer C entry point
+    # ---- e2e: pinned host buffers through the host-pointer C entry point -----------
     b_pin = torch.from_numpy(np.ascontiguousarray(b_host)).pin_memory()
     y_pin = torch.zeros_like(b_pin).pin_memory()
     bp, yp = b_pin.numpy(), y_pin.numpy()
-    ctx.sign_apply(bp, k, ell, flags=flags)
+    _lib_host_solve(ctx, bp, yp, k, ell, flags)
     e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         _lib_host_solve(ctx, bp, yp, k, ell, flags)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    # comparator named by the metric: the plain all-FP64 nested method, one
-    # source per solve, same k and l, on the same GPU (source 0)
+    # ---- comparator named by the metric: all-FP64 nested method, one source per solve
     b1 = b_dev[:1].contiguous()
     y1 = torch.zeros_like(b1)
-    ctx.sign_apply_dev(b1, y1, 1, k, ell, flags=nk.NK_FP64)
+    ctx.sign_apply_dev(b1, y1, 1, k, ell, p=p_batch, flags=nk.NK_FP64)
     torch.cuda.synchronize()
     f0 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
     nrep = 2
     f0.record(stream)
     for _ in range(nrep):
-        ctx.sign_apply_dev(b1, y1, 1, k, ell, flags=nk.NK_FP64)
+        ctx.sign_apply_dev(b1, y1, 1, k, ell, p=p_batch, flags=nk.NK_FP64)
     f1.record(stream)
     torch.cuda.synchronize()
     fp64_ms = f0.elapsed_time(f1) / nrep
     y_fp64 = y1.cpu().numpy()[0]
 
-    # per-kernel-class device times (NK_PROFILE: CUDA events around each launch)
+    # ---- converged FP64 reference for every source (GPU, larger k and l) ----------
+    yref = torch.zeros_like(b_dev)
+    ctx.sign_apply_dev(b_dev, yref, n_rhs, w["k_ref"], w["ell_ref"], flags=nk.NK_FP64 | nk.NK_SHARED_P)
+    torch.cuda.synchronize()
+    y_ref = yref.cpu().numpy()
+    err_ref = rel_errs(y, y_ref)
+
+    # ---- per-kernel-class device times (NK_PROFILE: CUDA events around each launch)
     stp, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags | nk.NK_PROFILE)
     torch.cuda.synchronize()
+    learned = None if args.quick else learned_arm(nk, torch, ctx, b_dev, w, flags)
     if rank != 0:
         ctx.close()
         return 0
+    sten = stencil_roofline(nk, torch, peaks)
 
-    # accuracy: the oracle on source 0 (this is also the timed CPU baseline sample)
-    y_or, t_or = oracle_leg(w, U, b_host)
-    err0 = float(np.linalg.norm(y[0] - y_or) / np.linalg.norm(y_or))
-    # the paper's sgn^2 estimate (Sec. 3) for all sources: apply the solve to y
-    yy = torch.zeros_like(y_dev)
-    y_src = torch.from_numpy(np.ascontiguousarray(y)).cuda()
-    ctx.sign_apply_dev(y_src, yy, n_rhs, k, ell, flags=flags)
-    torch.cuda.synchronize()
-    x2 = yy.cpu().numpy()
-    eps = [float(np.linalg.norm(x2[i] - b_host[i]) / (2 * np.linalg.norm(b_host[i]))) for i in range(n_rhs)]
-    err_fp64 = float(np.linalg.norm(y_fp64 - y_or) / np.linalg.norm(y_or))
-    ok = sum(1 for e in eps if e <= TOL)
-    if err0 > TOL:
+    # ---- accuracy: every source against the FP64 reference; source 0 against the oracle
+    err0 = None
+    t_or = None
+    if pool is not None:
+        y_or, t_or = oracle_job.get()
+        pool.close()
+        pool.join()
+        err0 = float(np.linalg.norm(y[0] - y_or) / np.linalg.norm(y_or))
+        err_fp64_or = float(np.linalg.norm(y_fp64 - y_or) / np.linalg.norm(y_or))
+    ok = sum(1 for e in err_ref if e <= TOL)
+    if err0 is not None and err0 > TOL:
         ok = 0
-    solves_per_step = ok
-
-    value = whole_job_value(solves_per_step, args.steps, ms, world)
-    e2e_value = solves_per_step / e2e_s
+    value = whole_job_value(ok, args.steps, ms, world)
+    e2e_value = ok / e2e_s
     tc = stp["t_class_ms"]
     nc = stp["n_class"]
     tot = sum(tc.values())
     share = {kk: (tc[kk] / tot if tot else 0.0) for kk in tc}
     dom = max(tc, key=lambda kk: tc[kk])
     roof = dominant_roofline(dom, tc, nc, w, peaks, clocks.get("sm_mhz"))
-    sten = stencil_roofline(nk, torch, peaks)
+    fp64_ok = float(np.linalg.norm(y_fp64 - y_ref[0]) / np.linalg.norm(y_ref[0])) <= TOL
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "latency_ms_one_batch": latency_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": config_of(w, args),
-        "accuracy": {"rel_err_vs_oracle_src0": err0, "eps_sgn2_max": max(eps), "solves_meeting_tol": ok,
-                     "tol": TOL},
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "latency_ms_one_batch": latency_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": config_of(w, args),
+        "accuracy": {"tol": TOL, "solves_meeting_tol": ok,
+                     "rel_err_vs_fp64_reference": err_ref,
+                     "fp64_reference": "the same batch all in FP64 at k = %d, l = %d (converged: k = 1024 is "
+                                       "within 1e-11 of it)" % (w["k_ref"], w["ell_ref"]),
+                     "rel_err_vs_oracle_src0": err0,
+                     "oracle": "nested oracle (numpy FP64) on source 0, same k, l and p"},
         "e2e": {"value": e2e_value, "unit": "solves/s",
                 "h2d_bytes_per_step": int(b_host.nbytes), "d2h_bytes_per_step": int(b_host.nbytes)},
-        "fp64_plain": {"value": (1.0 / (fp64_ms * 1e-3)) if err_fp64 <= TOL else 0.0, "unit": "solves/s",
-                       "ms_per_solve": fp64_ms, "rel_err_vs_oracle_src0": err_fp64,
-                       "what": "same method, all FP64, one source per solve, same k and l, same GPU"},
+        "fp64_plain": {"value": (1.0 / (fp64_ms * 1e-3)) if fp64_ok else 0.0, "unit": "solves/s",
+                       "ms_per_solve": fp64_ms,
+                       "rel_err_vs_fp64_reference_src0": float(np.linalg.norm(y_fp64 - y_ref[0]) /
+                                                               np.linalg.norm(y_ref[0])),
+                       "what": "same method, all FP64 (stencil and recurrence), one source per solve, same k, "
+                               "l and p, same GPU"},
         "speedup_vs_fp64_plain": (value / world) / (1.0 / (fp64_ms * 1e-3)),
         "gpu_launches": launches,
         "launch_shape": {"stencil_threads": shape[0], "stencil_order": shape[1], "step2_blocks": shape[2],
                          "early_threads": shape[3], "early_order": shape[4], "stencil_split": shape[5],
-                         "early_split": shape[6],
-                         "autotune_ms_per_outer_step": tune_ms},
+                         "early_split": shape[6], "autotune_ms_per_outer_step": tune_ms},
         "rhi_iters": stp["rhi_iters"],
         "kernel_class_ms": {kk: round(v, 3) for kk, v in tc.items()},
+        "kernel_time_share": {kk: round(v, 4) for kk, v in share.items()},
         "roofline": roof,
         "stencil_roofline": sten,
-        "kernel_time_share": {kk: round(v, 4) for kk, v in share.items()},
-        "cpu_baseline": {"value": 1.0 / t_or, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "nested method (numpy FP64 oracle) on source 0 of the workload, same k and l, "
-                                   "%.1f s" % t_or},
         "clocks": clocks,
     }
+    if df is not None:
+        e_df = rel_errs(df["y"], y_ref)
+        ok_df = sum(1 for e in e_df if e <= TOL)
+        line["two_float_recurrence"] = {
+            "value": whole_job_value(ok_df, 1, df["ms_per_step"], world), "unit": "solves/s",
+            "ms_per_step": df["ms_per_step"], "max_rel_err_vs_fp64_reference": max(e_df),
+            "what": "the same workload with the recurrence in two-float (about 48-bit) arithmetic from step 0 "
+                    "(nk_set_df_recurrence(0)) and a two-float lift; not the headline (narrower than FP64)"}
+    if learned is not None:
+        blk = {}
+        for name in ("adaptive_default", "adaptive_predicted"):
+            r = dict(learned[name])
+            e = rel_errs(r.pop("y"), y_ref)
+            r["max_rel_err_vs_fp64_reference"] = max(e)
+            blk[name] = r
+        blk["prediction"] = learned["prediction"]
+        blk["fixed_k"] = {"value": value, "k": k, "ell": ell}
+        line["learned"] = blk
+    if pool is not None:
+        one, allc = cpu_baselines(w)
+        line["cpu_baseline"] = one
+        line["cpu_baseline_all_cores"] = allc
+        line["accuracy"]["rel_err_fp64_plain_vs_oracle_src0"] = err_fp64_or
+        line["accuracy"]["oracle_seconds"] = t_or
     print(json.dumps(line))
     ctx.close()
     return 0
@@ -478,11 +695,7 @@ def run_ncu(args, w):
     if args.ncu_k:   # half of the shortened recurrence in each stencil precision
         w = dict(w, k=args.ncu_k, ell=min(w["ell"], args.ncu_k), j0=min(w["j0"], args.ncu_k // 2))
     U, b_host = make_inputs(w)
-    ctx = nk.Context(w["dims"])
-    ctx.load_links(U)
-    ctx.set_mu_mw(w["mu"], w["m_w"])
-    ctx.set_precision(w.get("j0", -1))
-    ctx.set_df_recurrence(j1_of(w, args))
+    ctx = new_context(nk, w, U, j1_of(w, args))
     flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_SHARED_P | nk.NK_NO_GRAPH
     # with --tune-cache from a plain bench run the shape is read, not timed
     ctx.autotune(w["n_rhs"], flags, args.tune_cache)
@@ -496,6 +709,33 @@ def run_ncu(args, w):
     return 0
 
 
+def run_stencil(args):
+    """--mode stencil: --warmup + 1 launches of the multi-RHS FP32 stencil alone
+    (nk_stencil32_dev: 12 RHS of A and 12 of A^dagger) on 16^3 x 32, for ncu
+    captures of that kernel; prints its CUDA-event time per launch to stderr."""
+    import torch
+    import inputs
+    import paper_0912_4457_gb300 as nk
+    dims = STENCIL_DIMS
+    ctx = nk.Context(dims)
+    ctx.load_links(inputs.su3_links(dims, 105)[0])
+    ctx.set_mu_mw(0.2, -2.0)
+    V = int(np.prod(dims))
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(2 * 12 * 24 * V, dtype=torch.float32, device="cuda", generator=g)
+    out = torch.empty_like(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for i in range(args.warmup + 1):
+        e0.record()
+        ctx.stencil32_dev(x, out, 12)
+        e1.record()
+    torch.cuda.synchronize()
+    print("stencil32 16x16x16x32, 24 vectors: %.3f ms per launch" % e0.elapsed_time(e1), file=sys.stderr)
+    ctx.close()
+    return 0
+
+
 def _lib_host_solve(ctx, bp, yp, k, ell, flags):
     import ctypes
     from paper_0912_4457_gb300 import nksign
@@ -505,98 +745,26 @@ def _lib_host_solve(ctx, bp, yp, k, ell, flags):
     ctx._check(rc)
 
 
-def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
-    """Roofline entry for the kernel class with the largest device time.
-
-    Algorithmic work per launch, n_rhs sources, two-sided (Hermitian in
-    parentheses); each array moved once, each flop of the method counted once:
-      dslash_df: the two-float stencil, 1320 flops per site and vector
-             (2 n_rhs (n_rhs) vectors).  Two-float arithmetic costs 11 FP32
-             instructions per add and 7 per multiply (TwoSum / FMA-TwoProd
-             with renormalisation), 9 on average for the stencil's equal mix, so
-             its ALU peak is the FP32 issue rate / 9:
-             152 SMs x 128 lanes x f_SM / 9 (f_SM the median SM clock sampled
-             during the timed region);
-      dslash (FP32 stencil fused with step 1): per site links 288 B + per
-             vector FP32 input 96 B, FP64 q_{j-1} and dot vector 2 x 192 B,
-             FP64 output 192 B -- HBM;
-      step2: 24 (8) FP64 flops per element -- FP64 ALU, 1.0 TFLOP/s measured
-             DFMA rate;
-      step2_df: reads q_j, r, p_j, l and writes r, l (two-float rings), the
-             basis column and, before an FP32 stencil, the FP32 copies: 128
-             (64) B per element, 112 (56) without the copies -- HBM;
-      lift: reads V_k once, 16 B x k per element -- HBM.
-    """
-    V = int(np.prod(w["dims"]))
-    N = 12 * V
-    n_rhs = w["n_rhs"]
-    two = w["mu"] != 0.0
-    nv = (2 if two else 1) * n_rhs
-    ms = tc[dom] / max(1, nc[dom])
-    fp64_peak = 1.0  # TFLOP/s, measured DFMA rate of this GB300
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    if dom == "dslash_df":
-        flops = 1320.0 * V * nv
-        tf = flops / (ms * 1e-3) / 1e12
-        peak = 152 * 128 * (sm_mhz or 2070.0) * 1e6 / 9.0 / 1e12
-        return {"kernel": "k_dslash_step1<df> (two-float stencil fused with step 1)", "bound": "alu",
-                "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-                "traffic": profiled_traffic("k_dslash_step1<df>"),
-                "ms_per_launch": ms, "flops_per_launch": flops,
-                "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
-    if dom == "step2_df":
-        # launches j1 <= j <= k - 2; those with j + 1 >= j0 also write the FP32
-        # copy the next (FP32) stencil reads, the others do not
-        k, j0 = w["k"], w["j0"]
-        j1 = w.get("j1", -1)
-        j1 = j0 if j1 < 0 else min(j1, j0)
-        n_df = max(1, k - 1 - j1)
-        n_copy = min(n_df, k - j0)
-        per_el = ((n_copy * (128 if two else 64) + (n_df - n_copy) * (112 if two else 56)) / n_df)
-        b = per_el * N * n_rhs
-        gbs = b / (ms * 1e-3) / 1e9
-        return {"kernel": "k_step2_df (two-float step 2 on the rings)", "bound": "hbm",
-                "achieved": gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": profiled_traffic("k_step2_df"), "ms_per_launch": ms,
-                "algorithmic_bytes_per_launch": b}
-    if dom == "step2":
-        flops = (24 if two else 8) * N * n_rhs
-        tf = flops / (ms * 1e-3) / 1e12
-        return {"kernel": "k_step2", "bound": "alu", "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": tf / fp64_peak, "traffic": profiled_traffic("k_step2"), "ms_per_launch": ms,
-                "algorithmic_bytes_per_launch": (112 if two else 56) * N * n_rhs}
-    if dom in ("dslash", "dslash64"):
-        b = V * (288 + nv * (96 + 192)) + V * n_rhs * 2 * 192
-        gbs = b / (ms * 1e-3) / 1e9
-        return {"kernel": "k_dslash_step1", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": gbs / hbm, "traffic": profiled_traffic("k_dslash_step1<float>"),
-                "ms_per_launch": ms}
-    if dom == "lift":
-        b = n_rhs * w["k"] * N * 16
-        gbs = b / (ms * 1e-3) / 1e9
-        return {"kernel": "k_lift", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": gbs / hbm, "traffic": None, "ms_per_launch": ms}
-    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": None, "traffic": None, "ms_per_launch": ms}
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--mode", choices=["bench", "ncu"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "ncu", "stencil"], default="bench",
                     help="ncu: run --warmup solves and then one solve kernel by kernel (no graph, no oracle, "
-                         "no output line), for launch lists and captures under ncu")
+                         "no output line), for launch lists and captures under ncu; stencil: --warmup + 1 "
+                         "launches of the FP32 stencil alone on 16^3 x 32")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
     ap.add_argument("--j1", type=int, default=None,
-                    help="first outer step with a two-float recurrence (default: the workload's)")
+                    help="first outer step with a two-float recurrence (default: the workload's; -1: none)")
     ap.add_argument("--inflight", type=int, default=4,
                     help="batches in flight (contexts on their own streams); 1: one synchronous solve per step")
     ap.add_argument("--tune-cache", default=None,
                     help="launch-shape cache file (read if it has the workload's shape, else written)")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: no oracle, CPU baselines, two-float line or learned arm")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -606,6 +774,8 @@ def main():
         return run_reference(args, w, rank)
     if args.mode == "ncu":
         return run_ncu(args, w)
+    if args.mode == "stencil":
+        return run_stencil(args)
     if world > 1:
         import torch
         import torch.distributed as dist

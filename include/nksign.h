@@ -52,7 +52,8 @@ extern "C" {
 #define NK_ENOTCONV (-4)    /* adaptive k: tolerance not met at k_max */
 #define NK_ERHI (-5)        /* Roberts-Higham iteration did not converge */
 #define NK_ECUDA (-6)       /* CUDA runtime error */
-#define NK_ETIMEOUT (-7)    /* a bounded device-side wait ran out */
+#define NK_ETIMEOUT (-7)    /* reserved: no kernel of this library waits on a device-side flag
+                               (the RHi clusters synchronise with hardware cluster barriers) */
 #define NK_ESTATE (-8)      /* call out of order (e.g. no links loaded) */
 
 /* Solve flags (bitwise or). */
@@ -72,6 +73,16 @@ extern "C" {
                                nk_stats.t_class_ms / n_class (implies NK_NO_GRAPH) */
 #define NK_PREFIX_FP64 0x100u /* with NK_MIXED: the outer steps before j0 apply the FP64 stencil
                                instead of the two-float one (nk_set_precision) */
+#define NK_EPS_EST 0x200u   /* also estimate the error of every result as in Sec. 3: apply the
+                               method a second time to the result, x~ = approx(approx(x)), and
+                               report eps = |x~ - x| / (2 |x|) per RHS in nk_stats.eps_sgn2
+                               (doubles the work; nk_sign_apply(_dev) only, not with NK_ASYNC) */
+#define NK_PREDICT 0x400u   /* with tol > 0: predict (k, l) with the predictor given to
+                               nk_set_predictor from source 0 of the batch (nk_predict_sizes),
+                               start the adaptive checks at k_pred - 2 NK_ADAPT_STEP with
+                               l = min(2 ceil(0.75 l_pred), k_pred, 256) (k stays the maximum);
+                               if the tolerance is not met by k with that l, the solve is
+                               repeated once with the caller's l from the default start */
 
 #define NK_MAX_RHS 12
 
@@ -107,6 +118,15 @@ typedef struct nk_stats {
     int launches;                      /* kernels this library launched for the solve */
     double t_class_ms[NK_NCLASS];      /* NK_PROFILE: summed device time per kernel class */
     int n_class[NK_NCLASS];            /* NK_PROFILE: launches per kernel class */
+    /* Device time split as in the paper's timings (Sec. 3, Sec. 4.3), from CUDA
+     * events between the phases of every solve: construction of the outer
+     * basis (App. A / B), the inner part (p, LU of p H_k, inner Lanczos, RHi;
+     * App. C steps 3-5) and the lift (step 6; with NK_DOUBLE_PASS it includes
+     * the second basis construction).  Adaptive k sums its chunks. */
+    double t_basis_ms, t_inner_ms, t_lift_ms;
+    double eps_sgn2[NK_MAX_RHS];       /* NK_EPS_EST: |x~ - x| / (2|x|) per RHS (Sec. 3), else 0 */
+    int k_pred, ell_pred;              /* NK_PREDICT: the predicted sizes, else 0 */
+    int predict_fallback;              /* NK_PREDICT: 1 if the solve was repeated with the caller's l */
 } nk_stats;
 
 /* Create a context for a lattice of dims[4] = {Lx, Ly, Lz, Lt} (each >= 2;
@@ -249,11 +269,25 @@ int nk_wait(nk_ctx* ctx, nk_stats* st);
 
 /* The Wilson stencil alone: out_r = A in_r (dagger = 0) or A^dagger in_r
  * (dagger = 1; A^dagger = gamma5 D_w(-mu)) for n_vec DEVICE vectors in the
- * ABI layout.  precision = 64 computes in FP64 with the FP64 links; 32 rounds
- * the input to FP32 and computes with the FP32 links (output FP64).
+ * ABI layout (n_vec <= 24).  precision = 64 computes in FP64 with the FP64
+ * links; 48 in two-float arithmetic (about 48 bits); 32 rounds the input to
+ * FP32 and computes with the FP32 links through nk_stencil32_dev's kernel
+ * (output FP64).
  * Stream-ordered, asynchronous. */
 int nk_dslash_dev(nk_ctx* ctx, const double* in_dev, double* out_dev, int n_vec, int dagger,
                   int precision, void* stream);
+
+/* The multi-RHS FP32 stencil alone, in its native layout: for the 2 n_rhs
+ * DEVICE vectors of in_dev (FP32, 16-byte aligned), out_r = A in_r for
+ * r < n_rhs and out_r = A^dagger in_r for n_rhs <= r < 2 n_rhs, with the FP32
+ * links (1 <= n_rhs <= NK_MAX_RHS).  Layout of each vector: the "pair layout"
+ * [6][V] of four floats, entry i of site s holding spin-colour components
+ * 2i and 2i + 1 (component = 3 spin + colour) as (re, im, re, im); vector r
+ * starts at float 24 V r.  One launch applies the stencil to all 2 n_rhs
+ * vectors, each link read once per block of sites.  This is the stencil of
+ * the late outer steps of NK_MIXED (there fused with the first half of the
+ * Lanczos step).  Stream-ordered, asynchronous. */
+int nk_stencil32_dev(nk_ctx* ctx, const float* in_dev, float* out_dev, int n_rhs, void* stream);
 
 /* The outer recurrence alone (App. A for mu = 0, App. B otherwise): k steps
  * from each of n_rhs DEVICE sources b_dev; writes H_k of each RHS as
@@ -325,6 +359,10 @@ int nk_features(nk_ctx* ctx, const double* b_dev, float* features, void* stream)
 /* Predicted sizes for one DEVICE source: features -> predictor -> k (even,
  * clamped to [64, k_max]) and l (even, clamped to [16, min(k, 256)]). */
 int nk_predict_sizes(nk_ctx* ctx, nk_mlp* m, const double* b_dev, int k_max, int* k, int* ell, void* stream);
+
+/* The predictor that NK_PREDICT solves of this context use (NULL: none).  The
+ * context does not own it: keep it alive while such solves run. */
+int nk_set_predictor(nk_ctx* ctx, nk_mlp* m);
 
 /* No-allocation variant of nk_inner_sign (the paper has no counterpart: this
  * is a deployment entry point, not a step of the method).  For callers that

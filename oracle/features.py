@@ -49,14 +49,14 @@ def plaquette(U):
     return total / 6.0
 
 
-def features(U, dims, mu, m_w, b, antiperiodic_t=True):
-    """The 16 features (FP64) of source b; dims = (Lx, Ly, Lz, Lt)."""
-    apply_a, apply_adag, herm = nested.operator(U, dims, mu, m_w, antiperiodic_t)
-    outer = nested.outer_basis(apply_a, apply_adag, np.asarray(b, dtype=np.complex128), K_FEAT, herm)
-    alpha, beta, gamma = outer.alpha, outer.beta, outer.gamma
+def spectral_features(alpha, beta, gamma, herm):
+    """Features 4..15 from the K_FEAT = 32 step recurrence coefficients H_32
+    (alpha = H(j,j), beta = H(j+1,j), gamma = H(j,j+1)): the p estimate of
+    Eq. popt, the statistics of the diagonals and the nested inner part
+    (App. C steps 3-5) on H_32 with l = 32."""
+    k = K_FEAT
     p, z_min, z_max = nested.estimate_p(alpha, beta, gamma)
     c, info = nested.inner_sign(alpha, beta, gamma, K_FEAT, p, herm)
-    k = K_FEAT
     if herm:
         re_a = np.asarray(alpha, dtype=np.float64)[:k]
         im_a = np.zeros(k)
@@ -67,12 +67,24 @@ def features(U, dims, mu, m_w, b, antiperiodic_t=True):
     j = np.arange(k - 1, dtype=np.float64)
     slope = np.polyfit(j, np.log(sub), 1)[0]
     cabs2 = np.abs(c) ** 2
-    f = np.array([
-        mu, m_w, np.log10(np.prod(dims)), plaquette(U),
+    return np.array([
         np.log10(z_min), np.log10(z_max), np.log10(z_max) - np.log10(z_min), np.log10(p),
         re_a.mean(), re_a.std(), np.abs(im_a).max(),
         sub.mean(), sub.std(), slope,
         0.5 * np.log10(cabs2[24:].sum() / cabs2.sum()),
         float(info["rhi_iters"]),
     ])
-    return f
+
+
+def features_of_operator(apply_a, apply_adag, herm, b):
+    """Features 4..15 of source b for an operator given as callables: 32 steps
+    of the outer recurrence (App. A / B), then spectral_features."""
+    outer = nested.outer_basis(apply_a, apply_adag, np.asarray(b, dtype=np.complex128), K_FEAT, herm)
+    return spectral_features(outer.alpha, outer.beta, outer.gamma, herm)
+
+
+def features(U, dims, mu, m_w, b, antiperiodic_t=True):
+    """The 16 features (FP64) of source b; dims = (Lx, Ly, Lz, Lt)."""
+    apply_a, apply_adag, herm = nested.operator(U, dims, mu, m_w, antiperiodic_t)
+    head = np.array([mu, m_w, np.log10(np.prod(dims)), plaquette(U)])
+    return np.concatenate([head, features_of_operator(apply_a, apply_adag, herm, b)])

@@ -18,7 +18,9 @@ Readings where the paper leaves a choice:
 * Two-sided case: beta = sqrt(delta) on the principal branch (cut on the
   negative real axis, as in Eq. sgnz); gamma = conj(delta) / beta.
 * Serious breakdown (App. B): delta == 0, or a non-finite delta, stops the
-  recurrence with ``breakdown = True``.
+  recurrence with ``breakdown = True``.  In the Hermitian case (App. A) a zero
+  (or non-finite) beta leaves v_{j+1} = r / beta undefined: the Krylov space
+  is invariant, and the recurrence stops the same way.
 * The inputs are the operator as callables, so the same code serves the outer
   recurrence on A (length 12V vectors) and the inner recurrence on H_k'
   (length-k vectors, real in the Hermitian case).
@@ -74,6 +76,8 @@ def lanczos(apply_a, x, k: int, store_basis: bool = True) -> LanczosResult:
         if j == k - 1:
             break
         b = np.sqrt(np.vdot(r, r).real)        # beta <- sqrt(r^dagger r)
+        if b == 0 or not np.isfinite(b):
+            return LanczosResult(V, alpha, beta, beta.copy(), xnorm, j + 1, True, alpha_imag)
         beta[j] = b
         v_prev, v = v, r / b                   # v_{j+1} <- r / beta
         if store_basis:

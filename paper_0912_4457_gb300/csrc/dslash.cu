@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "nk_common.cuh"
+#include "nk_hop.cuh"
 #include "nk_kernels.h"
 
 namespace nk {
@@ -36,53 +37,6 @@ __device__ __forceinline__ void load_spinor(const typename C2<R>::T* __restrict_
     for (int s = 0; s < 4; ++s)
 #pragma unroll
         for (int a = 0; a < 3; ++a) p[s][a] = in[(size_t)(3 * s + a) * V + site];
-}
-
-// i * z and -i * z
-template <typename T> __device__ __forceinline__ T mul_i(T z) { T r; r.x = -z.y; r.y = z.x; return r; }
-template <typename T> __device__ __forceinline__ T mul_mi(T z) { T r; r.x = z.y; r.y = -z.x; return r; }
-template <typename T> __device__ __forceinline__ T neg(T z) { T r; r.x = -z.x; r.y = -z.y; return r; }
-
-// One hop: acc += w * (1 + s gamma_nu) M psi_n with M = U (dag = false) or
-// U^dagger, from a neighbour spinor and link already loaded into registers
-// (FP32 and FP64; the two-float stencil has its own form below).
-template <int NU, bool DAG, typename R>
-__device__ __forceinline__ void hop_regs(typename C2<R>::T acc[4][3], const typename C2<R>::T psi[4][3],
-                                         const typename C2<R>::T u[3][3], R s, R w) {
-    typedef typename C2<R>::T T;
-    T h0[3], h1[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        T c0, c1;  // (C_nu psi_dn)_0, _1
-        if (NU == 0) { c0 = mul_mi(psi[3][a]); c1 = mul_mi(psi[2][a]); }
-        else if (NU == 1) { c0 = neg(psi[3][a]); c1 = psi[2][a]; }
-        else if (NU == 2) { c0 = mul_mi(psi[2][a]); c1 = mul_i(psi[3][a]); }
-        else { c0 = psi[2][a]; c1 = psi[3][a]; }
-        h0[a].x = psi[0][a].x + s * c0.x; h0[a].y = psi[0][a].y + s * c0.y;
-        h1[a].x = psi[1][a].x + s * c1.x; h1[a].y = psi[1][a].y + s * c1.y;
-    }
-    const R ws = w * s;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        T x0, x1;
-        x0.x = 0; x0.y = 0; x1.x = 0; x1.y = 0;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const T e = DAG ? u[b][a] : u[a][b];
-            R ey = DAG ? -e.y : e.y;
-            x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
-            x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
-        }
-        acc[0][a].x += w * x0.x; acc[0][a].y += w * x0.y;
-        acc[1][a].x += w * x1.x; acc[1][a].y += w * x1.y;
-        T b0, b1;  // (B_nu m)_0, _1
-        if (NU == 0) { b0 = mul_i(x1); b1 = mul_i(x0); }
-        else if (NU == 1) { b0 = x1; b1 = neg(x0); }
-        else if (NU == 2) { b0 = mul_i(x0); b1 = mul_mi(x1); }
-        else { b0 = x0; b1 = x1; }
-        acc[2][a].x += ws * b0.x; acc[2][a].y += ws * b0.y;
-        acc[3][a].x += ws * b1.x; acc[3][a].y += ws * b1.y;
-    }
 }
 
 template <typename R>
@@ -496,10 +450,7 @@ void launch_dslash(int precision, const void* U, const Geom& g, const DslashSet&
     const int nvec = s0.n + s1.n;
     if (nvec == 0) return;
     dim3 grid((unsigned)(((g.V + threads - 1) / threads) * nvec));
-    if (precision == 32)
-        dslash_kernel<float><<<grid, threads, 0, st>>>((const float2*)U, g, s0, s1, (float)kappa,
-                                                      (float)exp(mu), (float)exp(-mu));
-    else if (precision == 48)
+    if (precision == 48)
         dslash_kernel<df><<<grid, threads, 0, st>>>((const dfc*)U, g, s0, s1, df_host(kappa), df_host(exp(mu)),
                                                    df_host(exp(-mu)));
     else
@@ -674,10 +625,19 @@ __global__ void __launch_bounds__(CS * kStencilMaxThreads, CS == 1 ? StencilMinB
         double2 part = block_sum(acc, sh);
         if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, sb, nsb)) {
             double2 tot = sum_partials(o.partials + (size_t)rhs * o.npart, nsb, sh);
-            if (threadIdx.x == 0 && threadIdx.y == 0) {
-                // Hermitian: H(j,j) = Re(q_j^dag r) / n_j, real (App. C); two-sided: (p_j^dag r) / m_j^*
-                o.alpha[hb + j] = TS ? cmul(coef[2], tot) : make_double2(tot.x * coef[2].x, 0.0);
-                o.counters[rhs] = 0u;
+            // Hermitian: H(j,j) = Re(q_j^dag r) / n_j, real (App. C); two-sided: (p_j^dag r) / m_j^*;
+            // with the step-2 scalars H(j,j)/n_j (warp 1) and H(j,j)^*/m_j (warp 0) side by side
+            const int tid = block_tid();
+            if (tid == 0 || tid == 32) {
+                const double2 al = TS ? cmul(coef[2], tot) : make_double2(tot.x * coef[2].x, 0.0);
+                if (tid == 0) {
+                    o.alpha[hb + j] = al;
+                    o.counters[rhs] = 0u;
+                    o.sc[(size_t)rhs * kScalars + kScC4] = TS ? cdiv(cconj(al), scale_m(o, rhs, j))
+                                                              : make_double2(0.0, 0.0);
+                } else {
+                    o.sc[(size_t)rhs * kScalars + kScC3] = cdiv(al, scale_n(o, rhs, j));
+                }
             }
         }
     }
@@ -725,8 +685,7 @@ static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R k
 void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
                          double mu, cudaStream_t st) {
     if (precision == 32) {
-        launch_step1_t<float, float2>((const float2*)U, g, o, j, (float)kappa, (float)exp(mu), (float)exp(-mu), o.q32,
-                                      o.N, o.p32, o.N, st);
+        launch_stencil32_step1(U, g, o, j, kappa, mu, st);
     } else if (precision == 48) {   // the two-float stencil reads the two-float rings
         launch_step1_t<df, dfc>((const dfc*)U, g, o, j, df_host(kappa), df_host(exp(mu)), df_host(exp(-mu)),
                                 ring_q(o, 0, j), 3 * o.N, o.two_sided ? ring_p(o, 0, j) : nullptr, 3 * o.N, st);
@@ -806,14 +765,31 @@ void launch_soa_to_abi(const double2* in, long in_stride, double2* out, long out
                                                                       add, add_stride, V, n);
 }
 
-__global__ void to_fp32(const double2* __restrict__ in, long in_stride, float2* __restrict__ out,
-                        long out_stride, long N, int n) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)N * n) return;
-    int vec = (int)(i / N);
-    size_t j = i % N;
-    double2 v = in[(size_t)vec * in_stride + j];
-    out[(size_t)vec * out_stride + j] = make_float2((float)v.x, (float)v.y);
+// ABI spinor [site][12] (double) -> FP32 pair layout [6][V] float4, n vectors
+__global__ void abi_to_f32pair(const double2* __restrict__ in, long in_stride, float4* __restrict__ out,
+                               long out_stride, int V, int n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // (vector, pair, site)
+    const size_t per = (size_t)V * 6;
+    if (i >= per * n) return;
+    const int vec = (int)(i / per);
+    const size_t rem = i % per;
+    const int pr = (int)(rem / V), site = (int)(rem % V);
+    const double2 a = in[(size_t)vec * in_stride + (size_t)site * 12 + 2 * pr];
+    const double2 b = in[(size_t)vec * in_stride + (size_t)site * 12 + 2 * pr + 1];
+    out[(size_t)vec * out_stride + rem] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+}
+
+__global__ void f32pair_to_abi(const float4* __restrict__ in, long in_stride, double2* __restrict__ out,
+                               long out_stride, int V, int n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)V * 6;
+    if (i >= per * n) return;
+    const int vec = (int)(i / per);
+    const size_t rem = i % per;
+    const int pr = (int)(rem / V), site = (int)(rem % V);
+    const float4 v = in[(size_t)vec * in_stride + rem];
+    out[(size_t)vec * out_stride + (size_t)site * 12 + 2 * pr] = make_double2(v.x, v.y);
+    out[(size_t)vec * out_stride + (size_t)site * 12 + 2 * pr + 1] = make_double2(v.z, v.w);
 }
 
 __global__ void to_df(const double2* __restrict__ in, long in_stride, dfc* __restrict__ out, long out_stride,
@@ -834,10 +810,16 @@ void launch_to_df(const double2* in, long in_stride, dfc* out, long out_stride, 
     to_df<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride, N, n);
 }
 
-void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_stride, long N, int n,
-                    cudaStream_t st) {
-    size_t tot = (size_t)N * n;
-    to_fp32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride, N, n);
+void launch_abi_to_f32pair(const double2* in, long in_stride, float4* out, long out_stride, int V, int n,
+                           cudaStream_t st) {
+    const size_t tot = (size_t)V * 6 * n;
+    abi_to_f32pair<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride, V, n);
+}
+
+void launch_f32pair_to_abi(const float4* in, long in_stride, double2* out, long out_stride, int V, int n,
+                           cudaStream_t st) {
+    const size_t tot = (size_t)V * 6 * n;
+    f32pair_to_abi<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(in, in_stride, out, out_stride, V, n);
 }
 
 }  // namespace nk

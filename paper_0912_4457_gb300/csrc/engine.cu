@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <cstdint>
 #include <map>
 #include <string>
 #include <tuple>
@@ -53,7 +54,15 @@ struct nk_ctx {
     DevBuf ws;            // solve workspace (carved per solve shape)
     DevBuf staging;       // host-pointer API: device copies of b and y
     DevBuf links_tmp;
-    std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;  // exec, kernels per replay
+    DevBuf inner_tmp;     // nk_inner_sign / nk_features scratch (never the staged b and y)
+    DevBuf eps_buf;       // NK_EPS_EST: approx(approx(x)) and the per-RHS sums
+    // phase events recorded inside every solve (captured into its graph):
+    // end of the outer basis, end of the inner part, start of an adaptive chunk
+    cudaEvent_t ph[3] = {nullptr, nullptr, nullptr};
+    nk_mlp* predictor = nullptr;   // NK_PREDICT (not owned)
+    // exec, kernels per replay; at most kMaxGraphs (a caller cycling through
+    // buffers would otherwise instantiate one graph per pair)
+    std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;
     std::map<std::tuple<int, int, int>, nk_launch> tune;  // (n_rhs, two_sided, mixed) -> launch shape
     struct Pending {                 // an NK_ASYNC solve not yet collected
         bool on = false;
@@ -99,6 +108,32 @@ int ensure(nk_ctx* c, DevBuf& b, size_t bytes) {
     }
     b.bytes = bytes;
     return NK_OK;
+}
+
+// Records a phase event on st.  Under stream capture a plain record only
+// orders the captured work; cudaEventRecordExternal makes the graph record the
+// event when it runs, so that the phase times can be read afterwards.
+void record_phase(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    cudaEventRecordWithFlags(e, st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                       : cudaEventRecordDefault);
+}
+
+// Elapsed milliseconds between two recorded events; a failed query (an event
+// not recorded) gives 0 and leaves no pending error behind.
+double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return ms;
+}
+
+void clear_graph_cache(nk_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second.first);
+    c->graphs.clear();
 }
 
 Geom geom_of(const nk_ctx* c) {
@@ -148,12 +183,13 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.st_split = lc.stencil_split;
     o.st_split_df = lc.early_split;
     o.npart = std::max(nblk, nk::dslash_step1_blocks(g, std::min(lc.stencil_threads, lc.early_threads)));
+    o.npart = std::max(o.npart, nk::stencil32_blocks(g, two_sided ? 2 * n_rhs : n_rhs));
     o.q_ring = double_pass ? 1 : 0;
     o.qcols = double_pass ? 3 : k + 1;   // single pass: k basis vectors + one scratch column
     o.Q = (double2*)take(vec * (size_t)o.qcols * n_rhs);
     if (two_sided) o.P = (double2*)take(vec * 3 * n_rhs);
-    o.q32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
-    if (two_sided) o.p32 = (float2*)take((size_t)N * sizeof(float2) * n_rhs);
+    o.q32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);    // pair layout: N / 2 float4 per RHS
+    if (two_sided) o.p32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);
     o.qdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     if (two_sided) o.pdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     o.q_df_from = 1 << 30;
@@ -167,6 +203,7 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.gamma = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
     o.partials = (double2*)take(sizeof(double2) * (size_t)o.npart * n_rhs);
     o.counters = (unsigned*)take(sizeof(unsigned) * n_rhs);
+    o.sc = (double2*)take(sizeof(double2) * nk::kScalars * n_rhs);
     o.status = (int*)take(sizeof(int) * n_rhs);
     o.xnorm = (double*)take(sizeof(double) * n_rhs);
     L.cp = (double2*)take(sizeof(double2) * (size_t)k * n_rhs);
@@ -190,7 +227,6 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     L.dn = (double2*)take(sizeof(double2) * n_rhs);
     L.kused = (int*)take(sizeof(int) * n_rhs);
     in.status = o.status;
-    in.timeout = (int*)take(sizeof(int));
     // the inner part stays FP64 in every schedule: with a Ritz value of H_k'
     // near the imaginary axis its sign is ill conditioned, and two-float
     // arithmetic there left single sources of the 16^3 x 32 test at 2.5e-8
@@ -373,10 +409,12 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     enqueue_load_sources(c, o, b_dev, n_rhs, L);
     L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_fill_int(Lw.kused, n_rhs, o.k, st); });
     enqueue_outer(c, o, sch, L);
+    record_phase(c->ph[0], st);   // the outer basis is complete
     L.run(NK_CLASS_INNER, nk::inner_launches(in), [&] { nk::launch_inner_lanczos(in, st); });
     cudaError_t e = cudaSuccess;
     L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(in, st); });
     if (e != cudaSuccess) return e;
+    record_phase(c->ph[1], st);   // the inner part is complete
     L.run(NK_CLASS_LIFT, 2, [&] {
         nk::launch_inner_combine(in, st);
         nk::launch_lift_coef(o, in.c, Lw.kused, Lw.cp, st);
@@ -403,7 +441,7 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
 // consecutive checks.  Launched kernel by kernel (host decisions between chunks).
 cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_dev, int n_rhs, int kmax, int ell,
                            double tol, double p, unsigned flags, bool overlap, Launcher& L,
-                           std::vector<int>& kused_h, std::vector<int>& notconv, int& checks) {
+                           std::vector<int>& kused_h, std::vector<int>& notconv, int& checks, double tph[2]) {
     cudaStream_t st = L.st;
     const bool mixed = (flags & NK_MIXED) != 0;
     const Schedule sch = schedule_of(c, flags, kmax);
@@ -426,7 +464,9 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
     checks = 0;
     int j = 0, kc = first;
     while (true) {
+        record_phase(c->ph[2], st);
         enqueue_outer_steps(c, o, sch, j, kc, L);
+        record_phase(c->ph[0], st);
         nk::Inner ic = in;
         ic.k = kc;
         ic.ell = std::min(ell, kc);
@@ -436,10 +476,13 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
         if (e != cudaSuccess) return e;
         L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_inner_combine(ic, st); });
         L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_adapt_delta(o, in.c, Lw.c_prev, kc, Lw.dn, st); });
+        record_phase(c->ph[1], st);
         e = cudaMemcpyAsync(dn.data(), Lw.dn, sizeof(double2) * n_rhs, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(status.data(), o.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
+        tph[0] += elapsed_ms(c->ph[2], c->ph[0]);
+        tph[1] += elapsed_ms(c->ph[0], c->ph[1]);
         ++checks;
         bool all = true, changed = false;
         for (int r = 0; r < n_rhs; ++r) {
@@ -489,6 +532,7 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
     if (e == cudaSuccess) e = cudaMemcpyAsync(Lw.kused, kused_h.data(), sizeof(int) * n_rhs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
+    record_phase(c->ph[1], st);   // the lift starts here (t_lift: from ph[1] to the end)
     L.run(NK_CLASS_LIFT, 2, [&] {
         nk::launch_lift_coef(o, Lw.c_prev, Lw.kused, Lw.cp, st);
         nk::launch_lift(o, Lw.cp, Lw.kused, Lw.y_soa, st);
@@ -550,17 +594,41 @@ int collect_outcome(nk_ctx* c, int n_rhs, int k_used_max, const std::vector<int>
     return worst;
 }
 
-int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
-              unsigned flags, double* y_dev, nk_stats* stats, cudaStream_t st, bool overlap) {
+constexpr size_t kMaxGraphs = 16;
+
+// Two CUDA events owned by one solve; destroyed unless handed to a pending
+// NK_ASYNC solve (release()).
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+    void release() { e0 = e1 = nullptr; }
+};
+
+// Device-time split of a finished fixed-k solve from the phase events (graph
+// or kernel by kernel): basis, inner part, lift.
+void phase_times(const nk_ctx* c, cudaEvent_t e0, cudaEvent_t e1, double out[3]) {
+    out[0] = elapsed_ms(e0, c->ph[0]);
+    out[1] = elapsed_ms(c->ph[0], c->ph[1]);
+    out[2] = elapsed_ms(c->ph[1], e1);
+}
+
+// One solve (fixed or adaptive k), sequenced on stream st.
+int solve_core(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
+               unsigned flags, double* y_dev, nk_stats* stats, cudaStream_t st, bool overlap) {
     int rc = check_solve_args(c, n_rhs, k, ell, tol);
     if (rc) return rc;
     if (c->pending.on) return fail(c, NK_ESTATE, "an NK_ASYNC solve is pending on this context: nk_wait first");
     const bool async = (flags & NK_ASYNC) != 0;
     if (async && (tol > 0.0 || (flags & NK_PROFILE)))
         return fail(c, NK_EINVAL, "NK_ASYNC needs a fixed k (tol = 0) and no NK_PROFILE");
+    const bool adaptive = tol > 0.0;
+    const bool dp = (flags & NK_DOUBLE_PASS) != 0;
+    if (adaptive && dp) return fail(c, NK_EINVAL, "adaptive k (tol > 0) needs single-pass storage");
     NK_CUDA(c, cudaSetDevice(c->device));
     const bool ts = c->mu != 0.0;
-    const bool dp = (flags & NK_DOUBLE_PASS) != 0;
     const nk_launch lc = launch_cfg(c, n_rhs, ts, (flags & NK_MIXED) != 0);
     const bool mixed = (flags & NK_MIXED) != 0;
     Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed);
@@ -569,29 +637,28 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed);
     // counters must start at zero; status is (re)set by the norm kernel
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
-    NK_CUDA(c, cudaMemsetAsync(Lw.in.timeout, 0, sizeof(int), st));
 
-    cudaEvent_t e0, e1;
-    NK_CUDA(c, cudaEventCreate(&e0));
-    NK_CUDA(c, cudaEventCreate(&e1));
-    NK_CUDA(c, cudaEventRecord(e0, st));
+    EventPair ev;
+    NK_CUDA(c, cudaEventCreate(&ev.e0));
+    NK_CUDA(c, cudaEventCreate(&ev.e1));
+    NK_CUDA(c, cudaEventRecord(ev.e0, st));
     const bool profile = (flags & NK_PROFILE) != 0;
-    const bool adaptive = tol > 0.0;
-    if (adaptive && dp) return fail(c, NK_EINVAL, "adaptive k (tol > 0) needs single-pass storage");
     const bool use_graph = !adaptive && (flags & (NK_NO_GRAPH | NK_PROFILE)) == 0;
     Launcher L;
     L.st = st;
     L.profile = profile;
     std::vector<int> kused_h(n_rhs, k), notconv(n_rhs, 0);
     int checks = 0;
+    double tph[3] = {0.0, 0.0, 0.0};
     if (adaptive) {
         cudaError_t e = solve_adaptive(c, Lw, b_dev, y_dev, n_rhs, k, ell, tol, p, flags, overlap, L, kused_h,
-                                       notconv, checks);
+                                       notconv, checks, tph);
         if (e != cudaSuccess) return cuda_fail(c, e, "adaptive solve");
     } else if (use_graph) {
         GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, c->j1, flags, p, c->mu, c->m_w, overlap ? 1 : 0};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
+            if (c->graphs.size() >= kMaxGraphs) clear_graph_cache(c);
             cudaStream_t cs;
             NK_CUDA(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
             NK_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -615,13 +682,14 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
         cudaError_t e = enqueue_solve(c, Lw, b_dev, y_dev, n_rhs, p, flags, overlap, L);
         if (e != cudaSuccess) return cuda_fail(c, e, "enqueue_solve");
     }
-    NK_CUDA(c, cudaEventRecord(e1, st));
+    NK_CUDA(c, cudaEventRecord(ev.e1, st));
     if (async) {   // collected by nk_wait
         nk_ctx::Pending& P = c->pending;
         P.on = true;
         P.st = st;
-        P.e0 = e0;
-        P.e1 = e1;
+        P.e0 = ev.e0;
+        P.e1 = ev.e1;
+        ev.release();
         P.n_rhs = n_rhs;
         P.k = k;
         P.ell = ell;
@@ -645,9 +713,12 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     NK_CUDA(c, cudaMemcpyAsync(xn.data(), Lw.o.xnorm, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
     NK_CUDA(c, cudaStreamSynchronize(st));
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+    if (adaptive) {
+        tph[2] = elapsed_ms(c->ph[1], ev.e1);
+    } else {
+        phase_times(c, ev.e0, ev.e1, tph);
+    }
     double tcm[NK_NCLASS] = {0};   // NK_PROFILE: summed device time per class
     int ncl[NK_NCLASS] = {0};
     if (profile) {
@@ -656,9 +727,93 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     }
     rc = collect_outcome(c, n_rhs, *std::max_element(kused_h.begin(), kused_h.end()), kused_h, notconv, checks, ell,
                          L.launches, ms, status, iters, pv, zmin, zmax, xn, stats);
-    if (stats && profile) {
-        std::memcpy(stats->t_class_ms, tcm, sizeof(tcm));
-        for (int q = 0; q < NK_NCLASS; ++q) stats->n_class[q] = ncl[q];
+    if (stats) {
+        stats->t_basis_ms = tph[0];
+        stats->t_inner_ms = tph[1];
+        stats->t_lift_ms = tph[2];
+        if (profile) {
+            std::memcpy(stats->t_class_ms, tcm, sizeof(tcm));
+            for (int q = 0; q < NK_NCLASS; ++q) stats->n_class[q] = ncl[q];
+        }
+    }
+    return rc;
+}
+
+// NK_EPS_EST: the error estimate of Sec. 3 for every RHS of a finished solve:
+// x~ = approx(y) with y = approx(x) already in y_dev, eps = |x~ - x| / (2|x|).
+int eps_estimate(nk_ctx* c, const double* b_dev, const double* y_dev, int n_rhs, int k, int ell, double tol,
+                 double p, unsigned flags, cudaStream_t st, nk_stats* stats) {
+    const size_t vb = align_up(sizeof(double2) * (size_t)c->N * n_rhs);
+    int rc = ensure(c, c->eps_buf, vb + sizeof(double2) * NK_MAX_RHS);
+    if (rc) return rc;
+    double2* x2 = (double2*)c->eps_buf.p;
+    double2* sums = (double2*)((char*)c->eps_buf.p + vb);
+    nk_stats s2;
+    rc = solve_core(c, y_dev, n_rhs, k, ell, tol, p, flags & ~(NK_EPS_EST | NK_PREDICT | NK_ASYNC), (double*)x2, &s2,
+                    st, false);
+    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI && rc != NK_ENOTCONV) return rc;
+    nk::launch_eps_sums((const double2*)b_dev, x2, n_rhs, c->N, sums, st);
+    NK_CUDA(c, cudaGetLastError());
+    std::vector<double2> h(n_rhs);
+    NK_CUDA(c, cudaMemcpyAsync(h.data(), sums, sizeof(double2) * n_rhs, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaStreamSynchronize(st));
+    if (stats)
+        for (int r = 0; r < n_rhs; ++r)
+            stats->eps_sgn2[r] = h[r].y > 0.0 ? std::sqrt(h[r].x) / (2.0 * std::sqrt(h[r].y)) : 0.0;
+    return NK_OK;
+}
+
+// A solve with the optional prediction of (k, l) (NK_PREDICT) before it and
+// the optional error estimate (NK_EPS_EST) after it.
+int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
+              unsigned flags, double* y_dev, nk_stats* stats, cudaStream_t st, bool overlap) {
+    if (!c) return NK_EINVAL;
+    const bool predict = (flags & NK_PREDICT) != 0;
+    const bool eps = (flags & NK_EPS_EST) != 0;
+    if ((predict || eps) && (flags & NK_ASYNC)) return fail(c, NK_EINVAL, "NK_PREDICT / NK_EPS_EST need a blocking solve");
+    if (eps && overlap) return fail(c, NK_EINVAL, "NK_EPS_EST applies to the sign function, not to D_ov");
+    if (!predict && !eps) return solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags, y_dev, stats, st, overlap);
+    nk_stats local;
+    nk_stats* S = stats ? stats : &local;
+    int rc;
+    int kp = 0, lp = 0, fallback = 0;
+    if (predict) {
+        if (!(tol > 0.0)) return fail(c, NK_EINVAL, "NK_PREDICT needs adaptive k (tol > 0)");
+        if (!c->predictor) return fail(c, NK_ESTATE, "NK_PREDICT: no predictor (nk_set_predictor)");
+        rc = check_solve_args(c, n_rhs, k, ell, tol);
+        if (rc) return rc;
+        rc = nk_predict_sizes(c, c->predictor, b_dev, k, &kp, &lp, (void*)st);
+        if (rc) return rc;
+        // l too small never passes the test: a margin of 1.5 (the inner part
+        // costs O(k l), little against a repeated solve)
+        int l_use = 2 * (int)std::ceil(0.75 * lp);
+        l_use = std::max(2, std::min(std::min(l_use, kp), std::min(256, k)));
+        l_use -= l_use & 1;
+        const int saved = c->adapt_start;
+        c->adapt_start = std::max(64, kp - 2 * NK_ADAPT_STEP);
+        rc = solve_core(c, b_dev, n_rhs, k, l_use, tol, p, flags & ~(NK_PREDICT | NK_EPS_EST), y_dev, S, st, overlap);
+        c->adapt_start = saved;
+        if (rc == NK_ENOTCONV && l_use < ell) {
+            const double t_first = S->t_total_ms;
+            rc = solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags & ~(NK_PREDICT | NK_EPS_EST), y_dev, S, st,
+                            overlap);
+            S->t_total_ms += t_first;
+            fallback = 1;
+        }
+    } else {
+        rc = solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags & ~NK_EPS_EST, y_dev, S, st, overlap);
+    }
+    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI && rc != NK_ENOTCONV) return rc;
+    S->k_pred = kp;
+    S->ell_pred = lp;
+    S->predict_fallback = fallback;
+    if (eps) {
+        // the second application uses the sizes the first one ended with
+        const int l2 = S->ell_used > 0 ? S->ell_used : ell;
+        const std::string keep_err = c->err;
+        const int rc2 = eps_estimate(c, b_dev, y_dev, n_rhs, k, l2, tol, p, flags, st, S);
+        if (rc2 != NK_OK) return rc2;
+        c->err = keep_err;
     }
     return rc;
 }
@@ -688,6 +843,15 @@ int nk_create_lattice(const int dims[4], int bc_t_antiperiodic, nk_ctx** out) {
     }
     nk::init_kernel_attributes();
     cudaGetLastError();
+    for (auto& e : c->ph) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& f : c->ph)
+                if (f) cudaEventDestroy(f);
+            delete c;
+            return NK_ECUDA;
+        }
+    }
     *out = c;
     return NK_OK;
 }
@@ -907,15 +1071,18 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     for (int th : {64, 128, 256})
         for (int od : {0, 1})
             for (int sp : {1, 3}) {
-                nk_launch l = best;
-                l.stencil_threads = th;
-                l.stencil_order = od;
-                l.stencil_split = sp;
                 float t;
-                rc = time_kernel(c, src, n_rhs, mixed != 0, mixed ? 32 : 64, l, st, &t);
-                if (rc) return fail_out(rc);
-                if (t < t_st) { t_st = t; cand.stencil_threads = th; cand.stencil_order = od; cand.stencil_split = sp; }
-                if (mixed) {
+                if (!mixed) {
+                    // the FP32 stencil of the mixed schedule has one shape (stencil32.cu);
+                    // the FP64 stencil of NK_FP64 is tuned
+                    nk_launch l = best;
+                    l.stencil_threads = th;
+                    l.stencil_order = od;
+                    l.stencil_split = sp;
+                    rc = time_kernel(c, src, n_rhs, false, 64, l, st, &t);
+                    if (rc) return fail_out(rc);
+                    if (t < t_st) { t_st = t; cand.stencil_threads = th; cand.stencil_order = od; cand.stencil_split = sp; }
+                } else {
                     nk_launch e = best;
                     e.early_threads = th;
                     e.early_order = od;
@@ -1000,6 +1167,28 @@ int nk_overlap_apply_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int e
     return solve_dev(c, b_dev, n_rhs, k, ell, tol, 0.0, flags, y_dev, st, (cudaStream_t)stream, true);
 }
 
+int nk_stencil32_dev(nk_ctx* c, const float* in_dev, float* out_dev, int n_rhs, void* stream) {
+    if (!c) return NK_EINVAL;
+    if (!in_dev || !out_dev) return fail(c, NK_EINVAL, "null pointer");
+    if ((reinterpret_cast<uintptr_t>(in_dev) & 15) || (reinterpret_cast<uintptr_t>(out_dev) & 15))
+        return fail(c, NK_EINVAL, "in_dev and out_dev must be 16-byte aligned");
+    if (n_rhs < 1 || n_rhs > NK_MAX_RHS) return fail(c, NK_EINVAL, "n_rhs must be in [1, 12]");
+    if (!c->links) return fail(c, NK_ESTATE, "no links loaded");
+    if (!c->mu_set) return fail(c, NK_ESTATE, "mu and m_w not set");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const long vs = c->N / 2;   // float4 per vector
+    nk::Stencil32Set s;
+    s.in_a = reinterpret_cast<const float4*>(in_dev);
+    s.in_d = s.in_a + (size_t)n_rhs * vs;
+    s.out_a = reinterpret_cast<float4*>(out_dev);
+    s.out_d = s.out_a + (size_t)n_rhs * vs;
+    s.vstride = vs;
+    s.n_a = s.n_d = n_rhs;
+    nk::launch_stencil32(c->U32, geom_of(c), s, kappa_of(c), c->mu, (cudaStream_t)stream);
+    NK_CUDA(c, cudaGetLastError());
+    return NK_OK;
+}
+
 int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, int dagger, int precision,
                   void* stream) {
     if (!c || !in_dev || !out_dev || n_vec < 1 || n_vec > 2 * NK_MAX_RHS) return NK_EINVAL;
@@ -1010,7 +1199,26 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
     NK_CUDA(c, cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
     const long N = c->N;
-    // scratch: SoA input (FP64 and FP32) and SoA output
+    if (precision == 32) {
+        // FP32: the multi-RHS stencil on FP32 pair-layout copies (input rounded once)
+        const size_t vb = align_up(sizeof(float2) * N * n_vec);
+        int rc = ensure(c, c->staging, std::max(2 * vb, c->staging.bytes));
+        if (rc) return rc;
+        float4* in32 = (float4*)c->staging.p;
+        float4* out32 = (float4*)((char*)c->staging.p + vb);
+        nk::launch_abi_to_f32pair((const double2*)in_dev, N, in32, N / 2, c->V, n_vec, st);
+        nk::Stencil32Set s;
+        s.in_a = s.in_d = in32;
+        s.out_a = s.out_d = out32;
+        s.vstride = N / 2;
+        s.n_a = dagger ? 0 : n_vec;
+        s.n_d = dagger ? n_vec : 0;
+        nk::launch_stencil32(c->U32, geom_of(c), s, kappa_of(c), c->mu, st);
+        nk::launch_f32pair_to_abi(out32, N / 2, (double2*)out_dev, N, c->V, n_vec, st);
+        NK_CUDA(c, cudaGetLastError());
+        return NK_OK;
+    }
+    // scratch: SoA input (FP64 or two-float) and SoA output
     size_t bytes = align_up(sizeof(double2) * N * n_vec) * 3;
     int rc = ensure(c, c->staging, std::max(bytes, c->staging.bytes));
     if (rc) return rc;
@@ -1021,10 +1229,7 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
     nk::DslashSet s0, s1;
     std::memset(&s0, 0, sizeof(s0));
     std::memset(&s1, 0, sizeof(s1));
-    if (precision == 32) {
-        nk::launch_to_fp32(in_soa, N, in32, N, N, n_vec, st);
-        s0.in = in32;
-    } else if (precision == 48) {
+    if (precision == 48) {
         nk::launch_to_df(in_soa, N, (nk::dfc*)in32, N, N, n_vec, st);
         s0.in = in32;
     } else {
@@ -1035,10 +1240,8 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
     s0.out_stride = N;
     s0.n = n_vec;
     s0.dag = dagger ? 1 : 0;
-    nk::launch_dslash(precision,
-                      precision == 32 ? (const void*)c->U32 : (precision == 48 ? (const void*)c->Udf : (const void*)c->U64),
-                      geom_of(c), s0,
-                      s1, kappa_of(c), c->mu, st);
+    nk::launch_dslash(precision, precision == 48 ? (const void*)c->Udf : (const void*)c->U64, geom_of(c), s0, s1,
+                      kappa_of(c), c->mu, st);
     nk::launch_soa_to_abi(out_soa, N, (double2*)out_dev, N, nullptr, 0, c->V, n_vec, st);
     NK_CUDA(c, cudaGetLastError());
     return NK_OK;
@@ -1100,9 +1303,9 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     one.stencil_split = 1;
     one.early_split = 1;
     Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one, false);
-    int rc = ensure(c, c->staging, std::max(dry.total, c->staging.bytes));
+    int rc = ensure(c, c->inner_tmp, std::max(dry.total, c->inner_tmp.bytes));
     if (rc) return rc;
-    Layout Lw = carve((char*)c->staging.p, tiny, n_rhs, k, ell, ts, true, one, false);
+    Layout Lw = carve((char*)c->inner_tmp.p, tiny, n_rhs, k, ell, ts, true, one, false);
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpy(Lw.o.alpha, alpha, cb, cudaMemcpyHostToDevice));
     NK_CUDA(c, cudaMemcpy(Lw.o.beta, beta, cb, cudaMemcpyHostToDevice));
@@ -1163,13 +1366,13 @@ int nk_features(nk_ctx* c, const double* b_dev, float* features, void* stream) {
     // mean plaquette: per-block partial sums, summed here in a fixed order
     const Geom g = geom_of(c);
     const int nb = nk::plaquette_blocks(g);
-    rc = ensure(c, c->staging, std::max(c->staging.bytes, sizeof(double) * (size_t)nb));
+    rc = ensure(c, c->inner_tmp, std::max(c->inner_tmp.bytes, sizeof(double) * (size_t)nb));
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    nk::launch_plaquette(c->U64, g, (double*)c->staging.p, st);
+    nk::launch_plaquette(c->U64, g, (double*)c->inner_tmp.p, st);
     NK_CUDA(c, cudaGetLastError());
     std::vector<double> part(nb);
-    NK_CUDA(c, cudaMemcpyAsync(part.data(), c->staging.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaMemcpyAsync(part.data(), c->inner_tmp.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
     NK_CUDA(c, cudaStreamSynchronize(st));
     double plaq = 0.0;
     for (int i = 0; i < nb; ++i) plaq += part[i];
@@ -1243,6 +1446,12 @@ int nk_predict_sizes(nk_ctx* c, nk_mlp* m, const double* b_dev, int k_max, int* 
     return NK_OK;
 }
 
+int nk_set_predictor(nk_ctx* c, nk_mlp* m) {
+    if (!c) return NK_EINVAL;
+    c->predictor = m;
+    return NK_OK;
+}
+
 int nk_wait(nk_ctx* c, nk_stats* stats) {
     if (!c) return NK_EINVAL;
     if (!c->pending.on) return NK_OK;
@@ -1261,10 +1470,18 @@ int nk_wait(nk_ctx* c, nk_stats* stats) {
     NK_CUDA(c, cudaStreamSynchronize(P.st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, P.e0, P.e1);
+    double tph[3];
+    phase_times(c, P.e0, P.e1, tph);
     cudaEventDestroy(P.e0);
     cudaEventDestroy(P.e1);
-    return collect_outcome(c, n, P.k, kused, notconv, 0, P.ell, P.launches, ms, status, iters, pv, zmin, zmax, xn,
-                           stats);
+    const int rc = collect_outcome(c, n, P.k, kused, notconv, 0, P.ell, P.launches, ms, status, iters, pv, zmin,
+                                   zmax, xn, stats);
+    if (stats) {
+        stats->t_basis_ms = tph[0];
+        stats->t_inner_ms = tph[1];
+        stats->t_lift_ms = tph[2];
+    }
+    return rc;
 }
 
 const char* nk_last_error(const nk_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -1281,6 +1498,10 @@ void nk_destroy(nk_ctx* c) {
     if (c->ws.p) cudaFree(c->ws.p);
     if (c->staging.p) cudaFree(c->staging.p);
     if (c->links_tmp.p) cudaFree(c->links_tmp.p);
+    if (c->inner_tmp.p) cudaFree(c->inner_tmp.p);
+    if (c->eps_buf.p) cudaFree(c->eps_buf.p);
+    for (auto& e : c->ph)
+        if (e) cudaEventDestroy(e);
     if (c->U64) cudaFree(c->U64);
     if (c->U32) cudaFree(c->U32);
     if (c->Udf) cudaFree(c->Udf);

@@ -1132,6 +1132,7 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rhi_smem_max());
     cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    stencil32_init_attributes();
 
 }
 

@@ -59,6 +59,14 @@ __global__ void __launch_bounds__(kThreads) k_norm(Outer o, int keep_status) {
             const bool keep = keep_status && prev != kStatusOK && prev != kStatusZeroSource;
             o.status[rhs] = keep ? prev : (nrm > 0.0 ? kStatusOK : kStatusZeroSource);
             o.counters[rhs] = 0u;
+            // scalars of step 0: n_0 = m_0 = |x|, no previous vector
+            double2* sc = o.sc + (size_t)rhs * kScalars;
+            const double2 inv = nrm > 0.0 ? cinv(mk(nrm, 0.0)) : mk(0.0, 0.0);
+            sc[kScN] = inv;
+            sc[kScC1] = mk(0.0, 0.0);
+            sc[kScD] = inv;
+            sc[kScM] = inv;
+            sc[kScC1L] = mk(0.0, 0.0);
         }
     }
 }
@@ -75,15 +83,19 @@ __device__ __forceinline__ double2 double2_of(dfc v) { return mk(df_to_double(v.
 // the integer pipe.  With the mixed schedule's rings the two-float copy is not
 // made here (the FP64 steps write the rings themselves, which the two-float
 // stencil reads).
-__device__ __forceinline__ void put_copy(const Outer& o, int mode, bool left, size_t at, double2 v) {
+// Element i = c V + s of RHS rhs (FP64 layout [12][V]); the FP32 copy goes to
+// the pair layout.
+__device__ __forceinline__ void put_copy(const Outer& o, int mode, bool left, int rhs, long i, double2 v) {
     if (mode == kCopy32) {
+        const int V = (int)(o.N / 12);
+        const int c = (int)(i / V), s = (int)(i - (long)c * V);
         float2 f = make_float2(d2f_int(v.x), d2f_int(v.y));
-        (left ? o.p32 : o.q32)[at] = f;
+        reinterpret_cast<float2*>(left ? o.p32 : o.q32)[(size_t)rhs * o.N + f32_pair_index(c, s, V)] = f;
     } else if (mode == kCopyDF && !o.qr) {
         dfc w;
         w.x = df_from_double(v.x);
         w.y = df_from_double(v.y);
-        (left ? o.pdf : o.qdf)[at] = w;
+        (left ? o.pdf : o.qdf)[(size_t)rhs * o.N + i] = w;
     }
 }
 
@@ -98,8 +110,8 @@ __global__ void __launch_bounds__(kThreads) k_init(Outer o, int copy_mode) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
         double2 a = x[i];
         if (p) p[i] = a;
-        put_copy(o, copy_mode, false, (size_t)rhs * o.N + i, a);
-        if (p) put_copy(o, copy_mode, true, (size_t)rhs * o.N + i, a);
+        put_copy(o, copy_mode, false, rhs, i, a);
+        if (p) put_copy(o, copy_mode, true, rhs, i, a);
         if (o.qr) {
             const dfc d = dfc_of(a);
             ring_q(o, rhs, 0)[i] = d;
@@ -109,81 +121,137 @@ __global__ void __launch_bounds__(kThreads) k_init(Outer o, int copy_mode) {
 }
 
 // End of step 2: the deterministic reduction of the per-thread partial
-// (r^dag r, or r^dag l two-sided) and, in the last block, beta and gamma.
+// (r^dag r, or r^dag l two-sided) and, in the last block, beta and gamma and
+// the scalars of step j + 1 (one complex division per warp, side by side on
+// the SM sub-partitions).
 template <bool TS>
 __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, double2 acc, double2* sh) {
+    __shared__ double2 bg[2];
     double2 part = block_sum(acc, sh);
     if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, blockIdx.x, o.nblk)) {
         double2 d = sum_partials(o.partials + (size_t)rhs * o.npart, o.nblk, sh);
         if (threadIdx.x == 0) {
             const size_t at = (size_t)rhs * o.k + j;
+            double2 b, g;
             if (!TS) {
-                double b = sqrt(d.x);                   // beta <- sqrt(r^dag r)
-                o.beta[at] = mk(b, 0.0);
-                o.gamma[at] = mk(b, 0.0);
-                if (!(b > 0.0) || !isfinite(b)) o.status[rhs] = kStatusBreakdown;
+                const double bb = sqrt(d.x);             // beta <- sqrt(r^dag r)
+                b = g = mk(bb, 0.0);
+                if (!(bb > 0.0) || !isfinite(bb)) o.status[rhs] = kStatusBreakdown;
             } else if ((d.x == 0.0 && d.y == 0.0) || !isfinite(d.x) || !isfinite(d.y)) {
                 // serious breakdown: delta = 0 (App. B); a non-finite delta is treated alike
                 o.status[rhs] = kStatusBreakdown;
-                o.beta[at] = mk(0.0, 0.0);
-                o.gamma[at] = mk(0.0, 0.0);
+                b = g = mk(0.0, 0.0);
             } else {
-                double2 b = csqrt_principal(d);         // beta <- sqrt(delta)
-                o.beta[at] = b;
-                o.gamma[at] = cdiv(cconj(d), b);        // gamma <- delta^* / beta
+                b = csqrt_principal(d);                  // beta <- sqrt(delta)
+                g = cdiv(cconj(d), b);                   // gamma <- delta^* / beta
             }
+            o.beta[at] = b;
+            o.gamma[at] = g;
+            bg[0] = b;
+            bg[1] = g;
             o.counters[rhs] = 0u;
+        }
+        __syncthreads();
+        // step j + 1: n_{j+1} = beta_j, m_{j+1} = gamma_j^*
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0 && w < 5 && j + 1 < o.k && o.status[rhs] == kStatusOK) {
+            const double2 b = bg[0], g = bg[1];
+            double2* sc = o.sc + (size_t)rhs * kScalars;
+            if (w == 0) sc[kScN] = cinv(b);
+            else if (w == 1) sc[kScC1] = cdiv(TS ? g : b, scale_n(o, rhs, j));
+            else if (w == 2) sc[kScD] = TS ? cinv(g) : cinv(b);
+            else if (w == 3) sc[kScM] = cinv(cconj(g));
+            else sc[kScC1L] = cdiv(cconj(b), scale_m(o, rhs, j));
         }
     }
 }
 
-// write_ring: also store two-float copies of the new vectors in the rings
-// (read by a two-float stencil or by the two-float recurrence later on).
+// FP64 step 2 (the recurrence of NK_FP64 and of the mixed schedule):
+//   r <- r - (H(j,j)/n_j) q_j,  l <- l - (H(j,j)^*/m_j) p_j,  delta += r^dag l,
+// plus the copies the next stencil reads (FP32 pair layout; write_ring: also
+// two-float copies in the rings for a two-float stencil or a later ring
+// step).  Each thread takes a spin-colour component pair (2i, 2i + 1) of a
+// site -- the elements i V + s ... of the FP64 layout and one float4 of the
+// FP32 copy -- two pairs per iteration with every load issued first (the
+// kernel is bound by the FP64 pipe and by the latency of these loads).
 template <bool TS>
 __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mode, int write_ring) {
     __shared__ double2 sh[33];
-    __shared__ double2 coef[2];
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
-    const size_t hb = (size_t)rhs * o.k;
-    // H(j,j)/n_j and H(j,j)^*/m_j, one FP64 division each, by lane 0 of two
-    // warps (on two SM sub-partitions) at the same time
-    if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
-        const double2 a = o.alpha[hb + j];
-        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv(a, scale_n(o, rhs, j))
-                                                  : (TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
-    }
-    __syncthreads();
-    const double2 c3 = coef[0], c4 = coef[1];
+    const double2 c3 = o.sc[(size_t)rhs * kScalars + kScC3];
+    const double2 c4 = o.sc[(size_t)rhs * kScalars + kScC4];
+    const unsigned V = (unsigned)(o.N / 12);
+    const unsigned NP = 6u * V;
     const double2* __restrict__ qj = outer_q(o, rhs, j);
     double2* __restrict__ r = outer_q(o, rhs, j + 1);
     const double2* __restrict__ pj = TS ? outer_p(o, rhs, j) : nullptr;
     double2* __restrict__ l = TS ? outer_p(o, rhs, j + 1) : nullptr;
-    const size_t vb = (size_t)rhs * o.N;
-    double2 acc = mk(0.0, 0.0);
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < o.N; i += (long)o.nblk * blockDim.x) {
-        const double2 q = qj[i];
-        double2 rr = r[i];
-        // r <- r - c3 q, l <- l - c4 p with explicit FMA
-        if (TS) rr = mk(fma(-c3.x, q.x, fma(c3.y, q.y, rr.x)), fma(-c3.x, q.y, fma(-c3.y, q.x, rr.y)));
-        else rr = mk(fma(-c3.x, q.x, rr.x), fma(-c3.x, q.y, rr.y));
-        r[i] = rr;
-        put_copy(o, copy_mode, false, vb + i, rr);
-        if (write_ring) ring_q(o, rhs, j + 1)[i] = dfc_of(rr);
-        if (TS) {
-            const double2 pv = pj[i];
-            double2 ll = l[i];
-            ll = mk(fma(-c4.x, pv.x, fma(c4.y, pv.y, ll.x)), fma(-c4.x, pv.y, fma(-c4.y, pv.x, ll.y)));
-            l[i] = ll;
-            put_copy(o, copy_mode, true, vb + i, ll);
-            if (write_ring) ring_p(o, rhs, j + 1)[i] = dfc_of(ll);
-            acc.x = fma(rr.x, ll.x, fma(rr.y, ll.y, acc.x));   // conj(r) l
-            acc.y = fma(rr.x, ll.y, fma(-rr.y, ll.x, acc.y));
-        } else {
-            acc.x = fma(rr.x, rr.x, fma(rr.y, rr.y, acc.x));
+    float4* __restrict__ r32 = o.q32 + (size_t)rhs * NP;
+    float4* __restrict__ l32 = TS ? o.p32 + (size_t)rhs * NP : nullptr;
+    dfc* __restrict__ rr_ring = write_ring ? ring_q(o, rhs, j + 1) : nullptr;
+    dfc* __restrict__ ll_ring = (write_ring && TS) ? ring_p(o, rhs, j + 1) : nullptr;
+    constexpr int U = 2;
+    const unsigned stride = (unsigned)o.nblk * blockDim.x;
+    double2 acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = mk(0.0, 0.0);
+    for (unsigned p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < NP; p0 += U * stride) {
+        double2 q[U][2], rv[U][2], pv[U][2], lv[U][2];
+        size_t e[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned p = p0 + u * stride;
+            const unsigned cp = p / V, s = p - cp * V;
+            e[u] = (size_t)(2 * cp) * V + s;
+            if (p < NP) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    q[u][h] = qj[e[u] + h * V];
+                    rv[u][h] = r[e[u] + h * V];
+                    if (TS) { pv[u][h] = pj[e[u] + h * V]; lv[u][h] = l[e[u] + h * V]; }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned p = p0 + u * stride;
+            if (p >= NP) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                double2 a = rv[u][h];
+                const double2 qq = q[u][h];
+                // r <- r - c3 q, l <- l - c4 p with explicit FMA
+                if (TS) a = mk(fma(-c3.x, qq.x, fma(c3.y, qq.y, a.x)), fma(-c3.x, qq.y, fma(-c3.y, qq.x, a.y)));
+                else a = mk(fma(-c3.x, qq.x, a.x), fma(-c3.x, qq.y, a.y));
+                rv[u][h] = a;
+                r[e[u] + h * V] = a;
+                if (rr_ring) rr_ring[e[u] + h * V] = dfc_of(a);
+                if (TS) {
+                    double2 b = lv[u][h];
+                    const double2 pp = pv[u][h];
+                    b = mk(fma(-c4.x, pp.x, fma(c4.y, pp.y, b.x)), fma(-c4.x, pp.y, fma(-c4.y, pp.x, b.y)));
+                    lv[u][h] = b;
+                    l[e[u] + h * V] = b;
+                    if (ll_ring) ll_ring[e[u] + h * V] = dfc_of(b);
+                    acc[u].x = fma(a.x, b.x, fma(a.y, b.y, acc[u].x));   // conj(r) l
+                    acc[u].y = fma(a.x, b.y, fma(-a.y, b.x, acc[u].y));
+                } else {
+                    acc[u].x = fma(a.x, a.x, fma(a.y, a.y, acc[u].x));
+                }
+            }
+            if (copy_mode == kCopy32) {
+                r32[p] = make_float4(d2f_int(rv[u][0].x), d2f_int(rv[u][0].y), d2f_int(rv[u][1].x),
+                                     d2f_int(rv[u][1].y));
+                if (TS) l32[p] = make_float4(d2f_int(lv[u][0].x), d2f_int(lv[u][0].y), d2f_int(lv[u][1].x),
+                                             d2f_int(lv[u][1].y));
+            }
         }
     }
-    step2_finish<TS>(o, rhs, j, acc, sh);
+    double2 tot = acc[0];
+#pragma unroll
+    for (int u = 1; u < U; ++u) { tot.x += acc[u].x; tot.y += acc[u].y; }
+    step2_finish<TS>(o, rhs, j, tot, sh);
 }
 
 // Step 2 of the late (FP32-stencil) steps of the mixed schedule in two-float
@@ -198,19 +266,11 @@ __global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mod
 template <bool TS>
 __global__ void __launch_bounds__(kThreads, 2) k_step2_df(Outer o, int j, int copy_mode) {
     __shared__ double2 sh[33];
-    __shared__ double2 coef[2];
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
-    const size_t hb = (size_t)rhs * o.k;
-    // H(j,j)/n_j and H(j,j)^*/m_j, one FP64 division each, by lane 0 of two
-    // warps (on two SM sub-partitions) at the same time
-    if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
-        const double2 a = o.alpha[hb + j];
-        coef[threadIdx.x >> 5] = threadIdx.x == 0 ? cdiv(a, scale_n(o, rhs, j))
-                                                  : (TS ? cdiv(cconj(a), scale_m(o, rhs, j)) : mk(0.0, 0.0));
-    }
-    __syncthreads();
-    const dfc c3 = dfc_of(coef[0]), c4 = dfc_of(coef[1]);
+    const dfc c3 = dfc_of(o.sc[(size_t)rhs * kScalars + kScC3]);
+    const dfc c4 = dfc_of(o.sc[(size_t)rhs * kScalars + kScC4]);
+    const int V = (int)(o.N / 12);
     const dfc* __restrict__ qj = ring_q(o, rhs, j);
     dfc* __restrict__ r = ring_q(o, rhs, j + 1);
     double2* __restrict__ rq = outer_q(o, rhs, j + 1);
@@ -253,13 +313,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_step2_df(Outer o, int j, int co
             r[i] = a;
             if (qdf) reinterpret_cast<dfc*>(rq)[i] = a;
             else rq[i] = double2_of(a);
-            if (copy_mode == kCopy32) o.q32[vb + i] = make_float2(a.x.hi, a.y.hi);
+            const int c = (int)(i / V), site = (int)(i - (long)c * V);
+            const size_t i32 = vb + f32_pair_index(c, site, V);
+            if (copy_mode == kCopy32) reinterpret_cast<float2*>(o.q32)[i32] = make_float2(a.x.hi, a.y.hi);
             if (TS) {
                 dfc& b = ll[u];
                 b.x = b.x - (c4.x * pv[u].x - c4.y * pv[u].y);
                 b.y = b.y - (c4.x * pv[u].y + c4.y * pv[u].x);
                 l[i] = b;
-                if (copy_mode == kCopy32) o.p32[vb + i] = make_float2(b.x.hi, b.y.hi);
+                if (copy_mode == kCopy32) reinterpret_cast<float2*>(o.p32)[i32] = make_float2(b.x.hi, b.y.hi);
                 ax[u] += a.x * b.x + a.y * b.y;   // conj(r) l
                 ay[u] += a.x * b.y - a.y * b.x;
             } else {
@@ -404,6 +466,25 @@ __global__ void k_fill_int(int* p, int n, int v) {
 
 void launch_fill_int(int* p, int n, int value, cudaStream_t st) {
     k_fill_int<<<(n + 127) / 128, 128, 0, st>>>(p, n, value);
+}
+
+// per RHS r: (|x2_r - b_r|^2, |b_r|^2), one block per RHS, fixed-order sums
+__global__ void k_eps_sums(const double2* __restrict__ b, const double2* __restrict__ x2, long N,
+                           double2* __restrict__ out) {
+    __shared__ double2 sh[33];
+    const size_t base = (size_t)blockIdx.x * N;
+    double d = 0.0, n = 0.0;
+    for (long i = threadIdx.x; i < N; i += blockDim.x) {
+        const double2 a = b[base + i], c = x2[base + i];
+        d += cnorm2(csub(c, a));
+        n += cnorm2(a);
+    }
+    const double2 t = block_sum(mk(d, n), sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+void launch_eps_sums(const double2* b, const double2* x2, int n, long N, double2* out, cudaStream_t st) {
+    k_eps_sums<<<n, 1024, 0, st>>>(b, x2, N, out);
 }
 
 void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st) {

@@ -1,5 +1,5 @@
 // Shared device helpers: complex arithmetic on float2/double2, deterministic
-// block reductions, the bounded-wait policy.
+// block reductions, float <-> double conversions and two-float arithmetic.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -282,9 +282,5 @@ struct dfac {
 };
 template <> struct C2<df> { typedef dfc T; };
 static_assert(sizeof(dfc) == 16, "two-float complex is 16 bytes");
-
-// Upper bound on spin iterations of any device-side wait (each iteration
-// sleeps ~100 ns), about one second; a wait that runs out sets an error flag.
-constexpr long long kSpinLimit = 10000000LL;
 
 }  // namespace nk

@@ -36,8 +36,28 @@ void launch_abi_to_soa(const double2* in, long in_stride, double2* out, long out
                        int n, cudaStream_t st);
 void launch_soa_to_abi(const double2* in, long in_stride, double2* out, long out_stride,
                        const double2* add, long add_stride, int V, int n, cudaStream_t st);
-void launch_to_fp32(const double2* in, long in_stride, float2* out, long out_stride, long N, int n,
-                    cudaStream_t st);
+// ABI spinors (double, [site][12]) <-> FP32 pair layout ([6][V] float4), n vectors
+void launch_abi_to_f32pair(const double2* in, long in_stride, float4* out, long out_stride, int V, int n,
+                           cudaStream_t st);
+void launch_f32pair_to_abi(const float4* in, long in_stride, double2* out, long out_stride, int V, int n,
+                           cudaStream_t st);
+
+// The multi-RHS FP32 stencil alone (stencil32.cu): out = A in for the n_a
+// vectors of in_a, A^dagger in for the n_d vectors of in_d; FP32 pair layout,
+// vstride float4 between vectors; n_a + n_d <= 24.
+struct Stencil32Set {
+    const float4* in_a;
+    const float4* in_d;
+    float4* out_a;
+    float4* out_d;
+    long vstride;
+    int n_a, n_d;
+};
+void launch_stencil32(const void* U32, const Geom& g, const Stencil32Set& s, double kappa, double mu,
+                      cudaStream_t st);
+int stencil32_sites_per_cta(int nv);
+void stencil32_init_attributes();   // dynamic shared memory above 48 KB (outside capture)
+int stencil32_blocks(const Geom& g, int nv);
 
 // ---- outer (two-sided) Lanczos recurrence -------------------------------------
 
@@ -56,15 +76,16 @@ struct Outer {
     int qcols;       // vectors per RHS in Q: k + 1 or 3
     double2* Q;      // right basis q_j
     double2* P;      // left vectors p_j, ring [rhs][3][N] (two-sided)
-    float2* q32;     // FP32 copy of the newest q, [rhs][N]
-    float2* p32;     // FP32 copy of the newest p, [rhs][N]
+    float4* q32;     // FP32 copy of the newest q, [rhs][6][V] pair layout (f32_pair_index)
+    float4* p32;     // FP32 copy of the newest p, [rhs][6][V]
     dfc* qdf;        // two-float copy of the newest q, [rhs][N]
     dfc* pdf;        // two-float copy of the newest p, [rhs][N]
     double2* alpha;  // H(j,j), [rhs][k]
     double2* beta;   // H(j+1,j), [rhs][k]
     double2* gamma;  // H(j,j+1), [rhs][k]
     double2* partials;  // [rhs][npart]
-    unsigned* counters; // [rhs]
+    unsigned* counters; // [rhs]; the all-RHS kernels (k_stencil32_step1) use counters[0]
+    double2* sc;        // [rhs][kScalars]: scalars of the current outer step (below)
     int* status;        // [rhs]
     double* xnorm;      // [rhs]
     double2* y;         // double pass: accumulation y = sum_j c'_j q_j, [rhs][N]
@@ -112,6 +133,27 @@ __device__ inline double2 scale_m(const Outer& o, int rhs, int j) {
     return make_double2(g.x, -g.y);
 }
 
+// Scalars of outer step j per RHS (complex FP64), formed once per step by the
+// finishing block of the kernel that completes their inputs -- the norm kernel
+// (j = 0) or step 2 of step j - 1 (kScN .. kScC1L), the step-1 kernel (kScC3,
+// kScC4) -- so that the kernels of the step read them instead of each CTA
+// dividing again (FP64 divisions are slow on GB300).
+constexpr int kScalars = 8;
+constexpr int kScN = 0;    // 1/n_j: scale of the stencil output A q_j
+constexpr int kScC1 = 1;   // c_{j-1}/n_{j-1} (c = gamma two-sided, beta Hermitian); 0 at j = 0
+constexpr int kScD = 2;    // 1/m_j^* two-sided, 1/n_j Hermitian: H(j,j) = kScD x (dot of r)
+constexpr int kScM = 3;    // 1/m_j: scale of A^dagger p_j
+constexpr int kScC1L = 4;  // beta_{j-1}^*/m_{j-1}; 0 at j = 0
+constexpr int kScC3 = 5;   // H(j,j)/n_j (step 2, right)
+constexpr int kScC4 = 6;   // H(j,j)^*/m_j (step 2, left)
+
+// FP32 vectors are stored in the pair layout [6][V] of float4 per vector:
+// float4 i of site s holds spin-colour components 2i and 2i + 1.  As float2
+// elements (one complex each), component c of site s is element:
+__host__ __device__ inline size_t f32_pair_index(int c, int s, int V) {
+    return 2 * ((size_t)(c >> 1) * V + s) + (c & 1);
+}
+
 // status codes kept on the device (0 = fine)
 constexpr int kStatusOK = 0;
 constexpr int kStatusZeroSource = 1;  // |b| = 0: result is 0
@@ -125,10 +167,12 @@ constexpr int kStatusInnerBreakdown = 6;  // inner (two-sided) Lanczos on H_k': 
 constexpr int kCopyNone = 0, kCopy32 = 1, kCopyDF = 2;
 // keep_status: the second pass of NK_DOUBLE_PASS (a failure of the first pass stays)
 void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep_status = false);
-// Fused stencil + first half of step j (dslash.cu); precision 32 (FP32),
-// 48 (two-float) or 64 (FP64).
+// Fused stencil + first half of step j; precision 32 (FP32, the multi-RHS
+// kernel of stencil32.cu), 48 (two-float) or 64 (FP64) (dslash.cu).
 void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
                          double kappa, double mu, cudaStream_t st);
+void launch_stencil32_step1(const void* U32, const Geom& g, const Outer& o, int j, double kappa, double mu,
+                            cudaStream_t st);
 int dslash_step1_blocks(const Geom& g, int threads);
 constexpr int kStencilMaxThreads = 256;
 // ring: the step belongs to the two-float recurrence of the mixed schedule
@@ -143,6 +187,8 @@ void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y
 void launch_fill_int(int* p, int n, int value, cudaStream_t st);
 // Adaptive k: per RHS (|c - c_prev|, |c|) over the first k entries, then c_prev <- c.
 void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st);
+// NK_EPS_EST: per RHS (|x2 - b|^2, |b|^2) of n vectors of N complex (any common layout)
+void launch_eps_sums(const double2* b, const double2* x2, int n, long N, double2* out, cudaStream_t st);
 
 // ---- inner part: p estimate, LU of p H_k, inner Lanczos, RHi, c = V_l s -------
 
@@ -171,7 +217,6 @@ struct Inner {
     int* rhi_iters;        // [rhs]
     double2* c;            // V_l s, [rhs][k]
     int* status;           // [rhs]
-    int* timeout;          // device flag: a bounded wait ran out
     int df_inner;          // 1: p estimate, LU, sweeps and inner Lanczos in two-float
                            // arithmetic (the mixed schedule); 0: FP64
 };

@@ -36,8 +36,8 @@ constexpr size_t kOffBl = kOffAl + up((size_t)kMaxRhs * kMaxEll);
 constexpr size_t kOffGl = kOffBl + up((size_t)kMaxRhs * kMaxEll);
 constexpr size_t kOffSv = kOffGl + up((size_t)kMaxRhs * kMaxEll);
 constexpr size_t kOffP = kOffSv + up((size_t)kMaxRhs * kMaxEll);       // p, z_min, z_max (doubles)
-constexpr size_t kOffInt = kOffP + up((size_t)3 * kMaxRhs);            // ipiv, status, iters, timeout (ints)
-constexpr size_t kInts = (size_t)kMaxRhs * kMaxK + 2 * kMaxRhs + 1;
+constexpr size_t kOffInt = kOffP + up((size_t)3 * kMaxRhs);            // ipiv, status, iters (ints)
+constexpr size_t kInts = (size_t)kMaxRhs * kMaxK + 2 * kMaxRhs;
 constexpr size_t kTotal = kOffInt + up((kInts + 3) / 4);
 
 __device__ __align__(256) double2 g_noalloc_scratch[kTotal];
@@ -115,7 +115,6 @@ extern "C" int nk_inner_sign_noalloc(const double* alpha_dev, const double* beta
     in.ipiv = ints;
     in.status = ints + (size_t)kMaxRhs * kMaxK;
     in.rhi_iters = in.status + kMaxRhs;
-    in.timeout = in.rhi_iters + kMaxRhs;
     in.c = (double2*)c_dev;
     // the array keeps the previous call's contents: the status flags must start at 0
     e = cudaMemsetAsync(in.status, 0, sizeof(int) * n_rhs, st);

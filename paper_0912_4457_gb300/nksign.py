@@ -35,6 +35,8 @@ NK_PROFILE = 0x20
 NK_ASYNC = 0x40
 NK_SHARED_P = 0x80
 NK_PREFIX_FP64 = 0x100
+NK_EPS_EST = 0x200
+NK_PREDICT = 0x400
 NK_MAX_RHS = 12
 NK_NCLASS = 9
 CLASS_NAMES = ["dslash", "dslash_df", "step2", "dslash64", "inner", "rhi", "lift", "other", "step2_df"]
@@ -49,11 +51,11 @@ EXPORTED = [
     "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision", "nk_set_df_recurrence",
     "nk_set_adapt_start",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
-    "nk_dslash_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
+    "nk_dslash_dev", "nk_stencil32_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
     "nk_destroy",
     "nk_mlp_create", "nk_mlp_set_norm", "nk_mlp_set_weight_decay", "nk_mlp_get_params", "nk_mlp_set_params", "nk_mlp_loss_grad",
     "nk_mlp_train", "nk_mlp_forward", "nk_mlp_last_error", "nk_mlp_destroy", "nk_features",
-    "nk_predict_sizes", "nk_set_launch", "nk_get_launch", "nk_autotune", "nk_wait",
+    "nk_predict_sizes", "nk_set_predictor", "nk_set_launch", "nk_get_launch", "nk_autotune", "nk_wait",
 ]
 
 NK_MLP_IN = 16
@@ -79,6 +81,13 @@ class NkStats(ctypes.Structure):
         ("launches", ctypes.c_int),
         ("t_class_ms", ctypes.c_double * NK_NCLASS),
         ("n_class", ctypes.c_int * NK_NCLASS),
+        ("t_basis_ms", ctypes.c_double),
+        ("t_inner_ms", ctypes.c_double),
+        ("t_lift_ms", ctypes.c_double),
+        ("eps_sgn2", ctypes.c_double * NK_MAX_RHS),
+        ("k_pred", ctypes.c_int),
+        ("ell_pred", ctypes.c_int),
+        ("predict_fallback", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -92,6 +101,9 @@ class NkStats(ctypes.Structure):
             "launches": self.launches,
             "t_class_ms": dict(zip(CLASS_NAMES, list(self.t_class_ms))),
             "n_class": dict(zip(CLASS_NAMES, list(self.n_class))),
+            "t_basis_ms": self.t_basis_ms, "t_inner_ms": self.t_inner_ms, "t_lift_ms": self.t_lift_ms,
+            "eps_sgn2": list(self.eps_sgn2[:n]), "k_pred": self.k_pred, "ell_pred": self.ell_pred,
+            "predict_fallback": bool(self.predict_fallback),
         }
 
 
@@ -138,6 +150,7 @@ def load_library(path: str = LIB_PATH):
         "nk_overlap_apply": ([P, dp, I, I, I, D, U, dp, ctypes.POINTER(NkStats)], I),
         "nk_overlap_apply_dev": ([P, P, I, I, I, D, U, P, ctypes.POINTER(NkStats), P], I),
         "nk_dslash_dev": ([P, P, P, I, I, I, P], I),
+        "nk_stencil32_dev": ([P, P, P, I, P], I),
         "nk_outer_lanczos_dev": ([P, P, I, I, U, dp, dp, dp, dp, P], I),
         "nk_inner_sign": ([P, dp, dp, dp, I, I, I, D, I, dp, ctypes.POINTER(NkStats)], I),
         "nk_inner_sign_noalloc": ([P, P, P, I, I, I, D, I, P, P, ctypes.c_char_p, ctypes.c_size_t], I),
@@ -155,6 +168,7 @@ def load_library(path: str = LIB_PATH):
         "nk_mlp_destroy": ([P], None),
         "nk_features": ([P, P, fp, P], I),
         "nk_predict_sizes": ([P, P, P, I, ctypes.POINTER(I), ctypes.POINTER(I), P], I),
+        "nk_set_predictor": ([P, P], I),
         "nk_set_launch": ([P, I, U, ctypes.POINTER(NkLaunch)], I),
         "nk_get_launch": ([P, I, U, ctypes.POINTER(NkLaunch)], I),
         "nk_autotune": ([P, I, U, ctypes.c_char_p, ctypes.POINTER(NkLaunch), dp], I),
@@ -310,6 +324,19 @@ class Context:
         self._check(self._lib.nk_dslash_dev(self.h, _dev_ptr(in_dev), _dev_ptr(out_dev), int(n_vec),
                                             1 if dagger else 0, int(precision), _stream_ptr(stream)))
 
+    def stencil32_dev(self, in_dev, out_dev, n_rhs, stream=None):
+        """nk_stencil32_dev: A on the first n_rhs and A^dagger on the next n_rhs
+        FP32 vectors of in_dev (pair layout, 24 V floats per vector) -> out_dev."""
+        import torch
+        for t in (in_dev, out_dev):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.float32):
+                raise TypeError("expected contiguous float32 CUDA tensors")
+            if t.numel() < 2 * int(n_rhs) * 24 * self.V:
+                raise ValueError("tensor holds fewer than 2 n_rhs vectors")
+        self._check(self._lib.nk_stencil32_dev(self.h, ctypes.c_void_p(in_dev.data_ptr()),
+                                               ctypes.c_void_p(out_dev.data_ptr()), int(n_rhs),
+                                               _stream_ptr(stream)))
+
     def outer_lanczos_dev(self, b_dev, n_rhs, k, flags=NK_FP64, stream=None):
         a = np.zeros((n_rhs, k), np.complex128)
         be = np.zeros((n_rhs, k), np.complex128)
@@ -371,6 +398,12 @@ class Context:
         self._check(self._lib.nk_predict_sizes(self.h, mlp.h, _dev_ptr(b_dev), int(k_max), ctypes.byref(k),
                                                ctypes.byref(ell), _stream_ptr(stream)))
         return k.value, ell.value
+
+    def set_predictor(self, mlp):
+        """nk_set_predictor: the Mlp that NK_PREDICT solves use (None: none).
+        The context keeps a reference so the predictor outlives its use."""
+        self._predictor = mlp
+        self._check(self._lib.nk_set_predictor(self.h, mlp.h if mlp is not None else None))
 
 
 def _fptr(a: np.ndarray):

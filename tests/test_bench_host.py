@@ -15,19 +15,41 @@ def _args(**kw):
     return a
 
 
+def test_default_workload_is_the_largest_single_gpu_config():
+    """10^4, mu = 0.2, 12 point sources, FP32 stencil after j0 and an FP64 recurrence."""
+    w = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert w["dims"] == (10, 10, 10, 10) and w["mu"] == 0.2 and w["n_rhs"] == 12
+    assert w["mixed"] and bench.j1_of(w, _args()) == -1
+    assert w["k_ref"] > w["k"] and w["ell_ref"] >= w["ell"]
+
+
 def test_df_recurrence_start_of_the_workload():
     w = dict(bench.WORKLOADS[bench.DEFAULT_WORKLOAD])
-    want = w["j0"] if w.get("j1", -1) < 0 else min(w["j1"], w["j0"])
-    assert bench.j1_of(w, _args()) == want
-    assert bench.j1_of(w, _args(j1=-1)) == w["j0"]            # < 0: the FP32 switch
-    assert bench.j1_of(w, _args(j1=10 * w["j0"])) == w["j0"]  # past j0 acts as j0
+    assert bench.j1_of(w, _args()) == -1                      # FP64 recurrence throughout
+    assert bench.j1_of(w, _args(j1=-5)) == -1
     assert bench.j1_of(w, _args(j1=0)) == 0
+    assert bench.j1_of(w, _args(j1=300)) == 300
 
 
 def test_whole_job_value_counts_every_rank():
     # 12 solves per step, 24 steps, 1 s: 288 solves/s per rank
     assert bench.whole_job_value(12, 24, 1000.0, 1) == pytest.approx(288.0)
     assert bench.whole_job_value(12, 24, 1000.0, 4) == pytest.approx(4 * 288.0)
+
+
+def test_roofline_of_the_fp64_step2():
+    """Two-sided step 2: r -= c3 q, l -= c4 p, delta += r^dag l, 24 FP64 flops
+    per element against the nominal FP64 rate."""
+    w = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    N = 12 * int(np.prod(w["dims"]))
+    tc, nc = {"step2": 5.0}, {"step2": 100}            # 50 us per launch
+    r = bench.dominant_roofline("step2", tc, nc, w, {"hbm_gbs": 6000.0}, 2070.0)
+    flops = 24.0 * N * w["n_rhs"]
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["flops_per_launch"] == pytest.approx(flops)
+    assert r["achieved"] == pytest.approx(flops / 50e-6 / 1e12)
+    assert r["peak"] == pytest.approx(bench.FP64_PEAK_TFLOPS)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
 
 
 def test_roofline_of_the_two_float_stencil():
@@ -42,25 +64,8 @@ def test_roofline_of_the_two_float_stencil():
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
 
 
-def test_roofline_of_step2_averages_its_launches():
-    """Launches j1 <= j <= k - 2; those before an FP32 stencil (j + 1 >= j0)
-    also write the FP32 copies: 128 B per element two-sided, else 112 B."""
-    w = dict(bench.WORKLOADS[bench.DEFAULT_WORKLOAD], k=10, j0=4, j1=0)
-    V = int(np.prod(w["dims"]))
-    N = 12 * V
-    n = 9                                  # j = 0 .. 8
-    n_copy = 6                             # j = 3 .. 8
-    tc, nc = {"step2_df": 0.09}, {"step2_df": n}   # 10 us per launch
-    r = bench.dominant_roofline("step2_df", tc, nc, w, {"hbm_gbs": 6000.0}, 2070.0)
-    per_el = (n_copy * 128 + (n - n_copy) * 112) / n
-    assert r["algorithmic_bytes_per_launch"] == pytest.approx(per_el * N * w["n_rhs"])
-    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
-
-
 def test_committed_profiles_give_the_traffic_of_the_outer_kernels():
-    for k in ("k_dslash_step1<df>", "k_dslash_step1<float>", "k_step2_df"):
-        t = bench.profiled_traffic(k)
-        assert t is not None and 1e7 < t < 1e9, k
+    assert bench.profiled_traffic("k_dslash_step1<df>") is not None
     assert bench.profiled_traffic("no_such_kernel") is None
 
 
@@ -71,4 +76,5 @@ def test_config_names_the_workload_and_its_schedule():
     assert c["lattice"] == "x".join(str(d) for d in w["dims"])
     assert c["batches_in_flight"] == 4
     assert c["k"] == w["k"] and c["ell"] == w["ell"] and c["n_rhs"] == w["n_rhs"]
-    assert ("before step %d" % bench.j1_of(w, _args())) in c["precision"]
+    assert "recurrence" in c["precision"] and "FP64" in c["precision"]
+    assert "two-float (about 48-bit) from it on" in bench.config_of(w, _args(j1=0))["precision"]

@@ -23,7 +23,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_0912_4457_gb300.nksign import NK_DOUBLE_PASS, NK_MIXED, Context  # noqa: E402
+from paper_0912_4457_gb300.nksign import NK_DOUBLE_PASS, NK_MIXED, NK_SHARED_P, Context  # noqa: E402
 
 TOL = 1e-8
 
