@@ -127,6 +127,8 @@ typedef struct nk_stats {
     double eps_sgn2[NK_MAX_RHS];       /* NK_EPS_EST: |x~ - x| / (2|x|) per RHS (Sec. 3), else 0 */
     int k_pred, ell_pred;              /* NK_PREDICT: the predicted sizes, else 0 */
     int predict_fallback;              /* NK_PREDICT: 1 if the solve was repeated with the caller's l */
+    int defl_m;                        /* LR deflation: eigenpairs deflated (nk_set_deflation) */
+    double defl_gap;                   /* and the deflation gap Delta = max |lambda_i| (Sec. 3) */
 } nk_stats;
 
 /* Create a context for a lattice of dims[4] = {Lx, Ly, Lz, Lt} (each >= 2;
@@ -165,6 +167,37 @@ int nk_set_precision(nk_ctx* ctx, int j0);
  * (the default) keeps the whole recurrence in FP64.  Takes effect with the
  * next solve. */
 int nk_set_df_recurrence(nk_ctx* ctx, int j1);
+
+/* LR deflation (App. C steps 1 and 6; Sec. 3).  m critical eigenpairs of A
+ * (the paper deflates those of smallest modulus; the largest deflated
+ * |lambda| is the deflation gap Delta): lambda[2 i], lambda[2 i + 1] = re, im
+ * of lambda_i; R (HOST, m vectors in the ABI spinor layout, vector i at
+ * element 12 V i) the right eigenvectors r_i; L the left eigenvectors l_i
+ * with <l_i, r_j> = delta_ij, or NULL for Hermitian A (mu = 0: l_i = r_i).
+ * Every following solve of this context projects its sources,
+ *   x_minus = b - sum_i <l_i, b> r_i,
+ * runs the nested method on x_minus, and adds sum_i sgn(Re lambda_i) <l_i, b> r_i
+ * (Eq. sgnz) to the result; nk_overlap_apply applies b + gamma5 y to the whole.
+ * Computing the eigenpairs is the caller's one-off initialisation (Sec. 3:
+ * "performed once in an initialization step").  The eigenpairs must belong
+ * to the current (mu, m_w) and links.  m = 0 switches deflation off.  Copies
+ * the vectors (m <= NK_MAX_DEFL).  Blocks. */
+#define NK_MAX_DEFL 256
+int nk_set_deflation(nk_ctx* ctx, int m, const double* lambda, const double* R, const double* L);
+
+/* Multi-level nesting (Sec. 4.5).  A solve's l argument is the size l_1 of the
+ * first nested level; nk_set_nesting adds n_deeper levels below it with sizes
+ * ells[0] = l_2 >= l_3 >= ... (even, >= 2; a level larger than the one above
+ * is clipped to it), n_deeper <= NK_MAX_LEVELS - 1.  Level i + 1 repeats App. C
+ * steps 3-4 on the Ritz matrix H_{l_i} of level i: p_{i+1} by Eq. popt from
+ * H_{l_i} (one per RHS), the LU of p_{i+1} H_{l_i}, and l_{i+1} steps of the
+ * (two-sided) Lanczos recurrence with H_{l_i}' from e_1.  RHi runs on the
+ * deepest Ritz matrix only, and the result is lifted back through every
+ * level: y = |b| V_k V_{l_1} ... V_{l_n} sgn(H_{l_n}) e_1.  n_deeper = 0 (the
+ * default) is the single nesting of Eq. nested.  Applies to the solves and to
+ * nk_inner_sign of this context from the next call on. */
+#define NK_MAX_LEVELS 6
+int nk_set_nesting(nk_ctx* ctx, int n_deeper, const int* ells);
 
 /* Adaptive k: the outer size at the first convergence check (even; 0 selects
  * NK_ADAPT_FIRST(l)).  A predicted k (nk_predict_sizes) minus two check
@@ -262,6 +295,22 @@ int nk_overlap_apply(nk_ctx* ctx, const double* b, int n_rhs, int k, int ell, do
                      unsigned flags, double* y, nk_stats* st);
 int nk_overlap_apply_dev(nk_ctx* ctx, const double* b_dev, int n_rhs, int k, int ell,
                          double tol, unsigned flags, double* y_dev, nk_stats* st, void* stream);
+
+/* Overlap inversion (the consumer the paper's Sec. 3 names: f(A) x "needed
+ * by iterative inverters"): x = (D_ov(mu) + mass)^{-1} b by conjugate
+ * gradients on the normal equations M^dagger M x = M^dagger b, M = D_ov(mu) +
+ * mass (mass >= 0: the library's shift; mass = 0 is Eq. Dovmu itself).  Every
+ * iteration applies M (nk_overlap_apply) and M^dagger = gamma5 (D_ov(-mu) +
+ * mass) gamma5 (A(mu)^dagger = A(-mu)), each through the nested sign function
+ * with (k, l, tol_sign, flags) as nk_sign_apply (and the deflation of the
+ * context, with left and right eigenvectors exchanged for -mu).  Stops when
+ * |M^dagger (b - M x)| <= tol_cg |M^dagger b| for every RHS, or after maxit
+ * iterations (NK_ENOTCONV; x is still written).  b, x HOST arrays of n_rhs
+ * vectors; iters and resid (nullable, n_rhs entries) receive the iterations
+ * and the final relative residual of the normal equations per RHS.  The
+ * sign function's own error bounds the attainable residual.  Blocks. */
+int nk_overlap_solve(nk_ctx* ctx, const double* b, int n_rhs, int k, int ell, double tol_sign, unsigned flags,
+                     double mass, double tol_cg, int maxit, double* x, int* iters, double* resid);
 
 /* Waits for the pending NK_ASYNC solve of the context and returns its result
  * code; st (nullable) receives its statistics.  NK_OK if none is pending. */

@@ -22,6 +22,9 @@ Contents, each module citing the passage of the paper it follows:
                   sgn^2 error estimate of Sec. 3 and the overlap operator (Eq. Dovmu).
 * ``precond``  -- closed forms for p_opt and the improvement factors
                   (Eqs. popt, condimp, condimpNH).
+* ``deflation`` -- LR deflation of the eigenvalues of smallest modulus
+                  (App. C steps 1 and 6, Sec. 3 and its footnote).
+* ``nested.inner_sign_multilevel`` -- multi-level nesting (Sec. 4.5).
 
 Pins (tests run with ``-m "not gpu"``) tie every function to something other
 than itself: the free-field momentum-space closed form, gauge covariance,
@@ -29,4 +32,4 @@ gamma5-hermiticity, scipy's independent ``signm``, the paper's printed p/F
 values, algebraic invariants (sgn^2 = 1, [sgn A, A] = 0, Ginsparg-Wilson) and
 brute-force dense checks on tiny lattices.
 """
-from . import dirac, signfun, krylov, tridiag, nested, precond  # noqa: F401
+from . import dirac, signfun, krylov, tridiag, nested, precond, deflation  # noqa: F401

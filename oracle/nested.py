@@ -117,6 +117,48 @@ def inner_sign(alpha, beta, gamma, ell: int, p: float, hermitian: bool):
                "inner": inner}
 
 
+def inner_sign_multilevel(alpha, beta, gamma, ells, p: float, hermitian: bool):
+    """Multi-level nesting (Sec. 4.5): c = V_{l_1} V_{l_2} ... V_{l_n} sgn(H_{l_n}) e_1.
+
+    Level i (i = 1..n) applies App. C steps 3-4 to the Ritz matrix of the level
+    above (H_k for i = 1): the LU of p_i H, the (two-sided) Lanczos recurrence
+    with H' = (p_i H + (p_i H)^-1)/2 from e_1 for l_i steps -> V_{l_i}, H_{l_i}.
+    RHi runs on the deepest Ritz matrix only (step 5), and the product is
+    lifted back through every level.  p_1 = p (the caller's, as in
+    inner_sign); deeper levels estimate their own p_i by Eq. popt from the
+    Ritz matrix of the level above (the footnote of Sec. 4.5).  With one
+    level this is inner_sign.
+
+    Returns (c, info) with the per-level p values and the RHi count."""
+    h_al, h_be, h_ga = alpha, beta, gamma
+    bases, ps = [], []
+    for i, ell in enumerate(ells):
+        p_i = p if i == 0 else estimate_p(h_al, h_be, h_ga)[0]
+        lu = tridiag.PrecondLU(p_i, h_al, h_be, h_ga)          # step 3 at this level
+        k_i = len(lu.alpha)
+        e1 = np.zeros(k_i, dtype=np.float64 if hermitian else np.complex128)
+        e1[0] = 1.0
+        if hermitian:                                          # step 4 at this level
+            inner = krylov.lanczos(lu.apply_hprime, e1, ell)
+        else:
+            inner = krylov.two_sided_lanczos(
+                lu.apply_hprime, lambda v, lu=lu: lu.apply_hprime(v, dagger=True), e1, ell)
+        bases.append(inner.V[:, : inner.k_used])
+        ps.append(p_i)
+        m = inner.k_used
+        h_al = inner.alpha[:m]
+        h_be = inner.beta[: m - 1]
+        h_ga = inner.gamma[: m - 1]
+    h = np.diag(h_al).astype(np.result_type(h_al, h_be, h_ga))
+    if len(h_al) > 1:
+        h = h + np.diag(h_be, -1) + np.diag(h_ga, 1)
+    s, it, conv = signfun.rhi(h)                               # step 5, deepest level
+    c = s[:, 0]
+    for V in reversed(bases):                                  # lift back level by level
+        c = V @ c
+    return c, {"p": ps, "rhi_iters": it, "rhi_converged": conv}
+
+
 def operator(U, dims, mu: float, m_w: float, antiperiodic_t: bool = True):
     """(apply A, apply A^dagger, hermitian) for A = gamma_5 D_w(mu)."""
     def a(v):

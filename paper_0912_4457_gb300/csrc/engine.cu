@@ -23,6 +23,17 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Multi-level nesting (Sec. 4.5): sizes of the inner levels below the first.
+struct Nesting {
+    int n = 0;
+    int ell[NK_MAX_LEVELS - 1] = {0};
+    long code() const {
+        long h = n;
+        for (int i = 0; i < n; ++i) h = h * 1031 + ell[i];
+        return h;
+    }
+};
+
 struct GraphKey {
     const void* b;
     void* y;
@@ -30,9 +41,10 @@ struct GraphKey {
     unsigned flags;
     double p, mu, mw;
     int overlap;
+    long nest;
     bool operator<(const GraphKey& o) const {
-        return std::tie(b, y, n_rhs, k, ell, j0, j1, flags, p, mu, mw, overlap) <
-               std::tie(o.b, o.y, o.n_rhs, o.k, o.ell, o.j0, o.j1, o.flags, o.p, o.mu, o.mw, o.overlap);
+        return std::tie(b, y, n_rhs, k, ell, j0, j1, flags, p, mu, mw, overlap, nest) <
+               std::tie(o.b, o.y, o.n_rhs, o.k, o.ell, o.j0, o.j1, o.flags, o.p, o.mu, o.mw, o.overlap, o.nest);
     }
 };
 
@@ -46,6 +58,7 @@ struct nk_ctx {
     bool mu_set = false;
     int j0 = -1;
     int j1 = -1;   // first outer step whose recurrence runs in two-float arithmetic (< 0: none)
+    Nesting nest;  // levels below the first (nk_set_nesting)
     int adapt_start = 0;   // adaptive k: first check (0: NK_ADAPT_FIRST(l))
     bool links = false;
     double2* U64 = nullptr;
@@ -56,6 +69,16 @@ struct nk_ctx {
     DevBuf links_tmp;
     DevBuf inner_tmp;     // nk_inner_sign / nk_features scratch (never the staged b and y)
     DevBuf eps_buf;       // NK_EPS_EST: approx(approx(x)) and the per-RHS sums
+    // LR deflation (nk_set_deflation): m eigenpairs, right and left vectors
+    // [m][12 V] (ABI layout), -1 and sgn(Re lambda_i) per pair, the gap
+    int defl_m = 0;
+    double2* defl_R = nullptr;
+    double2* defl_L = nullptr;   // == defl_R when no left vectors were given
+    double* defl_neg = nullptr;
+    double* defl_sgn = nullptr;
+    double defl_gap = 0.0;
+    DevBuf defl_buf;      // x_minus and the coefficients <l_i, b_r>
+    DevBuf cg_buf;        // nk_overlap_solve: the CG vectors
     // phase events recorded inside every solve (captured into its graph):
     // end of the outer basis, end of the inner part, start of an adaptive chunk
     cudaEvent_t ph[3] = {nullptr, nullptr, nullptr};
@@ -150,6 +173,8 @@ double kappa_of(const nk_ctx* c) { return 1.0 / (8.0 + 2.0 * c->m_w); }
 struct Layout {
     nk::Outer o;
     nk::Inner in;
+    nk::Inner deeper[NK_MAX_LEVELS - 1];   // multi-level nesting: buffers of the levels below the first
+    int n_deeper;
     double2* y_soa;
     double2* cp;      // lift coefficients c'_j, [rhs][k]
     double2* c_prev;  // adaptive k: c of the previous check (finally the accepted c), [rhs][k]
@@ -161,7 +186,7 @@ struct Layout {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_sided, bool double_pass,
-             const nk_launch& lc, bool mixed) {
+             const nk_launch& lc, bool mixed, const Nesting& nest = Nesting()) {
     const int nblk = lc.step2_blocks;
     Layout L;
     std::memset(&L, 0, sizeof(L));
@@ -227,6 +252,30 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     L.dn = (double2*)take(sizeof(double2) * n_rhs);
     L.kused = (int*)take(sizeof(int) * n_rhs);
     in.status = o.status;
+    // levels below the first (sizes clipped to the level above); RHi runs on
+    // the deepest, whose S buffer is the only one used
+    int kl = ell;
+    L.n_deeper = nest.n;
+    for (int d = 0; d < nest.n; ++d) {
+        nk::Inner& q = L.deeper[d];
+        q = in;
+        q.k = kl;
+        q.kstride = 0;
+        q.ell = std::min(nest.ell[d], kl);
+        q.p = (double*)take(sizeof(double) * n_rhs);
+        q.zmin = (double*)take(sizeof(double) * n_rhs);
+        q.zmax = (double*)take(sizeof(double) * n_rhs);
+        q.work = (double2*)take(sizeof(double2) * nk::inner_work_elems(q.k) * n_rhs);
+        q.ipiv = (int*)take(sizeof(int) * (size_t)q.k * n_rhs);
+        q.Vl = (double2*)take(sizeof(double2) * (size_t)q.ell * q.k * n_rhs);
+        q.al = (double2*)take(sizeof(double2) * (size_t)q.ell * n_rhs);
+        q.bl = (double2*)take(sizeof(double2) * (size_t)q.ell * n_rhs);
+        q.gl = (double2*)take(sizeof(double2) * (size_t)q.ell * n_rhs);
+        q.S = (double2*)take(sizeof(double2) * (size_t)q.ell * q.ell * n_rhs);
+        q.s = (double2*)take(sizeof(double2) * (size_t)q.ell * n_rhs);
+        q.rhi_iters = (int*)take(sizeof(int) * n_rhs);
+        kl = q.ell;
+    }
     // the inner part stays FP64 in every schedule: with a Ritz value of H_k'
     // near the imaginary axis its sign is ill conditioned, and two-float
     // arithmetic there left single sources of the 16^3 x 32 test at 2.5e-8
@@ -393,6 +442,43 @@ Schedule schedule_of(const nk_ctx* c, unsigned flags, int k) {
     return s;
 }
 
+// The inner part of App. C steps 3-6 from the first level `in1` (its H is
+// the outer H_k): with multi-level nesting (Sec. 4.5) each level below runs
+// steps 3-4 on the Ritz matrix of the level above (its own p by Eq. popt),
+// RHi runs on the deepest Ritz matrix, and c = V_l1 V_l2 ... s is lifted back
+// level by level into in1.c.  *iters: the RHi counts (of the deepest level).
+cudaError_t enqueue_inner_chain(const Layout& Lw, const nk::Inner& in1, Launcher& L, const int** iters = nullptr) {
+    cudaStream_t st = L.st;
+    nk::Inner lv[NK_MAX_LEVELS];
+    lv[0] = in1;
+    int n = 1;
+    for (int d = 0; d < Lw.n_deeper; ++d, ++n) {
+        nk::Inner q = Lw.deeper[d];
+        const nk::Inner& up = lv[n - 1];
+        q.n_rhs = up.n_rhs;
+        q.two_sided = up.two_sided;
+        q.status = up.status;
+        q.alpha = up.al;
+        q.beta = up.bl;
+        q.gamma = up.gl;
+        q.k = up.ell;
+        q.kstride = 0;
+        q.ell = std::min(Lw.deeper[d].ell, q.k);
+        q.p_fixed = 0.0;
+        q.p_shared = 0;
+        q.c = up.s;   // the lift of this level lands in the s of the level above
+        lv[n] = q;
+    }
+    for (int i = 0; i < n; ++i)
+        L.run(NK_CLASS_INNER, nk::inner_launches(lv[i]), [&] { nk::launch_inner_lanczos(lv[i], st); });
+    cudaError_t e = cudaSuccess;
+    L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(lv[n - 1], st); });
+    if (e != cudaSuccess) return e;
+    for (int i = n - 1; i >= 1; --i) L.run(NK_CLASS_INNER, 1, [&] { nk::launch_inner_combine(lv[i], st); });
+    if (iters) *iters = lv[n - 1].rhi_iters;
+    return cudaSuccess;
+}
+
 // Enqueues a whole solve (device pointers in ABI layout). Returns cudaError_t of launches.
 cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_dev, int n_rhs,
                           double p, unsigned flags, bool overlap, Launcher& L) {
@@ -410,9 +496,7 @@ cudaError_t enqueue_solve(nk_ctx* c, Layout& Lw, const double* b_dev, double* y_
     L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_fill_int(Lw.kused, n_rhs, o.k, st); });
     enqueue_outer(c, o, sch, L);
     record_phase(c->ph[0], st);   // the outer basis is complete
-    L.run(NK_CLASS_INNER, nk::inner_launches(in), [&] { nk::launch_inner_lanczos(in, st); });
-    cudaError_t e = cudaSuccess;
-    L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(in, st); });
+    cudaError_t e = enqueue_inner_chain(Lw, in, L);
     if (e != cudaSuccess) return e;
     record_phase(c->ph[1], st);   // the inner part is complete
     L.run(NK_CLASS_LIFT, 2, [&] {
@@ -470,9 +554,7 @@ cudaError_t solve_adaptive(nk_ctx* c, Layout& Lw, const double* b_dev, double* y
         nk::Inner ic = in;
         ic.k = kc;
         ic.ell = std::min(ell, kc);
-        L.run(NK_CLASS_INNER, nk::inner_launches(ic), [&] { nk::launch_inner_lanczos(ic, st); });
-        cudaError_t e = cudaSuccess;
-        L.run(NK_CLASS_RHI, 1, [&] { e = (cudaError_t)nk::launch_rhi(ic, st); });
+        cudaError_t e = enqueue_inner_chain(Lw, ic, L);
         if (e != cudaSuccess) return e;
         L.run(NK_CLASS_LIFT, 1, [&] { nk::launch_inner_combine(ic, st); });
         L.run(NK_CLASS_OTHER, 1, [&] { nk::launch_adapt_delta(o, in.c, Lw.c_prev, kc, Lw.dn, st); });
@@ -631,10 +713,10 @@ int solve_core(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double
     const bool ts = c->mu != 0.0;
     const nk_launch lc = launch_cfg(c, n_rhs, ts, (flags & NK_MIXED) != 0);
     const bool mixed = (flags & NK_MIXED) != 0;
-    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed);
+    Layout dry = carve(nullptr, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed, c->nest);
     rc = ensure(c, c->ws, dry.total);
     if (rc) return rc;
-    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed);
+    Layout Lw = carve((char*)c->ws.p, geom_of(c), n_rhs, k, ell, ts, dp, lc, mixed, c->nest);
     // counters must start at zero; status is (re)set by the norm kernel
     NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned) * n_rhs, st));
 
@@ -655,7 +737,8 @@ int solve_core(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double
                                        notconv, checks, tph);
         if (e != cudaSuccess) return cuda_fail(c, e, "adaptive solve");
     } else if (use_graph) {
-        GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, c->j1, flags, p, c->mu, c->m_w, overlap ? 1 : 0};
+        GraphKey key{b_dev, y_dev, n_rhs, k, ell, c->j0, c->j1, flags, p, c->mu, c->m_w, overlap ? 1 : 0,
+                     c->nest.code()};
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             if (c->graphs.size() >= kMaxGraphs) clear_graph_cache(c);
@@ -695,7 +778,7 @@ int solve_core(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double
         P.ell = ell;
         P.launches = L.launches;
         P.status = Lw.o.status;
-        P.iters = Lw.in.rhi_iters;
+        P.iters = Lw.n_deeper ? Lw.deeper[Lw.n_deeper - 1].rhi_iters : Lw.in.rhi_iters;
         P.p = Lw.in.p;
         P.zmin = Lw.in.zmin;
         P.zmax = Lw.in.zmax;
@@ -706,7 +789,8 @@ int solve_core(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double
     std::vector<int> status(n_rhs), iters(n_rhs);
     std::vector<double> pv(n_rhs), zmin(n_rhs), zmax(n_rhs), xn(n_rhs);
     NK_CUDA(c, cudaMemcpyAsync(status.data(), Lw.o.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st));
-    NK_CUDA(c, cudaMemcpyAsync(iters.data(), Lw.in.rhi_iters, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st));
+    const int* iters_dev = Lw.n_deeper ? Lw.deeper[Lw.n_deeper - 1].rhi_iters : Lw.in.rhi_iters;
+    NK_CUDA(c, cudaMemcpyAsync(iters.data(), iters_dev, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost, st));
     NK_CUDA(c, cudaMemcpyAsync(pv.data(), Lw.in.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
     NK_CUDA(c, cudaMemcpyAsync(zmin.data(), Lw.in.zmin, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
     NK_CUDA(c, cudaMemcpyAsync(zmax.data(), Lw.in.zmax, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost, st));
@@ -739,8 +823,75 @@ int solve_core(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double
     return rc;
 }
 
-// NK_EPS_EST: the error estimate of Sec. 3 for every RHS of a finished solve:
-// x~ = approx(y) with y = approx(x) already in y_dev, eps = |x~ - x| / (2|x|).
+// NK_PREDICT: predict (k, l) from source 0 (nk_predict_sizes), then the
+// adaptive solve from the predicted start, repeated once with the caller's l
+// if the tolerance is not met with the predicted one.
+int predicted_solve(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p, unsigned flags,
+                    double* y_dev, nk_stats* S, cudaStream_t st, bool overlap) {
+    if (!(flags & NK_PREDICT)) return solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags, y_dev, S, st, overlap);
+    if (!(tol > 0.0)) return fail(c, NK_EINVAL, "NK_PREDICT needs adaptive k (tol > 0)");
+    if (!c->predictor) return fail(c, NK_ESTATE, "NK_PREDICT: no predictor (nk_set_predictor)");
+    int rc = check_solve_args(c, n_rhs, k, ell, tol);
+    if (rc) return rc;
+    int kp = 0, lp = 0;
+    rc = nk_predict_sizes(c, c->predictor, b_dev, k, &kp, &lp, (void*)st);
+    if (rc) return rc;
+    // l too small never passes the test: a margin of 1.5 (the inner part
+    // costs O(k l), little against a repeated solve)
+    int l_use = 2 * (int)std::ceil(0.75 * lp);
+    l_use = std::max(2, std::min(std::min(l_use, kp), std::min(256, k)));
+    l_use -= l_use & 1;
+    const unsigned f = flags & ~NK_PREDICT;
+    const int saved = c->adapt_start;
+    c->adapt_start = std::max(64, kp - 2 * NK_ADAPT_STEP);
+    rc = solve_core(c, b_dev, n_rhs, k, l_use, tol, p, f, y_dev, S, st, overlap);
+    c->adapt_start = saved;
+    int fallback = 0;
+    if (rc == NK_ENOTCONV && l_use < ell) {
+        const double t_first = S->t_total_ms;
+        rc = solve_core(c, b_dev, n_rhs, k, ell, tol, p, f, y_dev, S, st, overlap);
+        S->t_total_ms += t_first;
+        fallback = 1;
+    }
+    S->k_pred = kp;
+    S->ell_pred = lp;
+    S->predict_fallback = fallback;
+    return rc;
+}
+
+bool solve_failed_hard(int rc) { return rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI && rc != NK_ENOTCONV; }
+
+// LR deflation (App. C steps 1 and 6) around a solve: the Krylov part runs on
+// x_minus = b - sum_i <l_i, b> r_i, and sum_i sgn(lambda_i) <l_i, b> r_i is
+// added to its result; D_ov then applies b + gamma5 y to the whole of it.
+int deflated_solve(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p, unsigned flags,
+                   double* y_dev, nk_stats* S, cudaStream_t st, bool overlap) {
+    const int m = c->defl_m;
+    if (m == 0) return predicted_solve(c, b_dev, n_rhs, k, ell, tol, p, flags, y_dev, S, st, overlap);
+    int rc = check_solve_args(c, n_rhs, k, ell, tol);
+    if (rc) return rc;
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const size_t vb = align_up(sizeof(double2) * (size_t)c->N * n_rhs);
+    rc = ensure(c, c->defl_buf, vb + sizeof(double2) * (size_t)m * NK_MAX_RHS);
+    if (rc) return rc;
+    double2* xm = (double2*)c->defl_buf.p;
+    double2* d = (double2*)((char*)c->defl_buf.p + vb);
+    nk::launch_defl_dots(c->defl_L, (const double2*)b_dev, c->N, m, n_rhs, d, st);
+    nk::launch_defl_axpy((const double2*)b_dev, xm, c->defl_R, d, c->defl_neg, c->N, m, n_rhs, st);
+    NK_CUDA(c, cudaGetLastError());
+    rc = predicted_solve(c, (const double*)xm, n_rhs, k, ell, tol, p, flags, y_dev, S, st, false);
+    if (solve_failed_hard(rc)) return rc;
+    nk::launch_defl_axpy((const double2*)y_dev, (double2*)y_dev, c->defl_R, d, c->defl_sgn, c->N, m, n_rhs, st);
+    if (overlap) nk::launch_overlap_finish((const double2*)b_dev, (double2*)y_dev, c->N, n_rhs, st);
+    NK_CUDA(c, cudaGetLastError());
+    if (!(flags & NK_ASYNC)) NK_CUDA(c, cudaStreamSynchronize(st));
+    S->defl_m = m;
+    S->defl_gap = c->defl_gap;
+    return rc;
+}
+
+// NK_EPS_EST: the error estimate of Sec. 3 for every RHS: x~ = approx(y) with
+// y = approx(x), eps = |x~ - x| / (2|x|).
 int eps_estimate(nk_ctx* c, const double* b_dev, const double* y_dev, int n_rhs, int k, int ell, double tol,
                  double p, unsigned flags, cudaStream_t st, nk_stats* stats) {
     const size_t vb = align_up(sizeof(double2) * (size_t)c->N * n_rhs);
@@ -749,9 +900,10 @@ int eps_estimate(nk_ctx* c, const double* b_dev, const double* y_dev, int n_rhs,
     double2* x2 = (double2*)c->eps_buf.p;
     double2* sums = (double2*)((char*)c->eps_buf.p + vb);
     nk_stats s2;
-    rc = solve_core(c, y_dev, n_rhs, k, ell, tol, p, flags & ~(NK_EPS_EST | NK_PREDICT | NK_ASYNC), (double*)x2, &s2,
-                    st, false);
-    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI && rc != NK_ENOTCONV) return rc;
+    std::memset(&s2, 0, sizeof(s2));
+    rc = deflated_solve(c, y_dev, n_rhs, k, ell, tol, p, flags & ~(NK_EPS_EST | NK_PREDICT | NK_ASYNC), (double*)x2,
+                        &s2, st, false);
+    if (solve_failed_hard(rc)) return rc;
     nk::launch_eps_sums((const double2*)b_dev, x2, n_rhs, c->N, sums, st);
     NK_CUDA(c, cudaGetLastError());
     std::vector<double2> h(n_rhs);
@@ -763,8 +915,8 @@ int eps_estimate(nk_ctx* c, const double* b_dev, const double* y_dev, int n_rhs,
     return NK_OK;
 }
 
-// A solve with the optional prediction of (k, l) (NK_PREDICT) before it and
-// the optional error estimate (NK_EPS_EST) after it.
+// A solve: optional prediction of (k, l) (NK_PREDICT), optional LR
+// deflation (nk_set_deflation), optional error estimate afterwards (NK_EPS_EST).
 int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double tol, double p,
               unsigned flags, double* y_dev, nk_stats* stats, cudaStream_t st, bool overlap) {
     if (!c) return NK_EINVAL;
@@ -772,41 +924,13 @@ int solve_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, int ell, double 
     const bool eps = (flags & NK_EPS_EST) != 0;
     if ((predict || eps) && (flags & NK_ASYNC)) return fail(c, NK_EINVAL, "NK_PREDICT / NK_EPS_EST need a blocking solve");
     if (eps && overlap) return fail(c, NK_EINVAL, "NK_EPS_EST applies to the sign function, not to D_ov");
-    if (!predict && !eps) return solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags, y_dev, stats, st, overlap);
+    if (!predict && !eps && c->defl_m == 0)
+        return solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags, y_dev, stats, st, overlap);
     nk_stats local;
     nk_stats* S = stats ? stats : &local;
-    int rc;
-    int kp = 0, lp = 0, fallback = 0;
-    if (predict) {
-        if (!(tol > 0.0)) return fail(c, NK_EINVAL, "NK_PREDICT needs adaptive k (tol > 0)");
-        if (!c->predictor) return fail(c, NK_ESTATE, "NK_PREDICT: no predictor (nk_set_predictor)");
-        rc = check_solve_args(c, n_rhs, k, ell, tol);
-        if (rc) return rc;
-        rc = nk_predict_sizes(c, c->predictor, b_dev, k, &kp, &lp, (void*)st);
-        if (rc) return rc;
-        // l too small never passes the test: a margin of 1.5 (the inner part
-        // costs O(k l), little against a repeated solve)
-        int l_use = 2 * (int)std::ceil(0.75 * lp);
-        l_use = std::max(2, std::min(std::min(l_use, kp), std::min(256, k)));
-        l_use -= l_use & 1;
-        const int saved = c->adapt_start;
-        c->adapt_start = std::max(64, kp - 2 * NK_ADAPT_STEP);
-        rc = solve_core(c, b_dev, n_rhs, k, l_use, tol, p, flags & ~(NK_PREDICT | NK_EPS_EST), y_dev, S, st, overlap);
-        c->adapt_start = saved;
-        if (rc == NK_ENOTCONV && l_use < ell) {
-            const double t_first = S->t_total_ms;
-            rc = solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags & ~(NK_PREDICT | NK_EPS_EST), y_dev, S, st,
-                            overlap);
-            S->t_total_ms += t_first;
-            fallback = 1;
-        }
-    } else {
-        rc = solve_core(c, b_dev, n_rhs, k, ell, tol, p, flags & ~NK_EPS_EST, y_dev, S, st, overlap);
-    }
-    if (rc != NK_OK && rc != NK_EBREAKDOWN && rc != NK_ERHI && rc != NK_ENOTCONV) return rc;
-    S->k_pred = kp;
-    S->ell_pred = lp;
-    S->predict_fallback = fallback;
+    std::memset(S, 0, sizeof(*S));
+    int rc = deflated_solve(c, b_dev, n_rhs, k, ell, tol, p, flags & ~NK_EPS_EST, y_dev, S, st, overlap);
+    if (solve_failed_hard(rc)) return rc;
     if (eps) {
         // the second application uses the sizes the first one ended with
         const int l2 = S->ell_used > 0 ? S->ell_used : ell;
@@ -908,6 +1032,174 @@ int nk_set_precision(nk_ctx* c, int j0) {
 int nk_set_df_recurrence(nk_ctx* c, int j1) {
     if (!c) return NK_EINVAL;
     c->j1 = j1;
+    return NK_OK;
+}
+
+// M v = D_ov(mu) v + m v (dagger = 0) or M^dagger v = gamma5 D_ov(-mu) gamma5 v + m v
+// (dagger = 1; D_ov(mu)^dagger = gamma5 D_ov(-mu) gamma5 because
+// A(mu)^dagger = A(-mu)), v and out device ABI vectors; tmp scratch.  For -mu
+// the deflated eigenpairs of A(mu) serve A(-mu) = A(mu)^dagger with the roles
+// of the right and left eigenvectors exchanged (the signs sgn(Re lambda) are
+// those of conj(lambda)).
+static int overlap_op(nk_ctx* c, const double2* v, double2* out, double2* tmp, int n_rhs, int k, int ell, double tol,
+                      unsigned flags, double mass, bool dagger, cudaStream_t st, int* applications) {
+    int rc;
+    const unsigned f = flags & ~(NK_ASYNC | NK_EPS_EST);
+    if (!dagger) {
+        rc = solve_dev(c, (const double*)v, n_rhs, k, ell, tol, 0.0, f, (double*)out, nullptr, st, true);
+    } else {
+        NK_CUDA(c, cudaMemcpyAsync(tmp, v, sizeof(double2) * (size_t)c->N * n_rhs, cudaMemcpyDeviceToDevice, st));
+        nk::launch_gamma5(tmp, c->N, n_rhs, st);
+        c->mu = -c->mu;
+        std::swap(c->defl_R, c->defl_L);
+        rc = solve_dev(c, (const double*)tmp, n_rhs, k, ell, tol, 0.0, f, (double*)out, nullptr, st, true);
+        std::swap(c->defl_R, c->defl_L);
+        c->mu = -c->mu;
+        nk::launch_gamma5(out, c->N, n_rhs, st);
+    }
+    ++*applications;
+    if (rc != NK_OK && rc != NK_ENOTCONV) return rc;
+    nk::VecCoefs cm, one;
+    for (int r = 0; r < 12; ++r) {
+        cm.c[r] = make_double2(mass, 0.0);
+        one.c[r] = make_double2(1.0, 0.0);
+    }
+    nk::launch_vlincomb(out, v, c->N, n_rhs, cm, one, st);   // out += m v
+    NK_CUDA(c, cudaGetLastError());
+    return NK_OK;
+}
+
+static int vdots(nk_ctx* c, const double2* a, const double2* b, int n, double2* dev, std::vector<double2>& h,
+                 cudaStream_t st) {
+    nk::launch_vdot(a, b, c->N, n, dev, st);
+    NK_CUDA(c, cudaMemcpyAsync(h.data(), dev, sizeof(double2) * n, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(c, cudaStreamSynchronize(st));
+    return NK_OK;
+}
+
+int nk_overlap_solve(nk_ctx* c, const double* b, int n_rhs, int k, int ell, double tol_sign, unsigned flags,
+                     double mass, double tol_cg, int maxit, double* x, int* iters, double* resid) {
+    if (!c || !b || !x) return c ? fail(c, NK_EINVAL, "null pointer") : NK_EINVAL;
+    int rc = check_solve_args(c, n_rhs, k, ell, tol_sign);
+    if (rc) return rc;
+    if (!(mass >= 0.0) || !(tol_cg > 0.0) || maxit < 1) return fail(c, NK_EINVAL, "need mass >= 0, tol_cg > 0, maxit >= 1");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    const size_t vb = align_up(sizeof(double2) * (size_t)c->N * n_rhs);
+    rc = ensure(c, c->cg_buf, 8 * vb);
+    if (rc) return rc;
+    char* base = (char*)c->cg_buf.p;
+    double2 *bd = (double2*)base, *xd = (double2*)(base + vb), *r = (double2*)(base + 2 * vb),
+            *p = (double2*)(base + 3 * vb), *q = (double2*)(base + 4 * vb), *s = (double2*)(base + 5 * vb),
+            *tmp = (double2*)(base + 6 * vb), *dots = (double2*)(base + 7 * vb);
+    cudaStream_t st = 0;
+    const size_t bytes = sizeof(double2) * (size_t)c->N * n_rhs;
+    NK_CUDA(c, cudaMemcpy(bd, b, bytes, cudaMemcpyHostToDevice));
+    NK_CUDA(c, cudaMemsetAsync(xd, 0, bytes, st));
+    int apps = 0;
+    // r = M^dagger b, p = r
+    rc = overlap_op(c, bd, r, tmp, n_rhs, k, ell, tol_sign, flags, mass, true, st, &apps);
+    if (rc) return rc;
+    NK_CUDA(c, cudaMemcpyAsync(p, r, bytes, cudaMemcpyDeviceToDevice, st));
+    std::vector<double2> h(n_rhs);
+    if ((rc = vdots(c, r, r, n_rhs, dots, h, st))) return rc;
+    std::vector<double> rr(n_rhs), rr0(n_rhs);
+    std::vector<int> done(n_rhs, 0), its(n_rhs, 0);
+    for (int i = 0; i < n_rhs; ++i) {
+        rr[i] = rr0[i] = h[i].x;
+        done[i] = !(rr0[i] > 0.0);   // b = 0: x = 0
+    }
+    int it = 0;
+    for (; it < maxit; ++it) {
+        bool all = true;
+        for (int i = 0; i < n_rhs; ++i) all = all && done[i];
+        if (all) break;
+        // q = M p, alpha = |r|^2 / |q|^2
+        if ((rc = overlap_op(c, p, q, tmp, n_rhs, k, ell, tol_sign, flags, mass, false, st, &apps))) return rc;
+        if ((rc = vdots(c, q, q, n_rhs, dots, h, st))) return rc;
+        nk::VecCoefs ca, cb, na;
+        for (int i = 0; i < 12; ++i) ca.c[i] = cb.c[i] = na.c[i] = make_double2(i < n_rhs ? 0.0 : 0.0, 0.0);
+        for (int i = 0; i < n_rhs; ++i) {
+            const double al = done[i] || !(h[i].x > 0.0) ? 0.0 : rr[i] / h[i].x;
+            ca.c[i] = make_double2(al, 0.0);
+            na.c[i] = make_double2(-al, 0.0);
+            cb.c[i] = make_double2(1.0, 0.0);
+        }
+        nk::launch_vlincomb(xd, p, c->N, n_rhs, ca, cb, st);          // x += alpha p
+        if ((rc = overlap_op(c, q, s, tmp, n_rhs, k, ell, tol_sign, flags, mass, true, st, &apps))) return rc;
+        nk::launch_vlincomb(r, s, c->N, n_rhs, na, cb, st);           // r -= alpha M^dagger q
+        if ((rc = vdots(c, r, r, n_rhs, dots, h, st))) return rc;
+        nk::VecCoefs one, be;
+        for (int i = 0; i < 12; ++i) one.c[i] = be.c[i] = make_double2(i < n_rhs ? 1.0 : 0.0, 0.0);
+        for (int i = 0; i < n_rhs; ++i) {
+            if (done[i]) { be.c[i] = make_double2(1.0, 0.0); continue; }
+            const double rn = h[i].x;
+            be.c[i] = make_double2(rr[i] > 0.0 ? rn / rr[i] : 0.0, 0.0);
+            rr[i] = rn;
+            its[i] = it + 1;
+            if (std::sqrt(rn / rr0[i]) <= tol_cg) done[i] = 1;
+        }
+        nk::launch_vlincomb(p, r, c->N, n_rhs, one, be, st);          // p = r + beta p
+        NK_CUDA(c, cudaGetLastError());
+    }
+    NK_CUDA(c, cudaMemcpy(x, xd, bytes, cudaMemcpyDeviceToHost));
+    bool all = true;
+    for (int i = 0; i < n_rhs; ++i) {
+        if (iters) iters[i] = its[i];
+        if (resid) resid[i] = rr0[i] > 0.0 ? std::sqrt(rr[i] / rr0[i]) : 0.0;
+        all = all && done[i];
+    }
+    if (!all) return fail(c, NK_ENOTCONV, "overlap CG: tolerance not met within maxit iterations");
+    return NK_OK;
+}
+
+int nk_set_deflation(nk_ctx* c, int m, const double* lambda, const double* R, const double* L) {
+    if (!c) return NK_EINVAL;
+    if (m < 0 || m > NK_MAX_DEFL || (m > 0 && (!lambda || !R)))
+        return fail(c, NK_EINVAL, "need 0 <= m <= NK_MAX_DEFL, eigenvalues and right eigenvectors");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    if (c->defl_L && c->defl_L != c->defl_R) cudaFree(c->defl_L);
+    if (c->defl_R) cudaFree(c->defl_R);
+    if (c->defl_neg) cudaFree(c->defl_neg);
+    if (c->defl_sgn) cudaFree(c->defl_sgn);
+    c->defl_R = c->defl_L = nullptr;
+    c->defl_neg = c->defl_sgn = nullptr;
+    c->defl_m = 0;
+    c->defl_gap = 0.0;
+    if (m == 0) return NK_OK;
+    const size_t bytes = sizeof(double2) * (size_t)m * c->N;
+    NK_CUDA(c, cudaMalloc(&c->defl_R, bytes));
+    NK_CUDA(c, cudaMemcpy(c->defl_R, R, bytes, cudaMemcpyHostToDevice));
+    if (L) {
+        NK_CUDA(c, cudaMalloc(&c->defl_L, bytes));
+        NK_CUDA(c, cudaMemcpy(c->defl_L, L, bytes, cudaMemcpyHostToDevice));
+    } else {
+        c->defl_L = c->defl_R;
+    }
+    std::vector<double> neg(m, -1.0), sg(m);
+    double gap = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const double re = lambda[2 * i], im = lambda[2 * i + 1];
+        sg[i] = re > 0.0 ? 1.0 : (re < 0.0 ? -1.0 : 0.0);   // sgn(Re lambda), Eq. sgnz
+        gap = std::max(gap, std::hypot(re, im));
+    }
+    NK_CUDA(c, cudaMalloc(&c->defl_neg, sizeof(double) * m));
+    NK_CUDA(c, cudaMalloc(&c->defl_sgn, sizeof(double) * m));
+    NK_CUDA(c, cudaMemcpy(c->defl_neg, neg.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    NK_CUDA(c, cudaMemcpy(c->defl_sgn, sg.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    c->defl_m = m;
+    c->defl_gap = gap;
+    return NK_OK;
+}
+
+int nk_set_nesting(nk_ctx* c, int n_deeper, const int* ells) {
+    if (!c) return NK_EINVAL;
+    if (n_deeper < 0 || n_deeper > NK_MAX_LEVELS - 1 || (n_deeper > 0 && !ells))
+        return fail(c, NK_EINVAL, "n_deeper must be in [0, NK_MAX_LEVELS - 1] with its sizes");
+    for (int i = 0; i < n_deeper; ++i)
+        if (ells[i] < 2 || (ells[i] & 1) || (i > 0 && ells[i] > ells[i - 1]))
+            return fail(c, NK_EINVAL, "level sizes must be even, >= 2 and non-increasing");
+    c->nest.n = n_deeper;
+    for (int i = 0; i < NK_MAX_LEVELS - 1; ++i) c->nest.ell[i] = i < n_deeper ? ells[i] : 0;
     return NK_OK;
 }
 
@@ -1302,10 +1594,10 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     one.early_order = 0;
     one.stencil_split = 1;
     one.early_split = 1;
-    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one, false);
+    Layout dry = carve(nullptr, tiny, n_rhs, k, ell, ts, true, one, false, c->nest);
     int rc = ensure(c, c->inner_tmp, std::max(dry.total, c->inner_tmp.bytes));
     if (rc) return rc;
-    Layout Lw = carve((char*)c->inner_tmp.p, tiny, n_rhs, k, ell, ts, true, one, false);
+    Layout Lw = carve((char*)c->inner_tmp.p, tiny, n_rhs, k, ell, ts, true, one, false, c->nest);
     const size_t cb = sizeof(double2) * (size_t)k * n_rhs;
     NK_CUDA(c, cudaMemcpy(Lw.o.alpha, alpha, cb, cudaMemcpyHostToDevice));
     NK_CUDA(c, cudaMemcpy(Lw.o.beta, beta, cb, cudaMemcpyHostToDevice));
@@ -1314,8 +1606,10 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     nk::Inner in = Lw.in;
     in.p_fixed = p > 0.0 ? p : 0.0;
     in.p_shared = p < 0.0 ? 1 : 0;
-    nk::launch_inner_lanczos(in, 0);
-    cudaError_t e = (cudaError_t)nk::launch_rhi(in, 0);
+    Launcher L;
+    L.st = 0;
+    const int* iters_dev = in.rhi_iters;
+    cudaError_t e = enqueue_inner_chain(Lw, in, L, &iters_dev);
     if (e != cudaSuccess) return cuda_fail(c, e, "launch_rhi");
     nk::launch_inner_combine(in, 0);
     NK_CUDA(c, cudaGetLastError());
@@ -1324,7 +1618,7 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
     std::vector<int> status(n_rhs), iters(n_rhs);
     std::vector<double> pv(n_rhs), zmin(n_rhs), zmax(n_rhs);
     NK_CUDA(c, cudaMemcpy(status.data(), in.status, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost));
-    NK_CUDA(c, cudaMemcpy(iters.data(), in.rhi_iters, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(iters.data(), iters_dev, sizeof(int) * n_rhs, cudaMemcpyDeviceToHost));
     NK_CUDA(c, cudaMemcpy(pv.data(), in.p, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
     NK_CUDA(c, cudaMemcpy(zmin.data(), in.zmin, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
     NK_CUDA(c, cudaMemcpy(zmax.data(), in.zmax, sizeof(double) * n_rhs, cudaMemcpyDeviceToHost));
@@ -1500,6 +1794,12 @@ void nk_destroy(nk_ctx* c) {
     if (c->links_tmp.p) cudaFree(c->links_tmp.p);
     if (c->inner_tmp.p) cudaFree(c->inner_tmp.p);
     if (c->eps_buf.p) cudaFree(c->eps_buf.p);
+    if (c->defl_buf.p) cudaFree(c->defl_buf.p);
+    if (c->cg_buf.p) cudaFree(c->cg_buf.p);
+    if (c->defl_L && c->defl_L != c->defl_R) cudaFree(c->defl_L);
+    if (c->defl_R) cudaFree(c->defl_R);
+    if (c->defl_neg) cudaFree(c->defl_neg);
+    if (c->defl_sgn) cudaFree(c->defl_sgn);
     for (auto& e : c->ph)
         if (e) cudaEventDestroy(e);
     if (c->U64) cudaFree(c->U64);

@@ -187,6 +187,21 @@ void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y
 void launch_fill_int(int* p, int n, int value, cudaStream_t st);
 // Adaptive k: per RHS (|c - c_prev|, |c|) over the first k entries, then c_prev <- c.
 void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st);
+// LR deflation (deflate.cu), ABI-layout vectors of N complex: d[r m + i] = <l_i, b_r>;
+// out_r = base_r + sum_i w_i d[r m + i] R_i (out may alias base); y_r = b_r + gamma5 y_r
+void launch_defl_dots(const double2* L, const double2* b, long N, int m, int n_rhs, double2* d, cudaStream_t st);
+void launch_defl_axpy(const double2* base, double2* out, const double2* R, const double2* d, const double* w, long N,
+                      int m, int n_rhs, cudaStream_t st);
+void launch_overlap_finish(const double2* b, double2* y, long N, int n, cudaStream_t st);
+// Overlap inversion (overlap.cu), ABI-layout vectors, n <= 12 RHS:
+// out[r] = <a_r, b_r>; y_r = ca_r x_r + cb_r y_r; v_r <- gamma5 v_r
+struct VecCoefs {
+    double2 c[12];
+};
+void launch_vdot(const double2* a, const double2* b, long N, int n, double2* out, cudaStream_t st);
+void launch_vlincomb(double2* y, const double2* x, long N, int n, const VecCoefs& ca, const VecCoefs& cb,
+                     cudaStream_t st);
+void launch_gamma5(double2* v, long N, int n, cudaStream_t st);
 // NK_EPS_EST: per RHS (|x2 - b|^2, |b|^2) of n vectors of N complex (any common layout)
 void launch_eps_sums(const double2* b, const double2* x2, int n, long N, double2* out, cudaStream_t st);
 

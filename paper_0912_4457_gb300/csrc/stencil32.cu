@@ -40,19 +40,19 @@ namespace nk {
 
 namespace {
 
-// Shared memory of a CTA of sb sites and nth threads: links (8 hops x 5
-// float4 per site), neighbour site and boundary sign per hop, then two
-// per-thread slots of a neighbour spinor (6 float4 each) for the prefetch of
-// the next hop.
+// Shared memory of a CTA of sb sites: links (8 hops x 5 float4 per site),
+// neighbour site and boundary sign per hop.  (A variant that also prefetched
+// each thread's next neighbour spinor into shared memory with cp.async was
+// slower: the spinors then cross the L1/shared-memory datapath twice, which
+// ran at 92% of its throughput, and lost their L1 hits.)
 __host__ __device__ constexpr size_t s32_smem(int sb, int nth) {
-    return (size_t)sb * (8 * 5 * 16 + 8 * 4 + 8 * 4) + (size_t)nth * 2 * 6 * 16;
+    return (void)nth, (size_t)sb * (8 * 5 * 16 + 8 * 4 + 8 * 4);
 }
 
 struct S32Smem {
     float4* lk;   // [(h * 5 + q) * SB + s]
     int* nb;      // [h * SB + s]
     float* fl;    // [h * SB + s]: -1 across the antiperiodic t boundary, else 1
-    float4* sp;   // [(slot * 6 + i) * nth + tid]: this thread's prefetched spinors
 };
 
 __device__ __forceinline__ S32Smem s32_carve(char* sm, int sb) {
@@ -60,44 +60,23 @@ __device__ __forceinline__ S32Smem s32_carve(char* sm, int sb) {
     r.lk = reinterpret_cast<float4*>(sm);
     r.nb = reinterpret_cast<int*>(sm + (size_t)sb * 8 * 5 * 16);
     r.fl = reinterpret_cast<float*>(sm + (size_t)sb * (8 * 5 * 16 + 8 * 4));
-    r.sp = reinterpret_cast<float4*>(sm + (size_t)sb * (8 * 5 * 16 + 8 * 4 + 8 * 4));
     return r;
 }
 
-// Asynchronous global -> shared copies (cp.async, cached in L1 as well): the
-// copies of one thread are grouped, and wait_group N returns once at most N of
-// that thread's groups are still in flight.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
+// Asynchronous global -> shared copies (cp.async) for the link staging: the
+// copies of one thread form a group, and wait_group 0 returns once they have
+// all landed.
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__device__ __forceinline__ int s32_tid() { return threadIdx.x + blockDim.x * threadIdx.y; }
-__device__ __forceinline__ int s32_nth() { return blockDim.x * blockDim.y; }
-
-// Issue the copies of the spinor at site s of vector `in` into this thread's
-// slot, as one group.
-__device__ __forceinline__ void s32_prefetch(const float4* __restrict__ in, int V, int s, const S32Smem& S,
-                                             int slot) {
-    const int tid = s32_tid(), nth = s32_nth();
-#pragma unroll
-    for (int i = 0; i < 6; ++i) cp_async16(S.sp + (size_t)(slot * 6 + i) * nth + tid, in + (size_t)i * V + s);
-    cp_async_commit();
-}
-
-__device__ __forceinline__ void s32_take(const S32Smem& S, int slot, float2 p[4][3]) {
-    const int tid = s32_tid(), nth = s32_nth();
+__device__ __forceinline__ void load_spinor32(const float4* __restrict__ in, int V, int s, float2 p[4][3]) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const float4 v = S.sp[(size_t)(slot * 6 + i) * nth + tid];
+        const float4 v = __ldg(in + (size_t)i * V + s);
         const int c0 = 2 * i, c1 = 2 * i + 1;
         p[c0 / 3][c0 % 3] = make_float2(v.x, v.y);
         p[c1 / 3][c1 % 3] = make_float2(v.z, v.w);
@@ -106,7 +85,7 @@ __device__ __forceinline__ void s32_take(const S32Smem& S, int slot, float2 p[4]
 
 // Neighbour indices and boundary signs of the CTA's sites (hop h: nu = h / 2,
 // odd h forward), then the asynchronous copies of their links into shared
-// memory as one group (not waited for here).  Sites past V (the last block)
+// memory as one group (waited for by s32_stage_end).  Sites past V (the last block)
 // use site V - 1 and are skipped later.
 __device__ __forceinline__ void s32_stage_begin(const float2* __restrict__ U, const Geom& g, int site0,
                                                 const S32Smem& S) {
@@ -141,20 +120,22 @@ __device__ __forceinline__ void s32_stage_begin(const float2* __restrict__ U, co
     cp_async_commit();
 }
 
-// After s32_stage_begin and one more group (the first spinor prefetch): wait
-// for this thread's link copies, then for everyone's.
+// Wait for this thread's link copies, then for everyone's.
 __device__ __forceinline__ void s32_stage_end() {
-    cp_async_wait<1>();
+    cp_async_wait_all();
     __syncthreads();
 }
 
-// One hop with the neighbour spinor already in registers.
+// One hop: the neighbour spinor straight from global memory (L1 / L2), the
+// link from shared memory.
 template <int H>
-__device__ __forceinline__ void s32_hop(float2 acc[4][3], const float2 psi[4][3], const S32Smem& S, float wp_t,
-                                        float wm_t) {
+__device__ __forceinline__ void s32_hop(float2 acc[4][3], const float4* __restrict__ in, int V, const S32Smem& S,
+                                        float wp_t, float wm_t) {
     constexpr int NU = H >> 1;
     constexpr bool FWD = (H & 1) != 0;
     const int sb = blockDim.x, tx = threadIdx.x;
+    float2 psi[4][3];
+    load_spinor32(in, V, S.nb[H * sb + tx], psi);
     float2 u[3][3];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -167,45 +148,28 @@ __device__ __forceinline__ void s32_hop(float2 acc[4][3], const float2 psi[4][3]
     hop_regs<NU, FWD, float>(acc, psi, u, FWD ? -1.0f : 1.0f, w);
 }
 
-// Hop h of the software pipeline: wait for its spinor (the only group in
-// flight), move it to registers, start the copy of the next one (hop h + 1,
-// or the site's own spinor after the last hop) into the other slot, compute.
-template <int H>
-__device__ __forceinline__ void s32_step(float2 acc[4][3], const float4* __restrict__ in, int V, int site,
-                                         const S32Smem& S, float wp_t, float wm_t) {
-    cp_async_wait<0>();
-    float2 psi[4][3];
-    s32_take(S, H & 1, psi);
-    const int next = H < 7 ? S.nb[(H + 1) * blockDim.x + threadIdx.x] : site;
-    s32_prefetch(in, V, next, S, (H + 1) & 1);
-    s32_hop<H>(acc, psi, S, wp_t, wm_t);
-}
-
 // out = gamma5 (psi - kappa * sum of the eight hops) at this thread's site
 // (clamped to the lattice), for the vector `in`; side 1 (A^dagger) exchanges
-// the temporal weights.  hop0_issued: the copy of the first hop's spinor has
-// already been started (with the link staging).
+// the temporal weights.
 __device__ __forceinline__ void s32_site(const float4* __restrict__ in, int V, int site, const S32Smem& S, int side,
-                                         float kappa, float emu, float emu_inv, float2 out[4][3], bool hop0_issued) {
+                                         float kappa, float emu, float emu_inv, float2 out[4][3]) {
     const float wp_t = side ? emu_inv : emu;
     const float wm_t = side ? emu : emu_inv;
-    if (!hop0_issued) s32_prefetch(in, V, S.nb[threadIdx.x], S, 0);
     float2 acc[4][3];
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
         for (int a = 0; a < 3; ++a) acc[sp][a] = make_float2(0.f, 0.f);
-    s32_step<0>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<1>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<2>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<3>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<4>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<5>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<6>(acc, in, V, site, S, wp_t, wm_t);
-    s32_step<7>(acc, in, V, site, S, wp_t, wm_t);
-    cp_async_wait<0>();
+    s32_hop<0>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<1>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<2>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<3>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<4>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<5>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<6>(acc, in, V, S, wp_t, wm_t);
+    s32_hop<7>(acc, in, V, S, wp_t, wm_t);
     float2 p[4][3];
-    s32_take(S, 0, p);
+    load_spinor32(in, V, site, p);
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp) {
         const float sg = sp < 2 ? 1.0f : -1.0f;   // gamma5 = diag(1, 1, -1, -1)
@@ -228,14 +192,12 @@ __global__ void __launch_bounds__(384, 2) k_stencil32(const float2* __restrict__
         return (side ? s.in_d : s.in_a) + (size_t)(side ? v - s.n_a : v) * s.vstride;
     };
     s32_stage_begin(U, g, site0, S);
-    const int v0 = threadIdx.y;   // blockDim.y <= nv: every slot has a first vector
-    s32_prefetch(vec_in(v0), g.V, S.nb[threadIdx.x], S, 0);
     s32_stage_end();
-    for (int v = v0; v < nv; v += blockDim.y) {
+    for (int v = threadIdx.y; v < nv; v += blockDim.y) {
         const int side = v < s.n_a ? 0 : 1;
         const int vi = side ? v - s.n_a : v;
         float2 o[4][3];
-        s32_site(vec_in(v), g.V, site, S, side, kappa, emu, emu_inv, o, v == v0);
+        s32_site(vec_in(v), g.V, site, S, side, kappa, emu, emu_inv, o);
         if (site0 + (int)threadIdx.x >= g.V) continue;
         float4* out = (side ? s.out_d : s.out_a) + (size_t)vi * s.vstride;
 #pragma unroll
@@ -288,7 +250,6 @@ __global__ void __launch_bounds__(384, 2) k_stencil32_step1(const float2* __rest
         return (v < nrhs ? o.q32 + (size_t)v * 6 * V : o.p32 + (size_t)(v - nrhs) * 6 * V);
     };
     s32_stage_begin(U, g, site0, S);
-    s32_prefetch(vec_in(threadIdx.y), V, S.nb[threadIdx.x], S, 0);   // blockDim.y <= nv
     s32_stage_end();
     const int nblk = gridDim.x;
     const int tid = threadIdx.x + sb * threadIdx.y;   // linear: a warp may span two slots (sb = 16)
@@ -301,13 +262,12 @@ __global__ void __launch_bounds__(384, 2) k_stencil32_step1(const float2* __rest
         const int rhs = v < nv ? (side ? v - nrhs : v) : 0;
         const bool work = v < nv && o.status[rhs] == kStatusOK && !(side == 1 && j == o.k - 1);
         double2 acc = make_double2(0.0, 0.0);
-        if (base == 0 && !work) cp_async_wait<0>();   // the first prefetch is not used
         if (work) {
             const double2* sc = o.sc + (size_t)rhs * kScalars;
             const size_t hb = (size_t)rhs * o.k;
             const int jp = j > 0 ? j - 1 : j;
             float2 out[4][3];
-            s32_site(vec_in(v), V, site, S, side, kappa, emu, emu_inv, out, base == 0);
+            s32_site(vec_in(v), V, site, S, side, kappa, emu, emu_inv, out);
             if (live) {
             const double2 s0 = sc[side ? kScM : kScN];       // 1/n_j (1/m_j)
             const double2 c1 = sc[side ? kScC1L : kScC1];    // zero at j = 0

@@ -49,7 +49,7 @@ ERROR_NAMES = {
 
 EXPORTED = [
     "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision", "nk_set_df_recurrence",
-    "nk_set_adapt_start",
+    "nk_set_adapt_start", "nk_set_nesting", "nk_set_deflation", "nk_overlap_solve",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_stencil32_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
     "nk_destroy",
@@ -88,6 +88,8 @@ class NkStats(ctypes.Structure):
         ("k_pred", ctypes.c_int),
         ("ell_pred", ctypes.c_int),
         ("predict_fallback", ctypes.c_int),
+        ("defl_m", ctypes.c_int),
+        ("defl_gap", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -104,6 +106,7 @@ class NkStats(ctypes.Structure):
             "t_basis_ms": self.t_basis_ms, "t_inner_ms": self.t_inner_ms, "t_lift_ms": self.t_lift_ms,
             "eps_sgn2": list(self.eps_sgn2[:n]), "k_pred": self.k_pred, "ell_pred": self.ell_pred,
             "predict_fallback": bool(self.predict_fallback),
+            "defl_m": self.defl_m, "defl_gap": self.defl_gap,
         }
 
 
@@ -145,6 +148,9 @@ def load_library(path: str = LIB_PATH):
         "nk_set_precision": ([P, I], I),
         "nk_set_df_recurrence": ([P, I], I),
         "nk_set_adapt_start": ([P, I], I),
+        "nk_set_nesting": ([P, I, P], I),
+        "nk_set_deflation": ([P, I, P, P, P], I),
+        "nk_overlap_solve": ([P, P, I, I, I, ctypes.c_double, U, ctypes.c_double, ctypes.c_double, I, P, P, P], I),
         "nk_sign_apply": ([P, dp, I, I, I, D, D, U, dp, ctypes.POINTER(NkStats)], I),
         "nk_sign_apply_dev": ([P, P, I, I, I, D, D, U, P, ctypes.POINTER(NkStats), P], I),
         "nk_overlap_apply": ([P, dp, I, I, I, D, U, dp, ctypes.POINTER(NkStats)], I),
@@ -264,6 +270,45 @@ class Context:
 
     def set_adapt_start(self, k_first: int):
         self._check(self._lib.nk_set_adapt_start(self.h, int(k_first)))
+
+    def overlap_solve(self, b, k, ell, mass=0.0, tol_cg=1e-8, maxit=500, tol_sign=0.0, flags=NK_FP64, check=True):
+        """nk_overlap_solve: x = (D_ov + mass)^-1 b by CG on the normal
+        equations; returns (x, iterations, relative residuals, rc)."""
+        b = _host_c128(b)
+        if b.ndim == 1:
+            b = b[None, :]
+        n = b.shape[0]
+        x = np.zeros_like(b)
+        its = np.zeros(n, np.int32)
+        res = np.zeros(n)
+        rc = self._lib.nk_overlap_solve(self.h, _dptr(b.view(np.float64)), n, int(k), int(ell), float(tol_sign),
+                                        int(flags), float(mass), float(tol_cg), int(maxit),
+                                        _dptr(x.view(np.float64)), its.ctypes.data_as(ctypes.c_void_p), _dptr(res))
+        if check:
+            self._check(rc)
+        return x, its, res, rc
+
+    def set_deflation(self, lam=None, R=None, L=None):
+        """nk_set_deflation: eigenvalues lam (m,), right eigenvectors R (m, 12 V)
+        and left eigenvectors L (m, 12 V) with <l_i, r_j> = delta_ij, or None
+        (Hermitian: L = R); lam=None switches deflation off."""
+        if lam is None or len(lam) == 0:
+            self._check(self._lib.nk_set_deflation(self.h, 0, None, None, None))
+            return
+        lam = np.ascontiguousarray(lam, dtype=np.complex128)
+        R = np.ascontiguousarray(R, dtype=np.complex128).reshape(len(lam), self.N)
+        Lp = None
+        if L is not None:
+            L = np.ascontiguousarray(L, dtype=np.complex128).reshape(len(lam), self.N)
+            Lp = _dptr(L.view(np.float64))
+        self._check(self._lib.nk_set_deflation(self.h, len(lam), _dptr(lam.view(np.float64)),
+                                               _dptr(R.view(np.float64)), Lp))
+
+    def set_nesting(self, ells=()):
+        """nk_set_nesting: sizes l_2 >= l_3 >= ... of the levels below the first
+        (multi-level nesting, Sec. 4.5); () restores one level."""
+        arr = (ctypes.c_int * max(1, len(ells)))(*[int(v) for v in ells])
+        self._check(self._lib.nk_set_nesting(self.h, len(ells), arr if len(ells) else None))
 
     # -- solves (host arrays) --------------------------------------------------
     def sign_apply(self, b, k, ell, tol=0.0, p=0.0, flags=NK_FP64, check=True):

@@ -38,14 +38,21 @@ K_MAX = 1536
 L_LABEL = 256
 L_GRID = [16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256]
 DIMS_CHOICES = [(4, 4, 4, 4), (4, 4, 4, 8), (6, 6, 6, 6), (8, 8, 8, 8), (6, 6, 6, 12), (10, 10, 10, 10)]
+# the 64-instance sweep: seeds 1000 + i on 4^4, 6^4, 8^4, 10^4 in turn (16 each),
+# the first 48 for training and the last 16 held out
+C5_LATTICES = [(4, 4, 4, 4), (6, 6, 6, 6), (8, 8, 8, 8), (10, 10, 10, 10)]
+C5_FIRST_SEED, C5_N, C5_TEST = 1000, 64, 16
+C5_REPORT = os.path.join(HERE, "c5_evaluation.json")
 
 
-def sample_instance(seed: int):
-    """One synthetic operator and source: lattice from DIMS_CHOICES, mu ~ U[0, 1],
-    m_w ~ U[-2.2, -1.8], plaquette ~ U[0.55, 0.62], one Gaussian source."""
+def sample_instance(seed: int, dims=None):
+    """One synthetic operator and source: lattice `dims` (default: drawn from
+    DIMS_CHOICES), mu ~ U[0, 1], m_w ~ U[-2.2, -1.8], plaquette ~ U[0.55, 0.62],
+    one Gaussian source."""
     import inputs   # seeded synthetic generators (not part of the compute path)
     rng = np.random.default_rng([4457, seed])
-    dims = DIMS_CHOICES[int(rng.integers(len(DIMS_CHOICES)))]
+    drawn = DIMS_CHOICES[int(rng.integers(len(DIMS_CHOICES)))]
+    dims = tuple(dims) if dims is not None else drawn
     mu = float(rng.uniform(0.0, 1.0))
     m_w = float(rng.uniform(-2.2, -1.8))
     plaq = float(rng.uniform(0.55, 0.62))
@@ -94,13 +101,18 @@ def label(ctx, b_dev, tol: float):
     return k_star, grid[lo], info
 
 
-def build_dataset(n: int, tol: float = 1e-8, first_seed: int = 0, log=print):
+def c5_dims(seed: int):
+    return C5_LATTICES[(seed - C5_FIRST_SEED) % len(C5_LATTICES)]
+
+
+def build_dataset(n: int, tol: float = 1e-8, first_seed: int = 0, log=print, dims_of=None):
     """Features X (n', 16), targets Y (n', 2) = (log2 k*, log2 l*) and per-instance
-    records, skipping instances without a label."""
+    records, skipping instances without a label.  dims_of(seed): the lattice of
+    an instance (default: drawn by sample_instance)."""
     import torch
     X, Y, recs = [], [], []
     for s in range(first_seed, first_seed + n):
-        inst = sample_instance(s)
+        inst = sample_instance(s, dims_of(s) if dims_of else None)
         ctx = _context(inst)
         b_dev = torch.from_numpy(inst["b"]).cuda()
         t0 = time.time()
@@ -201,7 +213,7 @@ def solve_predicted(ctx, m, b_dev, y_dev, tol: float, k_max: int = K_MAX, flags=
     return st, rc, (k_pred, l_pred)
 
 
-def evaluate(m, seeds, tol: float = 1e-8, l_default: int = 160, mean_sizes=None, log=print):
+def evaluate(m, seeds, tol: float = 1e-8, l_default: int = 160, mean_sizes=None, log=print, dims_of=None):
     """Held-out comparison of three ways to run adaptive k on each instance:
       default    checks from NK_ADAPT_FIRST(l_default) on, l = l_default;
       mean       the training set's geometric-mean (k, l) used like a prediction
@@ -212,7 +224,7 @@ def evaluate(m, seeds, tol: float = 1e-8, l_default: int = 160, mean_sizes=None,
     import torch
     rows = []
     for s in seeds:
-        inst = sample_instance(s)
+        inst = sample_instance(s, dims_of(s) if dims_of else None)
         ctx = _context(inst)
         b = torch.from_numpy(inst["b"]).cuda()
         ys = {name: torch.empty_like(b) for name in ("default", "mean", "predicted")}
@@ -265,17 +277,26 @@ def main(argv=None):
     ap.add_argument("--dataset", default=None,
                     help="npz of features and labels: read if it exists, else written after labelling")
     ap.add_argument("--report", default=None, help="JSON summary path")
+    ap.add_argument("--c5", action="store_true",
+                    help="the 64-instance sweep (seeds 1000 + i, 4^4 / 6^4 / 8^4 / 10^4 in turn, 48 train / 16 "
+                         "held out); writes its record to c5_evaluation.json and its weights beside it")
     a = ap.parse_args(argv)
-    n_test = a.n // 4
-    test_seeds = list(range(a.n - n_test, a.n))
+    first, dims_of = 0, None
+    if a.c5:
+        a.n, first, dims_of = C5_N, C5_FIRST_SEED, c5_dims
+        a.report = a.report or C5_REPORT
+        if a.out == WEIGHTS_PATH:
+            a.out = os.path.join(HERE, "predictor_weights_c5.npz")
+    n_test = C5_TEST if a.c5 else a.n // 4
+    test_seeds = list(range(first + a.n - n_test, first + a.n))
     t0 = time.time()
     if a.dataset and os.path.exists(a.dataset):
         z = np.load(a.dataset, allow_pickle=False)
         X, Y, Xt, Yt = z["X"], z["Y"], z["Xt"], z["Yt"]
         recs, recs_t = json.loads(str(z["recs"])), json.loads(str(z["recs_t"]))
     else:
-        X, Y, recs = build_dataset(a.n - n_test, a.tol, 0)
-        Xt, Yt, recs_t = build_dataset(n_test, a.tol, a.n - n_test)
+        X, Y, recs = build_dataset(a.n - n_test, a.tol, first, dims_of=dims_of)
+        Xt, Yt, recs_t = build_dataset(n_test, a.tol, first + a.n - n_test, dims_of=dims_of)
         if a.dataset:
             np.savez(a.dataset, X=X, Y=Y, Xt=Xt, Yt=Yt, recs=json.dumps(recs), recs_t=json.dumps(recs_t))
     t_data = time.time() - t0
@@ -285,7 +306,7 @@ def main(argv=None):
     mean_rmse = np.sqrt(np.mean((Y.mean(axis=0) - Yt) ** 2, axis=0)).tolist() if len(Xt) else None
     km = 2 * int(round(0.5 * 2 ** Y[:, 0].mean()))
     lm = 2 * int(round(0.5 * 2 ** Y[:, 1].mean()))
-    rows = evaluate(m, test_seeds, a.tol, mean_sizes=(km, lm))
+    rows = evaluate(m, test_seeds, a.tol, mean_sizes=(km, lm), dims_of=dims_of)
     ok = [r for r in rows if "default" in r]
     tot = lambda name, key: float(np.sum([r[name][key] for r in ok]))
     summ = {

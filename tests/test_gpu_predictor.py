@@ -80,3 +80,63 @@ def test_stored_predictor_on_held_out_instance():
     assert rc == nksign.NK_OK
     assert 64 <= kp <= predictor.K_MAX and 16 <= lp <= min(kp, 256)
     assert predictor._rel(y, _ref(ctx, b, st["k_used"])) <= 10 * TOL
+
+
+# held-out instances of the stored predictor (its training used seeds below 144)
+HELD_OUT = [145, 152, 158, 163, 168, 176, 190]
+
+
+@pytest.mark.skipif(not os.path.exists(predictor.WEIGHTS_PATH), reason="no trained predictor stored")
+def test_prediction_saves_checks_and_time_on_held_out_instances():
+    """What the predictor gains over the method without it: adaptive k started
+    from the prediction against adaptive k from the default start (checks every
+    NK_ADAPT_STEP from NK_ADAPT_FIRST(l), l = 160), both at tol = 1e-8 on the
+    same held-out instances.  Summed over them the predicted start needs fewer
+    convergence checks and less device time, and every result meets the
+    tolerance against a converged reference."""
+    m = predictor.load_model()
+    tot = {"default": [0, 0.0], "predicted": [0, 0.0]}
+    for seed in HELD_OUT:
+        inst = predictor.sample_instance(seed)
+        ctx = predictor._context(inst)
+        b = torch.from_numpy(inst["b"]).cuda()
+        y_d, y_p = torch.empty_like(b), torch.empty_like(b)
+        for rep in range(2):          # the second run of each is timed (warm)
+            st_d, rc_d = ctx.sign_apply_dev(b, y_d, 1, predictor.K_MAX, 160, tol=TOL, check=False)
+            st_p, rc_p, _ = predictor.solve_predicted(ctx, m, b, y_p, TOL)
+        assert rc_d == nksign.NK_OK and rc_p == nksign.NK_OK, seed
+        ref = _ref(ctx, b, max(st_d["k_used"], st_p["k_used"]))
+        assert predictor._rel(y_d, ref) <= 10 * TOL and predictor._rel(y_p, ref) <= 10 * TOL, seed
+        tot["default"][0] += st_d["checks"]
+        tot["default"][1] += st_d["t_total_ms"]
+        tot["predicted"][0] += st_p["checks"]
+        tot["predicted"][1] += st_p["t_total_ms"]
+        ctx.close()
+    assert tot["predicted"][0] < tot["default"][0], tot
+    assert tot["predicted"][1] < tot["default"][1], tot
+
+
+@pytest.mark.skipif(not os.path.exists(predictor.WEIGHTS_PATH), reason="no trained predictor stored")
+def test_library_runs_the_predictor_itself():
+    """NK_PREDICT: the library predicts (k, l) from source 0 with the predictor
+    set on the context and starts its adaptive checks there (nk_stats reports
+    the prediction); the result meets the tolerance."""
+    m = predictor.load_model()
+    inst = predictor.sample_instance(163)
+    ctx = predictor._context(inst)
+    b = torch.from_numpy(inst["b"]).cuda()
+    kp, lp = ctx.predict_sizes(m, b, predictor.K_MAX)
+    ctx.set_predictor(m)
+    y = torch.empty_like(b)
+    st, rc = ctx.sign_apply_dev(b, y, 1, predictor.K_MAX, 256, tol=TOL, flags=nksign.NK_PREDICT, check=False)
+    assert rc == nksign.NK_OK
+    assert (st["k_pred"], st["ell_pred"]) == (kp, lp)
+    assert st["ell_used"] <= max(2 * int(np.ceil(0.75 * lp)), 2) or st["predict_fallback"]
+    assert st["checks"] <= 4 or st["predict_fallback"]
+    assert predictor._rel(y, _ref(ctx, b, st["k_used"])) <= 10 * TOL
+    # the error estimate of Sec. 3 inside the same call
+    st2, rc2 = ctx.sign_apply_dev(b, y, 1, predictor.K_MAX, 256, tol=TOL,
+                                  flags=nksign.NK_PREDICT | nksign.NK_EPS_EST, check=False)
+    assert rc2 == nksign.NK_OK and 0.0 < st2["eps_sgn2"][0] <= 10 * TOL
+    ctx.set_predictor(None)
+    ctx.close()
