@@ -77,7 +77,10 @@ def test_deflated_mixed_and_overlap(case):
     y64, st, _ = ctx.sign_apply(b, K, ELL, flags=NK_FP64)
     ymx, _, _ = ctx.sign_apply(b, K, ELL, flags=NK_MIXED)
     for i in range(2):
-        assert rel(ymx[i], y64[i]) < 1e-7
+        # k = 144 is far from converged here (error ~1e-5 at mu = 0.3): the FP32
+        # stencil moves the result well below the method's own error
+        assert rel(ymx[i], y64[i]) < 1e-6
+        assert rel(ymx[i], truth[i]) < 1.1 * rel(y64[i], truth[i]) + 1e-8
     d_ov, _, _ = ctx.overlap_apply(b, K, ELL, flags=NK_FP64)
     for i in range(2):
         want = b[i] + dirac.gamma5(y64[i], DIMS)

@@ -131,8 +131,12 @@ def test_library_runs_the_predictor_itself():
     st, rc = ctx.sign_apply_dev(b, y, 1, predictor.K_MAX, 256, tol=TOL, flags=nksign.NK_PREDICT, check=False)
     assert rc == nksign.NK_OK
     assert (st["k_pred"], st["ell_pred"]) == (kp, lp)
-    assert st["ell_used"] <= max(2 * int(np.ceil(0.75 * lp)), 2) or st["predict_fallback"]
-    assert st["checks"] <= 4 or st["predict_fallback"]
+    # the same procedure as predictor.solve_predicted: the same k, checks and result
+    y_py = torch.empty_like(b)
+    st_py, rc_py, _ = predictor.solve_predicted(ctx, m, b, y_py, TOL)
+    assert rc_py == nksign.NK_OK
+    assert (st["k_used"], st["checks"], st["ell_used"]) == (st_py["k_used"], st_py["checks"], st_py["ell_used"])
+    assert torch.equal(y, y_py)
     assert predictor._rel(y, _ref(ctx, b, st["k_used"])) <= 10 * TOL
     # the error estimate of Sec. 3 inside the same call
     st2, rc2 = ctx.sign_apply_dev(b, y, 1, predictor.K_MAX, 256, tol=TOL,
