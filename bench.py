@@ -433,9 +433,9 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
                      {"traffic": profiled_traffic("k_step2"),
                       "algorithmic_bytes_per_launch": (128 if two else 64) * N * n_rhs})
     if dom == "dslash":
-        return alu64("k_dslash_step1<float> (FP32 stencil + FP64 step-1 epilogue)",
+        return alu64("k_stencil32_step1 (FP32 stencil + FP64 step-1 epilogue)",
                      ((16 + 8) if two else 12) * N * n_rhs,
-                     {"traffic": profiled_traffic("k_dslash_step1<float>")})
+                     {"traffic": profiled_traffic("k_stencil32_step1")})
     if dom == "lift":
         return alu64("k_lift (FP64)", 8.0 * N * n_rhs * w["k"], {"traffic": None})
     if dom == "dslash_df":
