@@ -391,7 +391,8 @@ def stencil_roofline(nk, torch, peaks):
                       "loaded once per site block for all 24 vectors)",
             "lattice": "16x16x16x32", "bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs"),
             "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0), "ms_per_launch": ms,
-            "bytes_per_launch": total, "launches": reps, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+            "bytes_per_launch": total, "launches": reps, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": profiled_traffic("k_stencil32@16x16x16x32")}
 
 
 def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
@@ -399,12 +400,16 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
 
     Algorithmic work per launch, n_rhs sources, two-sided (Hermitian in
     parentheses); each array moved once, each flop of the method counted once:
-      step2 (FP64): r -= c3 q_j, l -= c4 p_j, delta += r^dag l: 24 (8) FP64
-             flops per element -- FP64 ALU, peak the nominal 1.25 TFLOP/s;
-      dslash (FP32 stencil fused with the FP64 step-1 epilogue): the FP64
-             part, r = s - c1 q_{j-1} and H(j,j) += p_j^dag r (16 (12) flops
-             per element) plus l = t - c1' p_{j-1} (8 flops), against the FP64
-             peak (the FP32 stencil part runs beside it on the FP32 pipe);
+      step2 (the FP64 recurrence kernels k_step1 and k_step2, one launch of
+             each per FP32 step): step 1 r = s - c1 q_{j-1}, l = t - c1' p_{j-1},
+             H(j,j) += p_j^dag r; step 2 r -= c3 q_j, l -= c4 p_j,
+             delta += r^dag l: 24 (8) FP64 flops per element in either kernel
+             -- FP64 ALU, peak the nominal 1.25 TFLOP/s; bytes per element:
+             step 1 loads s, t (FP32) and q_{j-1}, p_{j-1}, p_j, stores r, l
+             (96 (56) B), step 2 loads q_j, r, p_j, l, stores r, l and their
+             FP32 copies (112 (56) B);
+      dslash (the multi-RHS FP32 stencil of the FP32 steps): links 288 B per
+             site plus 96 B in and 96 B out per site and vector -- HBM;
       dslash_df: the two-float stencil, 1320 flops per site and vector;
              two-float arithmetic costs 9 FP32 instructions per flop on
              average, so its ALU peak is 152 x 128 x f_SM / 9;
@@ -424,18 +429,23 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
         tf = flops / (ms * 1e-3) / 1e12
         r = {"kernel": kernel, "bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
              "frac": tf / FP64_PEAK_TFLOPS, "ms_per_launch": ms, "flops_per_launch": flops,
-             "peak_derivation": "nominal dense FP64 rate of GB300 (1.25 TFLOP/s, 152 SMs)"}
+             "peak_derivation": "nominal dense FP64 rate of GB300 (1.25 TFLOP/s, 152 SMs); a DFMA throughput "
+                                "test on this pool measured 0.59-0.63 T DFMA/s, i.e. the same"}
         r.update(extra or {})
         return r
 
     if dom == "step2":
-        return alu64("k_step2 (FP64)", (24 if two else 8) * N * n_rhs,
-                     {"traffic": profiled_traffic("k_step2"),
-                      "algorithmic_bytes_per_launch": (128 if two else 64) * N * n_rhs})
+        t1, t2 = profiled_traffic("k_step1"), profiled_traffic("k_step2")
+        return alu64("k_step1 / k_step2 (FP64 recurrence, operands staged by bulk copies)",
+                     (24 if two else 8) * N * n_rhs,
+                     {"traffic": (t1 + t2) / 2 if (t1 is not None and t2 is not None) else None,
+                      "algorithmic_bytes_per_launch": (104 if two else 56) * N * n_rhs})
     if dom == "dslash":
-        return alu64("k_stencil32_step1 (FP32 stencil + FP64 step-1 epilogue)",
-                     ((16 + 8) if two else 12) * N * n_rhs,
-                     {"traffic": profiled_traffic("k_stencil32_step1")})
+        nbytes = (288.0 + nv * 192.0) * V
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"kernel": "k_stencil32 (multi-RHS FP32 stencil of the FP32 steps)", "bound": "hbm",
+                "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "ms_per_launch": ms,
+                "bytes_per_launch": nbytes, "traffic": profiled_traffic("k_stencil32@10x10x10x10")}
     if dom == "lift":
         return alu64("k_lift (FP64)", 8.0 * N * n_rhs * w["k"], {"traffic": None})
     if dom == "dslash_df":

@@ -52,8 +52,10 @@ extern "C" {
 #define NK_ENOTCONV (-4)    /* adaptive k: tolerance not met at k_max */
 #define NK_ERHI (-5)        /* Roberts-Higham iteration did not converge */
 #define NK_ECUDA (-6)       /* CUDA runtime error */
-#define NK_ETIMEOUT (-7)    /* reserved: no kernel of this library waits on a device-side flag
-                               (the RHi clusters synchronise with hardware cluster barriers) */
+#define NK_ETIMEOUT (-7)    /* a bounded device-side wait ran out: the streaming kernels of the
+                               outer recurrence wait at most one second for the bulk copies of
+                               each tile into shared memory; that RHS is failed (the RHi
+                               clusters synchronise with hardware cluster barriers) */
 #define NK_ESTATE (-8)      /* call out of order (e.g. no links loaded) */
 
 /* Solve flags (bitwise or). */
@@ -87,11 +89,14 @@ extern "C" {
 #define NK_MAX_RHS 12
 
 /* Kernel classes of a solve, for nk_stats.t_class_ms / n_class. */
-#define NK_CLASS_DSLASH 0     /* FP32 Wilson stencil A v (and A^dagger w) fused with
+#define NK_CLASS_DSLASH 0     /* FP32 Wilson stencil A v (and A^dagger w), multi-RHS (in the
+                                 optional two-float recurrence fused with its step 1) */
+#define NK_CLASS_DSLASH_DF 1  /* two-float (about 48-bit) stencil fused with the FP64
                                  r = Av - c v_prev and the H(j,j) reduction */
-#define NK_CLASS_DSLASH_DF 1  /* the same with the two-float (about 48-bit) stencil */
-#define NK_CLASS_STEP2 2      /* r -= H(j,j) v, beta / delta, stencil input copies (FP64) */
-#define NK_CLASS_DSLASH64 3   /* the same with the FP64 stencil */
+#define NK_CLASS_STEP2 2      /* the FP64 recurrence kernels: step 1 after an FP32 stencil
+                                 (r = Av - c v_prev, H(j,j)) and step 2 (r -= H(j,j) v,
+                                 beta / delta, stencil input copies) */
+#define NK_CLASS_DSLASH64 3   /* FP64 stencil fused with the FP64 step 1 */
 #define NK_CLASS_INNER 4    /* p estimate, LU of p H_k, inner Lanczos */
 #define NK_CLASS_RHI 5      /* Roberts-Higham iteration */
 #define NK_CLASS_LIFT 6     /* V_l s and |x| V_k c */

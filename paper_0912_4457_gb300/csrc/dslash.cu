@@ -682,8 +682,32 @@ static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R k
         launch_step1_cs<R, T, 1>(grid, dim3(threads, 1), U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps, st);
 }
 
-void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
-                         double mu, cudaStream_t st) {
+bool split_fp32_step(int precision, const Outer& o, int j) { return precision == 32 && j < o.ring_from && o.s32; }
+
+void launch_stencil32_step(const void* U32, const Geom& g, const Outer& o, int j, double kappa, double mu,
+                           cudaStream_t st) {
+    const long vs = o.N / 2;   // float4 per vector
+    Stencil32Set s;
+    s.in_a = o.q32;
+    s.in_d = o.p32;
+    s.out_a = o.s32;
+    s.out_d = o.s32 + (size_t)o.n_rhs * vs;
+    s.vstride = vs;
+    s.n_a = o.n_rhs;
+    s.n_d = (o.two_sided && j < o.k - 1) ? o.n_rhs : 0;   // the last step needs no new left vector
+    s.scale = o.sc;
+    launch_stencil32(U32, g, s, kappa, mu, st);
+}
+
+int launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
+                        double mu, cudaStream_t st) {
+    if (split_fp32_step(precision, o, j)) {
+        // FP64 recurrence: the multi-RHS FP32 stencil leaves (A q_j)/n_j and
+        // (A^dag p_j)/m_j in s32, a streaming FP64 kernel runs step 1 on them
+        launch_stencil32_step(U, g, o, j, kappa, mu, st);
+        launch_outer_step1(o, j, st);
+        return 2;
+    }
     if (precision == 32) {
         launch_stencil32_step1(U, g, o, j, kappa, mu, st);
     } else if (precision == 48) {   // the two-float stencil reads the two-float rings
@@ -694,6 +718,7 @@ void launch_dslash_step1(int precision, const void* U, const Geom& g, const Oute
         launch_step1_t<double, double2>((const double2*)U, g, o, j, kappa, exp(mu), exp(-mu), outer_q(o, 0, j), qs,
                                         o.two_sided ? outer_p(o, 0, j) : nullptr, 3 * o.N, st);
     }
+    return 1;
 }
 
 // ---- layout conversion -------------------------------------------------------

@@ -215,6 +215,7 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     if (two_sided) o.P = (double2*)take(vec * 3 * n_rhs);
     o.q32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);    // pair layout: N / 2 float4 per RHS
     if (two_sided) o.p32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);
+    if (mixed) o.s32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs * (two_sided ? 2 : 1));
     o.qdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     if (two_sided) o.pdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     o.q_df_from = 1 << 30;
@@ -286,12 +287,16 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
 }
 
 int blocks_per_rhs(long N, int n_rhs) {
-    // fixed per shape (deterministic reductions): about 8 elements per thread
-    // so the per-thread share of the FP64 reduction stays small, at most
-    // 4 x 152 blocks over all RHS, grid-stride beyond that
-    long need = (N + 2047) / 2048;
-    long cap = std::max(1L, (long)(4 * 152 / n_rhs));
-    return (int)std::max(1L, std::min(need, cap));
+    // fixed per shape and device (deterministic reductions): at least two
+    // tiles of sites per CTA of the streaming step kernels, and at most one
+    // wave of them over all RHS
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    const long V = N / 12;
+    const long need = std::max(1L, V / (2L * nk::stream_tile_sites()));
+    const long cap = std::max(1L, (long)sms * nk::stream_ctas_per_sm() / n_rhs);
+    return (int)std::min(need, cap);
 }
 
 // The launch shape of a solve: the tuned one for (n_rhs, two-sided, mixed),
@@ -343,13 +348,21 @@ struct Launcher {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
     template <typename F>
     void run(int cls, int nkernels, F&& f) {
+        run_counted(cls, [&] {
+            f();
+            return nkernels;
+        });
+    }
+    // f returns the number of kernels it launched
+    template <typename F>
+    void run_counted(int cls, F&& f) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (profile) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, st);
         }
-        f();
+        const int nkernels = f();
         if (profile) {
             cudaEventRecord(b, st);
             marks.push_back({cls, {a, b}});
@@ -405,7 +418,13 @@ void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, const Schedule& s, int j
         const int prec = s.prec(j);
         const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
         const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
-        L.run(cls, 1, [&] { nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
+        if (nk::split_fp32_step(prec, o, j)) {
+            // the stencil, then the FP64 step-1 kernel, timed with the FP64 recurrence
+            L.run(NK_CLASS_DSLASH, 1, [&] { nk::launch_stencil32_step(U, g, o, j, kap, c->mu, st); });
+            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step1(o, j, st); });
+        } else {
+            L.run_counted(cls, [&] { return nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
+        }
         if (j < o.k - 1) {
             const bool ring = s.mixed && j >= o.ring_from;
             const bool write_ring = s.mixed && (s.prec(j + 1) == 48 || j + 1 >= o.ring_from - 1);
@@ -634,6 +653,7 @@ int status_to_code(int s) {
         case nk::kStatusInnerBreakdown: return NK_EBREAKDOWN;
         case nk::kStatusRhi: return NK_ERHI;
         case nk::kStatusLU: return NK_ERHI;
+        case nk::kStatusTimeout: return NK_ETIMEOUT;
         default: return NK_ECUDA;
     }
 }
@@ -1476,6 +1496,7 @@ int nk_stencil32_dev(nk_ctx* c, const float* in_dev, float* out_dev, int n_rhs, 
     s.out_d = s.out_a + (size_t)n_rhs * vs;
     s.vstride = vs;
     s.n_a = s.n_d = n_rhs;
+    s.scale = nullptr;
     nk::launch_stencil32(c->U32, geom_of(c), s, kappa_of(c), c->mu, (cudaStream_t)stream);
     NK_CUDA(c, cudaGetLastError());
     return NK_OK;
@@ -1505,6 +1526,7 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
         s.vstride = N / 2;
         s.n_a = dagger ? 0 : n_vec;
         s.n_d = dagger ? n_vec : 0;
+        s.scale = nullptr;
         nk::launch_stencil32(c->U32, geom_of(c), s, kappa_of(c), c->mu, st);
         nk::launch_f32pair_to_abi(out32, N / 2, (double2*)out_dev, N, c->V, n_vec, st);
         NK_CUDA(c, cudaGetLastError());

@@ -30,6 +30,7 @@
 // regenerates bit-identical coefficients, which the double-pass mode relies on.
 #include "nk_common.cuh"
 #include "nk_kernels.h"
+#include "nk_tma.cuh"
 
 namespace nk {
 
@@ -136,10 +137,10 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
             if (!TS) {
                 const double bb = sqrt(d.x);             // beta <- sqrt(r^dag r)
                 b = g = mk(bb, 0.0);
-                if (!(bb > 0.0) || !isfinite(bb)) o.status[rhs] = kStatusBreakdown;
+                if (!(bb > 0.0) || !isfinite(bb)) mark_failed(o, rhs, kStatusBreakdown);
             } else if ((d.x == 0.0 && d.y == 0.0) || !isfinite(d.x) || !isfinite(d.y)) {
                 // serious breakdown: delta = 0 (App. B); a non-finite delta is treated alike
-                o.status[rhs] = kStatusBreakdown;
+                mark_failed(o, rhs, kStatusBreakdown);
                 b = g = mk(0.0, 0.0);
             } else {
                 b = csqrt_principal(d);                  // beta <- sqrt(delta)
@@ -166,93 +167,290 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
     }
 }
 
+// ---- streaming FP64 kernels of the FP64 recurrence ----------------------------
+// Step 1 (after the FP32 stencil) and step 2 stream their operand vectors
+// through shared memory with bulk asynchronous copies (the TMA engine,
+// cp.async.bulk, nk_tma.cuh).  A CTA owns a contiguous range of sites of one
+// RHS and walks it in tiles of kTile sites.  Warp w owns component pair w
+// (spin-colour components 2w and 2w + 1: rows 2w, 2w + 1 of an FP64 vector,
+// row w of an FP32 pair-layout vector) and runs its own pipeline: kStages
+// stage buffers with their own mbarriers, into which its lanes copy the
+// warp's rows of every operand vector for a tile, kStages - 1 tiles ahead of
+// its arithmetic; lane l then takes site s0 + l of the tile and writes its
+// results straight to global memory.  No CTA-wide barrier inside the loop:
+// the warps run independently.  GB300's FP64 pipe (about 0.6 T DFMA/s) is
+// kept busy by a few warps per SM as long as they have operands; the copies
+// keep enough bytes in flight for HBM without holding them in registers.
+constexpr int kTile = 32;                       // sites per tile = lanes of a warp
+constexpr int kStreamWarps = 6;                 // one per component pair
+constexpr int kStreamThreads = 32 * kStreamWarps;
+constexpr int kStages = 3;
+constexpr int kRowBytes = kTile * 16;           // one row of a tile: kTile 16-byte elements
+constexpr int kMaxWarpRows = 8;                 // rows of one warp's stage, at most
+
+// One operand vector of a streaming kernel (row r of V 16-byte elements at
+// base + r V 16 bytes): rows = 2 for an FP64 vector (warp w reads rows 2w,
+// 2w + 1), 1 for an FP32 pair-layout vector (row w), 0 for an absent operand.
+struct TileStream {
+    const char* base;
+    int rows;
+};
+
+// The copies of warp w for the tile of sites [s0, s0 + n): one row per lane
+// (the rows of stream k follow those of streams 0 .. k-1 in the stage),
+// armed on bar with their byte count by lane 0.
+template <int NS>
+__device__ __forceinline__ void issue_warp_tile(const TileStream (&ts)[NS], char* stage, uint64_t* bar, unsigned V,
+                                                unsigned s0, unsigned n, int w, int lane) {
+    int total = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) total += ts[k].rows;
+    const unsigned bytes = n * 16u;
+    if (lane == 0) {
+        fence_proxy_async_smem();   // the stage was last read through the generic proxy
+        mbar_arrive_expect_tx(bar, (unsigned)total * bytes);
+    }
+    __syncwarp();
+    int off = 0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int rows = ts[k].rows;
+        if (lane >= off && lane < off + rows) {
+            const unsigned row = (unsigned)(w * rows + lane - off);
+            bulk_copy_g2s(stage + (size_t)lane * kRowBytes, ts[k].base + ((size_t)row * V + s0) * 16, bytes, bar);
+        }
+        off += rows;
+    }
+}
+
+// The tile loop of warp w over the site range of CTA blockIdx.x (of o.nblk per
+// RHS): f(stage, s0, n) on each tile once its copies have landed.  Returns
+// false if a wait ran out (the warp's copies still in flight are then waited
+// for, bounded, before returning).
+template <int NS, typename F>
+__device__ __forceinline__ bool stream_tiles(const Outer& o, const TileStream (&ts)[NS], F&& f) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ uint64_t bar[kStreamWarps][kStages];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned V = (unsigned)(o.N / 12);
+    const unsigned s_lo = (unsigned)((unsigned long long)blockIdx.x * V / (unsigned)o.nblk);
+    const unsigned s_hi = (unsigned)((unsigned long long)(blockIdx.x + 1) * V / (unsigned)o.nblk);
+    const int ntiles = (int)((s_hi - s_lo + kTile - 1) / kTile);
+    const size_t stage_bytes = (size_t)kMaxWarpRows * kRowBytes;
+    char* mine = smem + (size_t)w * kStages * stage_bytes;
+    uint64_t* mbar = bar[w];
+    if (lane == 0) {
+#pragma unroll
+        for (int st = 0; st < kStages; ++st) mbar_init(&mbar[st], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    for (int t = 0; t < kStages - 1 && t < ntiles; ++t) {
+        const unsigned s0 = s_lo + t * kTile;
+        issue_warp_tile(ts, mine + t * stage_bytes, &mbar[t], V, s0, min((unsigned)kTile, s_hi - s0), w, lane);
+    }
+    int t = 0;
+    bool ok = true;
+    for (; t < ntiles; ++t) {
+        // the tile kStages - 1 ahead goes into the stage freed by tile t - 1
+        const int ahead = t + kStages - 1;
+        if (ahead < ntiles) {
+            const unsigned s0 = s_lo + ahead * kTile;
+            issue_warp_tile(ts, mine + (ahead % kStages) * stage_bytes, &mbar[ahead % kStages], V, s0,
+                            min((unsigned)kTile, s_hi - s0), w, lane);
+        }
+        const int st = t % kStages;
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[st], (unsigned)(t / kStages) & 1u, kWaitLimitNs));
+        if (!ok) break;
+        const unsigned s0 = s_lo + t * kTile;
+        f(mine + st * stage_bytes, s0, min((unsigned)kTile, s_hi - s0));
+        __syncwarp();   // every lane is done with the stage before it is refilled
+    }
+    if (ok) return true;
+    if (lane == 0)   // copies issued for tiles t .. t + kStages - 1
+        for (int u = t; u < ntiles && u < t + kStages; ++u)
+            mbar_wait_bounded(&mbar[u % kStages], (unsigned)(u / kStages) & 1u, kWaitLimitNs);
+    __syncwarp();
+    return false;
+}
+
+// The FP64 loops take no negated operand: in a throughput test on GB300 a
+// DFMA with a negated multiplicand ran at 85% of the rate of a plain one.  The
+// negated scalars are formed once per kernel by flipping the sign bit, and
+// the imaginary part of an inner product sums its two products separately.
+__device__ __forceinline__ double neg_bits(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ double2 neg_bits(double2 c) { return mk(neg_bits(c.x), neg_bits(c.y)); }
+// s - c p, with nc = -c
+__device__ __forceinline__ double2 cfma_sub(double2 s, double2 c, double2 nc, double2 p) {
+    return mk(fma(nc.x, p.x, fma(c.y, p.y, s.x)), fma(nc.x, p.y, fma(nc.y, p.x, s.y)));
+}
+// s + c p, with nc = -c
+__device__ __forceinline__ double2 cfma_add(double2 s, double2 c, double2 nc, double2 p) {
+    return mk(fma(c.x, p.x, fma(nc.y, p.y, s.x)), fma(c.x, p.y, fma(c.y, p.x, s.y)));
+}
+// conj(a) b accumulated as (re, im+, im-): im = im+ - im-
+struct Dot3 {
+    double re, ip, im;
+};
+__device__ __forceinline__ void dot3_add(Dot3& d, double2 a, double2 b) {
+    d.re = fma(a.x, b.x, fma(a.y, b.y, d.re));
+    d.ip = fma(a.x, b.y, d.ip);
+    d.im = fma(a.y, b.x, d.im);
+}
+
 // FP64 step 2 (the recurrence of NK_FP64 and of the mixed schedule):
 //   r <- r - (H(j,j)/n_j) q_j,  l <- l - (H(j,j)^*/m_j) p_j,  delta += r^dag l,
 // plus the copies the next stencil reads (FP32 pair layout; write_ring: also
 // two-float copies in the rings for a two-float stencil or a later ring
-// step).  Each thread takes a spin-colour component pair (2i, 2i + 1) of a
-// site -- the elements i V + s ... of the FP64 layout and one float4 of the
-// FP32 copy -- two pairs per iteration with every load issued first (the
-// kernel is bound by the FP64 pipe and by the latency of these loads).
+// step).  Stage rows of warp w (components 2w + h): q_j h, r 2 + h, p_j 4 + h,
+// l 6 + h.
 template <bool TS>
-__global__ void __launch_bounds__(kThreads) k_step2(Outer o, int j, int copy_mode, int write_ring) {
+__global__ void __launch_bounds__(kStreamThreads) k_step2(Outer o, int j, int copy_mode, int write_ring) {
     __shared__ double2 sh[33];
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
     const double2 c3 = o.sc[(size_t)rhs * kScalars + kScC3];
     const double2 c4 = o.sc[(size_t)rhs * kScalars + kScC4];
     const unsigned V = (unsigned)(o.N / 12);
-    const unsigned NP = 6u * V;
-    const double2* __restrict__ qj = outer_q(o, rhs, j);
-    double2* __restrict__ r = outer_q(o, rhs, j + 1);
-    const double2* __restrict__ pj = TS ? outer_p(o, rhs, j) : nullptr;
-    double2* __restrict__ l = TS ? outer_p(o, rhs, j + 1) : nullptr;
-    float4* __restrict__ r32 = o.q32 + (size_t)rhs * NP;
-    float4* __restrict__ l32 = TS ? o.p32 + (size_t)rhs * NP : nullptr;
+    const double2* qj = outer_q(o, rhs, j);
+    double2* r = outer_q(o, rhs, j + 1);
+    const double2* pj = TS ? outer_p(o, rhs, j) : nullptr;
+    double2* l = TS ? outer_p(o, rhs, j + 1) : nullptr;
+    float4* __restrict__ r32 = o.q32 + (size_t)rhs * 6 * V;
+    float4* __restrict__ l32 = TS ? o.p32 + (size_t)rhs * 6 * V : nullptr;
     dfc* __restrict__ rr_ring = write_ring ? ring_q(o, rhs, j + 1) : nullptr;
     dfc* __restrict__ ll_ring = (write_ring && TS) ? ring_p(o, rhs, j + 1) : nullptr;
-    constexpr int U = 2;
-    const unsigned stride = (unsigned)o.nblk * blockDim.x;
-    double2 acc[U];
+    const TileStream ts[4] = {{(const char*)qj, 2}, {(const char*)r, 2}, {(const char*)pj, TS ? 2 : 0},
+                              {(const char*)l, TS ? 2 : 0}};
+    const double2 nc3 = neg_bits(c3), nc4 = neg_bits(c4);
+    const int cp = threadIdx.x >> 5, sl = threadIdx.x & 31;
+    Dot3 acc = {0.0, 0.0, 0.0};
+    const bool ok = stream_tiles(o, ts, [&](const char* stage, unsigned s0, unsigned n) {
+        if ((unsigned)sl >= n) return;
+        const double2* sv = reinterpret_cast<const double2*>(stage);
+        double2 rv[2], lv[2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = mk(0.0, 0.0);
-    for (unsigned p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < NP; p0 += U * stride) {
-        double2 q[U][2], rv[U][2], pv[U][2], lv[U][2];
-        size_t e[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned p = p0 + u * stride;
-            const unsigned cp = p / V, s = p - cp * V;
-            e[u] = (size_t)(2 * cp) * V + s;
-            if (p < NP) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    q[u][h] = qj[e[u] + h * V];
-                    rv[u][h] = r[e[u] + h * V];
-                    if (TS) { pv[u][h] = pj[e[u] + h * V]; lv[u][h] = l[e[u] + h * V]; }
-                }
+        for (int h = 0; h < 2; ++h) {
+            const int c = 2 * cp + h;
+            const size_t e = (size_t)c * V + s0 + sl;
+            const double2 q = sv[h * kTile + sl], a0 = sv[(2 + h) * kTile + sl];
+            // r <- r - c3 q, l <- l - c4 p with explicit FMA
+            const double2 a = TS ? cfma_sub(a0, c3, nc3, q) : mk(fma(nc3.x, q.x, a0.x), fma(nc3.x, q.y, a0.y));
+            rv[h] = a;
+            r[e] = a;
+            if (rr_ring) rr_ring[e] = dfc_of(a);
+            if (TS) {
+                const double2 b = cfma_sub(sv[(6 + h) * kTile + sl], c4, nc4, sv[(4 + h) * kTile + sl]);
+                lv[h] = b;
+                l[e] = b;
+                if (ll_ring) ll_ring[e] = dfc_of(b);
+                dot3_add(acc, a, b);   // conj(r) l
+            } else {
+                acc.re = fma(a.x, a.x, fma(a.y, a.y, acc.re));
             }
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned p = p0 + u * stride;
-            if (p >= NP) break;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                double2 a = rv[u][h];
-                const double2 qq = q[u][h];
-                // r <- r - c3 q, l <- l - c4 p with explicit FMA
-                if (TS) a = mk(fma(-c3.x, qq.x, fma(c3.y, qq.y, a.x)), fma(-c3.x, qq.y, fma(-c3.y, qq.x, a.y)));
-                else a = mk(fma(-c3.x, qq.x, a.x), fma(-c3.x, qq.y, a.y));
-                rv[u][h] = a;
-                r[e[u] + h * V] = a;
-                if (rr_ring) rr_ring[e[u] + h * V] = dfc_of(a);
-                if (TS) {
-                    double2 b = lv[u][h];
-                    const double2 pp = pv[u][h];
-                    b = mk(fma(-c4.x, pp.x, fma(c4.y, pp.y, b.x)), fma(-c4.x, pp.y, fma(-c4.y, pp.x, b.y)));
-                    lv[u][h] = b;
-                    l[e[u] + h * V] = b;
-                    if (ll_ring) ll_ring[e[u] + h * V] = dfc_of(b);
-                    acc[u].x = fma(a.x, b.x, fma(a.y, b.y, acc[u].x));   // conj(r) l
-                    acc[u].y = fma(a.x, b.y, fma(-a.y, b.x, acc[u].y));
-                } else {
-                    acc[u].x = fma(a.x, a.x, fma(a.y, a.y, acc[u].x));
-                }
-            }
-            if (copy_mode == kCopy32) {
-                r32[p] = make_float4(d2f_int(rv[u][0].x), d2f_int(rv[u][0].y), d2f_int(rv[u][1].x),
-                                     d2f_int(rv[u][1].y));
-                if (TS) l32[p] = make_float4(d2f_int(lv[u][0].x), d2f_int(lv[u][0].y), d2f_int(lv[u][1].x),
-                                             d2f_int(lv[u][1].y));
-            }
+        if (copy_mode == kCopy32) {
+            const size_t f = (size_t)cp * V + s0 + sl;
+            r32[f] = make_float4(d2f_int(rv[0].x), d2f_int(rv[0].y), d2f_int(rv[1].x), d2f_int(rv[1].y));
+            if (TS) l32[f] = make_float4(d2f_int(lv[0].x), d2f_int(lv[0].y), d2f_int(lv[1].x), d2f_int(lv[1].y));
         }
+    });
+    double2 tot = mk(acc.re, acc.ip - acc.im);
+    if (!ok) {
+        if (threadIdx.x == 0) mark_failed(o, rhs, kStatusTimeout);
+        tot = mk(0.0, 0.0);
     }
-    double2 tot = acc[0];
-#pragma unroll
-    for (int u = 1; u < U; ++u) { tot.x += acc[u].x; tot.y += acc[u].y; }
     step2_finish<TS>(o, rhs, j, tot, sh);
 }
+
+// FP64 step 1 of the FP32-stencil steps of an FP64 recurrence, after the
+// multi-RHS FP32 stencil has left s = (A q_j)/n_j and t = (A^dag p_j)/m_j
+// (FP32, pair layout) in o.s32:
+//   r = s - (c_{j-1}/n_{j-1}) q_{j-1} -> q_{j+1},
+//   l = t - (beta^*_{j-1}/m_{j-1}) p_{j-1} -> p_{j+1}   (two-sided, not at the last step),
+//   H(j,j) = (p_j^dag r) / m_j^*  (Hermitian: Re(q_j^dag r) / n_j),
+// the stencil output entering the FP64 arithmetic exactly (FP32 -> FP64 on
+// the integer pipe).  The finishing block forms H(j,j) and the step-2
+// scalars.  PASS2 (the second pass of NK_DOUBLE_PASS) also accumulates
+// y += c'_j q_j.  Stage rows of warp w (components 2w + h): s 0, q_{j-1} 1 + h,
+// dot vector (p_j, or q_j Hermitian) 3 + h, then two-sided and not at the
+// last step t 5 and p_{j-1} 6 + h.
+template <bool TS, bool PASS2>
+__global__ void __launch_bounds__(kStreamThreads) k_step1(Outer o, int j) {
+    __shared__ double2 sh[33];
+    const int rhs = blockIdx.y;
+    if (o.status[rhs] != kStatusOK) return;
+    const double2* sc = o.sc + (size_t)rhs * kScalars;
+    const double2 c1 = sc[kScC1], c1l = sc[kScC1L];
+    const unsigned V = (unsigned)(o.N / 12);
+    const int jp = j > 0 ? j - 1 : j;   // c1 = 0 at j = 0
+    const bool left = TS && j < o.k - 1;   // the last step makes no new left vector
+    const float4* s_in = o.s32 + (size_t)rhs * 6 * V;
+    const float4* t_in = o.s32 + (size_t)(o.n_rhs + rhs) * 6 * V;
+    const double2* qprev = outer_q(o, rhs, jp);
+    const double2* pprev = TS ? outer_p(o, rhs, jp) : nullptr;
+    const double2* dotv = TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j);
+    double2* __restrict__ rn = outer_q(o, rhs, j + 1);
+    double2* __restrict__ ln = left ? outer_p(o, rhs, j + 1) : nullptr;
+    double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
+    const double2 cpj = PASS2 ? o.cp[(size_t)rhs * o.k + j] : mk(0.0, 0.0);
+    const double2* __restrict__ qj = outer_q(o, rhs, j);
+    const TileStream ts[5] = {{(const char*)s_in, 1}, {(const char*)qprev, 2}, {(const char*)dotv, 2},
+                              {(const char*)t_in, left ? 1 : 0}, {(const char*)pprev, left ? 2 : 0}};
+    const double2 nc1 = neg_bits(c1), nc1l = neg_bits(c1l), ncpj = neg_bits(cpj);
+    const int cp = threadIdx.x >> 5, sl = threadIdx.x & 31;
+    Dot3 acc = {0.0, 0.0, 0.0};
+    const bool ok = stream_tiles(o, ts, [&](const char* stage, unsigned s0, unsigned n) {
+        if ((unsigned)sl >= n) return;
+        const float4 sv4 = reinterpret_cast<const float4*>(stage)[sl];
+        const double2* sv = reinterpret_cast<const double2*>(stage);
+        float4 tv4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (left) tv4 = reinterpret_cast<const float4*>(stage)[5 * kTile + sl];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = 2 * cp + h;
+            const size_t e = (size_t)c * V + s0 + sl;
+            const float2 s2 = h ? make_float2(sv4.z, sv4.w) : make_float2(sv4.x, sv4.y);
+            double2 rr = mk(f2d_int(s2.x), f2d_int(s2.y));
+            const double2 qv = sv[(1 + h) * kTile + sl];
+            rr = TS ? cfma_sub(rr, c1, nc1, qv) : mk(fma(nc1.x, qv.x, rr.x), fma(nc1.x, qv.y, rr.y));
+            rn[e] = rr;
+            const double2 d = sv[(3 + h) * kTile + sl];
+            if (TS) dot3_add(acc, d, rr);   // conj(d) r
+            else acc.re = fma(d.x, rr.x, fma(d.y, rr.y, acc.re));
+            if (left) {
+                const float2 t2 = h ? make_float2(tv4.z, tv4.w) : make_float2(tv4.x, tv4.y);
+                ln[e] = cfma_sub(mk(f2d_int(t2.x), f2d_int(t2.y)), c1l, nc1l, sv[(6 + h) * kTile + sl]);
+            }
+            if (PASS2) yacc[e] = cfma_add(yacc[e], cpj, ncpj, qj[e]);
+        }
+    });
+    double2 tot = mk(acc.re, acc.ip - acc.im);
+    if (!ok) {
+        if (threadIdx.x == 0) mark_failed(o, rhs, kStatusTimeout);
+        tot = mk(0.0, 0.0);
+    }
+    const double2 part = block_sum(tot, sh);
+    if (finish_partial(part, o.partials + (size_t)rhs * o.npart, o.counters + rhs, blockIdx.x, o.nblk)) {
+        const double2 a = sum_partials(o.partials + (size_t)rhs * o.npart, o.nblk, sh);
+        // Hermitian: H(j,j) = Re(q_j^dag r) / n_j, real (App. C); two-sided: (p_j^dag r) / m_j^*
+        const double2 al = TS ? cmul(sc[kScD], a) : mk(a.x * sc[kScD].x, 0.0);
+        const int w = threadIdx.x >> 5;
+        if (threadIdx.x == 0) {
+            o.alpha[(size_t)rhs * o.k + j] = al;
+            o.counters[rhs] = 0u;
+        }
+        // the step-2 scalars H(j,j)/n_j and H(j,j)^*/m_j, one division per warp
+        if ((threadIdx.x & 31) == 0 && w == 1) o.sc[(size_t)rhs * kScalars + kScC3] = cdiv(al, scale_n(o, rhs, j));
+        if ((threadIdx.x & 31) == 0 && w == 2)
+            o.sc[(size_t)rhs * kScalars + kScC4] = TS ? cdiv(cconj(al), scale_m(o, rhs, j)) : mk(0.0, 0.0);
+    }
+}
+
+size_t step2_smem(bool) { return (size_t)kStreamWarps * kStages * kMaxWarpRows * kRowBytes; }
+size_t step1_smem(bool) { return (size_t)kStreamWarps * kStages * kMaxWarpRows * kRowBytes; }
 
 // Step 2 of the late (FP32-stencil) steps of the mixed schedule in two-float
 // arithmetic on the FP32 pipe, on the two-float rings: r and l (left in ring slot j + 1
@@ -433,12 +631,65 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep
     k_init<<<grid, kThreads, 0, st>>>(o, copy_mode);
 }
 
+void launch_outer_step1(const Outer& o, int j, cudaStream_t st) {
+    dim3 grid(o.nblk, o.n_rhs);
+    const bool pass2 = o.y != nullptr;
+    const size_t sm = step1_smem(o.two_sided != 0);
+    if (o.two_sided) {
+        if (pass2) k_step1<true, true><<<grid, kStreamThreads, sm, st>>>(o, j);
+        else k_step1<true, false><<<grid, kStreamThreads, sm, st>>>(o, j);
+    } else {
+        if (pass2) k_step1<false, true><<<grid, kStreamThreads, sm, st>>>(o, j);
+        else k_step1<false, false><<<grid, kStreamThreads, sm, st>>>(o, j);
+    }
+}
+
+// CTAs of the two-sided step-2 kernel that fit one SM (its stage buffers
+// decide), queried once per device after lanczos_init_attributes.
+int stream_ctas_per_sm() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2<true>, kStreamThreads, step2_smem(true)) !=
+                cudaSuccess || n < 1) {
+            cudaGetLastError();
+            return 1;   // attributes not set yet: not cached
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+int stream_tile_sites() { return kTile; }
+
+void lanczos_init_attributes() {
+    // dynamic shared memory above 48 KB for the stage buffers of the streaming
+    // kernels, and the largest shared-memory carveout so that several CTAs fit an SM
+    cudaFuncSetAttribute(k_step2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step2_smem(true));
+    cudaFuncSetAttribute(k_step2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step2_smem(false));
+    cudaFuncSetAttribute(k_step1<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(true));
+    cudaFuncSetAttribute(k_step1<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(true));
+    cudaFuncSetAttribute(k_step1<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(false));
+    cudaFuncSetAttribute(k_step1<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(false));
+    const int carve = cudaSharedmemCarveoutMaxShared;
+    cudaFuncSetAttribute(k_step2<true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    cudaFuncSetAttribute(k_step2<false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    cudaFuncSetAttribute(k_step1<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    cudaFuncSetAttribute(k_step1<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    cudaFuncSetAttribute(k_step1<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    cudaFuncSetAttribute(k_step1<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+}
+
 void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, bool write_ring, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
     const int wr = (write_ring && o.qr) ? 1 : 0;
     if (!ring || !o.qr) {   // FP64 step
-        if (o.two_sided) k_step2<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode, wr);
-        else k_step2<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode, wr);
+        const size_t sm = step2_smem(o.two_sided != 0);
+        if (o.two_sided) k_step2<true><<<grid, kStreamThreads, sm, st>>>(o, j, copy_mode, wr);
+        else k_step2<false><<<grid, kStreamThreads, sm, st>>>(o, j, copy_mode, wr);
     } else {
         if (o.two_sided) k_step2_df<true><<<grid, kThreads, 0, st>>>(o, j, copy_mode);
         else k_step2_df<false><<<grid, kThreads, 0, st>>>(o, j, copy_mode);

@@ -167,17 +167,19 @@ __device__ __forceinline__ double f2d_int(float f) {
 }
 
 // double -> float, rounded to nearest (ties away from zero in magnitude; ties
-// occur with probability 2^-29 and differ from round-to-even by one ulp)
+// occur with probability 2^-29 and differ from round-to-even by one ulp).
+// Every range check is made on the 32-bit high word: checks on the 64-bit
+// pattern of |d| were turned by the compiler into FP64 comparisons, which
+// issue on the scarce FP64 pipe.
 __device__ __forceinline__ float d2f_int(double d) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-    const unsigned long long a = u & 0x7fffffffffffffffULL;
-    const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
-    // (t wraps around below the normal float range; the underflow rule is applied last)
-    unsigned long long t = (a >> 29) + ((a >> 28) & 1ULL) - (896ULL << 23);
-    unsigned r = (unsigned)t;
-    if (a >= (1151ULL << 52) || t >= (255ULL << 23)) r = 0x7f800000u;  // overflow -> inf
-    if (a < (897ULL << 52)) r = 0u;                                    // below normal floats -> 0
-    if (a > 0x7ff0000000000000ULL) r = 0x7fc00000u;                     // NaN
+    const unsigned h = (unsigned)__double2hiint(d), l = (unsigned)__double2loint(d);
+    const unsigned s = h & 0x80000000u, ah = h & 0x7fffffffu;
+    // (wraps around below the normal float range; the underflow rule is applied last)
+    const unsigned t = (((ah - (896u << 20)) << 3) | (l >> 29)) + ((l >> 28) & 1u);
+    unsigned r = t;
+    if (ah >= (1151u << 20) || t >= (255u << 23)) r = 0x7f800000u;             // overflow -> inf
+    if (ah < (897u << 20)) r = 0u;                                               // below normal floats -> 0
+    if (ah > 0x7ff00000u || (ah == 0x7ff00000u && l != 0u)) r = 0x7fc00000u;     // NaN
     return __uint_as_float(s | r);
 }
 
@@ -185,13 +187,12 @@ __device__ __forceinline__ float d2f_int(double d) {
 // truncated to 24 significant bits (exact in float), lo the remaining 29 bits
 // rounded to a float.  Outside the normal float range: (d2f_int(d), 0).
 __device__ __forceinline__ float2 d2ff_int(double d) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-    const unsigned long long a = u & 0x7fffffffffffffffULL;
-    const unsigned s = (unsigned)(u >> 32) & 0x80000000u;
-    const unsigned e = (unsigned)(a >> 52);
-    const bool normal = a >= (897ULL << 52) && a < (1151ULL << 52);
-    float hi = __uint_as_float(s | (unsigned)((a >> 29) - (896ULL << 23)));
-    const unsigned mlo = (unsigned)(a & 0x1fffffffULL);               // d - hi = mlo * 2^(e - 1075)
+    const unsigned h = (unsigned)__double2hiint(d), l = (unsigned)__double2loint(d);
+    const unsigned s = h & 0x80000000u, ah = h & 0x7fffffffu;
+    const unsigned e = ah >> 20;
+    const bool normal = ah >= (897u << 20) && ah < (1151u << 20);
+    float hi = __uint_as_float(s | (((ah - (896u << 20)) << 3) | (l >> 29)));
+    const unsigned mlo = l & 0x1fffffffu;                                        // d - hi = mlo * 2^(e - 1075)
     float lo = __uint2float_rn(mlo) * __uint_as_float(((e > 948u ? e : 949u) - 948u) << 23);
     lo = __uint_as_float(__float_as_uint(lo) | s);
     if (e <= 948u) lo = 0.0f;

@@ -44,7 +44,11 @@ void launch_f32pair_to_abi(const float4* in, long in_stride, double2* out, long 
 
 // The multi-RHS FP32 stencil alone (stencil32.cu): out = A in for the n_a
 // vectors of in_a, A^dagger in for the n_d vectors of in_d; FP32 pair layout,
-// vstride float4 between vectors; n_a + n_d <= 24.
+// vstride float4 between vectors; n_a + n_d <= 24.  With scale set (the
+// step scalars of an outer recurrence, [rhs][kScalars]) output vector i of
+// A is multiplied by scale[i][kScN] (1/n_j) and of A^dagger by
+// scale[i][kScM] (1/m_j), in FP32: the application A v_j, A^dagger w_j of
+// the unnormalised basis.
 struct Stencil32Set {
     const float4* in_a;
     const float4* in_d;
@@ -52,6 +56,7 @@ struct Stencil32Set {
     float4* out_d;
     long vstride;
     int n_a, n_d;
+    const double2* scale;
 };
 void launch_stencil32(const void* U32, const Geom& g, const Stencil32Set& s, double kappa, double mu,
                       cudaStream_t st);
@@ -78,6 +83,7 @@ struct Outer {
     double2* P;      // left vectors p_j, ring [rhs][3][N] (two-sided)
     float4* q32;     // FP32 copy of the newest q, [rhs][6][V] pair layout (f32_pair_index)
     float4* p32;     // FP32 copy of the newest p, [rhs][6][V]
+    float4* s32;     // FP32 stencil output of the step, (A q_j)/n_j then (A^dag p_j)/m_j: [side][rhs][6][V]
     dfc* qdf;        // two-float copy of the newest q, [rhs][N]
     dfc* pdf;        // two-float copy of the newest p, [rhs][N]
     double2* alpha;  // H(j,j), [rhs][k]
@@ -162,15 +168,32 @@ constexpr int kStatusRhi = 3;         // RHi did not converge / singular pivot
 constexpr int kStatusLU = 4;          // singular p H_k
 constexpr int kStatusConverged = 5;   // adaptive k: frozen at its converged size (skipped by the kernels)
 constexpr int kStatusInnerBreakdown = 6;  // inner (two-sided) Lanczos on H_k': zero beta or delta
+constexpr int kStatusTimeout = 7;     // a bounded wait of a streaming kernel ran out (copies never landed)
+
+// First failure of an RHS wins (a later one does not overwrite it).
+__device__ inline void mark_failed(const Outer& o, int rhs, int code) { atomicCAS(o.status + rhs, kStatusOK, code); }
 
 // Copy modes for the next stencil's input: none, FP32, two-float.
 constexpr int kCopyNone = 0, kCopy32 = 1, kCopyDF = 2;
 // keep_status: the second pass of NK_DOUBLE_PASS (a failure of the first pass stays)
 void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep_status = false);
-// Fused stencil + first half of step j; precision 32 (FP32, the multi-RHS
-// kernel of stencil32.cu), 48 (two-float) or 64 (FP64) (dslash.cu).
-void launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
-                         double kappa, double mu, cudaStream_t st);
+// Stencil + first half of step j; precision 32 (FP32, the multi-RHS stencil
+// of stencil32.cu, then the FP64 step-1 kernel of lanczos.cu; fused with a
+// two-float epilogue in the two-float recurrence), 48 (two-float) or 64
+// (FP64) (dslash.cu).  Returns the number of kernels launched.
+int launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
+                        double kappa, double mu, cudaStream_t st);
+// The FP32 steps of an FP64 recurrence (precision 32 before o.ring_from, with
+// o.s32): the multi-RHS FP32 stencil, which leaves s = (A q_j)/n_j and
+// t = (A^dag p_j)/m_j in o.s32 (dslash.cu), then the first half of outer step
+// j in FP64 (lanczos.cu).
+bool split_fp32_step(int precision, const Outer& o, int j);
+void launch_stencil32_step(const void* U32, const Geom& g, const Outer& o, int j, double kappa, double mu,
+                           cudaStream_t st);
+void launch_outer_step1(const Outer& o, int j, cudaStream_t st);
+void lanczos_init_attributes();   // dynamic shared memory above 48 KB (outside capture)
+int stream_ctas_per_sm();         // CTAs of the streaming step kernels per SM
+int stream_tile_sites();          // sites per tile of the streaming step kernels
 void launch_stencil32_step1(const void* U32, const Geom& g, const Outer& o, int j, double kappa, double mu,
                             cudaStream_t st);
 int dslash_step1_blocks(const Geom& g, int threads);

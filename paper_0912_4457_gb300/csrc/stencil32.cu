@@ -18,9 +18,11 @@
 // each hop's nine elements are five float4 (the tenth element is padding).
 //
 // Two kernels share the site loop: k_stencil32 stores FP32 outputs (the
-// stencil alone, nk_stencil32_dev and nk_dslash_dev), k_stencil32_step1 runs
-// the first half of outer step j on the output (lanczos.cu describes the
-// unnormalised basis):
+// stencil alone, nk_stencil32_dev and nk_dslash_dev, and the stencil of the
+// FP32 steps of an FP64 recurrence, whose step 1 then runs as a streaming
+// FP64 kernel in lanczos.cu), k_stencil32_step1 runs the first half of outer
+// step j of the optional two-float recurrence on the output (lanczos.cu
+// describes the unnormalised basis):
 //   side 0: r = (A q_j) / n_j - (c_{j-1}/n_{j-1}) q_{j-1} -> q_{j+1},
 //           H(j,j) = (p_j^dag r) / m_j^*  (Hermitian: Re(q_j^dag r) / n_j),
 //   side 1: l = (A^dag p_j) / m_j - (beta^*_{j-1}/m_{j-1}) p_{j-1} -> p_{j+1},
@@ -199,6 +201,17 @@ __global__ void __launch_bounds__(384, 2) k_stencil32(const float2* __restrict__
         float2 o[4][3];
         s32_site(vec_in(v), g.V, site, S, side, kappa, emu, emu_inv, o);
         if (site0 + (int)threadIdx.x >= g.V) continue;
+        if (s.scale) {   // A v_j = (A q_j) / n_j (A^dagger w_j = (A^dagger p_j) / m_j), in FP32
+            const double2 z = s.scale[(size_t)vi * kScalars + (side ? kScM : kScN)];
+            const float2 f = make_float2(d2f_int(z.x), d2f_int(z.y));
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float2 w = o[sp][a];
+                    o[sp][a] = make_float2(w.x * f.x - w.y * f.y, w.x * f.y + w.y * f.x);
+                }
+        }
         float4* out = (side ? s.out_d : s.out_a) + (size_t)vi * s.vstride;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
