@@ -184,7 +184,7 @@ __device__ __forceinline__ void step2_finish(const Outer& o, int rhs, int j, dou
 constexpr int kTile = 32;                       // sites per tile = lanes of a warp
 constexpr int kStreamWarps = 6;                 // one per component pair
 constexpr int kStreamThreads = 32 * kStreamWarps;
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kRowBytes = kTile * 16;           // one row of a tile: kTile 16-byte elements
 constexpr int kMaxWarpRows = 8;                 // rows of one warp's stage, at most
 
@@ -573,12 +573,15 @@ __global__ void __launch_bounds__(kThreads) k_lift(Outer o, const double2* __res
     const double2* cr = cp + (size_t)rhs * o.k;
     const double2* Qr = o.Q + (size_t)rhs * o.qcols * o.N;
     const int ku = kused[rhs];
+    // two FMA per real part (`acc += a * b - c * d` would be a multiply, a fused
+    // multiply-add and an add on the FP64 pipe)
     double2 acc = mk(0.0, 0.0);
+#pragma unroll 4
     for (int j = 0; j < ku; ++j) {
-        double2 cj = __ldg(cr + j);
-        double2 v = Qr[(size_t)j * o.N + i];
-        acc.x += cj.x * v.x - cj.y * v.y;
-        acc.y += cj.x * v.y + cj.y * v.x;
+        const double2 cj = __ldg(cr + j);
+        const double2 v = Qr[(size_t)j * o.N + i];
+        acc.x = fma(cj.x, v.x, fma(neg_bits(cj.y), v.y, acc.x));
+        acc.y = fma(cj.x, v.y, fma(cj.y, v.x, acc.y));
     }
     yo[i] = acc;
 }

@@ -11,6 +11,12 @@
 
 namespace nk {
 
+// a * b + c with one rounding (FFMA / DFMA): the stencil's sums are written as
+// chains of these, since `x += a * b - c * d` compiles to a multiply, a fused
+// multiply-add and an add -- three instructions for two products
+__device__ __forceinline__ float mac(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mac(double a, double b, double c) { return fma(a, b, c); }
+
 // i * z and -i * z
 template <typename T> __device__ __forceinline__ T mul_i(T z) { T r; r.x = -z.y; r.y = z.x; return r; }
 template <typename T> __device__ __forceinline__ T mul_mi(T z) { T r; r.x = z.y; r.y = -z.x; return r; }
@@ -31,8 +37,8 @@ __device__ __forceinline__ void hop_regs(typename C2<R>::T acc[4][3], const type
         else if (NU == 1) { c0 = neg(psi[3][a]); c1 = psi[2][a]; }
         else if (NU == 2) { c0 = mul_mi(psi[2][a]); c1 = mul_i(psi[3][a]); }
         else { c0 = psi[2][a]; c1 = psi[3][a]; }
-        h0[a].x = psi[0][a].x + s * c0.x; h0[a].y = psi[0][a].y + s * c0.y;
-        h1[a].x = psi[1][a].x + s * c1.x; h1[a].y = psi[1][a].y + s * c1.y;
+        h0[a].x = mac(s, c0.x, psi[0][a].x); h0[a].y = mac(s, c0.y, psi[0][a].y);
+        h1[a].x = mac(s, c1.x, psi[1][a].x); h1[a].y = mac(s, c1.y, psi[1][a].y);
     }
     const R ws = w * s;
 #pragma unroll
@@ -42,19 +48,21 @@ __device__ __forceinline__ void hop_regs(typename C2<R>::T acc[4][3], const type
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const T e = DAG ? u[b][a] : u[a][b];
-            R ey = DAG ? -e.y : e.y;
-            x0.x += e.x * h0[b].x - ey * h0[b].y; x0.y += e.x * h0[b].y + ey * h0[b].x;
-            x1.x += e.x * h1[b].x - ey * h1[b].y; x1.y += e.x * h1[b].y + ey * h1[b].x;
+            const R ey = DAG ? -e.y : e.y;
+            x0.x = mac(e.x, h0[b].x, x0.x); x0.x = mac(-ey, h0[b].y, x0.x);
+            x0.y = mac(e.x, h0[b].y, x0.y); x0.y = mac(ey, h0[b].x, x0.y);
+            x1.x = mac(e.x, h1[b].x, x1.x); x1.x = mac(-ey, h1[b].y, x1.x);
+            x1.y = mac(e.x, h1[b].y, x1.y); x1.y = mac(ey, h1[b].x, x1.y);
         }
-        acc[0][a].x += w * x0.x; acc[0][a].y += w * x0.y;
-        acc[1][a].x += w * x1.x; acc[1][a].y += w * x1.y;
+        acc[0][a].x = mac(w, x0.x, acc[0][a].x); acc[0][a].y = mac(w, x0.y, acc[0][a].y);
+        acc[1][a].x = mac(w, x1.x, acc[1][a].x); acc[1][a].y = mac(w, x1.y, acc[1][a].y);
         T b0, b1;  // (B_nu m)_0, _1
         if (NU == 0) { b0 = mul_i(x1); b1 = mul_i(x0); }
         else if (NU == 1) { b0 = x1; b1 = neg(x0); }
         else if (NU == 2) { b0 = mul_i(x0); b1 = mul_mi(x1); }
         else { b0 = x0; b1 = x1; }
-        acc[2][a].x += ws * b0.x; acc[2][a].y += ws * b0.y;
-        acc[3][a].x += ws * b1.x; acc[3][a].y += ws * b1.y;
+        acc[2][a].x = mac(ws, b0.x, acc[2][a].x); acc[2][a].y = mac(ws, b0.y, acc[2][a].y);
+        acc[3][a].x = mac(ws, b1.x, acc[3][a].x); acc[3][a].y = mac(ws, b1.y, acc[3][a].y);
     }
 }
 
