@@ -682,10 +682,27 @@ static void launch_step1_t(const T* U, const Geom& g, const Outer& o, int j, R k
         launch_step1_cs<R, T, 1>(grid, dim3(threads, 1), U, g, o2, j, kappa, emu, emu_inv, qin, qs, pin, ps, st);
 }
 
-bool split_fp32_step(int precision, const Outer& o, int j) { return precision == 32 && j < o.ring_from && o.s32; }
+bool split_step(int precision, const Outer& o, int j) {
+    return j < o.ring_from && ((precision == 32 && o.s32) || (precision == 48 && o.s64));
+}
 
-void launch_stencil32_step(const void* U32, const Geom& g, const Outer& o, int j, double kappa, double mu,
-                           cudaStream_t st) {
+void launch_stencil_step(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
+                         double mu, cudaStream_t st) {
+    const int n_d = (o.two_sided && j < o.k - 1) ? o.n_rhs : 0;   // the last step needs no new left vector
+    if (precision == 48) {
+        StencilDfSet s;
+        s.in_a = ring_q(o, 0, j);
+        s.in_d = o.two_sided ? ring_p(o, 0, j) : nullptr;
+        s.in_stride = 3 * o.N;   // rings [rhs][3][N]
+        s.out_a = o.s64;
+        s.out_d = o.s64 + (size_t)o.n_rhs * o.N;
+        s.out_stride = o.N;
+        s.n_a = o.n_rhs;
+        s.n_d = n_d;
+        s.scale = o.sc;
+        launch_stencil_df(U, g, s, kappa, mu, st);
+        return;
+    }
     const long vs = o.N / 2;   // float4 per vector
     Stencil32Set s;
     s.in_a = o.q32;
@@ -694,18 +711,18 @@ void launch_stencil32_step(const void* U32, const Geom& g, const Outer& o, int j
     s.out_d = o.s32 + (size_t)o.n_rhs * vs;
     s.vstride = vs;
     s.n_a = o.n_rhs;
-    s.n_d = (o.two_sided && j < o.k - 1) ? o.n_rhs : 0;   // the last step needs no new left vector
+    s.n_d = n_d;
     s.scale = o.sc;
-    launch_stencil32(U32, g, s, kappa, mu, st);
+    launch_stencil32(U, g, s, kappa, mu, st);
 }
 
 int launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
                         double mu, cudaStream_t st) {
-    if (split_fp32_step(precision, o, j)) {
-        // FP64 recurrence: the multi-RHS FP32 stencil leaves (A q_j)/n_j and
-        // (A^dag p_j)/m_j in s32, a streaming FP64 kernel runs step 1 on them
-        launch_stencil32_step(U, g, o, j, kappa, mu, st);
-        launch_outer_step1(o, j, st);
+    if (split_step(precision, o, j)) {
+        // FP64 recurrence: the multi-RHS stencil leaves (A q_j)/n_j and
+        // (A^dag p_j)/m_j in s32 / s64, a streaming FP64 kernel runs step 1 on them
+        launch_stencil_step(precision, U, g, o, j, kappa, mu, st);
+        launch_outer_step1(o, j, precision == 48, st);
         return 2;
     }
     if (precision == 32) {

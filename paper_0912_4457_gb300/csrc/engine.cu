@@ -216,6 +216,7 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.q32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);    // pair layout: N / 2 float4 per RHS
     if (two_sided) o.p32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);
     if (mixed) o.s32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs * (two_sided ? 2 : 1));
+    if (mixed) o.s64 = (double2*)take(vec * n_rhs * (two_sided ? 2 : 1));
     o.qdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     if (two_sided) o.pdf = (nk::dfc*)take((size_t)N * 16 * n_rhs);
     o.q_df_from = 1 << 30;
@@ -418,10 +419,10 @@ void enqueue_outer_steps(nk_ctx* c, const nk::Outer& o, const Schedule& s, int j
         const int prec = s.prec(j);
         const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
         const int cls = prec == 64 ? NK_CLASS_DSLASH64 : (prec == 48 ? NK_CLASS_DSLASH_DF : NK_CLASS_DSLASH);
-        if (nk::split_fp32_step(prec, o, j)) {
+        if (nk::split_step(prec, o, j)) {
             // the stencil, then the FP64 step-1 kernel, timed with the FP64 recurrence
-            L.run(NK_CLASS_DSLASH, 1, [&] { nk::launch_stencil32_step(U, g, o, j, kap, c->mu, st); });
-            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step1(o, j, st); });
+            L.run(cls, 1, [&] { nk::launch_stencil_step(prec, U, g, o, j, kap, c->mu, st); });
+            L.run(NK_CLASS_STEP2, 1, [&] { nk::launch_outer_step1(o, j, prec == 48, st); });
         } else {
             L.run_counted(cls, [&] { return nk::launch_dslash_step1(prec, U, g, o, j, kap, c->mu, st); });
         }
@@ -1540,15 +1541,26 @@ int nk_dslash_dev(nk_ctx* c, const double* in_dev, double* out_dev, int n_vec, i
     double2* out_soa = (double2*)((char*)c->staging.p + align_up(sizeof(double2) * N * n_vec));
     float2* in32 = (float2*)((char*)out_soa + align_up(sizeof(double2) * N * n_vec));
     nk::launch_abi_to_soa((const double2*)in_dev, N, in_soa, N, c->V, n_vec, st);
+    if (precision == 48) {
+        // the multi-RHS two-float stencil of the solver's early steps
+        nk::launch_to_df(in_soa, N, (nk::dfc*)in32, N, N, n_vec, st);
+        nk::StencilDfSet sd;
+        sd.in_a = sd.in_d = (const nk::dfc*)in32;
+        sd.in_stride = N;
+        sd.out_a = sd.out_d = out_soa;
+        sd.out_stride = N;
+        sd.n_a = dagger ? 0 : n_vec;
+        sd.n_d = dagger ? n_vec : 0;
+        sd.scale = nullptr;
+        nk::launch_stencil_df(c->Udf, geom_of(c), sd, kappa_of(c), c->mu, st);
+        nk::launch_soa_to_abi(out_soa, N, (double2*)out_dev, N, nullptr, 0, c->V, n_vec, st);
+        NK_CUDA(c, cudaGetLastError());
+        return NK_OK;
+    }
     nk::DslashSet s0, s1;
     std::memset(&s0, 0, sizeof(s0));
     std::memset(&s1, 0, sizeof(s1));
-    if (precision == 48) {
-        nk::launch_to_df(in_soa, N, (nk::dfc*)in32, N, N, n_vec, st);
-        s0.in = in32;
-    } else {
-        s0.in = in_soa;
-    }
+    s0.in = in_soa;
     s0.in_stride = N;
     s0.out = out_soa;
     s0.out_stride = N;

@@ -1133,6 +1133,7 @@ void init_kernel_attributes() {
     cudaFuncSetAttribute(k_rhi<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(k_rhi<double2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     stencil32_init_attributes();
+    stencil_df_init_attributes();
     lanczos_init_attributes();
 
 }

@@ -186,7 +186,9 @@ constexpr int kStreamWarps = 6;                 // one per component pair
 constexpr int kStreamThreads = 32 * kStreamWarps;
 constexpr int kStages = 2;
 constexpr int kRowBytes = kTile * 16;           // one row of a tile: kTile 16-byte elements
-constexpr int kMaxWarpRows = 8;                 // rows of one warp's stage, at most
+constexpr int kStep2Rows = 8;                   // rows of one warp's stage: step 2
+constexpr int kStep1Rows = 8;                   // step 1 after the FP32 stencil
+constexpr int kStep1Rows64 = 10;                // step 1 after the two-float stencil (FP64 s, t)
 
 // One operand vector of a streaming kernel (row r of V 16-byte elements at
 // base + r V 16 bytes): rows = 2 for an FP64 vector (warp w reads rows 2w,
@@ -227,7 +229,7 @@ __device__ __forceinline__ void issue_warp_tile(const TileStream (&ts)[NS], char
 // RHS): f(stage, s0, n) on each tile once its copies have landed.  Returns
 // false if a wait ran out (the warp's copies still in flight are then waited
 // for, bounded, before returning).
-template <int NS, typename F>
+template <int ROWS, int NS, typename F>
 __device__ __forceinline__ bool stream_tiles(const Outer& o, const TileStream (&ts)[NS], F&& f) {
     extern __shared__ __align__(128) char smem[];
     __shared__ uint64_t bar[kStreamWarps][kStages];
@@ -236,7 +238,7 @@ __device__ __forceinline__ bool stream_tiles(const Outer& o, const TileStream (&
     const unsigned s_lo = (unsigned)((unsigned long long)blockIdx.x * V / (unsigned)o.nblk);
     const unsigned s_hi = (unsigned)((unsigned long long)(blockIdx.x + 1) * V / (unsigned)o.nblk);
     const int ntiles = (int)((s_hi - s_lo + kTile - 1) / kTile);
-    const size_t stage_bytes = (size_t)kMaxWarpRows * kRowBytes;
+    const size_t stage_bytes = (size_t)ROWS * kRowBytes;   // ROWS >= the streams' rows
     char* mine = smem + (size_t)w * kStages * stage_bytes;
     uint64_t* mbar = bar[w];
     if (lane == 0) {
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_step2(Outer o, int j, int co
     const double2 nc3 = neg_bits(c3), nc4 = neg_bits(c4);
     const int cp = threadIdx.x >> 5, sl = threadIdx.x & 31;
     Dot3 acc = {0.0, 0.0, 0.0};
-    const bool ok = stream_tiles(o, ts, [&](const char* stage, unsigned s0, unsigned n) {
+    const bool ok = stream_tiles<kStep2Rows>(o, ts, [&](const char* stage, unsigned s0, unsigned n) {
         if ((unsigned)sl >= n) return;
         const double2* sv = reinterpret_cast<const double2*>(stage);
         double2 rv[2], lv[2];
@@ -365,21 +367,24 @@ __global__ void __launch_bounds__(kStreamThreads) k_step2(Outer o, int j, int co
     step2_finish<TS>(o, rhs, j, tot, sh);
 }
 
-// FP64 step 1 of the FP32-stencil steps of an FP64 recurrence, after the
-// multi-RHS FP32 stencil has left s = (A q_j)/n_j and t = (A^dag p_j)/m_j
-// (FP32, pair layout) in o.s32:
+// FP64 step 1 of the FP32- and two-float-stencil steps of an FP64
+// recurrence, after the multi-RHS stencil has left s = (A q_j)/n_j and
+// t = (A^dag p_j)/m_j in o.s32 (FP32, pair layout) or, S64, in o.s64 (FP64
+// from the two-float stencil):
 //   r = s - (c_{j-1}/n_{j-1}) q_{j-1} -> q_{j+1},
 //   l = t - (beta^*_{j-1}/m_{j-1}) p_{j-1} -> p_{j+1}   (two-sided, not at the last step),
 //   H(j,j) = (p_j^dag r) / m_j^*  (Hermitian: Re(q_j^dag r) / n_j),
-// the stencil output entering the FP64 arithmetic exactly (FP32 -> FP64 on
-// the integer pipe).  The finishing block forms H(j,j) and the step-2
+// an FP32 stencil output entering the FP64 arithmetic exactly (FP32 -> FP64
+// on the integer pipe).  The finishing block forms H(j,j) and the step-2
 // scalars.  PASS2 (the second pass of NK_DOUBLE_PASS) also accumulates
-// y += c'_j q_j.  Stage rows of warp w (components 2w + h): s 0, q_{j-1} 1 + h,
-// dot vector (p_j, or q_j Hermitian) 3 + h, then two-sided and not at the
-// last step t 5 and p_{j-1} 6 + h.
-template <bool TS, bool PASS2>
+// y += c'_j q_j.  Stage rows of warp w (components 2w + h), with
+// F = 1 (FP32 s: one row of pairs) or 2 (FP64 s: rows h): s 0 .. F - 1,
+// q_{j-1} F + h, dot vector (p_j, or q_j Hermitian) F + 2 + h, then two-sided
+// and not at the last step t F + 4 .., p_{j-1} 2 F + 4 + h.
+template <bool TS, bool PASS2, bool S64>
 __global__ void __launch_bounds__(kStreamThreads) k_step1(Outer o, int j) {
     __shared__ double2 sh[33];
+    constexpr int F = S64 ? 2 : 1;
     const int rhs = blockIdx.y;
     if (o.status[rhs] != kStatusOK) return;
     const double2* sc = o.sc + (size_t)rhs * kScalars;
@@ -387,8 +392,9 @@ __global__ void __launch_bounds__(kStreamThreads) k_step1(Outer o, int j) {
     const unsigned V = (unsigned)(o.N / 12);
     const int jp = j > 0 ? j - 1 : j;   // c1 = 0 at j = 0
     const bool left = TS && j < o.k - 1;   // the last step makes no new left vector
-    const float4* s_in = o.s32 + (size_t)rhs * 6 * V;
-    const float4* t_in = o.s32 + (size_t)(o.n_rhs + rhs) * 6 * V;
+    const char* s_in = S64 ? (const char*)(o.s64 + (size_t)rhs * o.N) : (const char*)(o.s32 + (size_t)rhs * 6 * V);
+    const char* t_in = S64 ? (const char*)(o.s64 + (size_t)(o.n_rhs + rhs) * o.N)
+                           : (const char*)(o.s32 + (size_t)(o.n_rhs + rhs) * 6 * V);
     const double2* qprev = outer_q(o, rhs, jp);
     const double2* pprev = TS ? outer_p(o, rhs, jp) : nullptr;
     const double2* dotv = TS ? outer_p(o, rhs, j) : outer_q(o, rhs, j);
@@ -397,32 +403,47 @@ __global__ void __launch_bounds__(kStreamThreads) k_step1(Outer o, int j) {
     double2* __restrict__ yacc = PASS2 ? o.y + (size_t)rhs * o.N : nullptr;
     const double2 cpj = PASS2 ? o.cp[(size_t)rhs * o.k + j] : mk(0.0, 0.0);
     const double2* __restrict__ qj = outer_q(o, rhs, j);
-    const TileStream ts[5] = {{(const char*)s_in, 1}, {(const char*)qprev, 2}, {(const char*)dotv, 2},
-                              {(const char*)t_in, left ? 1 : 0}, {(const char*)pprev, left ? 2 : 0}};
+    const TileStream ts[5] = {{s_in, F}, {(const char*)qprev, 2}, {(const char*)dotv, 2},
+                              {t_in, left ? F : 0}, {(const char*)pprev, left ? 2 : 0}};
     const double2 nc1 = neg_bits(c1), nc1l = neg_bits(c1l), ncpj = neg_bits(cpj);
     const int cp = threadIdx.x >> 5, sl = threadIdx.x & 31;
     Dot3 acc = {0.0, 0.0, 0.0};
-    const bool ok = stream_tiles(o, ts, [&](const char* stage, unsigned s0, unsigned n) {
+    const bool ok = stream_tiles<S64 ? kStep1Rows64 : kStep1Rows>(o, ts, [&](const char* stage, unsigned s0,
+                                                                                unsigned n) {
         if ((unsigned)sl >= n) return;
-        const float4 sv4 = reinterpret_cast<const float4*>(stage)[sl];
         const double2* sv = reinterpret_cast<const double2*>(stage);
-        float4 tv4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (left) tv4 = reinterpret_cast<const float4*>(stage)[5 * kTile + sl];
+        const float4* sf = reinterpret_cast<const float4*>(stage);
+        float4 sv4 = make_float4(0.f, 0.f, 0.f, 0.f), tv4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!S64) {
+            sv4 = sf[sl];
+            if (left) tv4 = sf[(F + 4) * kTile + sl];
+        }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = 2 * cp + h;
             const size_t e = (size_t)c * V + s0 + sl;
-            const float2 s2 = h ? make_float2(sv4.z, sv4.w) : make_float2(sv4.x, sv4.y);
-            double2 rr = mk(f2d_int(s2.x), f2d_int(s2.y));
-            const double2 qv = sv[(1 + h) * kTile + sl];
+            double2 rr;
+            if (S64) {
+                rr = sv[h * kTile + sl];
+            } else {
+                const float2 s2 = h ? make_float2(sv4.z, sv4.w) : make_float2(sv4.x, sv4.y);
+                rr = mk(f2d_int(s2.x), f2d_int(s2.y));
+            }
+            const double2 qv = sv[(F + h) * kTile + sl];
             rr = TS ? cfma_sub(rr, c1, nc1, qv) : mk(fma(nc1.x, qv.x, rr.x), fma(nc1.x, qv.y, rr.y));
             rn[e] = rr;
-            const double2 d = sv[(3 + h) * kTile + sl];
+            const double2 d = sv[(F + 2 + h) * kTile + sl];
             if (TS) dot3_add(acc, d, rr);   // conj(d) r
             else acc.re = fma(d.x, rr.x, fma(d.y, rr.y, acc.re));
             if (left) {
-                const float2 t2 = h ? make_float2(tv4.z, tv4.w) : make_float2(tv4.x, tv4.y);
-                ln[e] = cfma_sub(mk(f2d_int(t2.x), f2d_int(t2.y)), c1l, nc1l, sv[(6 + h) * kTile + sl]);
+                double2 tt;
+                if (S64) {
+                    tt = sv[(F + 4 + h) * kTile + sl];
+                } else {
+                    const float2 t2 = h ? make_float2(tv4.z, tv4.w) : make_float2(tv4.x, tv4.y);
+                    tt = mk(f2d_int(t2.x), f2d_int(t2.y));
+                }
+                ln[e] = cfma_sub(tt, c1l, nc1l, sv[(2 * F + 4 + h) * kTile + sl]);
             }
             if (PASS2) yacc[e] = cfma_add(yacc[e], cpj, ncpj, qj[e]);
         }
@@ -449,8 +470,8 @@ __global__ void __launch_bounds__(kStreamThreads) k_step1(Outer o, int j) {
     }
 }
 
-size_t step2_smem(bool) { return (size_t)kStreamWarps * kStages * kMaxWarpRows * kRowBytes; }
-size_t step1_smem(bool) { return (size_t)kStreamWarps * kStages * kMaxWarpRows * kRowBytes; }
+size_t step2_smem() { return (size_t)kStreamWarps * kStages * kStep2Rows * kRowBytes; }
+size_t step1_smem(bool s64) { return (size_t)kStreamWarps * kStages * (s64 ? kStep1Rows64 : kStep1Rows) * kRowBytes; }
 
 // Step 2 of the late (FP32-stencil) steps of the mixed schedule in two-float
 // arithmetic on the FP32 pipe, on the two-float rings: r and l (left in ring slot j + 1
@@ -634,17 +655,19 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep
     k_init<<<grid, kThreads, 0, st>>>(o, copy_mode);
 }
 
-void launch_outer_step1(const Outer& o, int j, cudaStream_t st) {
+void launch_outer_step1(const Outer& o, int j, bool s64, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
     const bool pass2 = o.y != nullptr;
-    const size_t sm = step1_smem(o.two_sided != 0);
+    const size_t sm = step1_smem(s64);
+#define NK_STEP1(TS_, P2_, S_) k_step1<TS_, P2_, S_><<<grid, kStreamThreads, sm, st>>>(o, j)
     if (o.two_sided) {
-        if (pass2) k_step1<true, true><<<grid, kStreamThreads, sm, st>>>(o, j);
-        else k_step1<true, false><<<grid, kStreamThreads, sm, st>>>(o, j);
+        if (pass2) { if (s64) NK_STEP1(true, true, true); else NK_STEP1(true, true, false); }
+        else { if (s64) NK_STEP1(true, false, true); else NK_STEP1(true, false, false); }
     } else {
-        if (pass2) k_step1<false, true><<<grid, kStreamThreads, sm, st>>>(o, j);
-        else k_step1<false, false><<<grid, kStreamThreads, sm, st>>>(o, j);
+        if (pass2) { if (s64) NK_STEP1(false, true, true); else NK_STEP1(false, true, false); }
+        else { if (s64) NK_STEP1(false, false, true); else NK_STEP1(false, false, false); }
     }
+#undef NK_STEP1
 }
 
 // CTAs of the two-sided step-2 kernel that fit one SM (its stage buffers
@@ -656,7 +679,7 @@ int stream_ctas_per_sm() {
     if (dev < 0 || dev >= 64) dev = 0;
     if (!cached[dev]) {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2<true>, kStreamThreads, step2_smem(true)) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step2<true>, kStreamThreads, step2_smem()) !=
                 cudaSuccess || n < 1) {
             cudaGetLastError();
             return 1;   // attributes not set yet: not cached
@@ -671,26 +694,28 @@ int stream_tile_sites() { return kTile; }
 void lanczos_init_attributes() {
     // dynamic shared memory above 48 KB for the stage buffers of the streaming
     // kernels, and the largest shared-memory carveout so that several CTAs fit an SM
-    cudaFuncSetAttribute(k_step2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step2_smem(true));
-    cudaFuncSetAttribute(k_step2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step2_smem(false));
-    cudaFuncSetAttribute(k_step1<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(true));
-    cudaFuncSetAttribute(k_step1<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(true));
-    cudaFuncSetAttribute(k_step1<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(false));
-    cudaFuncSetAttribute(k_step1<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step1_smem(false));
     const int carve = cudaSharedmemCarveoutMaxShared;
-    cudaFuncSetAttribute(k_step2<true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    cudaFuncSetAttribute(k_step2<false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    cudaFuncSetAttribute(k_step1<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    cudaFuncSetAttribute(k_step1<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    cudaFuncSetAttribute(k_step1<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    cudaFuncSetAttribute(k_step1<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+#define NK_ATTR(K_, SM_)                                                                    \
+    cudaFuncSetAttribute(K_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SM_));     \
+    cudaFuncSetAttribute(K_, cudaFuncAttributePreferredSharedMemoryCarveout, carve)
+    NK_ATTR(k_step2<true>, step2_smem());
+    NK_ATTR(k_step2<false>, step2_smem());
+    NK_ATTR((k_step1<true, true, false>), step1_smem(false));
+    NK_ATTR((k_step1<true, false, false>), step1_smem(false));
+    NK_ATTR((k_step1<false, true, false>), step1_smem(false));
+    NK_ATTR((k_step1<false, false, false>), step1_smem(false));
+    NK_ATTR((k_step1<true, true, true>), step1_smem(true));
+    NK_ATTR((k_step1<true, false, true>), step1_smem(true));
+    NK_ATTR((k_step1<false, true, true>), step1_smem(true));
+    NK_ATTR((k_step1<false, false, true>), step1_smem(true));
+#undef NK_ATTR
 }
 
 void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, bool write_ring, cudaStream_t st) {
     dim3 grid(o.nblk, o.n_rhs);
     const int wr = (write_ring && o.qr) ? 1 : 0;
     if (!ring || !o.qr) {   // FP64 step
-        const size_t sm = step2_smem(o.two_sided != 0);
+        const size_t sm = step2_smem();
         if (o.two_sided) k_step2<true><<<grid, kStreamThreads, sm, st>>>(o, j, copy_mode, wr);
         else k_step2<false><<<grid, kStreamThreads, sm, st>>>(o, j, copy_mode, wr);
     } else {

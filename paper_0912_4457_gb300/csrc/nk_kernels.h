@@ -60,6 +60,25 @@ struct Stencil32Set {
 };
 void launch_stencil32(const void* U32, const Geom& g, const Stencil32Set& s, double kappa, double mu,
                       cudaStream_t st);
+
+// The multi-RHS two-float stencil (stencil_df.cu): out = A in for the n_a
+// vectors of in_a, A^dagger in for the n_d vectors of in_d; two-float input
+// and FP64 output vectors in the layout [12][V], in_stride / out_stride
+// elements between vectors; n_a + n_d <= 24.  With scale set (the step
+// scalars, [rhs][kScalars]) output vector i of A is multiplied by
+// scale[i][kScN] and of A^dagger by scale[i][kScM] in two-float arithmetic.
+struct StencilDfSet {
+    const dfc* in_a;
+    const dfc* in_d;
+    double2* out_a;
+    double2* out_d;
+    long in_stride, out_stride;
+    int n_a, n_d;
+    const double2* scale;
+};
+void launch_stencil_df(const void* Udf, const Geom& g, const StencilDfSet& s, double kappa, double mu,
+                       cudaStream_t st);
+void stencil_df_init_attributes();   // dynamic shared memory (outside capture)
 int stencil32_sites_per_cta(int nv);
 void stencil32_init_attributes();   // dynamic shared memory above 48 KB (outside capture)
 int stencil32_blocks(const Geom& g, int nv);
@@ -84,6 +103,7 @@ struct Outer {
     float4* q32;     // FP32 copy of the newest q, [rhs][6][V] pair layout (f32_pair_index)
     float4* p32;     // FP32 copy of the newest p, [rhs][6][V]
     float4* s32;     // FP32 stencil output of the step, (A q_j)/n_j then (A^dag p_j)/m_j: [side][rhs][6][V]
+    double2* s64;    // the same from the two-float stencil, FP64: [side][rhs][12][V]
     dfc* qdf;        // two-float copy of the newest q, [rhs][N]
     dfc* pdf;        // two-float copy of the newest p, [rhs][N]
     double2* alpha;  // H(j,j), [rhs][k]
@@ -183,14 +203,15 @@ void launch_outer_init(const Outer& o, int copy_mode, cudaStream_t st, bool keep
 // (FP64) (dslash.cu).  Returns the number of kernels launched.
 int launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer& o, int j,
                         double kappa, double mu, cudaStream_t st);
-// The FP32 steps of an FP64 recurrence (precision 32 before o.ring_from, with
-// o.s32): the multi-RHS FP32 stencil, which leaves s = (A q_j)/n_j and
-// t = (A^dag p_j)/m_j in o.s32 (dslash.cu), then the first half of outer step
-// j in FP64 (lanczos.cu).
-bool split_fp32_step(int precision, const Outer& o, int j);
-void launch_stencil32_step(const void* U32, const Geom& g, const Outer& o, int j, double kappa, double mu,
-                           cudaStream_t st);
-void launch_outer_step1(const Outer& o, int j, cudaStream_t st);
+// The FP32 and two-float steps of an FP64 recurrence (precision 32 or 48
+// before o.ring_from, with o.s32 / o.s64): the multi-RHS stencil, which leaves
+// s = (A q_j)/n_j and t = (A^dag p_j)/m_j in o.s32 (FP32) or o.s64 (FP64 from
+// the two-float stencil) (dslash.cu), then the first half of outer step j in
+// FP64 (lanczos.cu).
+bool split_step(int precision, const Outer& o, int j);
+void launch_stencil_step(int precision, const void* U, const Geom& g, const Outer& o, int j, double kappa,
+                         double mu, cudaStream_t st);
+void launch_outer_step1(const Outer& o, int j, bool s64, cudaStream_t st);
 void lanczos_init_attributes();   // dynamic shared memory above 48 KB (outside capture)
 int stream_ctas_per_sm();         // CTAs of the streaming step kernels per SM
 int stream_tile_sites();          // sites per tile of the streaming step kernels
