@@ -435,7 +435,7 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
         return r
 
     if dom == "step2":
-        t1, t2 = profiled_traffic("k_step1"), profiled_traffic("k_step2")
+        t1, t2 = profiled_traffic("k_step1"), profiled_traffic("k_step2")   # the FP32-step pair
         return alu64("k_step1 / k_step2 (FP64 recurrence, operands staged by bulk copies)",
                      (24 if two else 8) * N * n_rhs,
                      {"traffic": (t1 + t2) / 2 if (t1 is not None and t2 is not None) else None,
