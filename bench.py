@@ -411,8 +411,8 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
       dslash (the multi-RHS FP32 stencil of the FP32 steps): links 288 B per
              site plus 96 B in and 96 B out per site and vector -- HBM;
       dslash_df: the two-float stencil, 1320 flops per site and vector;
-             two-float arithmetic costs 9 FP32 instructions per flop on
-             average, so its ALU peak is 152 x 128 x f_SM / 9;
+             a two-float multiply-add costs 12 FP32 lane operations for its
+             2 flops, so its ALU peak is 152 x 128 x f_SM / 6;
       lift (FP64): y += c_j q_j over k columns: 8 FP64 flops per element and
              column -- FP64 ALU;
       inner / rhi: FP64 ALU, latency bound on few SMs (not modelled).
@@ -451,11 +451,13 @@ def dominant_roofline(dom, tc, nc, w, peaks, sm_mhz):
     if dom == "dslash_df":
         flops = 1320.0 * V * nv
         tf = flops / (ms * 1e-3) / 1e12
-        peak = 152 * 128 * (sm_mhz or 2070.0) * 1e6 / 9.0 / 1e12
-        return {"kernel": "k_dslash_step1<df> (two-float stencil fused with step 1)", "bound": "alu",
+        peak = 152 * 128 * (sm_mhz or 2070.0) * 1e6 / 6.0 / 1e12
+        return {"kernel": "k_stencil_df (multi-RHS two-float stencil)", "bound": "alu",
                 "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-                "traffic": profiled_traffic("k_dslash_step1<df>"), "ms_per_launch": ms, "flops_per_launch": flops,
-                "peak_derivation": "FP32 issue rate 152 x 128 x f_SM over 9 FP32 instructions per two-float flop"}
+                "traffic": profiled_traffic("k_stencil_df"), "ms_per_launch": ms, "flops_per_launch": flops,
+                "peak_derivation": "FP32 FMA pipe 152 x 128 lanes x f_SM over the 6 FP32 lane operations per "
+                                   "two-float flop of a two-float multiply-add (TwoProd by FMA, its two cross "
+                                   "terms, TwoSum and the trailing sum: 12 operations for 2 flops)"}
     return {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": None, "traffic": None, "ms_per_launch": ms, "hbm_gbs": hbm}
 
