@@ -190,6 +190,37 @@ int nk_set_df_recurrence(nk_ctx* ctx, int j1);
 #define NK_MAX_DEFL 256
 int nk_set_deflation(nk_ctx* ctx, int m, const double* lambda, const double* R, const double* L);
 
+/* The m eigenpairs of A = gamma5 D_w(mu) of smallest |lambda|: the critical
+ * eigenpairs that LR deflation removes (App. C step 1; Sec. 3 computes them
+ * once, as an initialisation, and deflates those of smallest modulus).  A
+ * Lanczos eigensolver on the device: k steps of the FP64 recurrence of App. A
+ * (mu = 0) or App. B (two-sided) from the start vector b (HOST, ABI spinor
+ * layout, nonzero) with both bases V_k and W_k kept; the eigenvalues of the
+ * tridiagonal H_k by the QL iteration; as candidates the 2 m + 8 distinct
+ * ones nearest zero (finite-precision Lanczos repeats a converged eigenvalue:
+ * up to 3 copies form one cluster); per cluster the right (and left)
+ * eigenvectors of H_k spanning its invariant subspace (block inverse
+ * iteration) and the refined combinations of them whose last component
+ * vanishes, lifted through the bases (Ritz vectors); the true residuals
+ * |A r - theta r| / |r| and |A^dagger l - theta^* l| / |l| (FP64 stencil),
+ * and per cluster the candidate of least residual on each side.
+ * Unrestarted: the small eigenvalues need k large enough for them to
+ * converge (several hundred on the small lattices of the tests; k = 12 V
+ * exhausts the space).
+ *   k     even, >= 2 m + 2; the workspace holds 2 (k + 1) vectors of 12 V,
+ *         and 2 (48 + m) + 1 more of temporary device memory
+ *   tol   residual bound for a returned pair
+ * Returns, for the found <= m converged candidates nearest zero, in order of
+ * |theta|: lambda (HOST, 2 m doubles: re, im), R (HOST, m vectors of 12 V
+ * complex, ABI layout, |r_i| = 1), L (HOST, the same, <l_i, r_i> = 1; at
+ * mu = 0 L may be NULL, else it receives r_i), resid (HOST, m, or NULL:
+ * the larger of the right and left residuals);
+ * these are the arguments of nk_set_deflation.  NK_OK when found = m,
+ * NK_ENOTCONV when fewer converged (the found ones are returned),
+ * NK_EBREAKDOWN on a Lanczos breakdown before step k. */
+int nk_eigs_smallest(nk_ctx* ctx, const double* b, int k, int m, double tol, double* lambda, double* R, double* L,
+                     double* resid, int* found);
+
 /* Multi-level nesting (Sec. 4.5).  A solve's l argument is the size l_1 of the
  * first nested level; nk_set_nesting adds n_deeper levels below it with sizes
  * ells[0] = l_2 >= l_3 >= ... (even, >= 2; a level larger than the one above

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libnksign.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["dslash.cu", "stencil32.cu", "stencil_df.cu", "lanczos.cu", "deflate.cu", "overlap.cu", "inner.cu", "engine.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["dslash.cu", "stencil32.cu", "stencil_df.cu", "lanczos.cu", "eigen.cu", "deflate.cu", "overlap.cu", "inner.cu", "engine.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

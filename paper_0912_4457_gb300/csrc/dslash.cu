@@ -733,7 +733,7 @@ int launch_dslash_step1(int precision, const void* U, const Geom& g, const Outer
     } else {
         const long qs = (long)o.qcols * o.N;
         launch_step1_t<double, double2>((const double2*)U, g, o, j, kappa, exp(mu), exp(-mu), outer_q(o, 0, j), qs,
-                                        o.two_sided ? outer_p(o, 0, j) : nullptr, 3 * o.N, st);
+                                        o.two_sided ? outer_p(o, 0, j) : nullptr, (long)o.pcols * o.N, st);
     }
     return 1;
 }

@@ -12,6 +12,9 @@
 #include <string>
 #include <tuple>
 #include <vector>
+#include <numeric>
+
+#include "tridiag_eig.h"
 
 #include "../../include/nksign.h"
 #include "nk_kernels.h"
@@ -186,7 +189,7 @@ struct Layout {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_sided, bool double_pass,
-             const nk_launch& lc, bool mixed, const Nesting& nest = Nesting()) {
+             const nk_launch& lc, bool mixed, const Nesting& nest = Nesting(), bool full_left = false) {
     const int nblk = lc.step2_blocks;
     Layout L;
     std::memset(&L, 0, sizeof(L));
@@ -212,7 +215,8 @@ Layout carve(char* base, const Geom& g, int n_rhs, int k, int ell, bool two_side
     o.q_ring = double_pass ? 1 : 0;
     o.qcols = double_pass ? 3 : k + 1;   // single pass: k basis vectors + one scratch column
     o.Q = (double2*)take(vec * (size_t)o.qcols * n_rhs);
-    if (two_sided) o.P = (double2*)take(vec * 3 * n_rhs);
+    o.pcols = full_left ? k + 1 : 3;
+    if (two_sided) o.P = (double2*)take(vec * (size_t)o.pcols * n_rhs);
     o.q32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);    // pair layout: N / 2 float4 per RHS
     if (two_sided) o.p32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs);
     if (mixed) o.s32 = (float4*)take((size_t)N * sizeof(float2) * n_rhs * (two_sided ? 2 : 1));
@@ -1209,6 +1213,295 @@ int nk_set_deflation(nk_ctx* c, int m, const double* lambda, const double* R, co
     NK_CUDA(c, cudaMemcpy(c->defl_sgn, sg.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
     c->defl_m = m;
     c->defl_gap = gap;
+    return NK_OK;
+}
+
+// ---- eigensolver of the deflation (App. C step 1; Sec. 3) -------------------------
+// k steps of the FP64 (two-sided) Lanczos recurrence from b with both bases
+// kept, the eigenvalues of H_k by QL, the distinct ones nearest zero as
+// candidates, their eigenvectors of H_k by inverse iteration lifted through
+// the bases on the device, and the true residual of each.
+int nk_eigs_smallest(nk_ctx* c, const double* b, int k, int m, double tol, double* lambda, double* R, double* L,
+                     double* resid, int* found) {
+    if (!c || !b || !lambda || !R || !found) return NK_EINVAL;
+    *found = 0;
+    if (m < 1 || m > NK_MAX_DEFL) return fail(c, NK_EINVAL, "need 1 <= m <= NK_MAX_DEFL");
+    if (k < 2 * m + 2 || (k & 1)) return fail(c, NK_EINVAL, "k must be even and >= 2 m + 2");
+    if (!(tol > 0.0)) return fail(c, NK_EINVAL, "tol must be positive");
+    if (!c->links) return fail(c, NK_ESTATE, "no links loaded (nk_load_links)");
+    if (!c->mu_set) return fail(c, NK_ESTATE, "mu and m_w not set (nk_set_mu_mw)");
+    const bool ts = c->mu != 0.0;
+    if (ts && !L) return fail(c, NK_EINVAL, "mu != 0: L receives the left eigenvectors");
+    NK_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t st = 0;
+    const long N = c->N;
+    const Geom g = geom_of(c);
+    // the recurrence, FP64, with V_k and W_k kept
+    const nk_launch lc = launch_cfg(c, 1, ts, false);
+    Layout dry = carve(nullptr, g, 1, k, 2, ts, false, lc, false, Nesting(), true);
+    int rc = ensure(c, c->ws, dry.total);
+    if (rc) return rc;
+    Layout Lw = carve((char*)c->ws.p, g, 1, k, 2, ts, false, lc, false, Nesting(), true);
+    rc = ensure(c, c->staging, std::max(c->staging.bytes, sizeof(double2) * (size_t)N));
+    if (rc) return rc;
+    NK_CUDA(c, cudaMemcpy(c->staging.p, b, sizeof(double2) * (size_t)N, cudaMemcpyHostToDevice));
+    NK_CUDA(c, cudaMemsetAsync(Lw.o.counters, 0, sizeof(unsigned), st));
+    Launcher Lz;
+    Lz.st = st;
+    enqueue_load_sources(c, Lw.o, (const double*)c->staging.p, 1, Lz);
+    enqueue_outer(c, Lw.o, schedule_of(c, NK_FP64, k), Lz);
+    NK_CUDA(c, cudaGetLastError());
+    std::vector<double2> al(k), be(k), ga(k);
+    double xn = 0.0;
+    int status = 0;
+    NK_CUDA(c, cudaMemcpy(al.data(), Lw.o.alpha, sizeof(double2) * k, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(be.data(), Lw.o.beta, sizeof(double2) * k, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(ga.data(), Lw.o.gamma, sizeof(double2) * k, cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(&xn, Lw.o.xnorm, sizeof(double), cudaMemcpyDeviceToHost));
+    NK_CUDA(c, cudaMemcpy(&status, Lw.o.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status == nk::kStatusZeroSource) return fail(c, NK_EINVAL, "zero start vector");
+    if (status != nk::kStatusOK) return fail(c, NK_EBREAKDOWN, "Lanczos breakdown before step k");
+    // H_k: diagonal H(j,j), sub-diagonal H(j+1,j) = beta_j, super-diagonal H(j,j+1) = gamma_j
+    std::vector<nk::cplx> a(k), sub(k - 1), sup(k - 1);
+    for (int j = 0; j < k; ++j) a[j] = ts ? nk::cplx(al[j].x, al[j].y) : nk::cplx(al[j].x, 0.0);
+    for (int j = 0; j + 1 < k; ++j) {
+        sub[j] = nk::cplx(be[j].x, ts ? be[j].y : 0.0);
+        sup[j] = ts ? nk::cplx(ga[j].x, ga[j].y) : sub[j];
+    }
+    std::vector<nk::cplx> w;
+    if (!nk::tridiag_eigvals(k, a.data(), sub.data(), sup.data(), w))
+        return fail(c, NK_ENOTCONV, "QL iteration on H_k did not converge");
+    // Clusters: the 2 m + 8 distinct eigenvalues of H_k nearest zero, each
+    // with the number (up to kCopies) of its repeated values.  Floating-point
+    // Lanczos repeats a converged eigenvalue, the copies agreeing to
+    // rounding; the eigenvectors of H_k for the copies of one cluster are not
+    // individually determined, only the invariant subspace they span is.
+    std::vector<int> order(k);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return std::abs(w[x]) < std::abs(w[y]); });
+    constexpr int kCopies = 3;
+    const int n_distinct = 2 * m + 8;
+    auto same = [](nk::cplx x, nk::cplx y) { return std::abs(x - y) <= 1e-8 * std::max(1.0, std::abs(y)); };
+    std::vector<nk::cplx> reps;
+    std::vector<int> copies;
+    for (int t = 0; t < k; ++t) {
+        const nk::cplx v = w[order[t]];
+        int q = 0;
+        while (q < (int)reps.size() && !same(v, reps[q])) ++q;
+        if (q == (int)reps.size()) {
+            if (q == n_distinct) break;
+            reps.push_back(v);
+            copies.push_back(0);
+        }
+        copies[q] = std::min(copies[q] + 1, kCopies);
+    }
+    const int ncl = (int)reps.size();
+    // Candidate Ritz vectors per cluster, as coefficients in the stored,
+    // unnormalised bases: r = sum_j y_j q_j / n_j, l = sum_j z_j p_j / m_j
+    // (n_0 = m_0 = |b|, n_{j+1} = beta_j, m_{j+1} = gamma_j^*).  For a cluster
+    // of c copies: the c basis vectors of its invariant subspace (block
+    // inverse iteration) and, for each pair of them, the combination whose
+    // last component vanishes.  The residual of a Ritz vector V_k y is
+    // |beta_k e_k^T y| |v_{k+1}| (A V_k = V_k H_k + beta_k v_{k+1} e_k^T), so
+    // within the cluster's subspace that combination is the refined Ritz
+    // vector, the one of least residual.  Left vectors the same way with
+    // A^dagger W_k = W_k H_k^dagger + gamma_k^* w_{k+1} e_k^T.
+    std::vector<int> owner_r, owner_l;
+    std::vector<double2> coef_r, coef_l;
+    auto add_candidates = [&](int q, bool left, std::vector<int>& owner, std::vector<double2>& coef) {
+        std::vector<std::vector<nk::cplx>> Y;
+        nk::tridiag_eigvecs(k, a.data(), sub.data(), sup.data(), reps[q], left, copies[q], Y);
+        const int nb = (int)Y.size();
+        for (int i = 0; i < nb; ++i)
+            for (int j = i + 1; j < nb; ++j) {
+                std::vector<nk::cplx> x(k);
+                double nrm = 0.0;
+                for (int t = 0; t < k; ++t) {
+                    x[t] = Y[j][k - 1] * Y[i][t] - Y[i][k - 1] * Y[j][t];
+                    nrm += std::norm(x[t]);
+                }
+                if (!(nrm > 0.0)) continue;
+                for (nk::cplx& v : x) v /= std::sqrt(nrm);
+                Y.push_back(x);
+            }
+        for (const auto& y : Y) {
+            owner.push_back(q);
+            for (int j = 0; j < k; ++j) {
+                const nk::cplx nj = j == 0 ? nk::cplx(xn, 0.0) : (left ? std::conj(sup[j - 1]) : sub[j - 1]);
+                const nk::cplx v = y[j] / nj;
+                coef.push_back(make_double2(v.real(), v.imag()));
+            }
+        }
+    };
+    for (int q = 0; q < ncl; ++q) {
+        add_candidates(q, false, owner_r, coef_r);
+        if (ts) add_candidates(q, true, owner_l, coef_l);
+    }
+    // device: candidates in chunks of kChunk vectors, X = the lifted vectors,
+    // AX = A X (A^dagger X for the left ones), residual |AX - theta X| / |X|
+    constexpr int kChunk = 48;
+    const int max_out = std::min(m, ncl);
+    double2 *d_coef = nullptr, *d_X = nullptr, *d_AX = nullptr, *d_R = nullptr, *d_L = nullptr, *d_dot = nullptr,
+            *d_abi = nullptr;
+    auto release = [&] {
+        for (double2* p : {d_coef, d_X, d_AX, d_R, d_L, d_dot, d_abi})
+            if (p) cudaFree(p);
+    };
+    const size_t vb = sizeof(double2) * (size_t)N;
+    if (cudaMalloc(&d_coef, sizeof(double2) * (size_t)kChunk * k) != cudaSuccess ||
+        cudaMalloc(&d_X, vb * kChunk) != cudaSuccess || cudaMalloc(&d_AX, vb * kChunk) != cudaSuccess ||
+        cudaMalloc(&d_R, vb * max_out) != cudaSuccess || (ts && cudaMalloc(&d_L, vb * max_out) != cudaSuccess) ||
+        cudaMalloc(&d_dot, sizeof(double2) * 2 * kChunk) != cudaSuccess || cudaMalloc(&d_abi, vb) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(c, NK_ENOMEM, "eigensolver buffers");
+    }
+#define NK_EIG_CUDA(x)                                              \
+    do {                                                            \
+        const cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) {                                    \
+            release();                                              \
+            return fail(c, NK_ECUDA, cudaGetErrorString(e_));       \
+        }                                                           \
+    } while (0)
+    auto residuals = [&](const std::vector<double2>& coef, const std::vector<int>& owner, bool left,
+                         std::vector<double>& res, std::vector<double>& nrm2) -> int {
+        const int nc = (int)owner.size();
+        res.assign(nc, 0.0);
+        nrm2.assign(nc, 0.0);
+        const double2* base = left ? nk::outer_p(Lw.o, 0, 0) : nk::outer_q(Lw.o, 0, 0);
+        std::vector<double2> dd(kChunk), rr(kChunk);
+        for (int t0 = 0; t0 < nc; t0 += kChunk) {
+            const int n = std::min(kChunk, nc - t0);
+            NK_EIG_CUDA(cudaMemcpy(d_coef, coef.data() + (size_t)t0 * k, sizeof(double2) * (size_t)n * k,
+                                   cudaMemcpyHostToDevice));
+            nk::launch_colcomb(base, N, k, d_coef, N, n, d_X, st);
+            nk::DslashSet s0, s1;
+            std::memset(&s0, 0, sizeof(s0));
+            std::memset(&s1, 0, sizeof(s1));
+            s0.in = d_X;
+            s0.in_stride = N;
+            s0.out = d_AX;
+            s0.out_stride = N;
+            s0.n = n;
+            s0.dag = left ? 1 : 0;
+            nk::launch_dslash(64, c->U64, g, s0, s1, kappa_of(c), c->mu, st);
+            for (int g0 = 0; g0 < n; g0 += 12) {
+                const int ng = std::min(12, n - g0);
+                nk::VecCoefs ca, cb;
+                for (int i = 0; i < ng; ++i) {
+                    const nk::cplx th = reps[owner[t0 + g0 + i]];
+                    const nk::cplx ths = left ? std::conj(th) : th;
+                    ca.c[i] = make_double2(-ths.real(), -ths.imag());
+                    cb.c[i] = make_double2(1.0, 0.0);
+                }
+                double2* ax = d_AX + (size_t)g0 * N;
+                double2* x = d_X + (size_t)g0 * N;
+                nk::launch_vlincomb(ax, x, N, ng, ca, cb, st);   // A x - theta x
+                nk::launch_vdot(ax, ax, N, ng, d_dot, st);
+                nk::launch_vdot(x, x, N, ng, d_dot + kChunk, st);
+                NK_EIG_CUDA(cudaMemcpy(dd.data() + g0, d_dot, sizeof(double2) * ng, cudaMemcpyDeviceToHost));
+                NK_EIG_CUDA(cudaMemcpy(rr.data() + g0, d_dot + kChunk, sizeof(double2) * ng, cudaMemcpyDeviceToHost));
+            }
+            for (int i = 0; i < n; ++i) {
+                nrm2[t0 + i] = rr[i].x;
+                res[t0 + i] = std::sqrt(dd[i].x / std::max(rr[i].x, 1e-300));
+            }
+        }
+        return NK_OK;
+    };
+    std::vector<double> res_r, nrm_r, res_l, nrm_l;
+    rc = residuals(coef_r, owner_r, false, res_r, nrm_r);
+    if (rc) return rc;
+    if (ts) {
+        rc = residuals(coef_l, owner_l, true, res_l, nrm_l);
+        if (rc) return rc;
+    }
+    // per cluster the right (and left) candidate of least residual; the
+    // cluster's residual is the larger of the two
+    std::vector<int> best_r(ncl, -1), best_l(ncl, -1);
+    for (int t = 0; t < (int)owner_r.size(); ++t) {
+        int& b_ = best_r[owner_r[t]];
+        if (b_ < 0 || res_r[t] < res_r[b_]) b_ = t;
+    }
+    for (int t = 0; t < (int)owner_l.size(); ++t) {
+        int& b_ = best_l[owner_l[t]];
+        if (b_ < 0 || res_l[t] < res_l[b_]) b_ = t;
+    }
+    std::vector<double> res_cl(ncl);
+    for (int q = 0; q < ncl; ++q) res_cl[q] = std::max(res_r[best_r[q]], ts ? res_l[best_l[q]] : 0.0);
+    // the converged clusters (residual <= tol); of two whose eigenvalues lie
+    // within their residuals of each other (approximations of one eigenvalue
+    // of A) the one of smaller residual; the m nearest zero
+    std::vector<int> keep;
+    for (int q = 0; q < ncl; ++q) {
+        if (!(res_cl[q] <= tol)) continue;
+        int dup = -1;
+        for (int i = 0; i < (int)keep.size(); ++i)
+            if (std::abs(reps[q] - reps[keep[i]]) <= res_cl[q] + res_cl[keep[i]]) dup = i;
+        if (dup < 0) keep.push_back(q);
+        else if (res_cl[q] < res_cl[keep[dup]]) keep[dup] = q;
+    }
+    std::sort(keep.begin(), keep.end(), [&](int x, int y) { return std::abs(reps[x]) < std::abs(reps[y]); });
+    if ((int)keep.size() > max_out) keep.resize(max_out);
+    const int nf = (int)keep.size();
+    // the chosen vectors, lifted again (the same coefficients and kernel give
+    // the same vectors), normalised to |r| = 1 and <l, r> = 1
+    for (int side = 0; side < (ts ? 2 : 1); ++side) {
+        const std::vector<double2>& coef = side ? coef_l : coef_r;
+        const std::vector<int>& best = side ? best_l : best_r;
+        std::vector<double2> cc((size_t)nf * k);
+        for (int i = 0; i < nf; ++i)
+            std::copy(coef.begin() + (size_t)best[keep[i]] * k, coef.begin() + (size_t)(best[keep[i]] + 1) * k,
+                      cc.begin() + (size_t)i * k);
+        for (int t0 = 0; t0 < nf; t0 += kChunk) {
+            const int n = std::min(kChunk, nf - t0);
+            NK_EIG_CUDA(cudaMemcpy(d_coef, cc.data() + (size_t)t0 * k, sizeof(double2) * (size_t)n * k,
+                                   cudaMemcpyHostToDevice));
+            nk::launch_colcomb(side ? nk::outer_p(Lw.o, 0, 0) : nk::outer_q(Lw.o, 0, 0), N, k, d_coef, N, n,
+                               (side ? d_L : d_R) + (size_t)t0 * N, st);
+        }
+    }
+    for (int g0 = 0; g0 < nf; g0 += 12) {
+        const int ng = std::min(12, nf - g0);
+        nk::VecCoefs ca, cb;
+        for (int i = 0; i < ng; ++i) {
+            ca.c[i] = make_double2(0.0, 0.0);
+            cb.c[i] = make_double2(1.0 / std::sqrt(nrm_r[best_r[keep[g0 + i]]]), 0.0);
+        }
+        double2* rg = d_R + (size_t)g0 * N;
+        nk::launch_vlincomb(rg, rg, N, ng, ca, cb, st);   // |r| = 1
+        if (ts) {
+            double2* lg = d_L + (size_t)g0 * N;
+            std::vector<double2> s(ng);
+            nk::launch_vdot(lg, rg, N, ng, d_dot, st);
+            NK_EIG_CUDA(cudaMemcpy(s.data(), d_dot, sizeof(double2) * ng, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < ng; ++i) {
+                const nk::cplx sc = 1.0 / std::conj(nk::cplx(s[i].x, s[i].y));   // l <- l / <l, r>^*
+                cb.c[i] = make_double2(sc.real(), sc.imag());
+            }
+            nk::launch_vlincomb(lg, lg, N, ng, ca, cb, st);
+        }
+    }
+    for (int i = 0; i < nf; ++i) {
+        const int q = keep[i];
+        nk::launch_soa_to_abi(d_R + (size_t)i * N, N, d_abi, N, nullptr, 0, c->V, 1, st);
+        NK_EIG_CUDA(cudaMemcpy(R + (size_t)i * 2 * N, d_abi, vb, cudaMemcpyDeviceToHost));
+        if (ts) {
+            nk::launch_soa_to_abi(d_L + (size_t)i * N, N, d_abi, N, nullptr, 0, c->V, 1, st);
+            NK_EIG_CUDA(cudaMemcpy(L + (size_t)i * 2 * N, d_abi, vb, cudaMemcpyDeviceToHost));
+        } else if (L) {
+            std::memcpy(L + (size_t)i * 2 * N, R + (size_t)i * 2 * N, vb);
+        }
+        lambda[2 * i] = reps[q].real();
+        lambda[2 * i + 1] = ts ? reps[q].imag() : 0.0;
+        if (resid) resid[i] = res_cl[q];
+    }
+    NK_EIG_CUDA(cudaGetLastError());
+#undef NK_EIG_CUDA
+    release();
+    *found = nf;
+    if (nf < m) return fail(c, NK_ENOTCONV, "fewer than m eigenpairs reached tol at this k");
     return NK_OK;
 }
 

@@ -99,7 +99,8 @@ struct Outer {
     int q_ring;      // 0: Q holds all k vectors (+1 scratch) [rhs][k+1][N]; 1: ring [rhs][3][N] (double pass)
     int qcols;       // vectors per RHS in Q: k + 1 or 3
     double2* Q;      // right basis q_j
-    double2* P;      // left vectors p_j, ring [rhs][3][N] (two-sided)
+    double2* P;      // left vectors p_j, ring [rhs][3][N] (two-sided), or all [rhs][k+1][N] (pcols = k + 1)
+    int pcols;       // vectors per RHS in P: 3 (ring) or k + 1 (the eigensolver keeps W_k)
     float4* q32;     // FP32 copy of the newest q, [rhs][6][V] pair layout (f32_pair_index)
     float4* p32;     // FP32 copy of the newest p, [rhs][6][V]
     float4* s32;     // FP32 stencil output of the step, (A q_j)/n_j then (A^dag p_j)/m_j: [side][rhs][6][V]
@@ -140,7 +141,7 @@ __host__ __device__ inline double2* outer_q(const Outer& o, int rhs, int j) {
     return o.Q + ((size_t)rhs * o.qcols + (o.q_ring ? j % 3 : j)) * o.N;
 }
 __host__ __device__ inline double2* outer_p(const Outer& o, int rhs, int j) {
-    return o.P + ((size_t)rhs * 3 + j % 3) * o.N;
+    return o.P + ((size_t)rhs * o.pcols + (o.pcols == 3 ? j % 3 : j)) * o.N;
 }
 // (byte arithmetic: dfc, a two-float complex of 16 bytes, may be incomplete here)
 __host__ __device__ inline dfc* ring_q(const Outer& o, int rhs, int j) {
@@ -228,6 +229,10 @@ void launch_outer_step2(const Outer& o, int j, int copy_mode, bool ring, bool wr
 // adaptive, the converged size); coefficients beyond it are zero.
 void launch_lift_coef(const Outer& o, const double2* c, const int* kused, double2* cp, cudaStream_t st);
 void launch_lift(const Outer& o, const double2* cp, const int* kused, double2* y, cudaStream_t st);
+// out_i = sum_{j < ncols} coef[i ncols + j] base[j col_stride + n] for the n_out
+// output vectors i (eigen.cu): Ritz vectors from a stored basis
+void launch_colcomb(const double2* base, long col_stride, int ncols, const double2* coef, long N, int n_out,
+                    double2* out, cudaStream_t st);
 void launch_fill_int(int* p, int n, int value, cudaStream_t st);
 // Adaptive k: per RHS (|c - c_prev|, |c|) over the first k entries, then c_prev <- c.
 void launch_adapt_delta(const Outer& o, const double2* c, double2* c_prev, int k, double2* dn, cudaStream_t st);

@@ -49,7 +49,7 @@ ERROR_NAMES = {
 
 EXPORTED = [
     "nk_create_lattice", "nk_load_links", "nk_load_links_dev", "nk_set_mu_mw", "nk_set_precision", "nk_set_df_recurrence",
-    "nk_set_adapt_start", "nk_set_nesting", "nk_set_deflation", "nk_overlap_solve",
+    "nk_set_adapt_start", "nk_set_nesting", "nk_set_deflation", "nk_eigs_smallest", "nk_overlap_solve",
     "nk_sign_apply", "nk_sign_apply_dev", "nk_overlap_apply", "nk_overlap_apply_dev",
     "nk_dslash_dev", "nk_stencil32_dev", "nk_outer_lanczos_dev", "nk_inner_sign", "nk_inner_sign_noalloc", "nk_last_error",
     "nk_destroy",
@@ -150,6 +150,7 @@ def load_library(path: str = LIB_PATH):
         "nk_set_adapt_start": ([P, I], I),
         "nk_set_nesting": ([P, I, P], I),
         "nk_set_deflation": ([P, I, P, P, P], I),
+        "nk_eigs_smallest": ([P, dp, I, I, D, dp, dp, P, P, P], I),
         "nk_overlap_solve": ([P, P, I, I, I, ctypes.c_double, U, ctypes.c_double, ctypes.c_double, I, P, P, P], I),
         "nk_sign_apply": ([P, dp, I, I, I, D, D, U, dp, ctypes.POINTER(NkStats)], I),
         "nk_sign_apply_dev": ([P, P, I, I, I, D, D, U, P, ctypes.POINTER(NkStats), P], I),
@@ -303,6 +304,26 @@ class Context:
             Lp = _dptr(L.view(np.float64))
         self._check(self._lib.nk_set_deflation(self.h, len(lam), _dptr(lam.view(np.float64)),
                                                _dptr(R.view(np.float64)), Lp))
+
+    def eigs_smallest(self, b, k, m, tol=1e-10, check=True):
+        """nk_eigs_smallest: the m eigenpairs of A of smallest |lambda| from a
+        k-step Lanczos eigensolver started at b (12 V complex).  Returns
+        (lam (found,), R (found, 12 V), L (found, 12 V), resid (found,), rc);
+        L = R at mu = 0.  With check, rc != NK_OK raises."""
+        b = _host_c128(b).reshape(self.N)
+        lam = np.zeros(m, np.complex128)
+        R = np.zeros((m, self.N), np.complex128)
+        L = np.zeros((m, self.N), np.complex128)
+        res = np.zeros(m)
+        found = ctypes.c_int(0)
+        rc = self._lib.nk_eigs_smallest(self.h, _dptr(b.view(np.float64)), int(k), int(m), float(tol),
+                                        _dptr(lam.view(np.float64)), _dptr(R.view(np.float64)),
+                                        L.ctypes.data_as(ctypes.c_void_p), res.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(found))
+        if check:
+            self._check(rc)
+        n = found.value
+        return lam[:n], R[:n], L[:n], res[:n], rc
 
     def set_nesting(self, ells=()):
         """nk_set_nesting: sizes l_2 >= l_3 >= ... of the levels below the first
