@@ -464,8 +464,7 @@ int nk_set_predictor(nk_ctx* ctx, nk_mlp* m);
  * Limits: n_rhs <= NK_NOALLOC_MAX_RHS, k <= NK_NOALLOC_MAX_K,
  * l <= NK_NOALLOC_MAX_ELL; larger sizes return NK_EINVAL with a message.
  * The first call on each device looks up the array's device address and sets
- * kernel attributes; make that first call before any stream capture.  The
- * array is shared by all calls and keeps the previous call's contents, so
+ * kernel attributes.  The array is shared by all calls and keeps the previous call's contents, so
  * calls whose GPU work overlaps (other streams, other host threads) race on
  * it.  Stream-ordered on `stream`; returns after the stream has finished the
  * call (it reads the per-RHS status back).  err (may be NULL) receives a

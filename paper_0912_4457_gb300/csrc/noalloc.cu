@@ -76,7 +76,7 @@ extern "C" int nk_inner_sign_noalloc(const double* alpha_dev, const double* beta
         return set_err(err, err_len, NK_ECUDA, "cudaGetDevice failed");
     if (!g_scratch_addr[dev]) {
         // first call on this device: resolve the array's device address and
-        // set the kernel attributes the RHi launch needs (not capturable)
+        // set the kernel attributes the RHi launch needs
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)

@@ -3,7 +3,7 @@
 The kernel takes 2 n_rhs FP32 vectors in its pair layout ([6][V] of four
 floats per vector: components 2i and 2i + 1 of a site, re/im interleaved) and
 applies A to the first n_rhs and A^dagger to the others.  Cases cover both
-block shapes (16 sites for 16 or more vectors, 32 below), a lattice whose
+block shapes (8 sites above 12 vectors, 32 up to 12), a lattice whose
 volume is not a multiple of the block (ragged last block), periodic and
 antiperiodic t.  Tolerance: FP32 rounding of the input, the links and ~100
 flops per component (2e-6 relative, as for the FP32 stencil elsewhere).
