@@ -499,6 +499,137 @@ def learned_arm(nk, torch, ctx, b_dev, w, flags):
     return out
 
 
+def multilevel_arm(nk, torch, ctx, b_dev, w, flags, y_ref):
+    """Multi-level nesting (Sec. 4.5) on the batch of the workload: one level
+    (l = w["ell"]) against deeper chains l -> l_2 -> ... (RHi on the deepest
+    Ritz matrix).  One batch at a time (graph, CUDA events around two warm
+    solves); the inner part's device time from NK_PROFILE (classes inner +
+    rhi); every source against the FP64 reference, so a chain too short for
+    the tolerance shows as such."""
+    n_rhs, k, ell = w["n_rhs"], w["k"], w["ell"]
+    y = torch.zeros_like(b_dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for levels in ((), (96,), (64,), (64, 16), (32, 8)):
+        name = "levels_" + "_".join(str(v) for v in (ell, *levels))
+        ctx.set_nesting(levels)
+        try:
+            ctx.sign_apply_dev(b_dev, y, n_rhs, k, ell, flags=flags)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                ctx.sign_apply_dev(b_dev, y, n_rhs, k, ell, flags=flags)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            err = rel_errs(y.cpu().numpy(), y_ref)
+            st, _ = ctx.sign_apply_dev(b_dev, y, n_rhs, k, ell, flags=flags | nk.NK_PROFILE)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_nesting(())
+        ms = e0.elapsed_time(e1) / 2
+        ok = sum(1 for e in err if e <= TOL)
+        out[name] = {"ells": [ell, *levels], "ms_per_batch": ms, "solves_per_s_one_batch": ok / (ms * 1e-3),
+                     "inner_ms": st["t_class_ms"]["inner"] + st["t_class_ms"]["rhi"],
+                     "rhi_iters_max": max(st["rhi_iters"]), "max_rel_err_vs_fp64_reference": max(err)}
+    return out
+
+
+DEFLATION_CASE = dict(dims=(6, 6, 6, 6), mu=0.0, m_w=-2.0, link_seed=102, eig_seed=203, k_eig=2400, m=16,
+                      tol_eig=1e-10, k_max=1536, ell=128, k_fixed=256, k_ref=1536, ell_ref=256)
+
+
+def deflation_arm(nk, torch):
+    """LR deflation (App. C steps 1 and 6) with its eigenpairs from the
+    device eigensolver (nk_eigs_smallest: k_eig FP64 Lanczos steps from a
+    Gaussian vector, the m pairs of smallest |lambda| with residual <=
+    tol_eig; a one-off initialisation, timed separately).  Then the 12
+    spin-colour point sources at 6^4, mu = 0, FP64, adaptive k (tol = TOL)
+    without and with the deflation: k reached per source, device time, and
+    every source against the undeflated FP64 solve at k = 1536, l = 256; and
+    the error of both at a fixed smaller k (k_fixed)."""
+    import inputs
+    c = DEFLATION_CASE
+    U, _ = inputs.su3_links(c["dims"], c["link_seed"])
+    flags = nk.NK_FP64 | nk.NK_SHARED_P
+    ctx = nk.Context(c["dims"])
+    try:
+        ctx.load_links(U)
+        ctx.set_mu_mw(c["mu"], c["m_w"])
+        t0 = time.perf_counter()
+        lam, R, L, res, rc_e = ctx.eigs_smallest(inputs.gaussian_sources(c["dims"], c["eig_seed"])[0], c["k_eig"],
+                                                 c["m"], tol=c["tol_eig"], check=False)
+        t_eig = time.perf_counter() - t0
+        b_dev = torch.from_numpy(np.ascontiguousarray(inputs.point_sources(c["dims"]))).cuda()
+        n = b_dev.shape[0]
+        yref = torch.zeros_like(b_dev)
+        ctx.sign_apply_dev(b_dev, yref, n, c["k_ref"], c["ell_ref"], flags=flags)
+        torch.cuda.synchronize()
+        y_ref = yref.cpu().numpy()
+        out = {"lattice": "x".join(map(str, c["dims"])), "mu": c["mu"], "tol": TOL, "k_fixed": c["k_fixed"],
+               "eigensolver": {"k": c["k_eig"], "m": c["m"], "tol": c["tol_eig"], "rc": rc_e, "found": len(lam),
+                               "max_residual": float(max(res)) if len(res) else None,
+                               "abs_lambda": [float(abs(x)) for x in lam], "wall_s": t_eig}}
+        y = torch.zeros_like(b_dev)
+        for name, pairs in (("undeflated", None), ("deflated", (lam, R, L) if len(lam) else None)):
+            if name == "deflated" and pairs is None:
+                break
+            ctx.set_deflation(*(pairs or (None,)))
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, rc = ctx.sign_apply_dev(b_dev, y, n, c["k_max"], c["ell"], tol=TOL, flags=flags, check=False)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+            err = rel_errs(y.cpu().numpy(), y_ref)
+            ctx.sign_apply_dev(b_dev, y, n, c["k_fixed"], c["ell"], flags=flags)
+            torch.cuda.synchronize()
+            err_fixed = rel_errs(y.cpu().numpy(), y_ref)
+            out[name] = {"k_rhs": st["k_rhs"], "checks": st["checks"], "device_ms": st["t_total_ms"],
+                         "wall_ms": 1e3 * wall, "rc": rc, "defl_m": st["defl_m"], "defl_gap": st["defl_gap"],
+                         "max_rel_err_vs_fp64_reference": max(err),
+                         "solves_meeting_tol": sum(1 for e in err if e <= TOL),
+                         "max_rel_err_at_k_fixed": max(err_fixed)}
+        ctx.set_deflation(None)
+    finally:
+        ctx.close()
+    return out
+
+
+OVERLAP_CASE = dict(dims=(6, 6, 6, 6), mu=0.3, m_w=-2.0, link_seed=102, source_seed=202, k=512, ell=128,
+                    mass=0.05, tol_cg=1e-8, maxit=400)
+
+
+def overlap_arm(nk):
+    """Overlap inversion x = (D_ov(mu) + mass)^-1 b (CG on the normal
+    equations, every iteration one sign evaluation of A(mu) and one of
+    A(-mu)) on the 6^4, mu = 0.3 configuration's sizes (k = 512, l = 128,
+    FP64), one Gaussian source; the true residual |b - (D_ov + mass) x| / |b|
+    from one more overlap application."""
+    import inputs
+    c = OVERLAP_CASE
+    U, _ = inputs.su3_links(c["dims"], c["link_seed"])
+    b = inputs.gaussian_sources(c["dims"], c["source_seed"])
+    ctx = nk.Context(c["dims"])
+    try:
+        ctx.load_links(U)
+        ctx.set_mu_mw(c["mu"], c["m_w"])
+        t0 = time.perf_counter()
+        x, its, res, rc = ctx.overlap_solve(b, c["k"], c["ell"], mass=c["mass"], tol_cg=c["tol_cg"],
+                                            maxit=c["maxit"], flags=nk.NK_FP64, check=False)
+        wall = time.perf_counter() - t0
+        dx, _, _ = ctx.overlap_apply(x, c["k"], c["ell"], flags=nk.NK_FP64)
+        true_res = float(np.linalg.norm(b - dx - c["mass"] * x) / np.linalg.norm(b))
+    finally:
+        ctx.close()
+    return {"lattice": "x".join(map(str, c["dims"])), "mu": c["mu"], "k": c["k"], "ell": c["ell"],
+            "mass": c["mass"], "tol_cg": c["tol_cg"], "rc": rc, "cg_iterations": int(its[0]),
+            "normal_eq_rel_residual": float(res[0]), "true_rel_residual": true_res, "wall_s": wall,
+            "ms_per_iteration": 1e3 * wall / max(1, int(its[0])),
+            "what": "CG on M^dagger M x = M^dagger b, M = D_ov(mu) + mass, two FP64 sign evaluations per "
+                    "iteration, one Gaussian source"}
+
+
 def run_gpu(args, w, rank, world, local_rank):
     import multiprocessing as mp
     import torch
@@ -610,6 +741,7 @@ def run_gpu(args, w, rank, world, local_rank):
     stp, _ = ctx.sign_apply_dev(b_dev, y_dev, n_rhs, k, ell, flags=flags | nk.NK_PROFILE)
     torch.cuda.synchronize()
     learned = None if args.quick else learned_arm(nk, torch, ctx, b_dev, w, flags)
+    multilevel = None if args.quick else multilevel_arm(nk, torch, ctx, b_dev, w, flags, y_ref)
     if rank != 0:
         ctx.close()
         return 0
@@ -685,6 +817,11 @@ def run_gpu(args, w, rank, world, local_rank):
         blk["prediction"] = learned["prediction"]
         blk["fixed_k"] = {"value": value, "k": k, "ell": ell}
         line["learned"] = blk
+    if multilevel is not None:
+        line["multilevel"] = multilevel
+    if not args.quick:
+        line["deflation"] = deflation_arm(nk, torch)
+        line["overlap_solve"] = overlap_arm(nk)
     if pool is not None:
         one, allc = cpu_baselines(w)
         line["cpu_baseline"] = one
@@ -763,10 +900,11 @@ def main():
     ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--mode", choices=["bench", "ncu", "stencil"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "ncu", "stencil", "rows"], default="bench",
                     help="ncu: run --warmup solves and then one solve kernel by kernel (no graph, no oracle, "
                          "no output line), for launch lists and captures under ncu; stencil: --warmup + 1 "
-                         "launches of the FP32 stencil alone on 16^3 x 32")
+                         "launches of the FP32 stencil alone on 16^3 x 32; rows: only the deflation and "
+                         "overlap-inversion blocks of the bench line, printed as one JSON line")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
     ap.add_argument("--j1", type=int, default=None,
@@ -788,6 +926,11 @@ def main():
         return run_ncu(args, w)
     if args.mode == "stencil":
         return run_stencil(args)
+    if args.mode == "rows":
+        import torch
+        import paper_0912_4457_gb300 as nk
+        print(json.dumps({"deflation": deflation_arm(nk, torch), "overlap_solve": overlap_arm(nk)}))
+        return 0
     if world > 1:
         import torch
         import torch.distributed as dist
