@@ -885,6 +885,30 @@ def run_stencil(args):
     return 0
 
 
+def run_rows(args, w):
+    """--mode rows: the multi-level, deflation and overlap-inversion blocks of
+    the bench line alone (multi-level on the workload's batch against its FP64
+    reference), printed as one JSON line."""
+    import torch
+    import paper_0912_4457_gb300 as nk
+    U, b_host = make_inputs(w)
+    n_rhs = w["n_rhs"]
+    flags = (nk.NK_MIXED if w["mixed"] else nk.NK_FP64) | nk.NK_SHARED_P
+    ctx = new_context(nk, w, U, j1_of(w, args))
+    try:
+        ctx.autotune(n_rhs, flags, args.tune_cache)
+        b_dev = torch.from_numpy(np.ascontiguousarray(b_host)).cuda()
+        yref = torch.zeros_like(b_dev)
+        ctx.sign_apply_dev(b_dev, yref, n_rhs, w["k_ref"], w["ell_ref"], flags=nk.NK_FP64 | nk.NK_SHARED_P)
+        torch.cuda.synchronize()
+        multilevel = multilevel_arm(nk, torch, ctx, b_dev, w, flags, yref.cpu().numpy())
+    finally:
+        ctx.close()
+    print(json.dumps({"multilevel": multilevel, "deflation": deflation_arm(nk, torch),
+                      "overlap_solve": overlap_arm(nk)}))
+    return 0
+
+
 def _lib_host_solve(ctx, bp, yp, k, ell, flags):
     import ctypes
     from paper_0912_4457_gb300 import nksign
@@ -903,8 +927,8 @@ def main():
     ap.add_argument("--mode", choices=["bench", "ncu", "stencil", "rows"], default="bench",
                     help="ncu: run --warmup solves and then one solve kernel by kernel (no graph, no oracle, "
                          "no output line), for launch lists and captures under ncu; stencil: --warmup + 1 "
-                         "launches of the FP32 stencil alone on 16^3 x 32; rows: only the deflation and "
-                         "overlap-inversion blocks of the bench line, printed as one JSON line")
+                         "launches of the FP32 stencil alone on 16^3 x 32; rows: only the multi-level, deflation "
+                         "and overlap-inversion blocks of the bench line, printed as one JSON line")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-k", type=int, default=0, help="--mode ncu: outer steps (0: the workload's k)")
     ap.add_argument("--j1", type=int, default=None,
@@ -927,10 +951,7 @@ def main():
     if args.mode == "stencil":
         return run_stencil(args)
     if args.mode == "rows":
-        import torch
-        import paper_0912_4457_gb300 as nk
-        print(json.dumps({"deflation": deflation_arm(nk, torch), "overlap_solve": overlap_arm(nk)}))
-        return 0
+        return run_rows(args, w)
     if world > 1:
         import torch
         import torch.distributed as dist
