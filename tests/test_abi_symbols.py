@@ -71,6 +71,18 @@ def test_null_context_is_rejected_by_every_setter_and_wait(lib):
     assert lib.nk_get_launch(None, 12, 0, None) == -1
 
 
+def test_eigensolver_rejects_null_arguments_without_gpu(lib):
+    """nk_eigs_smallest checks its context and output pointers before any
+    device work."""
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    f = lib.nk_eigs_smallest
+    f.argtypes, f.restype = [P, P, I, I, D, P, P, P, P, P], I
+    buf = (ctypes.c_double * 64)()
+    found = ctypes.c_int(5)
+    assert f(None, buf, 32, 4, 1e-9, buf, buf, buf, buf, ctypes.byref(found)) == -1
+    assert f(None, buf, 32, 4, 1e-9, buf, buf, buf, buf, None) == -1
+
+
 def test_noalloc_binding_refuses_undersized_tensors_before_any_launch():
     """inner_sign_noalloc reads n_rhs * k complex entries of each input and
     writes as many to c; a smaller tensor is refused in the binding with
