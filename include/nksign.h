@@ -67,7 +67,11 @@ extern "C" {
 #define NK_ASYNC 0x40u      /* nk_sign_apply_dev / nk_overlap_apply_dev with tol = 0: enqueue the
                                solve and return without waiting; nk_wait collects its outcome.
                                One pending solve per context (its workspace); two contexts on two
-                               streams keep two batches in flight. */
+                               streams keep two batches in flight.  Until nk_wait, the calls that
+                               write the context's workspace, links or deflation vectors (the
+                               solves, nk_load_links(_dev), nk_set_deflation, nk_eigs_smallest,
+                               nk_autotune, nk_outer_lanczos_dev, nk_inner_sign, nk_features,
+                               nk_predict_sizes, nk_overlap_solve) return NK_ESTATE. */
 #define NK_SHARED_P 0x80u   /* one p for the whole batch (Eq. popt with z_min and z_max of A taken as
                                the extremes of the per-RHS estimates over the batch: every RHS
                                shares A), instead of one per RHS; p > 0 overrides both */

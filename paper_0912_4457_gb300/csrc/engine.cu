@@ -329,8 +329,16 @@ bool valid_launch(const nk_launch& l) {
            l.step2_blocks >= 1 && l.step2_blocks <= 4096;
 }
 
+// Entry points that write the context's workspace, links or deflation
+// vectors refuse while an NK_ASYNC solve still uses them.
+static int busy(nk_ctx* c) {
+    return c->pending.on ? fail(c, NK_ESTATE, "an NK_ASYNC solve is pending on this context: nk_wait first")
+                         : NK_OK;
+}
+
 int check_solve_args(nk_ctx* c, int n_rhs, int k, int ell, double tol) {
     if (!c) return NK_EINVAL;
+    if (int rb = busy(c)) return rb;
     if (!c->links) return fail(c, NK_ESTATE, "no links loaded (nk_load_links)");
     if (!c->mu_set) return fail(c, NK_ESTATE, "mu and m_w not set (nk_set_mu_mw)");
     if (n_rhs < 1 || n_rhs > NK_MAX_RHS) return fail(c, NK_EINVAL, "n_rhs must be in [1, 12]");
@@ -1007,6 +1015,7 @@ int nk_create_lattice(const int dims[4], int bc_t_antiperiodic, nk_ctx** out) {
 
 static int load_links_impl(nk_ctx* c, const double* U, bool host, cudaStream_t st) {
     if (!c || !U) return NK_EINVAL;
+    if (int rb = busy(c)) return rb;
     NK_CUDA(c, cudaSetDevice(c->device));
     const size_t n = (size_t)c->V * 36;
     if (!c->U64) {
@@ -1179,6 +1188,7 @@ int nk_overlap_solve(nk_ctx* c, const double* b, int n_rhs, int k, int ell, doub
 
 int nk_set_deflation(nk_ctx* c, int m, const double* lambda, const double* R, const double* L) {
     if (!c) return NK_EINVAL;
+    if (int rb = busy(c)) return rb;
     if (m < 0 || m > NK_MAX_DEFL || (m > 0 && (!lambda || !R)))
         return fail(c, NK_EINVAL, "need 0 <= m <= NK_MAX_DEFL, eigenvalues and right eigenvectors");
     NK_CUDA(c, cudaSetDevice(c->device));
@@ -1225,6 +1235,7 @@ int nk_eigs_smallest(nk_ctx* c, const double* b, int k, int m, double tol, doubl
                      double* resid, int* found) {
     if (!c || !b || !lambda || !R || !found) return NK_EINVAL;
     *found = 0;
+    if (int rb = busy(c)) return rb;
     if (m < 1 || m > NK_MAX_DEFL) return fail(c, NK_EINVAL, "need 1 <= m <= NK_MAX_DEFL");
     if (k < 2 * m + 2 || (k & 1)) return fail(c, NK_EINVAL, "k must be even and >= 2 m + 2");
     if (!(tol > 0.0)) return fail(c, NK_EINVAL, "tol must be positive");
@@ -1615,6 +1626,7 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
 int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk_launch* out, double* ms_per_step) {
     int rc = shape_args(c, n_rhs);
     if (rc) return rc;
+    if ((rc = busy(c))) return rc;
     if (!c->links) return fail(c, NK_ESTATE, "links not loaded");
     NK_CUDA(c, cudaSetDevice(c->device));
     const int ts = c->mu != 0.0 ? 1 : 0;
@@ -1904,6 +1916,7 @@ int nk_outer_lanczos_dev(nk_ctx* c, const double* b_dev, int n_rhs, int k, unsig
 int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const double* gamma, int n_rhs, int k,
                   int ell, double p, int hermitian, double* cout, nk_stats* st) {
     if (!c || !alpha || !beta || !gamma || !cout) return NK_EINVAL;
+    if (int rb = busy(c)) return rb;
     if (n_rhs < 1 || n_rhs > NK_MAX_RHS || k < 2 || ell < 2 || ell > k || ell > 256 || (k & 1) || (ell & 1) ||
         k > nk::kMaxInnerK)
         return fail(c, NK_EINVAL, "bad n_rhs, k or l");
@@ -1973,6 +1986,7 @@ int nk_inner_sign(nk_ctx* c, const double* alpha, const double* beta, const doub
 
 int nk_features(nk_ctx* c, const double* b_dev, float* features, void* stream) {
     if (!c || !b_dev || !features) return c ? fail(c, NK_EINVAL, "null pointer") : NK_EINVAL;
+    if (int rb = busy(c)) return rb;
     if (!c->links || !c->mu_set) return fail(c, NK_ESTATE, "links or (mu, m_w) not set");
     const int k = 32, ell = 32;
     std::vector<double> al(2 * k), be(2 * k), ga(2 * k), cf(2 * k);

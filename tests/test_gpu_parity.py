@@ -470,8 +470,9 @@ def test_invalid_arguments(k, ell, n_rhs):
 
 def test_async_two_contexts_match_sync(c1):
     """NK_ASYNC: two contexts on two streams with both batches in flight give
-    the synchronous result bit for bit; a second solve on a context with one
-    pending is refused (NK_ESTATE), and nk_wait with nothing pending is a no-op."""
+    the synchronous result bit for bit; a second solve, the eigensolver, a
+    link load or a deflation change on a context with one pending is refused
+    (NK_ESTATE), and nk_wait with nothing pending is a no-op."""
     dims, U, b, truth = c1
     k, ell = 256, 64
     ctx_a, ctx_b = make_ctx(dims, 101, 0.3), make_ctx(dims, 101, 0.3)
@@ -489,6 +490,12 @@ def test_async_two_contexts_match_sync(c1):
         _, rc = ctx_a.sign_apply_dev(bd, ya, 3, k, ell, flags=NK_MIXED | nksign.NK_ASYNC, stream=sa,
                                      check=False)
         assert rc == nksign.NK_ESTATE
+        # so are the calls that write its workspace, links or deflation vectors
+        assert ctx_a.eigs_smallest(b[0], 32, 4, check=False)[4] == nksign.NK_ESTATE
+        with pytest.raises(nksign.NkError):
+            ctx_a.load_links(U)
+        with pytest.raises(nksign.NkError):
+            ctx_a.set_deflation(None)
         st_a, rc_a = ctx_a.wait()
         st_b, rc_b = ctx_b.wait()
         assert rc_a == 0 and rc_b == 0
