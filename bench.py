@@ -52,8 +52,10 @@ WORKLOADS = {
     # converges by k = 1024 (1e-11 against k = 1536); the FP32 switch j0 sets
     # the error of the mixed schedule (j0 = 128: 2.9e-8, 256: 1.5e-9,
     # 384: 6e-11 against FP64 k = 1536), l = 128 leaves it unchanged.
-    "10^4-mu0.2-12pt": dict(dims=(10, 10, 10, 10), mu=0.2, m_w=-2.0, link_seed=104, k=1024, ell=128, j0=256,
-                            j1=-1, n_rhs=12, source="point", mixed=True, k_ref=1536, ell_ref=256),
+    # A second nested level l_2 = 64 below l = 128 (Sec. 4.5) leaves the error
+    # unchanged (1.55e-9) and halves the size of the RHi matrix.
+    "10^4-mu0.2-12pt": dict(dims=(10, 10, 10, 10), mu=0.2, m_w=-2.0, link_seed=104, k=1024, ell=128, nest=(64,),
+                            j0=256, j1=-1, n_rhs=12, source="point", mixed=True, k_ref=1536, ell_ref=256),
     # 8^4, mu = 0.3 (two-sided), 12 point sources
     "8^4-mu0.3-12pt": dict(dims=(8, 8, 8, 8), mu=0.3, m_w=-2.0, link_seed=103, k=896, ell=160, j0=256, j1=-1,
                            n_rhs=12, source="point", mixed=True, k_ref=1280, ell_ref=256),
@@ -173,11 +175,12 @@ def make_inputs(w):
 # ---- oracle legs (CPU; spawned processes, never forked after CUDA is up) ----------
 
 def _oracle_solve(args):
-    """The nested oracle on one source (same k, l and p as the GPU batch)."""
-    U, dims, mu, m_w, b0, k, ell, p = args
+    """The nested oracle on one source (same k, l, nested levels and p as the
+    GPU batch)."""
+    U, dims, mu, m_w, b0, k, ell, p, ells = args
     from oracle import nested
     t0 = time.perf_counter()
-    y, _ = nested.sign_apply(U, dims, mu, m_w, b0, k, ell, p=p)
+    y, _ = nested.sign_apply(U, dims, mu, m_w, b0, k, ell, p=p, ells=ells)
     return y, time.perf_counter() - t0
 
 
@@ -294,7 +297,7 @@ def config_of(w, args):
             "p": "one p per batch: Eq. popt with z_min, z_max of A estimated as the extremes over the "
                  "batch's H_k (power / inverse iteration)",
             "graph": True, "parallelism": "replicas" if args.gpus > 1 else "single",
-            "batches_in_flight": args.inflight,
+            "batches_in_flight": args.inflight, "nested_levels": [w["ell"], *w.get("nest", ())],
             "l2": "working set (Krylov basis %.1f GB per batch) larger than L2" % (
                 12 * w["n_rhs"] * np.prod(w["dims"]) * w["k"] * 16 / 1e9)}
 
@@ -305,6 +308,7 @@ def new_context(nk, w, U, j1, shape=None, n_rhs=None, flags=0):
     c.set_mu_mw(w["mu"], w["m_w"])
     c.set_precision(w.get("j0", -1))
     c.set_df_recurrence(j1)
+    c.set_nesting(w.get("nest", ()))
     if shape is not None:
         c.set_launch(n_rhs, flags, *shape)
     return c
@@ -526,7 +530,7 @@ def multilevel_arm(nk, torch, ctx, b_dev, w, flags, y_ref):
             st, _ = ctx.sign_apply_dev(b_dev, y, n_rhs, k, ell, flags=flags | nk.NK_PROFILE)
             torch.cuda.synchronize()
         finally:
-            ctx.set_nesting(())
+            ctx.set_nesting(w.get("nest", ()))
         ms = e0.elapsed_time(e1) / 2
         ok = sum(1 for e in err if e <= TOL)
         out[name] = {"ells": [ell, *levels], "ms_per_batch": ms, "solves_per_s_one_batch": ok / (ms * 1e-3),
@@ -661,7 +665,8 @@ def run_gpu(args, w, rank, world, local_rank):
     pool = None
     if rank == 0 and not args.quick:
         pool = mp.get_context("spawn").Pool(1)
-        oracle_job = pool.apply_async(_oracle_solve, ((U, w["dims"], w["mu"], w["m_w"], b_host[0], k, ell, p_batch),))
+        oracle_job = pool.apply_async(_oracle_solve, ((U, w["dims"], w["mu"], w["m_w"], b_host[0], k, ell, p_batch,
+                                                        tuple(w.get("nest", ()))),))
 
     # ---- headline: fixed k, batches in flight -----------------------------------
     inflight = max(1, args.inflight)
@@ -937,13 +942,17 @@ def main():
                     help="batches in flight (contexts on their own streams); 1: one synchronous solve per step")
     ap.add_argument("--tune-cache", default=None,
                     help="launch-shape cache file (read if it has the workload's shape, else written)")
+    ap.add_argument("--nest", default="",
+                    help="comma-separated sizes l_2, l_3, ... of nested levels below l (Sec. 4.5; default none)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: no oracle, CPU baselines, two-float line or learned arm")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.nest:
+        w["nest"] = tuple(int(v) for v in args.nest.split(","))
     if args.impl == "reference":
         return run_reference(args, w, rank)
     if args.mode == "ncu":

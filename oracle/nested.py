@@ -177,8 +177,10 @@ def outer_basis(apply_a, apply_adag, x, k: int, hermitian: bool):
     return krylov.two_sided_lanczos(apply_a, apply_adag, x, k)
 
 
-def nested_sign(apply_a, apply_adag, x, k: int, ell: int, hermitian: bool, p=None):
-    """Nested approximation to sgn(A) x (Eq. nested, App. C steps 2-6)."""
+def nested_sign(apply_a, apply_adag, x, k: int, ell: int, hermitian: bool, p=None, ells=()):
+    """Nested approximation to sgn(A) x (Eq. nested, App. C steps 2-6); with
+    ells = (l_2, l_3, ...) the inner part nests further levels below l
+    (Sec. 4.5, inner_sign_multilevel)."""
     outer = outer_basis(apply_a, apply_adag, x, k, hermitian)
     if outer.breakdown:
         raise FloatingPointError("two-sided Lanczos: serious breakdown at step %d" % outer.k_used)
@@ -187,7 +189,11 @@ def nested_sign(apply_a, apply_adag, x, k: int, ell: int, hermitian: bool, p=Non
         p, z_min, z_max = estimate_p(alpha, beta, gamma)
     else:
         z_min = z_max = float("nan")
-    c, info = inner_sign(alpha, beta, gamma, ell, p, hermitian)
+    if ells:
+        c, info = inner_sign_multilevel(alpha, beta, gamma, (ell, *ells), p, hermitian)
+        info["p_levels"] = info.pop("p")
+    else:
+        c, info = inner_sign(alpha, beta, gamma, ell, p, hermitian)
     y = outer.xnorm * (outer.V @ c)                            # step 6
     info.update(p=p, z_min=z_min, z_max=z_max, outer=outer, c=c)
     return y, info
@@ -208,12 +214,13 @@ def plain_sign(apply_a, apply_adag, x, k: int, hermitian: bool, method: str = "r
 
 
 def sign_apply(U, dims, mu, m_w, x, k=None, ell=None, p=None, method="nested",
-               antiperiodic_t=True):
-    """sgn(gamma_5 D_w(mu)) x by the nested, plain or dense method."""
+               antiperiodic_t=True, ells=()):
+    """sgn(gamma_5 D_w(mu)) x by the nested (optionally multi-level, ells),
+    plain or dense method."""
     a, adag, herm = operator(U, dims, mu, m_w, antiperiodic_t)
     x = np.asarray(x, dtype=np.complex128)
     if method == "nested":
-        return nested_sign(a, adag, x, k, ell, herm, p)
+        return nested_sign(a, adag, x, k, ell, herm, p, ells)
     if method == "plain":
         return plain_sign(a, adag, x, k, herm)
     if method == "dense":

@@ -44,3 +44,19 @@ def test_levels_converge_to_the_sign_of_h_k(ritz, ells):
     c, info = nested.inner_sign_multilevel(o.alpha, o.beta, o.gamma, ells, p, herm)
     assert info["rhi_converged"] and len(info["p"]) == len(ells)
     assert np.linalg.norm(c - truth) / np.linalg.norm(truth) < 1e-8
+
+
+def test_nested_solve_with_levels_reaches_the_dense_sign():
+    """sign_apply with further levels (ells) against the dense spectral sign
+    of A on 2^4 (N = 192): k = 192 exhausts the space, so the levels are the
+    only approximation left."""
+    dims = (2, 2, 2, 2)
+    U = inputs.su3_links(dims, 111)[0]
+    x = inputs.gaussian_sources(dims, 211)[0]
+    for mu in (0.0, 0.3):
+        truth, _ = nested.sign_apply(U, dims, mu, M_W, x, method="dense")
+        one, _ = nested.sign_apply(U, dims, mu, M_W, x, 192, 128)
+        two, info = nested.sign_apply(U, dims, mu, M_W, x, 192, 128, ells=(64,))
+        assert len(info["p_levels"]) == 2 and info["p_levels"][0] == info["p"]
+        for y in (one, two):
+            assert np.linalg.norm(y - truth) / np.linalg.norm(truth) < 1e-8
