@@ -943,7 +943,8 @@ def main():
     ap.add_argument("--tune-cache", default=None,
                     help="launch-shape cache file (read if it has the workload's shape, else written)")
     ap.add_argument("--nest", default="",
-                    help="comma-separated sizes l_2, l_3, ... of nested levels below l (Sec. 4.5; default none)")
+                    help="comma-separated sizes l_2, l_3, ... of nested levels below l (Sec. 4.5), or 'none' "
+                         "for one level (default: the workload's)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: no oracle, CPU baselines, two-float line or learned arm")
     args = ap.parse_args()
@@ -951,7 +952,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     w = dict(WORKLOADS[args.workload])
-    if args.nest:
+    if args.nest == "none":
+        w["nest"] = ()
+    elif args.nest:
         w["nest"] = tuple(int(v) for v in args.nest.split(","))
     if args.impl == "reference":
         return run_reference(args, w, rank)
