@@ -221,7 +221,8 @@ int nk_set_deflation(nk_ctx* ctx, int m, const double* lambda, const double* R, 
  * the larger of the right and left residuals);
  * these are the arguments of nk_set_deflation.  NK_OK when found = m,
  * NK_ENOTCONV when fewer converged (the found ones are returned),
- * NK_EBREAKDOWN on a Lanczos breakdown before step k. */
+ * NK_EBREAKDOWN on a Lanczos breakdown before step k.  Blocks; allocates its
+ * temporary device memory per call (a one-off initialisation). */
 int nk_eigs_smallest(nk_ctx* ctx, const double* b, int k, int m, double tol, double* lambda, double* R, double* L,
                      double* resid, int* found);
 
