@@ -207,7 +207,11 @@ int nk_set_deflation(nk_ctx* ctx, int m, const double* lambda, const double* R, 
  * iteration) and the refined combinations of them whose last component
  * vanishes, lifted through the bases (Ritz vectors); the true residuals
  * |A r - theta r| / |r| and |A^dagger l - theta^* l| / |l| (FP64 stencil),
- * and per cluster the candidate of least residual on each side.
+ * and per cluster the candidate of least residual on each side; the returned
+ * eigenvalue is the Rayleigh quotient <l, A r> (<l, r> = 1) where its
+ * residuals are not larger than those of H_k's eigenvalue (H_k's is good to
+ * about the residual, the quotient to about the product of the left and
+ * right residuals), else H_k's.
  * Unrestarted: the small eigenvalues need k large enough for them to
  * converge (several hundred on the small lattices of the tests; k = 12 V
  * exhausts the space).

@@ -1494,8 +1494,66 @@ int nk_eigs_smallest(nk_ctx* c, const double* b, int k, int m, double tol, doubl
             nk::launch_vlincomb(lg, lg, N, ng, ca, cb, st);
         }
     }
+    // The Rayleigh quotient of each returned pair, theta' = <l, A r> (<l, r> =
+    // 1; Hermitian: <r, A r>, |r| = 1), with its residuals: H_k's eigenvalue
+    // is good to about the residual, theta' to about the product of the left
+    // and right residuals.  theta' replaces it where its residual is not
+    // larger (the Hermitian quotient minimises |A r - theta r|; the two-sided
+    // one need not).
+    std::vector<nk::cplx> th_out(nf);
+    std::vector<double> res_out(nf);
+    {
+        std::vector<double2> dd(12), rr(12);
+        for (int t0 = 0; t0 < nf; t0 += kChunk) {
+            const int n = std::min(kChunk, nf - t0);
+            for (int side = 0; side < (ts ? 2 : 1); ++side) {
+                double2* v = (side ? d_L : d_R) + (size_t)t0 * N;
+                double2* av = side ? d_AX : d_X;
+                nk::DslashSet s0, s1;
+                std::memset(&s0, 0, sizeof(s0));
+                std::memset(&s1, 0, sizeof(s1));
+                s0.in = v;
+                s0.in_stride = N;
+                s0.out = av;
+                s0.out_stride = N;
+                s0.n = n;
+                s0.dag = side;
+                nk::launch_dslash(64, c->U64, g, s0, s1, kappa_of(c), c->mu, st);
+                for (int g0 = 0; g0 < n; g0 += 12) {
+                    const int ng = std::min(12, n - g0);
+                    if (side == 0) {   // theta' = <l, A r>
+                        nk::launch_vdot((ts ? d_L : d_R) + (size_t)(t0 + g0) * N, av + (size_t)g0 * N, N, ng, d_dot,
+                                        st);
+                        NK_EIG_CUDA(cudaMemcpy(dd.data(), d_dot, sizeof(double2) * ng, cudaMemcpyDeviceToHost));
+                        for (int i = 0; i < ng; ++i)
+                            th_out[t0 + g0 + i] = nk::cplx(dd[i].x, ts ? dd[i].y : 0.0);
+                    }
+                    nk::VecCoefs ca, cb;
+                    for (int i = 0; i < ng; ++i) {
+                        const nk::cplx t = side ? std::conj(th_out[t0 + g0 + i]) : th_out[t0 + g0 + i];
+                        ca.c[i] = make_double2(-t.real(), -t.imag());
+                        cb.c[i] = make_double2(1.0, 0.0);
+                    }
+                    double2* ag = av + (size_t)g0 * N;
+                    double2* vg = v + (size_t)g0 * N;
+                    nk::launch_vlincomb(ag, vg, N, ng, ca, cb, st);   // A v - theta v
+                    nk::launch_vdot(ag, ag, N, ng, d_dot, st);
+                    nk::launch_vdot(vg, vg, N, ng, d_dot + kChunk, st);
+                    NK_EIG_CUDA(cudaMemcpy(dd.data(), d_dot, sizeof(double2) * ng, cudaMemcpyDeviceToHost));
+                    NK_EIG_CUDA(cudaMemcpy(rr.data(), d_dot + kChunk, sizeof(double2) * ng, cudaMemcpyDeviceToHost));
+                    for (int i = 0; i < ng; ++i) {
+                        const double r_ = std::sqrt(dd[i].x / std::max(rr[i].x, 1e-300));
+                        double& ro = res_out[t0 + g0 + i];
+                        ro = side ? std::max(ro, r_) : r_;
+                    }
+                }
+            }
+        }
+    }
     for (int i = 0; i < nf; ++i) {
         const int q = keep[i];
+        const bool refined = res_out[i] <= res_cl[q];
+        const nk::cplx lam = refined ? th_out[i] : reps[q];
         nk::launch_soa_to_abi(d_R + (size_t)i * N, N, d_abi, N, nullptr, 0, c->V, 1, st);
         NK_EIG_CUDA(cudaMemcpy(R + (size_t)i * 2 * N, d_abi, vb, cudaMemcpyDeviceToHost));
         if (ts) {
@@ -1504,9 +1562,9 @@ int nk_eigs_smallest(nk_ctx* c, const double* b, int k, int m, double tol, doubl
         } else if (L) {
             std::memcpy(L + (size_t)i * 2 * N, R + (size_t)i * 2 * N, vb);
         }
-        lambda[2 * i] = reps[q].real();
-        lambda[2 * i + 1] = ts ? reps[q].imag() : 0.0;
-        if (resid) resid[i] = res_cl[q];
+        lambda[2 * i] = lam.real();
+        lambda[2 * i + 1] = ts ? lam.imag() : 0.0;
+        if (resid) resid[i] = refined ? res_out[i] : res_cl[q];
     }
     NK_EIG_CUDA(cudaGetLastError());
 #undef NK_EIG_CUDA

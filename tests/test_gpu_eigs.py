@@ -9,7 +9,7 @@ eigenvectors lifted through the bases:
   the dense A, the eigenvectors are those of the oracle up to a phase, and a
   solve deflated with them equals the solve deflated with the oracle's pairs;
 * mu = 0.3 (two-sided): the m eigenvalues are those of smallest modulus of
-  the dense A, the reported residual is the larger of the true right and
+  the dense A (the Rayleigh quotients <l, A r>, to 1e-12), the reported residual is the larger of the true right and
   left residuals, <l_i, r_i> = 1, and a solve deflated with them equals the
   solve deflated with the oracle's pairs.
 At k = 1200 (mu = 0) the converged eigenvalues come in repeated copies (loss
@@ -103,8 +103,9 @@ def test_two_sided_eigenpairs_are_eigenpairs_of_the_dense_operator(links):
     lam, R, L, res, rc = ctx.eigs_smallest(inputs.gaussian_sources(DIMS, 41)[0], k, m, tol=tol)
     assert rc == 0 and len(lam) == m
     assert np.all(np.diff(np.abs(lam)) >= 0)
-    # the m eigenvalues of smallest modulus, to about the residual
-    assert np.max(np.abs(np.sort_complex(lam) - np.sort_complex(smallest))) < 1e-8
+    # the m eigenvalues of smallest modulus: Rayleigh quotients, far more
+    # accurate than the residual (1e-9) that H_k's eigenvalues are limited to
+    assert np.max(np.abs(np.sort_complex(lam) - np.sort_complex(smallest))) < 1e-12
     for i in range(m):
         r, l = R[i], L[i]
         res_r = np.linalg.norm(a @ r - lam[i] * r)
