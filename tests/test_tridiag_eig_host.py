@@ -135,3 +135,42 @@ def test_doubled_eigenvalues_give_an_orthonormal_basis_of_the_cluster(harness):
             u = u / np.linalg.norm(u)
             M = np.array([[np.vdot(u, y[:30]), np.vdot(u, y[30:])] for y in Y])
             assert abs(np.linalg.det(M)) == pytest.approx(1.0, abs=1e-8)
+
+
+def test_refined_combination_of_a_repeated_ritz_value(harness):
+    """What the eigensolver's candidates rest on: the Hermitian Lanczos
+    recurrence of App. A (the oracle's, no reorthogonalisation) on 3^3 x 4 at
+    k = 1200 repeats its converged eigenvalues.  For each doubled eigenvalue
+    among those of H_k nearest zero, the two-vector basis of its invariant
+    subspace (block inverse iteration) combined so that the last component
+    vanishes lifts, through V_k, to an eigenvector of the dense A: the
+    residual of V_k y is |beta_k e_k^T y| |v_{k+1}| in the recurrence."""
+    from oracle import dirac, krylov
+    import inputs
+    dims = (3, 3, 3, 4)
+    U = inputs.su3_links(dims, 31)[0]
+    a = dirac.dense_A(U, dims, 0.0, -2.0)
+    r = krylov.lanczos(lambda v: a @ v, inputs.gaussian_sources(dims, 41)[0], 1200)
+    al, be = r.alpha.astype(complex), r.beta.astype(complex)
+    ok, w, _ = run(harness, al, be, be)
+    assert ok
+    w = w[np.argsort(np.abs(w))][:24]
+    doubled = []
+    for t in w:
+        if any(abs(t - d) <= 1e-8 * max(1.0, abs(d)) for d in doubled):
+            continue
+        if sum(abs(t - u) <= 1e-8 * max(1.0, abs(t)) for u in w) >= 2:
+            doubled.append(t)
+    assert len(doubled) >= 4
+    _, _, vecs = run(harness, al, be, be, [(t, 0, 2) for t in doubled])
+
+    def res(t, y):
+        x = r.V @ y
+        return np.linalg.norm(a @ x - t * x) / np.linalg.norm(x)
+
+    worst_single = 0.0
+    for t, Y in zip(doubled, vecs):
+        assert res(t, Y[1, -1] * Y[0] - Y[0, -1] * Y[1]) < 1e-12
+        worst_single = max(worst_single, min(res(t, Y[0]), res(t, Y[1])))
+    # without the combination some cluster has no good vector
+    assert worst_single > 1e-9
