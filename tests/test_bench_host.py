@@ -79,3 +79,29 @@ def test_config_names_the_workload_and_its_schedule():
     assert c["k"] == w["k"] and c["ell"] == w["ell"] and c["n_rhs"] == w["n_rhs"]
     assert "recurrence" in c["precision"] and "FP64" in c["precision"]
     assert "two-float (about 48-bit) from it on" in bench.config_of(w, _args(j1=0))["precision"]
+
+
+def test_nested_levels_of_the_workload_and_its_record():
+    """The bench workload nests l_2 = 64 below l = 128 (Sec. 4.5); the line's
+    config records the chain, and every level is even and no larger than the
+    one above."""
+    w = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    chain = [w["ell"], *w.get("nest", ())]
+    assert chain == [128, 64]
+    assert all(v % 2 == 0 and v >= 2 for v in chain) and chain == sorted(chain, reverse=True)
+    cfg = bench.config_of(w, _args())
+    assert cfg["nested_levels"] == chain
+
+
+def test_next_row_cases_are_valid_calls():
+    """The deflation and overlap blocks call the library with arguments its
+    header accepts: eigensolver k even and >= 2 m + 2, m <= 256; solve sizes
+    even, l <= k <= 1536, l <= 256; the fixed-k comparison below the
+    adaptive maximum."""
+    d = bench.DEFLATION_CASE
+    assert d["k_eig"] % 2 == 0 and d["k_eig"] >= 2 * d["m"] + 2 and 1 <= d["m"] <= 256
+    for k, ell in ((d["k_max"], d["ell"]), (d["k_ref"], d["ell_ref"]), (d["k_fixed"], d["ell"])):
+        assert k % 2 == 0 and ell % 2 == 0 and 2 <= ell <= min(k, 256) and k <= 1536
+    assert d["k_fixed"] < d["k_max"] and d["tol_eig"] > 0
+    o = bench.OVERLAP_CASE
+    assert o["k"] % 2 == 0 and o["ell"] % 2 == 0 and o["ell"] <= o["k"] <= 1536 and o["mass"] >= 0
