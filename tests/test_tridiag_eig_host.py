@@ -174,3 +174,15 @@ def test_refined_combination_of_a_repeated_ritz_value(harness):
         worst_single = max(worst_single, min(res(t, Y[0]), res(t, Y[1])))
     # without the combination some cluster has no good vector
     assert worst_single > 1e-9
+
+
+def test_defective_matrix_is_reported_and_skew_matrix_solved(harness):
+    """The complex orthogonal rotations of the symmetrised QL can break down:
+    [[1, 1], [-1, -1]] (symmetrised [[1, i], [i, -1]], a double eigenvalue 0
+    with one eigenvector) is reported as not converged, which the eigensolver
+    returns as NK_ENOTCONV; a skew tridiagonal (eigenvalues +-i sqrt 2, 0,
+    the spectrum on which the sign function is undefined) is solved."""
+    ok, _, _ = run(harness, [1.0, -1.0], [-1.0], [1.0])
+    assert not ok
+    ok, got, _ = run(harness, [0.0, 0.0, 0.0], [-1.0, -1.0], [1.0, 1.0])
+    assert ok and match(got, np.array([1j * np.sqrt(2.0), 0.0, -1j * np.sqrt(2.0)])) < 1e-14
