@@ -105,3 +105,24 @@ def test_next_row_cases_are_valid_calls():
     assert d["k_fixed"] < d["k_max"] and d["tol_eig"] > 0
     o = bench.OVERLAP_CASE
     assert o["k"] % 2 == 0 and o["ell"] % 2 == 0 and o["ell"] <= o["k"] <= 1536 and o["mass"] >= 0
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """--impl reference: the oracle's outer recurrence on a bounded sample,
+    one JSON line with the contract's keys (run here on a 4^4 stand-in of the
+    workload with a one-second budget)."""
+    import json
+    w = dict(bench.WORKLOADS[bench.DEFAULT_WORKLOAD], dims=(4, 4, 4, 4), k=64)
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 1.0)
+    args = _args(steps=2, warmup=1)
+    assert bench.run_reference(args, w, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "solves/s"
+    assert line["value"] > 0 and line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == bench.DEFAULT_WORKLOAD
+    # other ranks print nothing
+    assert bench.run_reference(args, w, 1) == 0 and capsys.readouterr().out == ""
