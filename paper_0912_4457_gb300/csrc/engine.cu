@@ -1656,9 +1656,10 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
     enqueue_outer(c, Lw.o, sch, L, kTuneWarm);
     const Geom g = geom_of(c);
     const void* U = prec == 64 ? (const void*)c->U64 : (prec == 48 ? (const void*)c->Udf : (const void*)c->U32);
-    cudaEvent_t e0, e1;
-    NK_CUDA(c, cudaEventCreate(&e0));
-    NK_CUDA(c, cudaEventCreate(&e1));
+    EventPair ev;   // destroyed on every return
+    NK_CUDA(c, cudaEventCreate(&ev.e0));
+    NK_CUDA(c, cudaEventCreate(&ev.e1));
+    const cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     float best = 1e30f;
     for (int round = 0; round < kTuneRounds; ++round) {
         NK_CUDA(c, cudaEventRecord(e0, st));
@@ -1675,8 +1676,6 @@ static int time_kernel(nk_ctx* c, const double* src, int n_rhs, bool mixed, int 
         NK_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
         best = std::min(best, ms / kTuneReps);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     *per_launch_ms = best;
     return NK_OK;
 }
@@ -1729,7 +1728,11 @@ int nk_autotune(nk_ctx* c, int n_rhs, unsigned flags, const char* cache_path, nk
     if (rc) return rc;
     cudaStream_t st;
     NK_CUDA(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    NK_CUDA(c, cudaMemsetAsync(c->staging.p, 0x3F, sb, st));
+    const cudaError_t e_fill = cudaMemsetAsync(c->staging.p, 0x3F, sb, st);
+    if (e_fill != cudaSuccess) {
+        cudaStreamDestroy(st);
+        return cuda_fail(c, e_fill, "autotune input");
+    }
     const double* src = (const double*)c->staging.p;
     nk_launch best = launch_cfg(c, n_rhs, ts != 0, mixed != 0);
     best.stencil_threads = 128;
